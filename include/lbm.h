@@ -1,0 +1,228 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) coupled lattice Boltzmann /
+ * rigid-body swimmer step.
+ *
+ * One call of lbm_step advances a D3Q19 fluid with moving rigid bodies by
+ * the coupled step of Pickl et al., "All good things come in threes" (arXiv
+ * 1108.0786), Algorithm 2: map the bodies onto the lattice (Sec. 2.3), fused
+ * stream + velocity-corrected bounce-back + reconstruction of uncovered
+ * cells + LBGK collision (Eq. 1-4 and the moving-wall rule of Sec. 2.3),
+ * momentum-exchange force and torque per body (Eq. hydroF), drive
+ * (Eq. FB1-FB3), damped springs (Eq. osci_i, osci_j) and the rigid-body
+ * time step (Algorithm 1, Eq. totalFSwimmer).  Everything runs on the
+ * device; the host never synchronises inside lbm_step.
+ *
+ * Units: lattice units, dx = dt = 1, rest density 1.  Cell (x, y, z) has its
+ * centre at the integer point (x, y, z) and linear index
+ * c = (z * ny + y) * nx + x.  A non-periodic axis has halfway no-slip walls
+ * half a cell outside its first and last cell centres.
+ *
+ * Population order (19 directions e_a):
+ *    0:( 0, 0, 0)
+ *    1:(+1, 0, 0)  2:(-1, 0, 0)  3:( 0,+1, 0)  4:( 0,-1, 0)  5:( 0, 0,+1)  6:( 0, 0,-1)
+ *    7:(+1,+1, 0)  8:(-1,-1, 0)  9:(+1,-1, 0) 10:(-1,+1, 0)
+ *   11:(+1, 0,+1) 12:(-1, 0,-1) 13:(+1, 0,-1) 14:(-1, 0,+1)
+ *   15:( 0,+1,+1) 16:( 0,-1,-1) 17:( 0,+1,-1) 18:( 0,-1,+1)
+ *
+ * Body state (13 doubles): position[3], unit quaternion (w, x, y, z)[4],
+ * velocity[3], angular velocity[3], all in the world frame.  The body-frame
+ * x axis is the capsule axis and the drive direction.
+ *
+ * Ownership: a handle owns every byte of device memory it uses.  It
+ * allocates lazily, at the first call that needs the device (lbm_step,
+ * lbm_set_fields, lbm_get_*), through the allocator installed with
+ * lbm_set_allocator or, if none, cudaMalloc.  Host pointers passed in are
+ * read during the call only; host output buffers are owned by the caller.
+ *
+ * Errors: every int-returning call returns LBM_OK (0) or a negative
+ * LBM_E_* code and stores a message for lbm_last_error.  Errors found on
+ * the device (overlapping bodies, a body crossing a wall, a non-finite body
+ * state, a body faster than LBM_MAX_BODY_STEP per step) are latched in a
+ * device status word and returned by the next synchronising call (lbm_sync,
+ * lbm_get_*, lbm_save); the state after such an error is unspecified.
+ * Nothing is thrown across the ABI.  A handle is not thread safe.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK            0
+#define LBM_E_ARG        -1   /* bad argument */
+#define LBM_E_OOM        -2   /* device or host allocation failed */
+#define LBM_E_OVERLAP    -3   /* a cell lies inside two bodies */
+#define LBM_E_OUTSIDE    -4   /* a body crosses a wall of the domain */
+#define LBM_E_NAN        -5   /* non-finite body state */
+#define LBM_E_LINKS      -6   /* link list capacity exceeded */
+#define LBM_E_TIMEOUT    -7   /* a bounded device wait expired */
+#define LBM_E_CUDA       -8   /* CUDA runtime error */
+#define LBM_E_STATE      -9   /* call not allowed in the current state */
+#define LBM_E_UNSTABLE  -10   /* a body moved more than LBM_MAX_BODY_STEP in one step */
+
+/* bc bitmask: periodic axes; the other axes get halfway no-slip walls */
+#define LBM_BC_PERIODIC_X 1
+#define LBM_BC_PERIODIC_Y 2
+#define LBM_BC_PERIODIC_Z 4
+
+#define LBM_SHAPE_SPHERE  0
+#define LBM_SHAPE_CAPSULE 1   /* cylinder of `length` along body x + two caps */
+
+/* population storage; the collision runs in FP64 for LBM_PREC_F64 and in
+ * FP32 otherwise.  Populations are stored as deviations f_a - w_a from the
+ * rest equilibrium. */
+#define LBM_PREC_F64  0
+#define LBM_PREC_F32  1
+#define LBM_PREC_F16  2   /* deviations scaled by 2^LBM_F16_SCALE_EXP */
+#define LBM_PREC_BF16 3
+
+#define LBM_OPT_NO_FLUID  1   /* bodies only: no mapping, no hydrodynamic force */
+
+#define LBM_FIELD_RHO   0     /* density, cells */
+#define LBM_FIELD_U     1     /* velocity, [3][cells] */
+#define LBM_FIELD_FLAGS 2     /* uint8 per cell: 0 fluid, 1 + body id if solid */
+#define LBM_FIELD_POP   3     /* post-collision populations, [19][cells] */
+
+#define LBM_DTYPE_F64 0
+#define LBM_DTYPE_F32 1
+#define LBM_DTYPE_U8  2
+
+#define LBM_MAX_BODIES     254
+#define LBM_MAX_BODY_STEP  0.5   /* largest displacement of a body per step */
+
+/* kernel slots reported by lbm_time_kernels */
+#define LBM_KERNEL_REMAP          0
+#define LBM_KERNEL_STREAM_COLLIDE 1
+#define LBM_KERNEL_LINKS          2
+#define LBM_KERNEL_FORCE          3
+#define LBM_KERNEL_INTEGRATE      4
+#define LBM_NUM_KERNELS           5
+
+typedef struct lbm_s lbm_t;
+
+/* Device allocator hook: return `bytes` of device memory (256-byte aligned)
+ * usable on the handle's stream, or NULL; free_fn releases it. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, void *ctx);
+
+/* Create a lattice of nx*ny*nz cells with LBGK relaxation time tau > 1/2
+ * (Eq. 1-2; viscosity (tau - 1/2)/3), FP32 storage, no body force.
+ * Allocates no device memory.  Errors: LBM_E_ARG, LBM_E_OOM (host). */
+int lbm_create(int nx, int ny, int nz, double tau, int bc, lbm_t **out);
+
+/* As lbm_create with a storage precision (LBM_PREC_*), a body-force density
+ * g[3] acting on the fluid through Guo's forcing term and on each body as
+ * g times its volume (g may be NULL for zero), and LBM_OPT_* options. */
+int lbm_create_ex(int nx, int ny, int nz, double tau, int bc, int precision,
+                  const double g[3], int options, lbm_t **out);
+
+/* Release the handle and all device memory it owns (synchronises). */
+int lbm_destroy(lbm_t *h);
+
+/* Install the device allocator; only before the first device allocation. */
+int lbm_set_allocator(lbm_t *h, lbm_alloc_fn alloc_fn, lbm_free_fn free_fn, void *ctx);
+
+/* CUDA stream (a cudaStream_t) on which all work is enqueued; NULL is the
+ * legacy default stream.  The device is the current device at the first
+ * device allocation. */
+int lbm_set_stream(lbm_t *h, void *stream);
+
+/* Add a rigid body (Sec. 2.2, 3.1-3.2): sphere of `radius` (length 0) or
+ * capsule of cylinder `length` and cap `radius` along the body x axis, of
+ * `mass`, centre pos[3] and orientation orient[4] (unit quaternion w,x,y,z,
+ * normalised here; NULL for identity).  Inertia is that of a uniform solid.
+ * Only before the first step.  Returns the body id (>= 0). */
+int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass,
+                 const double pos[3], const double orient[4]);
+
+/* Damped harmonic spring between bodies i and j (Eq. spring_i, damp_i,
+ * osci_i, osci_j): F_i = -k (|d| - rest) d/|d| - damping (V_i - V_j),
+ * d = X_i - X_j, F_j = -F_i; rest is the centre-to-centre rest length.
+ * Only before the first step.  Returns the spring id. */
+int lbm_add_spring(lbm_t *h, int i, int j, double k, double rest, double damping);
+
+/* Add a drive term on `body` (Eq. FB1-FB3): the force
+ * amp * sin(2 pi freq t - phase) along the body x axis for
+ * t >= phase / (2 pi freq), zero before; t is the step index.  Terms on one
+ * body add up, so the middle body's -(F2 + F3) is two terms.  Only before
+ * the first step.  Returns the term id. */
+int lbm_set_drive(lbm_t *h, int body, double amp, double freq, double phase);
+
+/* Switch drive term `term` off for t >= t_off (the paper's protocol stops
+ * the drives at t1 and t2, Sec. 5.1). */
+int lbm_set_drive_window(lbm_t *h, int term, double t_off);
+
+/* Overwrite the current state (13 doubles) of a body.  After the first
+ * step the position may change by less than LBM_MAX_BODY_STEP per axis
+ * (else LBM_E_STATE).  Synchronous. */
+int lbm_set_body_state(lbm_t *h, int body, const double state[13]);
+
+/* Overwrite the post-collision populations of the last completed step
+ * (before the first step: the populations the first step streams from).
+ * Only LBM_FIELD_POP with LBM_DTYPE_F64 host data [19][cells].  Synchronous. */
+int lbm_set_fields(lbm_t *h, int what, const void *host_in, int dtype);
+
+/* Enqueue n coupled steps on the handle's stream (CUDA graphs; no host
+ * synchronisation).  Returns launch errors only. */
+int lbm_step(lbm_t *h, int n);
+
+/* Wait for all enqueued work and return any latched device error. */
+int lbm_sync(lbm_t *h);
+
+/* Number of completed (enqueued) steps. */
+long long lbm_steps_done(lbm_t *h);
+
+/* Body states after the last step, out[bodies][13] (synchronises). */
+int lbm_get_bodies(lbm_t *h, double *out);
+
+/* Hydrodynamic force and torque of the last step, out[bodies][6]: F[3],
+ * T[3]; the torque is about the body centre (synchronises). */
+int lbm_get_forces(lbm_t *h, double *out);
+
+/* Copy a field of the last completed step to host memory (synchronises):
+ * RHO = sum f~, U = (sum e f~ - g/2)/rho, solid cells report rho = 1 and
+ * u = 0; FLAGS as LBM_FIELD_FLAGS; POP = f~ as [19][cells].  dtype
+ * LBM_DTYPE_F64 or LBM_DTYPE_F32 for RHO, U, POP; LBM_DTYPE_U8 for FLAGS. */
+int lbm_get_fields(lbm_t *h, int what, void *out, int dtype);
+
+/* As lbm_get_fields into caller-owned device memory (enqueued, no sync). */
+int lbm_get_fields_device(lbm_t *h, int what, void *dev_out, int dtype);
+
+/* Record every step's body states in a device ring buffer of `capacity`
+ * steps (0 disables).  Only before the first step. */
+int lbm_enable_history(lbm_t *h, int capacity);
+
+/* Copy the recorded states, oldest first, out[n][bodies][13] with
+ * n = min(steps done, capacity, max_steps); *n_out = n (synchronises). */
+int lbm_get_history(lbm_t *h, double *out, int max_steps, int *n_out);
+
+/* Checkpoint / restore the full state (populations, both flag epochs, both
+ * body states, forces, step counter) to / from a file (synchronises).  The
+ * handle given to lbm_load must have the same lattice, bodies and
+ * precision. */
+int lbm_save(lbm_t *h, const char *path);
+int lbm_load(lbm_t *h, const char *path);
+
+/* Diagnostic timing: run n steps launching each kernel separately with CUDA
+ * events around it on the handle's stream, and write the average duration
+ * in milliseconds of each kernel slot (LBM_KERNEL_*) to ms_out[slots]; a
+ * slot that does not run is reported as 0.  The state advances by n steps. */
+int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots);
+
+/* Kernel launches one step makes (for launch accounting). */
+int lbm_kernels_per_step(lbm_t *h);
+
+/* Algorithmic bytes per cell the stream-collide kernel moves:
+ * 2 * 19 * sizeof(population) + 1 flag byte. */
+int lbm_bytes_per_cell(lbm_t *h);
+
+/* Message of the last error on this handle (never NULL). */
+const char *lbm_last_error(lbm_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

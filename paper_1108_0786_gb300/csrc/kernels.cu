@@ -1,0 +1,480 @@
+// kernels.cu -- the per-body kernels of one coupled step and the field
+// export / import kernels:
+//   remap      map the bodies onto the lattice (Sec. 2.3), epoch flags
+//   links      per-body list of fluid->solid links (ballot + block scan)
+//   force      momentum-exchange force and torque (Eq. hydroF), FP64,
+//              warp-shuffle reduction in a fixed order (deterministic)
+//   integrate  drive (Eq. FB1-FB3), springs (Eq. osci_i, osci_j) and the
+//              rigid-body time step (Algorithm 1), FP64, one thread a body
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+__device__ inline bool cell_inside(const Domain &d, const BodyProps &p, const BodyState &b, int x,
+                                   int y, int z) {
+    double o[3];
+    offset_from(d, b, x, y, z, o);
+    if (p.shape == 0) return o[0] * o[0] + o[1] * o[1] + o[2] * o[2] <= p.r * p.r;
+    double R[3][3];
+    quat_to_matrix(b.q, R);
+    const double a0 = R[0][0], a1 = R[1][0], a2 = R[2][0];
+    double s = o[0] * a0 + o[1] * a1 + o[2] * a2;
+    const double h = 0.5 * p.l;
+    s = s > h ? h : (s < -h ? -h : s);
+    const double e0 = o[0] - s * a0, e1 = o[1] - s * a1, e2 = o[2] - s * a2;
+    return e0 * e0 + e1 * e1 + e2 * e2 <= p.r * p.r;
+}
+
+__device__ inline uint8_t wall_bit(const Domain &d, int x, int y, int z) {
+    const bool w = (!d.px && (x == 0 || x == d.nx - 1)) || (!d.py && (y == 0 || y == d.ny - 1)) ||
+                   (!d.pz && (z == 0 || z == d.nz - 1));
+    return w ? F_WALL : 0;
+}
+
+__global__ void init_flags_kernel(const Domain d, uint8_t *f0, uint8_t *f1, uint8_t *b0, uint8_t *b1) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.C) return;
+    const int x = (int)(c % d.nx);
+    const int y = (int)((c / d.nx) % d.ny);
+    const int z = (int)(c / ((long long)d.nx * d.ny));
+    const uint8_t w = wall_bit(d, x, y, z);
+    f0[c] = w;
+    f1[c] = w;
+    b0[c] = NO_BODY;
+    b1[c] = NO_BODY;
+}
+
+// Remap: block row blockIdx.y = body b; the threads cover the cube of side
+// 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) at state n.  Every covered
+// cell gets its epoch-n flags from the geometry of all bodies and the
+// epoch-(n-1) buffer; overlapping cubes write identical values.
+__global__ void remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
+    const Domain d = dv.dom;
+    const int b = blockIdx.y;
+    const BodyProps pb = dv.props[b];
+    const BodyState sb = sp.body_cur[b];
+    const int half = pb.E + REMAP_MARGIN;
+    const int side = 2 * half + 1;
+    const long long vol = (long long)side * side * side;
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l == 0) {
+        // a body may not cross a wall (its extent beyond the wall planes)
+        double R[3][3];
+        quat_to_matrix(sb.q, R);
+        const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
+        for (int k = 0; k < 3; ++k) {
+            if (per[k]) continue;
+            const double ext = pb.r + (pb.shape == 1 ? 0.5 * pb.l * fabs(R[k][0]) : 0.0);
+            if (sb.X[k] - ext < -0.5 || sb.X[k] + ext > n3[k] - 0.5) atomicOr(dv.status, ST_OUTSIDE);
+        }
+    }
+    if (l >= vol) return;
+    const int lx = (int)(l % side), ly = (int)((l / side) % side), lz = (int)(l / ((long long)side * side));
+    int x = (int)floor(sb.X[0]) - half + lx;
+    int y = (int)floor(sb.X[1]) - half + ly;
+    int z = (int)floor(sb.X[2]) - half + lz;
+    if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else if (x < 0 || x >= d.nx) return;
+    if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else if (y < 0 || y >= d.ny) return;
+    if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else if (z < 0 || z >= d.nz) return;
+    const long long c = ((long long)z * d.ny + y) * d.nx + x;
+
+    int id = NO_BODY;
+    for (int k = 0; k < dv.nb; ++k) {
+        const BodyState sk = sp.body_cur[k];
+        const BodyProps pk = dv.props[k];
+        double o[3];
+        offset_from(d, sk, x, y, z, o);
+        const double reach = pk.r + 0.5 * pk.l;
+        if (fabs(o[0]) > reach || fabs(o[1]) > reach || fabs(o[2]) > reach) continue;
+        if (!cell_inside(d, pk, sk, x, y, z)) continue;
+        if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
+        id = k;
+    }
+    const uint8_t solid = id != NO_BODY ? F_SOLID : 0;
+    uint8_t flags = solid | wall_bit(d, x, y, z);
+    if (!init_mode) {
+        const uint8_t prev = sp.flags_prev[c] & F_SOLID;
+        if (prev) flags |= F_SOLID_PREV;
+        // does any pull source x - e_a hold an obstacle of step n-1?
+        for (int a = 1; a < Q; ++a) {
+            int sx = x - ex(a), sy = y - ey(a), sz = z - ez(a);
+            if ((!d.px && (sx < 0 || sx >= d.nx)) || (!d.py && (sy < 0 || sy >= d.ny)) ||
+                (!d.pz && (sz < 0 || sz >= d.nz)))
+                continue;
+            sx = wrap_axis(sx, d.nx); sy = wrap_axis(sy, d.ny); sz = wrap_axis(sz, d.nz);
+            if (sp.flags_prev[((long long)sz * d.ny + sy) * d.nx + sx] & F_SOLID) {
+                flags |= F_NEAR;
+                break;
+            }
+        }
+        if ((solid != 0) != (prev != 0) || (solid && sp.bid_prev[c] != id)) dv.changed[sp.parity] = 1;
+    }
+    sp.flags_cur[c] = flags;
+    sp.bid_cur[c] = (uint8_t)id;
+}
+
+// Links: block (k, b) scans z-plane k of the cube of side 2 E_b + 3 around
+// floor(X_b) and stores the links (x_f, a) with x_f fluid and x_f + e_a a
+// cell of body b, in (y, x, a) order, into segment (b, k).  Runs only when
+// the remap changed a flag; otherwise the previous lists stand.
+__global__ void links_kernel(const Device dv, const StepPtrs sp) {
+    if (dv.changed[sp.parity] == 0) return;
+    const Domain d = dv.dom;
+    const int b = blockIdx.y, k = blockIdx.x;
+    const BodyProps pb = dv.props[b];
+    const int half = pb.E + 1;
+    const int side = 2 * half + 1;
+    int *count = dv.seg_count + (long long)b * dv.link_side + k;
+    if (k >= side) {
+        if (threadIdx.x == 0) *count = 0;
+        return;
+    }
+    const BodyState sb = sp.body_cur[b];
+    Link *seg = dv.links + ((long long)b * dv.link_side + k) * dv.seg_cap;
+    const int ox = (int)floor(sb.X[0]) - half, oy = (int)floor(sb.X[1]) - half;
+    int z = (int)floor(sb.X[2]) - half + k;
+    bool zok = true;
+    if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else zok = z >= 0 && z < d.nz;
+
+    __shared__ int warp_tot[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int area = side * side;
+    for (int start = 0; start < area; start += blockDim.x) {
+        const int l = start + threadIdx.x;
+        unsigned mask = 0;
+        long long c = 0;
+        if (zok && l < area) {
+            int x = ox + l % side, y = oy + l / side;
+            bool ok = true;
+            if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else ok = ok && x >= 0 && x < d.nx;
+            if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else ok = ok && y >= 0 && y < d.ny;
+            if (ok) {
+                c = ((long long)z * d.ny + y) * d.nx + x;
+                if (!(sp.flags_cur[c] & F_SOLID)) {
+                    for (int a = 1; a < Q; ++a) {
+                        int nx_ = x + ex(a), ny_ = y + ey(a), nz_ = z + ez(a);
+                        if ((!d.px && (nx_ < 0 || nx_ >= d.nx)) || (!d.py && (ny_ < 0 || ny_ >= d.ny)) ||
+                            (!d.pz && (nz_ < 0 || nz_ >= d.nz)))
+                            continue;
+                        nx_ = wrap_axis(nx_, d.nx); ny_ = wrap_axis(ny_, d.ny); nz_ = wrap_axis(nz_, d.nz);
+                        const long long n = ((long long)nz_ * d.ny + ny_) * d.nx + nx_;
+                        if ((sp.flags_cur[n] & F_SOLID) && sp.bid_cur[n] == b) mask |= 1u << a;
+                    }
+                }
+            }
+        }
+        // block-wide exclusive scan of the per-thread link counts
+        const int cnt = __popc(mask);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            if (w < warp) before += warp_tot[w];
+            total += warp_tot[w];
+        }
+        int pos = base + before + incl - cnt;
+        while (mask) {
+            const int a = __ffs(mask) - 1;
+            mask &= mask - 1;
+            if (pos < dv.seg_cap) seg[pos] = Link{(uint32_t)c, (uint32_t)a};
+            else atomicOr(dv.status, ST_LINKS);
+            ++pos;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base;
+}
+
+template <typename T> __device__ inline double load_dev(const T *p, float inv_scale);
+template <> __device__ inline double load_dev<double>(const double *p, float) { return *p; }
+template <> __device__ inline double load_dev<float>(const float *p, float) { return (double)*p; }
+template <> __device__ inline double load_dev<__half>(const __half *p, float s) {
+    return (double)(__half2float(*p) * s);
+}
+template <> __device__ inline double load_dev<__nv_bfloat16>(const __nv_bfloat16 *p, float) {
+    return (double)__bfloat162float(*p);
+}
+
+constexpr int FORCE_THREADS = 256;
+constexpr int MAX_SEGMENTS = 1024;
+
+// Momentum exchange (Eq. hydroF): one block per body sums
+//   F = sum e_a [2 f~_a(x_f) + 6 w_a rho(x_f) e_-a . u_w(x_f + e_a)],
+//   T = sum (x_f + e_a / 2 - X) x F_link
+// over the body's links with f~ of step n (dst) and the state of step n.
+template <typename T>
+__global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, const StepPtrs sp) {
+    const Domain d = dv.dom;
+    const int b = blockIdx.x;
+    const BodyProps pb = dv.props[b];
+    const BodyState sb = sp.body_cur[b];
+    const int side = 2 * (pb.E + 1) + 1;
+    const int *counts = dv.seg_count + (long long)b * dv.link_side;
+    const Link *links = dv.links + (long long)b * dv.link_side * dv.seg_cap;
+    const T *pop = static_cast<const T *>(sp.dst);
+    const long long C = d.C;
+    const float s = dv.f16_inv_scale;
+
+    __shared__ int prefix[MAX_SEGMENTS + 1];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int k = 0; k < side; ++k) {
+            prefix[k] = acc;
+            acc += counts[k];
+        }
+        prefix[side] = acc;
+    }
+    __syncthreads();
+    const int total = prefix[side];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < total; j += FORCE_THREADS) {
+        int lo = 0, hi = side - 1;       // segment k with prefix[k] <= j < prefix[k+1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const Link lk = links[(long long)lo * dv.seg_cap + (j - prefix[lo])];
+        const long long c = lk.cell;
+        const int a = (int)lk.dir;
+        double rho = 1.0;
+        for (int q = 0; q < Q; ++q) rho += load_dev<T>(pop + q * C + c, s);
+        const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
+        const int x = (int)(c % d.nx), y = (int)((c / d.nx) % d.ny),
+                  z = (int)(c / ((long long)d.nx * d.ny));
+        double u[3];
+        surface_velocity(d, sb, x + ex(a), y + ey(a), z + ez(a), u);
+        const double eu = -(ex(a) * u[0] + ey(a) * u[1] + ez(a) * u[2]);   // e_-a . u_w
+        const double mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
+        const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
+        double o[3];
+        offset_from(d, sb, x + 0.5 * ex(a), y + 0.5 * ey(a), z + 0.5 * ez(a), o);
+        acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];
+        acc[3] += o[1] * fl[2] - o[2] * fl[1];
+        acc[4] += o[2] * fl[0] - o[0] * fl[2];
+        acc[5] += o[0] * fl[1] - o[1] * fl[0];
+    }
+    // fixed-order reduction: warp shuffles, then warp 0 over the warp sums
+    __shared__ double part[FORCE_THREADS / 32][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) part[warp][i] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double v = lane < FORCE_THREADS / 32 ? part[lane][i] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) dv.fh[b * 6 + i] = v;
+        }
+    }
+}
+
+// Rigid-body step (Algorithm 1, Eq. totalFSwimmer): thread b sums the
+// hydrodynamic force, g times the volume, its drive terms in order and its
+// springs in order, then advances by semi-implicit Euler (dt = 1).
+__global__ void integrate_kernel(const Device dv, const StepPtrs sp) {
+    const int b = threadIdx.x;
+    const long long tstep = *dv.t_dev;
+    if (b < dv.nb) {
+        const double t = (double)tstep;
+        const BodyProps pb = dv.props[b];
+        BodyState s = sp.body_cur[b];
+        double R[3][3];
+        quat_to_matrix(s.q, R);
+        double F[3], Tq[3];
+        for (int i = 0; i < 3; ++i) {
+            F[i] = dv.fh[b * 6 + i] + dv.g[i] * pb.volume;
+            Tq[i] = dv.fh[b * 6 + 3 + i];
+        }
+        for (int k = 0; k < dv.nd; ++k) {
+            const DriveTerm dt = dv.drives[k];
+            if (dt.body != b) continue;
+            const double omega = 2.0 * M_PI * dt.freq;
+            if (t < dt.phase / omega || t >= dt.t_off) continue;
+            const double f = dt.amp * sin(omega * t - dt.phase);
+            for (int i = 0; i < 3; ++i) F[i] += f * R[i][0];
+        }
+        for (int k = 0; k < dv.ns; ++k) {
+            const Spring sp_ = dv.springs[k];
+            if (sp_.i != b && sp_.j != b) continue;
+            const BodyState si = sp.body_cur[sp_.i], sj = sp.body_cur[sp_.j];
+            const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
+            const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+            for (int i = 0; i < 3; ++i) {
+                const double dir = len > 0 ? dd[i] / len : 0.0;
+                const double fi = -sp_.k * (len - sp_.rest) * dir - sp_.gamma * (si.V[i] - sj.V[i]);
+                F[i] += sp_.i == b ? fi : -fi;
+            }
+        }
+        BodyState n = s;
+        for (int i = 0; i < 3; ++i) {
+            n.V[i] = s.V[i] + F[i] / pb.m;
+            n.X[i] = s.X[i] + n.V[i];
+        }
+        // Omega += R diag(1/I) R^T T
+        double Tb[3], dW[3];
+        for (int i = 0; i < 3; ++i) Tb[i] = R[0][i] * Tq[0] + R[1][i] * Tq[1] + R[2][i] * Tq[2];
+        for (int i = 0; i < 3; ++i) Tb[i] /= pb.inertia[i];
+        for (int i = 0; i < 3; ++i) dW[i] = R[i][0] * Tb[0] + R[i][1] * Tb[1] + R[i][2] * Tb[2];
+        for (int i = 0; i < 3; ++i) n.W[i] = s.W[i] + dW[i];
+        // q += 1/2 (0, Omega) (x) q, renormalised
+        const double w = s.q[0], v0 = s.q[1], v1 = s.q[2], v2 = s.q[3];
+        const double c0 = n.W[1] * v2 - n.W[2] * v1, c1 = n.W[2] * v0 - n.W[0] * v2,
+                     c2 = n.W[0] * v1 - n.W[1] * v0;
+        double q4[4] = {w - 0.5 * (n.W[0] * v0 + n.W[1] * v1 + n.W[2] * v2),
+                        v0 + 0.5 * (w * n.W[0] + c0), v1 + 0.5 * (w * n.W[1] + c1),
+                        v2 + 0.5 * (w * n.W[2] + c2)};
+        const double nn = sqrt(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
+        for (int i = 0; i < 4; ++i) n.q[i] = q4[i] / nn;
+        bool finite = true;
+        for (int i = 0; i < 3; ++i)
+            finite = finite && isfinite(n.X[i]) && isfinite(n.V[i]) && isfinite(n.W[i]);
+        if (!finite) atomicOr(dv.status, ST_NAN);
+        else if (fabs(n.V[0]) > MAX_STEP || fabs(n.V[1]) > MAX_STEP || fabs(n.V[2]) > MAX_STEP)
+            atomicOr(dv.status, ST_UNSTABLE);
+        sp.body_next[b] = n;
+        if (dv.hist) {
+            double *h = dv.hist + ((tstep % dv.hist_cap) * dv.nb + b) * 13;
+            const double *src = &n.X[0];
+            for (int i = 0; i < 13; ++i) h[i] = src[i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *dv.t_dev = tstep + 1;
+        dv.changed[sp.parity ^ 1] = 0;
+    }
+}
+
+// ---- field export / import -----------------------------------------------
+
+template <typename T, typename O>
+__global__ void export_kernel(const Device dv, const T *pop, const uint8_t *flags, const uint8_t *bid,
+                              int what, int mask_solid, O *out) {
+    const Domain d = dv.dom;
+    const long long C = d.C;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const float s = dv.f16_inv_scale;
+    const bool solid = mask_solid && (flags[c] & F_SOLID);
+    if (what == 2) {
+        reinterpret_cast<uint8_t *>(out)[c] = solid ? (uint8_t)(bid[c] + 1) : 0;
+        return;
+    }
+    if (what == 3) {
+        for (int a = 0; a < Q; ++a) out[a * C + c] = (O)(wgt(a) + load_dev<T>(pop + a * C + c, s));
+        return;
+    }
+    double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < Q; ++a) {
+        const double v = load_dev<T>(pop + a * C + c, s);
+        drho += v;
+        j[0] += ex(a) * v; j[1] += ey(a) * v; j[2] += ez(a) * v;
+    }
+    const double rho = 1.0 + drho;
+    if (what == 0) {
+        out[c] = (O)(solid ? 1.0 : rho);
+    } else {
+        for (int i = 0; i < 3; ++i) out[i * C + c] = (O)(solid ? 0.0 : (j[i] - 0.5 * dv.g[i]) / rho);
+    }
+}
+
+template <typename T>
+__global__ void import_kernel(const Device dv, T *pop, const double *in) {
+    const long long C = dv.dom.C;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    for (int a = 0; a < Q; ++a) {
+        const double delta = in[a * C + c] - wgt(a);
+        if constexpr (sizeof(T) == 8) pop[a * C + c] = delta;
+        else if constexpr (sizeof(T) == 4) pop[a * C + c] = (float)delta;
+        else if constexpr (std::is_same<T, __half>::value) pop[a * C + c] = __float2half_rn((float)delta * dv.f16_scale);
+        else pop[a * C + c] = __float2bfloat16_rn((float)delta);
+    }
+}
+
+unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8_t *bid0, uint8_t *bid1,
+                       cudaStream_t s) {
+    init_flags_kernel<<<blocks_for(dv.dom.C, 256), 256, 0, s>>>(dv.dom, flags0, flags1, bid0, bid1);
+}
+
+void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s) {
+    const long long side = dv.remap_side;
+    const unsigned bx = blocks_for(side * side * side, 256);
+    remap_kernel<<<dim3(bx, dv.nb), 256, 0, s>>>(dv, sp, init_mode);
+}
+
+void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    links_kernel<<<dim3(dv.link_side, dv.nb), 256, 0, s>>>(dv, sp);
+}
+
+void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    switch (dv.precision) {
+    case 0: force_kernel<double><<<dv.nb, FORCE_THREADS, 0, s>>>(dv, sp); break;
+    case 1: force_kernel<float><<<dv.nb, FORCE_THREADS, 0, s>>>(dv, sp); break;
+    case 2: force_kernel<__half><<<dv.nb, FORCE_THREADS, 0, s>>>(dv, sp); break;
+    default: force_kernel<__nv_bfloat16><<<dv.nb, FORCE_THREADS, 0, s>>>(dv, sp); break;
+    }
+}
+
+void launch_integrate(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    integrate_kernel<<<1, 256, 0, s>>>(dv, sp);
+}
+
+template <typename O>
+static void export_typed(const Device &dv, const void *pop, const uint8_t *flags, const uint8_t *bid,
+                         int what, int mask_solid, O *out, cudaStream_t s) {
+    const unsigned bl = blocks_for(dv.dom.C, 256);
+    switch (dv.precision) {
+    case 0: export_kernel<double, O><<<bl, 256, 0, s>>>(dv, (const double *)pop, flags, bid, what, mask_solid, out); break;
+    case 1: export_kernel<float, O><<<bl, 256, 0, s>>>(dv, (const float *)pop, flags, bid, what, mask_solid, out); break;
+    case 2: export_kernel<__half, O><<<bl, 256, 0, s>>>(dv, (const __half *)pop, flags, bid, what, mask_solid, out); break;
+    default: export_kernel<__nv_bfloat16, O><<<bl, 256, 0, s>>>(dv, (const __nv_bfloat16 *)pop, flags, bid, what, mask_solid, out); break;
+    }
+}
+
+void launch_export(const Device &dv, const void *pop, const uint8_t *flags, const uint8_t *bid, int what,
+                   int mask_solid, void *out, int dtype, cudaStream_t s) {
+    if (dtype == 1) export_typed<float>(dv, pop, flags, bid, what, mask_solid, static_cast<float *>(out), s);
+    else export_typed<double>(dv, pop, flags, bid, what, mask_solid, static_cast<double *>(out), s);
+}
+
+void launch_import_pop(const Device &dv, void *pop, const double *in, cudaStream_t s) {
+    const unsigned bl = blocks_for(dv.dom.C, 256);
+    switch (dv.precision) {
+    case 0: import_kernel<double><<<bl, 256, 0, s>>>(dv, (double *)pop, in); break;
+    case 1: import_kernel<float><<<bl, 256, 0, s>>>(dv, (float *)pop, in); break;
+    case 2: import_kernel<__half><<<bl, 256, 0, s>>>(dv, (__half *)pop, in); break;
+    default: import_kernel<__nv_bfloat16><<<bl, 256, 0, s>>>(dv, (__nv_bfloat16 *)pop, in); break;
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,177 @@
+// lbm_internal.cuh -- device-side types, lattice tables and helpers shared by
+// the kernels and the runtime of the GB300 coupled LBM / rigid-body step.
+//
+// Data layout in HBM (one handle):
+//   pop[2]     populations, SoA [19][C] of the storage type, ping-pong by step
+//              parity; stored as deviations delta_a = f_a - w_a (FP16 scaled)
+//   flags[2]   uint8 per cell and flag epoch (bits below), ping-pong by parity
+//   bid[2]     uint8 body id of solid cells per epoch (0xFF: none)
+//   bodies[2]  BodyState per body (FP64), ping-pong: state n and n-1 / n+1
+//   links      per (body, z-plane) segments of fluid->solid links
+// C = nx * ny * nz, cell index c = (z * ny + y) * nx + x.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// D3Q19 velocity set (Qian, d'Humieres, Lallemand), in the order of lbm.h,
+// as constexpr functions so that unrolled loops fold them to immediates.
+__host__ __device__ constexpr int ex(int a) {
+    switch (a) {
+    case 1: case 7: case 9: case 11: case 13: return 1;
+    case 2: case 8: case 10: case 12: case 14: return -1;
+    default: return 0;
+    }
+}
+__host__ __device__ constexpr int ey(int a) {
+    switch (a) {
+    case 3: case 7: case 10: case 15: case 17: return 1;
+    case 4: case 8: case 9: case 16: case 18: return -1;
+    default: return 0;
+    }
+}
+__host__ __device__ constexpr int ez(int a) {
+    switch (a) {
+    case 5: case 11: case 14: case 15: case 18: return 1;
+    case 6: case 12: case 13: case 16: case 17: return -1;
+    default: return 0;
+    }
+}
+// opposite direction: pairs (1,2), (3,4), ... are each other's reverse
+__host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+// weights 1/3 (rest), 1/18 (axes), 1/36 (diagonals)
+__host__ __device__ constexpr double wgt(int a) { return a == 0 ? 1.0 / 3.0 : (a < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+// flag bits of one cell in epoch n
+constexpr uint8_t F_SOLID = 1;      // solid at n
+constexpr uint8_t F_SOLID_PREV = 2; // solid at n-1 (uncovered if F_SOLID is clear)
+constexpr uint8_t F_NEAR = 4;       // some neighbour x - e_b was solid at n-1
+constexpr uint8_t F_WALL = 8;       // some neighbour lies beyond a no-slip wall
+constexpr uint8_t NO_BODY = 0xFF;
+
+// device status word bits
+constexpr int ST_OVERLAP = 1, ST_OUTSIDE = 2, ST_NAN = 4, ST_UNSTABLE = 8, ST_LINKS = 16;
+
+// cells added around a body's extent in the remap region; with at most
+// MAX_STEP lattice units of motion per step the region covers every cell
+// whose flags can differ from the static value in either epoch buffer
+constexpr int REMAP_MARGIN = 4;
+constexpr double MAX_STEP = 0.5;
+
+struct BodyProps {
+    int shape;          // 0 sphere, 1 capsule
+    int E;              // ceil(r + l/2) + 1: half-width of the box that holds every solid cell
+    double r, l, m, volume;
+    double inertia[3];      // body-frame principal moments of inertia
+};
+
+struct BodyState {      // 13 doubles, the layout of lbm_get_bodies
+    double X[3], q[4], V[3], W[3];
+};
+
+struct Spring {
+    int i, j;
+    double k, rest, gamma;
+};
+
+struct DriveTerm {
+    int body;
+    double amp, freq, phase, t_off;
+};
+
+struct Link {
+    uint32_t cell;
+    uint32_t dir;
+};
+
+struct Domain {
+    int nx, ny, nz;
+    int px, py, pz;     // periodic flags
+    long long C;
+};
+
+__host__ __device__ inline int wrap_axis(int i, int n) {
+    // i in [-n, 2n)
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+__device__ inline double min_image(double d, int n, int periodic) {
+    return periodic ? d - n * rint(d / n) : d;
+}
+
+__device__ inline void quat_to_matrix(const double q[4], double R[3][3]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+// offset of lattice point p from the body centre (periodic minimum image)
+__device__ inline void offset_from(const Domain &d, const BodyState &b, double px, double py,
+                                   double pz, double o[3]) {
+    o[0] = min_image(px - b.X[0], d.nx, d.px);
+    o[1] = min_image(py - b.X[1], d.ny, d.py);
+    o[2] = min_image(pz - b.X[2], d.nz, d.pz);
+}
+
+// velocity of the body surface at lattice point p: V + Omega x (p - X)
+__device__ inline void surface_velocity(const Domain &d, const BodyState &b, double px, double py,
+                                        double pz, double u[3]) {
+    double o[3];
+    offset_from(d, b, px, py, pz, o);
+    u[0] = b.V[0] + (b.W[1] * o[2] - b.W[2] * o[1]);
+    u[1] = b.V[1] + (b.W[2] * o[0] - b.W[0] * o[2]);
+    u[2] = b.V[2] + (b.W[0] * o[1] - b.W[1] * o[0]);
+}
+
+// kernel launch parameters of one step
+struct StepPtrs {
+    const void *src;        // populations of step n-1
+    void *dst;              // populations of step n
+    const uint8_t *flags_prev, *bid_prev;   // epoch n-1
+    uint8_t *flags_cur, *bid_cur;           // epoch n
+    const BodyState *body_prev;             // state n-1
+    const BodyState *body_cur;              // state n
+    BodyState *body_next;                   // state n+1
+    int parity;
+};
+
+struct Device {
+    Domain dom;
+    int precision;          // LBM_PREC_*
+    int nb, ns, nd;
+    double tau, omega, g[3];
+    int forced;
+    float f16_scale, f16_inv_scale;
+    const BodyProps *props;
+    const Spring *springs;
+    const DriveTerm *drives;
+    double *fh;             // [nb][6] force, torque of the last step
+    Link *links;            // [nb][link_side][seg_cap]
+    int *seg_count;         // [nb][link_side]
+    int link_side, seg_cap, remap_side;
+    int *status;
+    int *changed;           // [2]: some cell changed solidity or body in epoch parity p
+    long long *t_dev;       // step counter seen by the drive
+    double *hist;           // [hist_cap][nb][13] or null
+    int hist_cap;
+};
+
+// ---- launch wrappers (kernels.cu / stream_collide.cu) ----------------------
+void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8_t *bid0,
+                       uint8_t *bid1, cudaStream_t s);
+void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s);
+void launch_stream_collide(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+void launch_integrate(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+void launch_export(const Device &dv, const void *pop, const uint8_t *flags, const uint8_t *bid,
+                   int what, int mask_solid, void *out, int dtype, cudaStream_t s);
+void launch_import_pop(const Device &dv, void *pop, const double *in, cudaStream_t s);
+int stream_collide_vector_width(const Device &dv);
+
+}  // namespace lbm

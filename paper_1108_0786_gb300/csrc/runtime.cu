@@ -1,0 +1,705 @@
+// runtime.cu -- the C ABI of include/lbm.h: handle, device memory through an
+// allocator hook, the step as a CUDA graph per step parity, the device status
+// word, field export / import, history, checkpoint and kernel timing.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <cmath>
+#include <algorithm>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+using lbm::BodyProps;
+using lbm::BodyState;
+using lbm::DriveTerm;
+using lbm::Spring;
+
+namespace {
+constexpr int CHUNK_STEPS = 16;     // steps per chunk graph (even)
+const char SAVE_MAGIC[8] = {'L', 'B', 'M', '3', 'S', 'A', 'V', '1'};
+}  // namespace
+
+struct lbm_s {
+    // configuration (host)
+    int nx = 0, ny = 0, nz = 0, bc = 0, precision = 1, options = 0;
+    double tau = 1.0, g[3] = {0, 0, 0};
+    long long C = 0;
+    std::vector<BodyProps> props;
+    std::vector<BodyState> init_state;
+    std::vector<Spring> springs;
+    std::vector<DriveTerm> drives;
+    int hist_cap = 0;
+    // device
+    bool ready = false, graphs_ready = false;
+    int device = 0;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    lbm_alloc_fn afn = nullptr;
+    lbm_free_fn ffn = nullptr;
+    void *actx = nullptr;
+    std::vector<void *> allocs;
+    lbm::Device dv{};
+    void *pop[2] = {nullptr, nullptr};
+    uint8_t *flags[2] = {nullptr, nullptr}, *bid[2] = {nullptr, nullptr};
+    BodyState *bodies[2] = {nullptr, nullptr};
+    long long steps = 0;
+    cudaGraphExec_t single[2] = {nullptr, nullptr};
+    cudaGraphExec_t chunk = nullptr;
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_t *h, int code, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(lbm_t *h, cudaError_t e, const char *what) {
+    return fail(h, LBM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+size_t pop_bytes(int precision) { return precision == 0 ? 8 : (precision == 1 ? 4 : 2); }
+
+void *dalloc(lbm_t *h, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (h->afn) {
+        p = h->afn(bytes, h->actx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    return p;
+}
+
+void dfree(lbm_t *h, void *p) {
+    if (!p) return;
+    if (h->afn) {
+        if (h->ffn) h->ffn(p, h->actx);
+    } else {
+        cudaFree(p);
+    }
+}
+
+template <typename T>
+int alloc_into(lbm_t *h, T **out, size_t bytes) {
+    void *p = dalloc(h, bytes);
+    if (!p) return fail(h, LBM_E_OOM, "device allocation of %zu bytes failed", bytes);
+    h->allocs.push_back(p);
+    *out = static_cast<T *>(p);
+    return LBM_OK;
+}
+
+bool fluid(const lbm_t *h) { return !(h->options & LBM_OPT_NO_FLUID); }
+int nb(const lbm_t *h) { return (int)h->props.size(); }
+
+lbm::StepPtrs step_ptrs(lbm_t *h, int p) {
+    const int q = p ^ 1;
+    lbm::StepPtrs sp{};
+    sp.src = h->pop[q];
+    sp.dst = h->pop[p];
+    sp.flags_prev = h->flags[q];
+    sp.bid_prev = h->bid[q];
+    sp.flags_cur = h->flags[p];
+    sp.bid_cur = h->bid[p];
+    sp.body_prev = h->bodies[q];
+    sp.body_cur = h->bodies[p];
+    sp.body_next = h->bodies[q];
+    sp.parity = p;
+    return sp;
+}
+
+// the kernels of one step of parity p, in Algorithm 2's order
+void enqueue_step(lbm_t *h, int p, cudaStream_t s) {
+    const lbm::StepPtrs sp = step_ptrs(h, p);
+    const bool bodies = nb(h) > 0;
+    if (bodies && fluid(h)) lbm::launch_remap(h->dv, sp, 0, s);
+    if (fluid(h)) lbm::launch_stream_collide(h->dv, sp, s);
+    if (bodies && fluid(h)) {
+        lbm::launch_links(h->dv, sp, s);
+        lbm::launch_force(h->dv, sp, s);
+    }
+    if (bodies) lbm::launch_integrate(h->dv, sp, s);
+}
+
+int kernels_per_step(const lbm_t *h) {
+    const bool bodies = nb(h) > 0;
+    return (bodies && fluid(h) ? 1 : 0) + (fluid(h) ? 1 : 0) + (bodies && fluid(h) ? 2 : 0) + (bodies ? 1 : 0);
+}
+
+// flags of the epoch before the first step: the mapping of state 0
+int init_flags(lbm_t *h) {
+    lbm::launch_init_flags(h->dv, h->flags[0], h->flags[1], h->bid[0], h->bid[1], h->stream);
+    if (nb(h) > 0 && fluid(h)) {
+        lbm::StepPtrs sp = step_ptrs(h, 1);
+        sp.body_cur = h->bodies[0];
+        lbm::launch_remap(h->dv, sp, 1, h->stream);
+    }
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+int upload_bodies(lbm_t *h) {
+    const size_t bs = sizeof(BodyState) * nb(h);
+    if (!bs) return LBM_OK;
+    CK(cudaMemcpyAsync(h->bodies[0], h->init_state.data(), bs, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->bodies[1], h->init_state.data(), bs, cudaMemcpyHostToDevice, h->stream));
+    return LBM_OK;
+}
+
+int ensure_device(lbm_t *h) {
+    if (h->ready) return LBM_OK;
+    CK(cudaGetDevice(&h->device));
+    int rc;
+    const size_t es = pop_bytes(h->precision);
+    const long long C = h->C;
+    const int B = nb(h);
+    int emax = 0;
+    for (const auto &p : h->props) emax = std::max(emax, p.E);
+    lbm::Device &dv = h->dv;
+    dv.dom = lbm::Domain{h->nx, h->ny, h->nz, (h->bc & 1) ? 1 : 0, (h->bc & 2) ? 1 : 0, (h->bc & 4) ? 1 : 0, C};
+    dv.precision = h->precision;
+    dv.nb = B;
+    dv.ns = (int)h->springs.size();
+    dv.nd = (int)h->drives.size();
+    dv.tau = h->tau;
+    dv.omega = 1.0 / h->tau;
+    for (int i = 0; i < 3; ++i) dv.g[i] = h->g[i];
+    dv.forced = (h->g[0] != 0.0 || h->g[1] != 0.0 || h->g[2] != 0.0) ? 1 : 0;
+    dv.f16_scale = h->precision == LBM_PREC_F16 ? 1024.0f : 1.0f;
+    dv.f16_inv_scale = 1.0f / dv.f16_scale;
+    dv.remap_side = 2 * (emax + lbm::REMAP_MARGIN) + 1;
+    dv.link_side = 2 * (emax + 1) + 1;
+    dv.seg_cap = dv.link_side * dv.link_side * 18;
+    dv.hist_cap = h->hist_cap;
+
+    for (int i = 0; i < 2; ++i) {
+        if ((rc = alloc_into(h, &h->pop[i], es * lbm::Q * C))) return rc;
+        if ((rc = alloc_into(h, &h->flags[i], (size_t)C))) return rc;
+        if ((rc = alloc_into(h, &h->bid[i], (size_t)C))) return rc;
+        if ((rc = alloc_into(h, &h->bodies[i], sizeof(BodyState) * std::max(B, 1)))) return rc;
+    }
+    BodyProps *props; Spring *springs; DriveTerm *drives;
+    if ((rc = alloc_into(h, &props, sizeof(BodyProps) * std::max(B, 1)))) return rc;
+    if ((rc = alloc_into(h, &springs, sizeof(Spring) * std::max<size_t>(h->springs.size(), 1)))) return rc;
+    if ((rc = alloc_into(h, &drives, sizeof(DriveTerm) * std::max<size_t>(h->drives.size(), 1)))) return rc;
+    if ((rc = alloc_into(h, &dv.fh, sizeof(double) * 6 * std::max(B, 1)))) return rc;
+    const size_t nlinks = (size_t)std::max(B, 1) * dv.link_side * dv.seg_cap;
+    if ((rc = alloc_into(h, &dv.links, sizeof(lbm::Link) * (B > 0 && fluid(h) ? nlinks : 1)))) return rc;
+    if ((rc = alloc_into(h, &dv.seg_count, sizeof(int) * std::max(B, 1) * dv.link_side))) return rc;
+    if ((rc = alloc_into(h, &dv.status, sizeof(int) * 4))) return rc;
+    dv.changed = dv.status + 2;
+    if ((rc = alloc_into(h, &dv.t_dev, sizeof(long long)))) return rc;
+    dv.hist = nullptr;
+    if (h->hist_cap > 0 && (rc = alloc_into(h, &dv.hist, sizeof(double) * 13 * h->hist_cap * std::max(B, 1))))
+        return rc;
+    dv.props = props;
+    dv.springs = springs;
+    dv.drives = drives;
+
+    cudaStream_t s = h->stream;
+    CK(cudaMemsetAsync(h->pop[0], 0, es * lbm::Q * C, s));   // deviation 0: fluid at rest
+    CK(cudaMemsetAsync(h->pop[1], 0, es * lbm::Q * C, s));
+    CK(cudaMemsetAsync(dv.fh, 0, sizeof(double) * 6 * std::max(B, 1), s));
+    CK(cudaMemsetAsync(dv.seg_count, 0, sizeof(int) * std::max(B, 1) * dv.link_side, s));
+    const int st[4] = {0, 0, 1, 0};           // status, pad, changed[0] = 1, changed[1] = 0
+    CK(cudaMemcpyAsync(dv.status, st, sizeof st, cudaMemcpyHostToDevice, s));
+    const long long t0 = 0;
+    CK(cudaMemcpyAsync(dv.t_dev, &t0, sizeof t0, cudaMemcpyHostToDevice, s));
+    if (B) CK(cudaMemcpyAsync(props, h->props.data(), sizeof(BodyProps) * B, cudaMemcpyHostToDevice, s));
+    if (!h->springs.empty())
+        CK(cudaMemcpyAsync(springs, h->springs.data(), sizeof(Spring) * h->springs.size(), cudaMemcpyHostToDevice, s));
+    if (!h->drives.empty())
+        CK(cudaMemcpyAsync(drives, h->drives.data(), sizeof(DriveTerm) * h->drives.size(), cudaMemcpyHostToDevice, s));
+    if ((rc = upload_bodies(h))) return rc;
+    if ((rc = init_flags(h))) return rc;
+    CK(cudaStreamSynchronize(s));
+    h->ready = true;
+    return LBM_OK;
+}
+
+int build_graphs(lbm_t *h) {
+    if (h->graphs_ready) return LBM_OK;
+    if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    for (int p = 0; p < 2; ++p) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(h, p, h->cap);
+        CK(cudaStreamEndCapture(h->cap, &g));
+        CK(cudaGraphInstantiate(&h->single[p], g, 0));
+        cudaGraphDestroy(g);
+    }
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < CHUNK_STEPS; ++i) enqueue_step(h, i & 1, h->cap);
+    CK(cudaStreamEndCapture(h->cap, &g));
+    CK(cudaGraphInstantiate(&h->chunk, g, 0));
+    cudaGraphDestroy(g);
+    h->graphs_ready = true;
+    return LBM_OK;
+}
+
+int check_status(lbm_t *h) {
+    int st = 0;
+    CK(cudaMemcpy(&st, h->dv.status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st & lbm::ST_NAN) return fail(h, LBM_E_NAN, "non-finite body state");
+    if (st & lbm::ST_OVERLAP) return fail(h, LBM_E_OVERLAP, "two bodies cover the same cell");
+    if (st & lbm::ST_OUTSIDE) return fail(h, LBM_E_OUTSIDE, "a body crosses a wall of the domain");
+    if (st & lbm::ST_UNSTABLE)
+        return fail(h, LBM_E_UNSTABLE, "a body moved more than %g lattice units in one step", LBM_MAX_BODY_STEP);
+    if (st & lbm::ST_LINKS) return fail(h, LBM_E_LINKS, "link list capacity exceeded");
+    return LBM_OK;
+}
+
+int sync_and_check(lbm_t *h) {
+    if (!h->ready) return LBM_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    return check_status(h);
+}
+
+void release_device(lbm_t *h) {
+    if (h->ready) cudaStreamSynchronize(h->stream);
+    for (int p = 0; p < 2; ++p)
+        if (h->single[p]) cudaGraphExecDestroy(h->single[p]);
+    if (h->chunk) cudaGraphExecDestroy(h->chunk);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    for (void *p : h->allocs) dfree(h, p);
+    h->allocs.clear();
+}
+
+int last_parity(const lbm_t *h) { return (int)((h->steps + 1) & 1); }
+
+}  // namespace
+
+// the library is built with hidden visibility; only the C ABI is exported
+#pragma GCC visibility push(default)
+extern "C" {
+
+int lbm_create_ex(int nx, int ny, int nz, double tau, int bc, int precision, const double g[3],
+                  int options, lbm_t **out) {
+    if (!out) return LBM_E_ARG;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5) || bc < 0 || bc > 7 || precision < 0 || precision > 3 ||
+        (options & ~LBM_OPT_NO_FLUID))
+        return LBM_E_ARG;
+    const long long C = (long long)nx * ny * nz;
+    if (C > (1LL << 31) - 1) return LBM_E_ARG;   // link cells are 32-bit indices
+    lbm_t *h = new (std::nothrow) lbm_s();
+    if (!h) return LBM_E_OOM;
+    h->nx = nx; h->ny = ny; h->nz = nz; h->bc = bc; h->tau = tau;
+    h->precision = precision; h->options = options; h->C = C;
+    if (g)
+        for (int i = 0; i < 3; ++i) h->g[i] = g[i];
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_create(int nx, int ny, int nz, double tau, int bc, lbm_t **out) {
+    return lbm_create_ex(nx, ny, nz, tau, bc, LBM_PREC_F32, nullptr, 0, out);
+}
+
+int lbm_destroy(lbm_t *h) {
+    if (!h) return LBM_OK;
+    release_device(h);
+    delete h;
+    return LBM_OK;
+}
+
+int lbm_set_allocator(lbm_t *h, lbm_alloc_fn a, lbm_free_fn f, void *ctx) {
+    if (!h) return LBM_E_ARG;
+    if (h->ready) return fail(h, LBM_E_STATE, "allocator must be set before the first device allocation");
+    if ((a == nullptr) != (f == nullptr)) return fail(h, LBM_E_ARG, "allocator needs both functions");
+    h->afn = a; h->ffn = f; h->actx = ctx;
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_t *h, void *stream) {
+    if (!h) return LBM_E_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return LBM_OK;
+}
+
+int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass, const double pos[3],
+                 const double orient[4]) {
+    if (!h || !pos) return LBM_E_ARG;
+    if (h->ready) return fail(h, LBM_E_STATE, "bodies must be added before the first step");
+    if ((int)h->props.size() >= LBM_MAX_BODIES) return fail(h, LBM_E_ARG, "at most %d bodies", LBM_MAX_BODIES);
+    if (shape != LBM_SHAPE_SPHERE && shape != LBM_SHAPE_CAPSULE) return fail(h, LBM_E_ARG, "unknown shape");
+    if (!(radius > 0) || !(mass > 0) || !(length >= 0) || (shape == LBM_SHAPE_SPHERE && length != 0) ||
+        !(radius + 0.5 * length < 500.0))
+        return fail(h, LBM_E_ARG, "bad body dimensions");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(pos[i])) return fail(h, LBM_E_ARG, "non-finite position");
+    BodyProps p{};
+    p.shape = shape; p.r = radius; p.l = length; p.m = mass;
+    p.E = (int)std::ceil(radius + 0.5 * length) + 1;
+    const double r = radius, l = length;
+    double I[3];
+    if (shape == LBM_SHAPE_SPHERE) {
+        p.volume = 4.0 / 3.0 * M_PI * r * r * r;
+        I[0] = I[1] = I[2] = 0.4 * mass * r * r;
+    } else {
+        // uniform solid capsule: cylinder of length l plus two hemispheres
+        const double vc = M_PI * r * r * l, vh = 2.0 / 3.0 * M_PI * r * r * r;
+        p.volume = vc + 2.0 * vh;
+        const double mc = mass * vc / p.volume, mh = mass * vh / p.volume;
+        I[0] = 0.5 * mc * r * r + 2.0 * (0.4 * mh * r * r);
+        I[1] = I[2] = mc * (r * r / 4.0 + l * l / 12.0) + 2.0 * mh * (0.4 * r * r + l * l / 4.0 + 3.0 * l * r / 8.0);
+    }
+    for (int i = 0; i < 3; ++i) p.inertia[i] = I[i];
+    BodyState s{};
+    for (int i = 0; i < 3; ++i) s.X[i] = pos[i];
+    if (orient) {
+        const double n = std::sqrt(orient[0] * orient[0] + orient[1] * orient[1] + orient[2] * orient[2] +
+                                   orient[3] * orient[3]);
+        if (!(n > 0)) return fail(h, LBM_E_ARG, "zero quaternion");
+        for (int i = 0; i < 4; ++i) s.q[i] = orient[i] / n;
+    } else {
+        s.q[0] = 1.0;
+    }
+    h->props.push_back(p);
+    h->init_state.push_back(s);
+    return (int)h->props.size() - 1;
+}
+
+int lbm_add_spring(lbm_t *h, int i, int j, double k, double rest, double damping) {
+    if (!h) return LBM_E_ARG;
+    if (h->ready) return fail(h, LBM_E_STATE, "springs must be added before the first step");
+    const int B = nb(h);
+    if (i < 0 || j < 0 || i >= B || j >= B || i == j || !(k >= 0) || !(rest >= 0) || !(damping >= 0))
+        return fail(h, LBM_E_ARG, "bad spring");
+    h->springs.push_back(Spring{i, j, k, rest, damping});
+    return (int)h->springs.size() - 1;
+}
+
+int lbm_set_drive(lbm_t *h, int body, double amp, double freq, double phase) {
+    if (!h) return LBM_E_ARG;
+    if (h->ready) return fail(h, LBM_E_STATE, "drives must be added before the first step");
+    if (body < 0 || body >= nb(h) || !(freq > 0) || !(phase >= 0) || !std::isfinite(amp))
+        return fail(h, LBM_E_ARG, "bad drive");
+    h->drives.push_back(DriveTerm{body, amp, freq, phase, INFINITY});
+    return (int)h->drives.size() - 1;
+}
+
+int lbm_set_drive_window(lbm_t *h, int term, double t_off) {
+    if (!h || term < 0 || term >= (int)h->drives.size()) return LBM_E_ARG;
+    if (h->ready) return fail(h, LBM_E_STATE, "drive windows must be set before the first step");
+    h->drives[term].t_off = t_off;
+    return LBM_OK;
+}
+
+int lbm_set_body_state(lbm_t *h, int b, const double state[13]) {
+    if (!h || !state || b < 0 || b >= nb(h)) return LBM_E_ARG;
+    BodyState s;
+    std::memcpy(&s, state, sizeof s);
+    const double n = std::sqrt(s.q[0] * s.q[0] + s.q[1] * s.q[1] + s.q[2] * s.q[2] + s.q[3] * s.q[3]);
+    if (!(n > 0)) return fail(h, LBM_E_ARG, "zero quaternion");
+    for (int i = 0; i < 4; ++i) s.q[i] /= n;
+    if (!h->ready || h->steps == 0) {
+        h->init_state[b] = s;
+        if (!h->ready) return LBM_OK;
+        int rc;
+        if ((rc = upload_bodies(h))) return rc;
+        if ((rc = init_flags(h))) return rc;
+        CK(cudaStreamSynchronize(h->stream));
+        return LBM_OK;
+    }
+    int rc = sync_and_check(h);
+    if (rc) return rc;
+    BodyState *cur = h->bodies[h->steps & 1] + b;
+    BodyState old;
+    CK(cudaMemcpy(&old, cur, sizeof old, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 3; ++i)
+        if (!(std::fabs(s.X[i] - old.X[i]) < LBM_MAX_BODY_STEP))
+            return fail(h, LBM_E_STATE, "after the first step a body may move by less than %g per axis",
+                        LBM_MAX_BODY_STEP);
+    CK(cudaMemcpy(cur, &s, sizeof s, cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+int lbm_set_fields(lbm_t *h, int what, const void *in, int dtype) {
+    if (!h || !in) return LBM_E_ARG;
+    if (what != LBM_FIELD_POP || dtype != LBM_DTYPE_F64)
+        return fail(h, LBM_E_ARG, "only LBM_FIELD_POP as LBM_DTYPE_F64 can be set");
+    int rc = ensure_device(h);
+    if (rc) return rc;
+    if ((rc = sync_and_check(h))) return rc;
+    const size_t bytes = sizeof(double) * lbm::Q * h->C;
+    double *tmp = static_cast<double *>(dalloc(h, bytes));
+    if (!tmp) return fail(h, LBM_E_OOM, "device allocation of %zu bytes failed", bytes);
+    cudaError_t e = cudaMemcpyAsync(tmp, in, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        lbm::launch_import_pop(h->dv, h->pop[last_parity(h)], tmp, h->stream);
+        e = cudaStreamSynchronize(h->stream);
+    }
+    dfree(h, tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_fields");
+    return LBM_OK;
+}
+
+int lbm_step(lbm_t *h, int n) {
+    if (!h || n < 0) return LBM_E_ARG;
+    int rc = ensure_device(h);
+    if (rc) return rc;
+    if ((rc = build_graphs(h))) return rc;
+    while (n > 0) {
+        const int p = (int)(h->steps & 1);
+        if (p == 0 && n >= CHUNK_STEPS) {
+            CK(cudaGraphLaunch(h->chunk, h->stream));
+            h->steps += CHUNK_STEPS;
+            n -= CHUNK_STEPS;
+        } else {
+            CK(cudaGraphLaunch(h->single[p], h->stream));
+            h->steps += 1;
+            n -= 1;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_t *h) {
+    if (!h) return LBM_E_ARG;
+    return sync_and_check(h);
+}
+
+long long lbm_steps_done(lbm_t *h) { return h ? h->steps : -1; }
+
+int lbm_get_bodies(lbm_t *h, double *out) {
+    if (!h || !out) return LBM_E_ARG;
+    if (!h->ready) {
+        std::memcpy(out, h->init_state.data(), sizeof(BodyState) * nb(h));
+        return LBM_OK;
+    }
+    int rc = sync_and_check(h);
+    if (rc) return rc;
+    if (nb(h)) CK(cudaMemcpy(out, h->bodies[h->steps & 1], sizeof(BodyState) * nb(h), cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+int lbm_get_forces(lbm_t *h, double *out) {
+    if (!h || !out) return LBM_E_ARG;
+    if (!h->ready) {
+        std::memset(out, 0, sizeof(double) * 6 * nb(h));
+        return LBM_OK;
+    }
+    int rc = sync_and_check(h);
+    if (rc) return rc;
+    if (nb(h)) CK(cudaMemcpy(out, h->dv.fh, sizeof(double) * 6 * nb(h), cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+static size_t field_elems(const lbm_t *h, int what) {
+    return (size_t)h->C * (what == LBM_FIELD_U ? 3 : (what == LBM_FIELD_POP ? lbm::Q : 1));
+}
+
+static int check_field_args(lbm_t *h, int what, int dtype) {
+    if (what < 0 || what > 3) return fail(h, LBM_E_ARG, "unknown field");
+    if (what == LBM_FIELD_FLAGS ? dtype != LBM_DTYPE_U8 : (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32))
+        return fail(h, LBM_E_ARG, "unsupported dtype for this field");
+    return LBM_OK;
+}
+
+int lbm_get_fields_device(lbm_t *h, int what, void *dev_out, int dtype) {
+    if (!h || !dev_out) return LBM_E_ARG;
+    int rc = check_field_args(h, what, dtype);
+    if (rc) return rc;
+    if ((rc = ensure_device(h))) return rc;
+    const int p = last_parity(h);
+    if (what == LBM_FIELD_FLAGS && h->steps == 0) {
+        CK(cudaMemsetAsync(dev_out, 0, (size_t)h->C, h->stream));
+        return LBM_OK;
+    }
+    lbm::launch_export(h->dv, h->pop[p], h->flags[p], h->bid[p], what, h->steps > 0 ? 1 : 0, dev_out, dtype,
+                       h->stream);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_t *h, int what, void *out, int dtype) {
+    if (!h || !out) return LBM_E_ARG;
+    int rc = check_field_args(h, what, dtype);
+    if (rc) return rc;
+    if ((rc = ensure_device(h))) return rc;
+    if ((rc = sync_and_check(h))) return rc;
+    const size_t es = what == LBM_FIELD_FLAGS ? 1 : (dtype == LBM_DTYPE_F32 ? 4 : 8);
+    const size_t bytes = field_elems(h, what) * es;
+    void *tmp = dalloc(h, bytes);
+    if (!tmp) return fail(h, LBM_E_OOM, "device allocation of %zu bytes failed", bytes);
+    rc = lbm_get_fields_device(h, what, tmp, dtype);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    dfree(h, tmp);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_get_fields");
+    return LBM_OK;
+}
+
+int lbm_enable_history(lbm_t *h, int capacity) {
+    if (!h || capacity < 0) return LBM_E_ARG;
+    if (h->ready) return fail(h, LBM_E_STATE, "history must be enabled before the first step");
+    h->hist_cap = capacity;
+    return LBM_OK;
+}
+
+int lbm_get_history(lbm_t *h, double *out, int max_steps, int *n_out) {
+    if (!h || !out || !n_out || max_steps < 0) return LBM_E_ARG;
+    *n_out = 0;
+    if (!h->ready || h->hist_cap == 0 || nb(h) == 0) return LBM_OK;
+    int rc = sync_and_check(h);
+    if (rc) return rc;
+    const long long n = std::min<long long>(std::min<long long>(h->steps, h->hist_cap), max_steps);
+    const size_t per = (size_t)13 * nb(h);
+    std::vector<double> ring(per * h->hist_cap);
+    CK(cudaMemcpy(ring.data(), h->dv.hist, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < n; ++i) {
+        const long long t = h->steps - n + i;           // step whose result is state t + 1
+        std::memcpy(out + i * per, ring.data() + (t % h->hist_cap) * per, sizeof(double) * per);
+    }
+    *n_out = (int)n;
+    return LBM_OK;
+}
+
+namespace {
+struct SaveHeader {
+    char magic[8];
+    int nx, ny, nz, precision, nb, pad;
+    long long steps;
+};
+}  // namespace
+
+int lbm_save(lbm_t *h, const char *path) {
+    if (!h || !path) return LBM_E_ARG;
+    int rc = ensure_device(h);
+    if (rc) return rc;
+    if ((rc = sync_and_check(h))) return rc;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(h, LBM_E_ARG, "cannot open %s", path);
+    SaveHeader hd{};
+    std::memcpy(hd.magic, SAVE_MAGIC, 8);
+    hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.precision = h->precision; hd.nb = nb(h);
+    hd.steps = h->steps;
+    bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1;
+    const size_t pb = pop_bytes(h->precision) * lbm::Q * h->C;
+    std::vector<char> buf(std::max<size_t>(pb, 64));
+    auto put = [&](const void *dev, size_t bytes) {
+        if (!ok) return;
+        if (cudaMemcpy(buf.data(), dev, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) { ok = false; return; }
+        ok = std::fwrite(buf.data(), 1, bytes, f) == bytes;
+    };
+    put(h->pop[last_parity(h)], pb);
+    for (int i = 0; i < 2; ++i) { put(h->flags[i], h->C); put(h->bid[i], h->C); }
+    if (nb(h)) {
+        for (int i = 0; i < 2; ++i) put(h->bodies[i], sizeof(BodyState) * nb(h));
+        put(h->dv.fh, sizeof(double) * 6 * nb(h));
+    }
+    put(h->dv.t_dev, sizeof(long long));
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? LBM_OK : fail(h, LBM_E_ARG, "writing %s failed", path);
+}
+
+int lbm_load(lbm_t *h, const char *path) {
+    if (!h || !path) return LBM_E_ARG;
+    int rc = ensure_device(h);
+    if (rc) return rc;
+    if ((rc = sync_and_check(h))) return rc;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(h, LBM_E_ARG, "cannot open %s", path);
+    SaveHeader hd{};
+    bool ok = std::fread(&hd, sizeof hd, 1, f) == 1 && std::memcmp(hd.magic, SAVE_MAGIC, 8) == 0 &&
+              hd.nx == h->nx && hd.ny == h->ny && hd.nz == h->nz && hd.precision == h->precision &&
+              hd.nb == nb(h);
+    if (!ok) {
+        std::fclose(f);
+        return fail(h, LBM_E_ARG, "%s does not match this lattice", path);
+    }
+    h->steps = hd.steps;
+    const size_t pb = pop_bytes(h->precision) * lbm::Q * h->C;
+    std::vector<char> buf(std::max<size_t>(pb, 64));
+    auto get = [&](void *dev, size_t bytes) {
+        if (!ok) return;
+        ok = std::fread(buf.data(), 1, bytes, f) == bytes &&
+             cudaMemcpy(dev, buf.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    get(h->pop[last_parity(h)], pb);
+    for (int i = 0; i < 2; ++i) { get(h->flags[i], h->C); get(h->bid[i], h->C); }
+    if (nb(h)) {
+        for (int i = 0; i < 2; ++i) get(h->bodies[i], sizeof(BodyState) * nb(h));
+        get(h->dv.fh, sizeof(double) * 6 * nb(h));
+    }
+    get(h->dv.t_dev, sizeof(long long));
+    std::fclose(f);
+    if (!ok) return fail(h, LBM_E_ARG, "reading %s failed", path);
+    // the next step rebuilds its link lists from the restored flags
+    const int st[4] = {0, 0, 1, 1};
+    CK(cudaMemcpy(h->dv.status, st, sizeof st, cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots) {
+    if (!h || n < 0 || !ms_out || slots < 0) return LBM_E_ARG;
+    int rc = ensure_device(h);
+    if (rc) return rc;
+    if ((rc = sync_and_check(h))) return rc;
+    double total[LBM_NUM_KERNELS] = {0, 0, 0, 0, 0};
+    cudaEvent_t ev[2 * LBM_NUM_KERNELS];
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    const bool bodies = nb(h) > 0, fl = fluid(h);
+    cudaStream_t s = h->stream;
+    for (int it = 0; it < n; ++it) {
+        const int p = (int)(h->steps & 1);
+        const lbm::StepPtrs sp = step_ptrs(h, p);
+        bool ran[LBM_NUM_KERNELS] = {false, false, false, false, false};
+        auto run = [&](int slot, auto &&fn) {
+            cudaEventRecord(ev[2 * slot], s);
+            fn();
+            cudaEventRecord(ev[2 * slot + 1], s);
+            ran[slot] = true;
+        };
+        if (bodies && fl) run(LBM_KERNEL_REMAP, [&] { lbm::launch_remap(h->dv, sp, 0, s); });
+        if (fl) run(LBM_KERNEL_STREAM_COLLIDE, [&] { lbm::launch_stream_collide(h->dv, sp, s); });
+        if (bodies && fl) {
+            run(LBM_KERNEL_LINKS, [&] { lbm::launch_links(h->dv, sp, s); });
+            run(LBM_KERNEL_FORCE, [&] { lbm::launch_force(h->dv, sp, s); });
+        }
+        if (bodies) run(LBM_KERNEL_INTEGRATE, [&] { lbm::launch_integrate(h->dv, sp, s); });
+        h->steps += 1;
+        CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < LBM_NUM_KERNELS; ++k) {
+            if (!ran[k]) continue;
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+            total[k] += ms;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < slots && k < LBM_NUM_KERNELS; ++k) ms_out[k] = n ? total[k] / n : 0.0;
+    return check_status(h);
+}
+
+int lbm_kernels_per_step(lbm_t *h) { return h ? kernels_per_step(h) : LBM_E_ARG; }
+
+int lbm_bytes_per_cell(lbm_t *h) { return h ? (int)(2 * lbm::Q * pop_bytes(h->precision) + 1) : LBM_E_ARG; }
+
+const char *lbm_last_error(lbm_t *h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"
+#pragma GCC visibility pop

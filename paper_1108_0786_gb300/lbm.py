@@ -1,0 +1,309 @@
+"""ctypes binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every step of the coupled method runs in the CUDA library
+``_build/liblbm.so``; this module only converts Python / numpy / torch
+arguments.  ``Lattice`` raises if the library or a CUDA device is missing:
+there is no CPU fallback.
+
+PyTorch supplies device memory and streams: ``Lattice(..., torch_memory=True)``
+installs torch's caching allocator as the library's allocator hook and runs
+the library on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+OK = 0
+E_ARG, E_OOM, E_OVERLAP, E_OUTSIDE, E_NAN, E_LINKS, E_TIMEOUT, E_CUDA, E_STATE, E_UNSTABLE = (
+    -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
+BC_PERIODIC_X, BC_PERIODIC_Y, BC_PERIODIC_Z = 1, 2, 4
+SHAPE_SPHERE, SHAPE_CAPSULE = 0, 1
+PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = 0, 1, 2, 3
+OPT_NO_FLUID = 1
+FIELD_RHO, FIELD_U, FIELD_FLAGS, FIELD_POP = 0, 1, 2, 3
+DTYPE_F64, DTYPE_F32, DTYPE_U8 = 0, 1, 2
+KERNEL_NAMES = ("remap", "stream_collide", "links", "force", "integrate")
+PRECISIONS = {"f64": PREC_F64, "f32": PREC_F32, "f16": PREC_F16, "bf16": PREC_BF16}
+
+EXPORTED = (
+    "lbm_create", "lbm_create_ex", "lbm_destroy", "lbm_set_allocator", "lbm_set_stream",
+    "lbm_add_body", "lbm_add_spring", "lbm_set_drive", "lbm_set_drive_window",
+    "lbm_set_body_state", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_steps_done",
+    "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
+    "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
+    "lbm_kernels_per_step", "lbm_bytes_per_cell", "lbm_last_error",
+)
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(path: Optional[str] = None):
+    """Load the CUDA library (no compilation); raises OSError if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise OSError(f"CUDA library {p} is missing: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(p)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    DP = ctypes.POINTER(ctypes.c_double)
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "lbm_create": ([I, I, I, D, I, PP], I),
+        "lbm_create_ex": ([I, I, I, D, I, I, DP, I, PP], I),
+        "lbm_destroy": ([P], I),
+        "lbm_set_allocator": ([P, ALLOC_FN, FREE_FN, P], I),
+        "lbm_set_stream": ([P, P], I),
+        "lbm_add_body": ([P, I, D, D, D, DP, DP], I),
+        "lbm_add_spring": ([P, I, I, D, D, D], I),
+        "lbm_set_drive": ([P, I, D, D, D], I),
+        "lbm_set_drive_window": ([P, I, D], I),
+        "lbm_set_body_state": ([P, I, DP], I),
+        "lbm_set_fields": ([P, I, P, I], I),
+        "lbm_step": ([P, I], I),
+        "lbm_sync": ([P], I),
+        "lbm_steps_done": ([P], ctypes.c_longlong),
+        "lbm_get_bodies": ([P, DP], I),
+        "lbm_get_forces": ([P, DP], I),
+        "lbm_get_fields": ([P, I, P, I], I),
+        "lbm_get_fields_device": ([P, I, P, I], I),
+        "lbm_enable_history": ([P, I], I),
+        "lbm_get_history": ([P, DP, I, ctypes.POINTER(I)], I),
+        "lbm_save": ([P, ctypes.c_char_p], I),
+        "lbm_load": ([P, ctypes.c_char_p], I),
+        "lbm_time_kernels": ([P, I, DP, I], I),
+        "lbm_kernels_per_step": ([P], I),
+        "lbm_bytes_per_cell": ([P], I),
+        "lbm_last_error": ([P], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lbm error {code}: {msg}")
+        self.code = code
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Lattice:
+    """One D3Q19 lattice with rigid bodies on the current CUDA device.
+
+    Mirrors ``include/lbm.h``: ``add_body``, ``add_spring``, ``set_drive``,
+    ``step``, ``bodies``, ``forces``, ``field`` ...  With ``torch_memory``
+    (default) device memory comes from torch's caching allocator and work
+    runs on torch's current stream.
+    """
+
+    def __init__(self, nx, ny, nz, tau, bc=7, precision="f32", g=(0.0, 0.0, 0.0), options=0,
+                 torch_memory=True):
+        self._lib = load_library()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.shape = (nz, ny, nx)
+        self.cells = nx * ny * nz
+        self.precision = prec
+        self.g = tuple(float(v) for v in g)
+        h = ctypes.c_void_p()
+        gg = np.ascontiguousarray(g, dtype=np.float64)
+        rc = self._lib.lbm_create_ex(nx, ny, nz, float(tau), int(bc), prec, _dp(gg), int(options),
+                                     ctypes.byref(h))
+        if rc != OK:
+            raise LbmError(rc, "lbm_create_ex failed")
+        self._h = h
+        self.nbodies = 0
+        self._callbacks = None
+        if torch_memory:
+            self._use_torch()
+
+    # -- plumbing ---------------------------------------------------------
+    def _use_torch(self):
+        import torch
+        if not torch.cuda.is_available():
+            raise LbmError(E_CUDA, "no CUDA device: the library has no CPU path")
+        dev = torch.cuda.current_device()
+        stream = torch.cuda.current_stream(dev)
+
+        def alloc(nbytes, ctx):
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+
+        def free(ptr, ctx):
+            if ptr:
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._callbacks = (ALLOC_FN(alloc), FREE_FN(free))
+        self._check(self._lib.lbm_set_allocator(self._h, self._callbacks[0], self._callbacks[1], None))
+        self._check(self._lib.lbm_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+        self._torch_stream = stream
+
+    def _check(self, rc):
+        if rc < 0:
+            raise LbmError(rc, self._lib.lbm_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle: int):
+        self._check(self._lib.lbm_set_stream(self._h, ctypes.c_void_p(stream_handle)))
+
+    # -- setup ------------------------------------------------------------
+    def add_body(self, shape, radius, length, mass, pos, orient=(1.0, 0.0, 0.0, 0.0)):
+        p = np.ascontiguousarray(pos, dtype=np.float64)
+        q = np.ascontiguousarray(orient, dtype=np.float64)
+        b = self._check(self._lib.lbm_add_body(self._h, int(shape), float(radius), float(length),
+                                               float(mass), _dp(p), _dp(q)))
+        self.nbodies += 1
+        return b
+
+    def add_spring(self, i, j, k, rest, damping):
+        return self._check(self._lib.lbm_add_spring(self._h, int(i), int(j), float(k), float(rest),
+                                                    float(damping)))
+
+    def set_drive(self, body, amp, freq, phase):
+        return self._check(self._lib.lbm_set_drive(self._h, int(body), float(amp), float(freq),
+                                                   float(phase)))
+
+    def set_drive_window(self, term, t_off):
+        return self._check(self._lib.lbm_set_drive_window(self._h, int(term), float(t_off)))
+
+    def set_body_state(self, body, state):
+        s = np.ascontiguousarray(state, dtype=np.float64)
+        assert s.size == 13
+        return self._check(self._lib.lbm_set_body_state(self._h, int(body), _dp(s)))
+
+    def set_pop(self, pop):
+        p = np.ascontiguousarray(pop, dtype=np.float64).reshape(-1)
+        assert p.size == 19 * self.cells
+        return self._check(self._lib.lbm_set_fields(self._h, FIELD_POP, p.ctypes.data_as(ctypes.c_void_p),
+                                                    DTYPE_F64))
+
+    def enable_history(self, capacity):
+        return self._check(self._lib.lbm_enable_history(self._h, int(capacity)))
+
+    # -- stepping ---------------------------------------------------------
+    def step(self, n=1):
+        return self._check(self._lib.lbm_step(self._h, int(n)))
+
+    def sync(self):
+        return self._check(self._lib.lbm_sync(self._h))
+
+    @property
+    def steps_done(self):
+        return int(self._lib.lbm_steps_done(self._h))
+
+    # -- results ----------------------------------------------------------
+    def bodies(self):
+        out = np.zeros((self.nbodies, 13))
+        self._check(self._lib.lbm_get_bodies(self._h, _dp(out)))
+        return out
+
+    def forces(self):
+        out = np.zeros((self.nbodies, 6))
+        self._check(self._lib.lbm_get_forces(self._h, _dp(out)))
+        return out
+
+    def field(self, what, dtype=DTYPE_F64):
+        nz, ny, nx = self.shape
+        if what == FIELD_FLAGS:
+            dtype = DTYPE_U8
+            out = np.zeros((nz, ny, nx), dtype=np.uint8)
+        else:
+            npd = np.float64 if dtype == DTYPE_F64 else np.float32
+            lead = {FIELD_RHO: (), FIELD_U: (3,), FIELD_POP: (19,)}[what]
+            out = np.zeros(lead + (nz, ny, nx), dtype=npd)
+        self._check(self._lib.lbm_get_fields(self._h, int(what), out.ctypes.data_as(ctypes.c_void_p),
+                                             int(dtype)))
+        return out
+
+    def field_device(self, what, out_tensor, dtype=DTYPE_F64):
+        """Write a field into a caller-owned CUDA tensor (enqueued, no sync)."""
+        return self._check(self._lib.lbm_get_fields_device(self._h, int(what),
+                                                           ctypes.c_void_p(out_tensor.data_ptr()),
+                                                           int(dtype)))
+
+    def rho(self):
+        return self.field(FIELD_RHO)
+
+    def u(self):
+        return self.field(FIELD_U)
+
+    def flags(self):
+        return self.field(FIELD_FLAGS)
+
+    def pop(self):
+        return self.field(FIELD_POP)
+
+    def history(self, max_steps=None):
+        cap = max_steps if max_steps is not None else self.steps_done
+        out = np.zeros((max(cap, 0), self.nbodies, 13))
+        n = ctypes.c_int(0)
+        self._check(self._lib.lbm_get_history(self._h, _dp(out), int(cap), ctypes.byref(n)))
+        return out[: n.value]
+
+    def save(self, path):
+        return self._check(self._lib.lbm_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        return self._check(self._lib.lbm_load(self._h, os.fsencode(path)))
+
+    def time_kernels(self, n):
+        """Average per-kernel duration in ms over n eagerly launched steps."""
+        out = np.zeros(len(KERNEL_NAMES))
+        self._check(self._lib.lbm_time_kernels(self._h, int(n), _dp(out), len(KERNEL_NAMES)))
+        return dict(zip(KERNEL_NAMES, out.tolist()))
+
+    @property
+    def kernels_per_step(self):
+        return self._check(self._lib.lbm_kernels_per_step(self._h))
+
+    @property
+    def bytes_per_cell(self):
+        return self._check(self._lib.lbm_bytes_per_cell(self._h))
+
+
+def from_scenario(sc, precision="f32", torch_memory=True, options=0, history=0):
+    """Build a Lattice from a seeded ``workloads.Scenario``."""
+    lat = Lattice(sc.nx, sc.ny, sc.nz, sc.tau, sc.bc, precision, sc.g, options, torch_memory)
+    if history:
+        lat.enable_history(history)
+    for b in sc.bodies:
+        lat.add_body(b.shape, b.radius, b.length, b.mass, b.pos, b.orient)
+    for s in sc.springs:
+        lat.add_spring(s.i, s.j, s.k, s.rest, s.damping)
+    for d in sc.drives:
+        t = lat.set_drive(d.body, d.amp, d.freq, d.phase)
+        if math.isfinite(d.t_off):
+            lat.set_drive_window(t, d.t_off)
+    return lat

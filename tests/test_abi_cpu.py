@@ -1,0 +1,76 @@
+"""The C-ABI library loads and exports every entry point of include/lbm.h.
+
+These tests need no GPU: they build the library (nvcc cross-compiles for
+sm_103a), load it, and exercise only host-side calls (handle creation and
+argument checks), which allocate no device memory.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1108_0786_gb300 import _build, lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    return re.findall(r"^\s*(?:int|long long|const char \*)\s*(lbm_\w+)\s*\(", hdr, re.M)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return lbm.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lbm.EXPORTED)
+
+
+def test_only_the_c_abi_is_exported(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    text_syms = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert text_syms == set(declared_symbols())
+
+
+def test_host_side_calls_without_a_device(lib):
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(8, 8, 8, 1.0, 7, ctypes.byref(h)) == 0
+    p = np.array([4.0, 4.0, 4.0])
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert lib.lbm_add_body(h, 0, 2.0, 0.0, 10.0, p.ctypes.data_as(dp), None) == 0
+    assert lib.lbm_add_body(h, 1, 1.5, 3.0, 12.0, p.ctypes.data_as(dp), None) == 1
+    assert lib.lbm_add_spring(h, 0, 1, 0.01, 5.0, 0.001) == 0
+    assert lib.lbm_add_spring(h, 0, 0, 0.01, 5.0, 0.001) == lbm.E_ARG
+    assert lib.lbm_set_drive(h, 0, 1e-4, 1 / 400, 0.0) == 0
+    assert lib.lbm_set_drive(h, 7, 1e-4, 1 / 400, 0.0) == lbm.E_ARG
+    assert lib.lbm_add_body(h, 0, -1.0, 0.0, 10.0, p.ctypes.data_as(dp), None) == lbm.E_ARG
+    out = np.zeros(26)
+    assert lib.lbm_get_bodies(h, out.ctypes.data_as(dp)) == 0
+    assert np.array_equal(out[:3], p) and out[3] == 1.0
+    assert lib.lbm_kernels_per_step(h) == 5
+    assert lib.lbm_bytes_per_cell(h) == 2 * 19 * 4 + 1
+    assert lib.lbm_destroy(h) == 0
+
+
+@pytest.mark.parametrize("args", [(0, 8, 8, 1.0, 7), (8, 8, 8, 0.5, 7), (8, 8, 8, 1.0, 9)])
+def test_create_rejects_bad_arguments(lib, args):
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(*args, ctypes.byref(h)) == lbm.E_ARG
+
+
+def test_bytes_per_cell_by_precision(lib):
+    for prec, es in ((lbm.PREC_F64, 8), (lbm.PREC_F32, 4), (lbm.PREC_F16, 2), (lbm.PREC_BF16, 2)):
+        h = ctypes.c_void_p()
+        assert lib.lbm_create_ex(16, 8, 8, 1.0, 7, prec, None, 0, ctypes.byref(h)) == 0
+        assert lib.lbm_bytes_per_cell(h) == 2 * 19 * es + 1
+        lib.lbm_destroy(h)

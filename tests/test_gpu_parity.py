@@ -1,0 +1,237 @@
+"""GPU path against the FP64 oracle on the same seeded inputs (C ABI).
+
+FP64 storage must match the oracle's populations to 1e-12 absolute and body
+trajectories to 1e-10 relative.  FP32 deviation storage must match the
+oracle's velocity field to 1e-5 relative L2 and the net swimmer displacement
+to 1e-3 relative.  Cases span several thread blocks with ragged tails (odd
+and non-multiple-of-vector x sizes), walls on every axis, body force,
+capsules at arbitrary orientation and bodies that cross cell centres
+(remap and refill events).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle_helpers import oracle_from_scenario
+from paper_1108_0786_gb300 import lbm, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-12
+TRAJ_TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1108_0786_gb300 import _build
+    _build.build()
+
+
+def pair(sc, precision="f64", **kw):
+    return lbm.from_scenario(sc, precision=precision, **kw), oracle_from_scenario(sc)
+
+
+def rel_traj_err(a, b):
+    return np.abs(a[:, :3] - b[:, :3]).max() / np.abs(b[:, :3]).max()
+
+
+def seeded_pop(shape, seed, amp=2e-3):
+    """Random populations around the rest equilibrium (splitmix64 stream)."""
+    _, w = oracle.lattice()
+    rng = wl.SplitMix64(seed)
+    nz, ny, nx = shape
+    n = 19 * nx * ny * nz
+    u = np.frombuffer(np.array([rng.next_u64() for _ in range(n)], dtype=np.uint64).tobytes(),
+                      dtype=np.uint64)
+    noise = (u >> np.uint64(11)).astype(np.float64) / float(1 << 53) * 2 - 1
+    return w[:, None, None, None] * (1.0 + amp * noise.reshape(19, nz, ny, nx))
+
+
+def test_fp64_three_sphere_swimmer_1000_steps():
+    """32^3 periodic, three spheres r = 3, drive a = 1e-4, T = 400: the
+    FP64 method on its full 1000-step run."""
+    sc = wl.three_sphere_periodic()
+    gpu, ref = pair(sc)
+    for _ in range(10):
+        gpu.step(100)
+        ref.step(100)
+        assert rel_traj_err(gpu.bodies(), ref.bodies()) < TRAJ_TOL
+    assert np.abs(gpu.pop() - ref.pop()).max() < POP_TOL
+    assert np.array_equal(gpu.flags(), ref.flags())
+    fg, fr = gpu.forces(), ref.forces()
+    assert np.abs(fg - fr).max() < 1e-12 + 1e-10 * np.abs(fr).max()
+    b = gpu.bodies()
+    assert np.abs(b[:, 3:7] - ref.bodies()[:, 3:7]).max() < 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,nz,bc", [
+    (37, 19, 23, wl.PERIODIC_X),              # odd x: one cell per thread; walls in y and z
+    (38, 21, 17, 2 | 4),                      # even x: two cells per thread; walls in x
+    (40, 24, 20, 0),                          # walls on all six faces
+    (36, 20, 28, 7),                          # fully periodic
+])
+def test_fp64_ragged_boxes_walls_force_capsules(nx, ny, nz, bc):
+    sc = wl.Scenario("ragged", nx, ny, nz, 0.8, bc=bc, g=(3e-6, -2e-6, 1e-6))
+    q = (0.9, 0.2, -0.3, 0.25)
+    n = math.sqrt(sum(v * v for v in q))
+    q = tuple(v / n for v in q)
+    sc.bodies.append(wl.Body(wl.CAPSULE, 3.2, 5.0, 900.0, (nx / 2 - 5.3, ny / 2 + 0.4, nz / 2 - 0.2), q))
+    sc.bodies.append(wl.Body(wl.SPHERE, 2.7, 0.0, 300.0, (nx / 2 + 7.1, ny / 2 - 0.6, nz / 2 + 0.9)))
+    sc.springs.append(wl.Spring(0, 1, 0.02, 12.0, 0.01))
+    sc.drives.append(wl.Drive(0, 2e-3, 1 / 50.0, 0.0))
+    sc.drives.append(wl.Drive(1, -2e-3, 1 / 50.0, 0.0))
+    gpu, ref = pair(sc)
+    pop = seeded_pop(gpu.shape, 1000 + nx)
+    gpu.set_pop(pop)
+    ref.set_pop(pop)
+    for state_b, v in ((0, (4e-3, -2e-3, 1e-3)), (1, (-3e-3, 1e-3, 2e-3))):
+        s = ref.bodies()[state_b].copy()
+        s[7:10] = v
+        s[10:13] = (1e-3, -2e-3, 5e-4)
+        gpu.set_body_state(state_b, s)
+        ref.set_body_state(state_b, s)
+    for _ in range(4):
+        gpu.step(15)
+        ref.step(15)
+        assert np.abs(gpu.pop() - ref.pop()).max() < POP_TOL
+        assert np.array_equal(gpu.flags(), ref.flags())
+        assert rel_traj_err(gpu.bodies(), ref.bodies()) < TRAJ_TOL
+        fr = ref.forces()
+        assert np.abs(gpu.forces() - fr).max() < 1e-12 + 1e-10 * np.abs(fr).max()
+    assert np.abs(gpu.u() - ref.u()).max() < 1e-12
+    assert np.abs(gpu.rho() - ref.rho()).max() < 1e-12
+
+
+def test_fp64_bodies_crossing_cells_remap_and_refill():
+    """Heavy bodies with prescribed velocities sweep across many cell
+    centres: every step turns fluid cells solid and uncovers others."""
+    sc = wl.Scenario("sweep", 48, 30, 26, 1.0)
+    sc.bodies.append(wl.Body(wl.SPHERE, 4.3, 0.0, 1e9, (12.2, 14.7, 12.9)))
+    c = math.cos(0.3)
+    sc.bodies.append(wl.Body(wl.CAPSULE, 3.1, 6.0, 1e9, (32.4, 15.3, 13.2), (c, 0.0, math.sin(0.3), 0.0)))
+    gpu, ref = pair(sc)
+    for b, v, w in ((0, (0.11, 0.04, -0.03), (0, 0, 0)), (1, (-0.07, -0.05, 0.06), (0.01, -0.02, 0.015))):
+        s = ref.bodies()[b].copy()
+        s[7:10] = v
+        s[10:13] = w
+        gpu.set_body_state(b, s)
+        ref.set_body_state(b, s)
+    flags_seen = set()
+    for _ in range(12):
+        gpu.step(5)
+        ref.step(5)
+        fl = ref.flags()
+        flags_seen.add(fl.tobytes())
+        assert np.array_equal(gpu.flags(), fl)
+        assert np.abs(gpu.pop() - ref.pop()).max() < POP_TOL
+        fr = ref.forces()
+        assert np.abs(gpu.forces() - fr).max() < 1e-12 + 1e-10 * np.abs(fr).max()
+        assert rel_traj_err(gpu.bodies(), ref.bodies()) < TRAJ_TOL
+    assert len(flags_seen) == 12
+
+
+def test_fp64_single_step_edge_cases():
+    """One step from a random state; a 1-cell-thick periodic slab and a
+    domain narrower than a vector of cells."""
+    for nx, ny, nz in ((1, 16, 1), (3, 5, 7), (2, 2, 2)):
+        sc = wl.Scenario("tiny", nx, ny, nz, 0.7, g=(1e-5, 0, 0))
+        gpu, ref = pair(sc)
+        pop = seeded_pop(gpu.shape, nx * 100 + ny)
+        gpu.set_pop(pop)
+        ref.set_pop(pop)
+        gpu.step(3)
+        ref.step(3)
+        assert np.abs(gpu.pop() - ref.pop()).max() < POP_TOL
+
+
+def test_fp32_swimmer_against_fp64_oracle():
+    """FP32 deviation storage: velocity field within 1e-5 relative L2 and
+    net swimmer displacement within 1e-3 of the FP64 oracle."""
+    sc = wl.three_sphere_periodic()
+    gpu, ref = pair(sc, precision="f32")
+    x0 = ref.bodies()[:, 0].mean()
+    gpu.step(sc.steps)
+    ref.step(sc.steps)
+    ug, ur = gpu.u(), ref.u()
+    rel_l2 = np.linalg.norm(ug - ur) / np.linalg.norm(ur)
+    assert rel_l2 < 1e-5, rel_l2
+    dg = gpu.bodies()[:, 0].mean() - x0
+    dr = ref.bodies()[:, 0].mean() - x0
+    assert abs(dg - dr) <= 1e-3 * abs(dr) + 1e-9, (dg, dr)
+    assert np.array_equal(gpu.flags(), ref.flags())
+
+
+def test_device_errors_are_reported():
+    lat = lbm.Lattice(24, 24, 24, 1.0, precision="f64")
+    lat.add_body(wl.SPHERE, 3.0, 0.0, 100.0, (8.0, 12.0, 12.0))
+    lat.add_body(wl.SPHERE, 3.0, 0.0, 100.0, (12.5, 12.0, 12.0))
+    lat.step(1)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.sync()
+    assert ei.value.code == lbm.E_OVERLAP
+    lat2 = lbm.Lattice(24, 24, 24, 1.0, bc=wl.PERIODIC_X, precision="f32")
+    lat2.add_body(wl.SPHERE, 3.0, 0.0, 100.0, (12.0, 2.0, 12.0))
+    lat2.step(1)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat2.bodies()
+    assert ei.value.code == lbm.E_OUTSIDE
+
+
+def test_checkpoint_round_trip_is_bitwise(tmp_path):
+    sc = wl.three_sphere_periodic()
+    lat = lbm.from_scenario(sc, precision="f32")
+    lat.step(50)
+    path = str(tmp_path / "state.bin")
+    lat.save(path)
+    lat.step(70)
+    a_pop, a_bodies = lat.pop(), lat.bodies()
+    lat2 = lbm.from_scenario(sc, precision="f32")
+    lat2.load(path)
+    assert lat2.steps_done == 50
+    lat2.step(70)
+    assert np.array_equal(lat2.pop(), a_pop)
+    assert np.array_equal(lat2.bodies(), a_bodies)
+
+
+def test_history_matches_per_step_states():
+    sc = wl.three_sphere_periodic()
+    lat = lbm.from_scenario(sc, precision="f32", history=64)
+    states = []
+    for _ in range(20):
+        lat.step(1)
+        states.append(lat.bodies())
+    hist = lat.history()
+    assert hist.shape == (20, 3, 13)
+    assert np.array_equal(hist, np.array(states))
+    lat.step(100)
+    hist = lat.history()
+    assert hist.shape == (64, 3, 13)
+    assert np.array_equal(hist[-1], lat.bodies())
+
+
+def test_kernel_timing_and_launch_accounting():
+    sc = wl.three_sphere_periodic()
+    lat = lbm.from_scenario(sc, precision="f32")
+    lat.step(2)
+    ms = lat.time_kernels(3)
+    assert lat.kernels_per_step == 5
+    assert all(v > 0 for v in ms.values()), ms
+    assert lat.steps_done == 5
+
+
+def test_graph_steps_equal_eager_steps():
+    """The CUDA-graph path (chunks of 16 steps) and single-step launches
+    give bitwise identical states."""
+    sc = wl.three_sphere_periodic()
+    a = lbm.from_scenario(sc, precision="f32")
+    b = lbm.from_scenario(sc, precision="f32")
+    a.step(37)
+    for _ in range(37):
+        b.step(1)
+    assert np.array_equal(a.pop(), b.pop())
+    assert np.array_equal(a.bodies(), b.bodies())
