@@ -1,0 +1,388 @@
+"""Throughput of the coupled D3Q19 LBM / rigid-body swimmer step on GB300.
+
+One step is one pass of the whole hot path (remap, fused stream + bounce-back
++ refill + LBGK, link lists, momentum exchange, drive + springs + rigid-body
+integration) over the capsule-swarm workload: a 512 x 256 x 256 periodic box
+(33.5 M cells) holding 8 seeded three-capsule swimmers (capsules of radius 4
+and cylinder length 8), FP32 deviation storage.  The metric is coupled-step
+MLUPS (cells x steps / s / 1e6, solid cells included).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own seeded replica of the
+workload (weak scaling, no data-path collective); rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS & % HBM roofline (FP32 vs FP16-store); adjoint/forward time"
+UNIT = "MLUPS"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stream_collide_capsule_swarm_traffic.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_1108_0786_gb300", "csrc", "stream_collide.cu")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", default="f32", choices=("f32", "f16", "bf16", "f64"))
+    ap.add_argument("--nx", type=int, default=512)
+    ap.add_argument("--ny", type=int, default=256)
+    ap.add_argument("--nz", type=int, default=256)
+    ap.add_argument("--no-variants", action="store_true", help="skip the other storage precisions")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+# ---- distributed plumbing ------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" and torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks --------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for _, _, flags in rows for n, f in zip(names, flags) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- helpers ---------------------------------------------------------------
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def recorded_traffic(cells):
+    """DRAM bytes per stream-collide launch from the committed ncu summary,
+    scaled to ``cells``; None if the kernel source changed since."""
+    try:
+        vals = {}
+        with open(TRAFFIC_FILE) as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        return float(vals["dram_bytes_per_cell"]) * cells
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def workload(args, rank):
+    from paper_1108_0786_gb300 import workloads as wl
+    return wl.capsule_swarm(nx=args.nx, ny=args.ny, nz=args.nz, swimmers=8, seed=1108 + rank,
+                            steps=args.steps)
+
+
+def timed_steps(lat, steps, world, device):
+    import torch
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    start.record(stream)
+    lat.step(steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    lat.sync()
+    return max_over_ranks(start.elapsed_time(end), world, device)
+
+
+def e2e_run(sc, args, world, device):
+    """The same metric end to end through the C ABI with host buffers: the
+    initial populations are uploaded from pinned host memory (lbm_set_fields)
+    and every step's body states are read back (lbm_get_bodies)."""
+    import numpy as np
+    import torch
+    from paper_1108_0786_gb300 import lbm
+    lat = lbm.from_scenario(sc, precision=args.precision)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)     # the fluid at rest
+    pinned = torch.empty((19, sc.cells), dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.from_numpy(w)[:, None].expand(19, sc.cells))
+    host_pop = pinned.numpy()
+    lat.step(1)
+    lat.sync()
+    out = np.zeros((lat.nbodies, 13))
+    steps = args.steps
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.set_pop(host_pop)
+    for _ in range(steps):
+        lat.step(1)
+        out = lat.bodies()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, device)
+    value = sc.cells * steps * world / (ms / 1e3) / 1e6
+    h2d = 19 * sc.cells * 8 / steps
+    lat.close()
+    del pinned
+    return {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(out.nbytes),
+            "note": "lbm_set_fields from pinned host memory once (FP64, amortised over the steps), "
+                    "then per step lbm_step(1) + lbm_get_bodies (host sync)"}
+
+
+def variant_runs(sc, args, steps):
+    """Throughput of the other storage precisions and their error against the
+    FP64 path (the GPU FP64 path matches the oracle to 1e-12)."""
+    import numpy as np
+    from paper_1108_0786_gb300 import lbm
+    res = {}
+    ref = lbm.from_scenario(sc, precision="f64")
+    x0 = ref.bodies()[:, :3].copy()
+    ref.step(steps)
+    ref_u = ref.u()
+    ref_x = ref.bodies()[:, :3]
+    ref_disp = np.linalg.norm(ref_x - x0, axis=1)
+    for prec in ("f32", "f16", "bf16", "f64"):
+        lat = lbm.from_scenario(sc, precision=prec) if prec != "f64" else None
+        if lat is not None:
+            lat.step(steps)
+            u = lat.u()
+            xb = lat.bodies()[:, :3]
+            disp_err = float(np.abs(np.linalg.norm(xb - x0, axis=1) - ref_disp).max() / ref_disp.max())
+            u_err = float(np.linalg.norm(u - ref_u) / np.linalg.norm(ref_u))
+        else:
+            lat, disp_err, u_err = ref, 0.0, 0.0
+        lat.step(10)
+        lat.sync()
+        import torch
+        ms_k = lat.time_kernels(10)["stream_collide"]
+        t = timed_steps(lat, 200, 1, None)
+        res[prec] = {"mlups": round(sc.cells * 200 / (t / 1e3) / 1e6, 1),
+                     "stream_collide_gbs": round(lat.bytes_per_cell * sc.cells / (ms_k / 1e3) / 1e9, 1),
+                     "bytes_per_cell": lat.bytes_per_cell,
+                     "u_rel_l2_vs_f64": u_err, "displacement_rel_err_vs_f64": disp_err,
+                     "error_after_steps": steps}
+        lat.close()
+    return res
+
+
+def cpu_baseline(args):
+    """The FP64 oracle, as it stands, on the host cores: a few coupled steps
+    of the full-size workload (same domain and bodies)."""
+    import oracle
+    sc = workload(args, 0)
+    o = oracle.from_scenario(sc)
+    o.step(1)
+    n = 3
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    value = sc.cells * n / dt / 1e6
+    o.close()
+    return {"value": round(value, 2), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} coupled FP64 steps of the full {sc.nx}x{sc.ny}x{sc.nz} workload "
+                      f"({len(sc.bodies)} capsules) after 1 untimed step"}
+
+
+# ---- arms ------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1108_0786_gb300 import _build, lbm
+    if rank == 0 or world > 1:
+        _build.build()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    sc = workload(args, rank)
+    lat = lbm.from_scenario(sc, precision=args.precision)
+    lat.step(args.warmup)
+    lat.sync()
+    with ClockSampler(local) as clk:
+        ms = timed_steps(lat, args.steps, world, device)
+    clocks = clk.summary()
+    value = sc.cells * args.steps * world / (ms / 1e3) / 1e6
+    # dominant kernel: per-launch durations with CUDA events on the launching stream
+    kms = lat.time_kernels(50)
+    bpc = lat.bytes_per_cell
+    peak, peak_kind = hbm_peak()
+    achieved = bpc * sc.cells / (kms["stream_collide"] / 1e3) / 1e9
+    traffic = recorded_traffic(sc.cells)
+    launches = lat.kernels_per_step * args.steps
+    lat.close()
+    torch.cuda.empty_cache()
+    e2e = e2e_run(sc, args, world, device)
+    torch.cuda.empty_cache()
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f16": "f16", "bf16": "bf16", "f64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"capsule swarm {sc.nx}x{sc.ny}x{sc.nz} periodic D3Q19, tau=1, "
+                               f"8 three-capsule swimmers (r=4, l=8), {args.precision} deviation storage",
+                   "cells": sc.cells, "bodies": len(sc.bodies), "springs": len(sc.springs),
+                   "precision": args.precision, "replicas": world,
+                   "l2": "inputs larger than L2: %.2f GB of populations per step vs 129 MB L2"
+                         % (bpc * sc.cells / 1e9)},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": "stream_collide", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "traffic": None if traffic is None else round(traffic),
+                     "algorithmic_bytes": bpc * sc.cells,
+                     "launch_ms": round(kms["stream_collide"], 4),
+                     "per_kernel_ms": {k: round(v, 4) for k, v in kms.items()}},
+        "clocks": clocks,
+    }
+    if not args.no_variants and rank == 0 and world == 1:
+        line["storage_variants"] = variant_runs(workload(args, 0), args, 200)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step is one coupled FP64 step of
+    a 128 x 64 x 64 crop of the workload holding one three-capsule swimmer."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1108_0786_gb300 import workloads as wl
+    sc = wl.capsule_swarm(nx=128, ny=64, nz=64, swimmers=1, seed=1108, steps=args.steps)
+    o = oracle.from_scenario(sc)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = sc.cells * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / max(args.steps, 1), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "capsule swarm crop 128x64x64 periodic, 1 three-capsule swimmer "
+                                   "(r=4, l=8), FP64 CPU oracle"},
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "every step: one coupled FP64 step of a 128x64x64 crop of the "
+                                       "capsule-swarm workload with one swimmer"},
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

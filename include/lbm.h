@@ -77,6 +77,7 @@ extern "C" {
 #define LBM_PREC_F64  0
 #define LBM_PREC_F32  1
 #define LBM_PREC_F16  2   /* deviations scaled by 2^LBM_F16_SCALE_EXP */
+#define LBM_F16_SCALE_EXP 10
 #define LBM_PREC_BF16 3
 
 #define LBM_OPT_NO_FLUID  1   /* bodies only: no mapping, no hydrodynamic force */
@@ -94,12 +95,13 @@ extern "C" {
 #define LBM_MAX_BODY_STEP  0.5   /* largest displacement of a body per step */
 
 /* kernel slots reported by lbm_time_kernels */
-#define LBM_KERNEL_REMAP          0
-#define LBM_KERNEL_STREAM_COLLIDE 1
-#define LBM_KERNEL_LINKS          2
-#define LBM_KERNEL_FORCE          3
-#define LBM_KERNEL_INTEGRATE      4
-#define LBM_NUM_KERNELS           5
+#define LBM_KERNEL_REMAP          0   /* map bodies to the lattice */
+#define LBM_KERNEL_STREAM_COLLIDE 1   /* bulk pull + LBGK over all cells */
+#define LBM_KERNEL_BOUNDARY       2   /* refill / bounce-back cells near bodies and walls */
+#define LBM_KERNEL_LINKS          3   /* per-body link lists */
+#define LBM_KERNEL_FORCE          4   /* momentum exchange */
+#define LBM_KERNEL_INTEGRATE      5   /* drive, springs, rigid-body step */
+#define LBM_NUM_KERNELS           6
 
 typedef struct lbm_s lbm_t;
 
@@ -211,6 +213,11 @@ int lbm_load(lbm_t *h, const char *path);
  * in milliseconds of each kernel slot (LBM_KERNEL_*) to ms_out[slots]; a
  * slot that does not run is reported as 0.  The state advances by n steps. */
 int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots);
+
+/* Launch shape of the bulk stream-collide kernel: cells_per_thread
+ * consecutive x cells per thread (1, 2, 4; 8 for 16-bit storage; nx must be
+ * a multiple), or 0 for the default.  Only before the first step. */
+int lbm_tune(lbm_t *h, int cells_per_thread);
 
 /* Kernel launches one step makes (for launch accounting). */
 int lbm_kernels_per_step(lbm_t *h);

@@ -102,6 +102,22 @@ def equilibrium(rho, u):
     return out
 
 
+def from_scenario(sc, options=0):
+    """An Oracle holding the domain, bodies, springs and drive terms of a
+    seeded scenario (any object with the fields of ``workloads.Scenario``)."""
+    import math
+    o = Oracle(sc.nx, sc.ny, sc.nz, sc.tau, sc.bc, sc.g, options)
+    for b in sc.bodies:
+        o.add_body(b.shape, b.radius, b.length, b.mass, b.pos, b.orient)
+    for s in sc.springs:
+        o.add_spring(s.i, s.j, s.k, s.rest, s.damping)
+    for d in sc.drives:
+        t = o.set_drive(d.body, d.amp, d.freq, d.phase)
+        if math.isfinite(d.t_off):
+            o.set_drive_window(t, d.t_off)
+    return o
+
+
 class OracleError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"oracle error {code}: {msg}")

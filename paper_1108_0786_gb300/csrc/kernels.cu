@@ -54,10 +54,33 @@ __global__ void init_flags_kernel(const Domain d, uint8_t *f0, uint8_t *f1, uint
 // Remap: block row blockIdx.y = body b; the threads cover the cube of side
 // 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) at state n.  Every covered
 // cell gets its epoch-n flags from the geometry of all bodies and the
-// epoch-(n-1) buffer; overlapping cubes write identical values.
-__global__ void remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
+// epoch-(n-1) buffer; overlapping cubes write identical values.  Bodies are
+// culled with integer boxes first, so the FP64 inside test runs only for
+// the bodies whose box holds the cell.
+constexpr int REMAP_THREADS = 256;
+
+__global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
     const Domain d = dv.dom;
     const int b = blockIdx.y;
+    __shared__ int box[LBM_MAX_BODIES_DEV][6];     // wrapped lower corner, width per axis
+    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
+    for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) {
+        const BodyState sk = sp.body_cur[k];
+        const BodyProps pk = dv.props[k];
+        const double reach = pk.r + 0.5 * pk.l;
+        for (int a = 0; a < 3; ++a) {
+            int lo = (int)floor(sk.X[a] - reach), hi = (int)floor(sk.X[a] + reach);
+            int width = hi - lo + 1;
+            if (per[a]) {
+                lo %= n3[a];
+                if (lo < 0) lo += n3[a];
+                if (width > n3[a]) width = n3[a];
+            }
+            box[k][a] = lo;
+            box[k][3 + a] = width;
+        }
+    }
+    __syncthreads();
     const BodyProps pb = dv.props[b];
     const BodyState sb = sp.body_cur[b];
     const int half = pb.E + REMAP_MARGIN;
@@ -68,7 +91,6 @@ __global__ void remap_kernel(const Device dv, const StepPtrs sp, int init_mode) 
         // a body may not cross a wall (its extent beyond the wall planes)
         double R[3][3];
         quat_to_matrix(sb.q, R);
-        const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
         for (int k = 0; k < 3; ++k) {
             if (per[k]) continue;
             const double ext = pb.r + (pb.shape == 1 ? 0.5 * pb.l * fabs(R[k][0]) : 0.0);
@@ -84,16 +106,18 @@ __global__ void remap_kernel(const Device dv, const StepPtrs sp, int init_mode) 
     if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else if (y < 0 || y >= d.ny) return;
     if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else if (z < 0 || z >= d.nz) return;
     const long long c = ((long long)z * d.ny + y) * d.nx + x;
+    const int p3[3] = {x, y, z};
 
     int id = NO_BODY;
     for (int k = 0; k < dv.nb; ++k) {
-        const BodyState sk = sp.body_cur[k];
-        const BodyProps pk = dv.props[k];
-        double o[3];
-        offset_from(d, sk, x, y, z, o);
-        const double reach = pk.r + 0.5 * pk.l;
-        if (fabs(o[0]) > reach || fabs(o[1]) > reach || fabs(o[2]) > reach) continue;
-        if (!cell_inside(d, pk, sk, x, y, z)) continue;
+        bool in = true;
+        for (int a = 0; a < 3 && in; ++a) {
+            int o = p3[a] - box[k][a];
+            if (per[a] && o < 0) o += n3[a];
+            in = o >= 0 && o < box[k][3 + a];
+        }
+        if (!in) continue;
+        if (!cell_inside(d, dv.props[k], sp.body_cur[k], x, y, z)) continue;
         if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
         id = k;
     }
@@ -216,14 +240,17 @@ template <> __device__ inline double load_dev<__nv_bfloat16>(const __nv_bfloat16
 constexpr int FORCE_THREADS = 256;
 constexpr int MAX_SEGMENTS = 1024;
 
-// Momentum exchange (Eq. hydroF): one block per body sums
+// Momentum exchange (Eq. hydroF): blocks (k, b), k < FORCE_BLOCKS, split the
+// links of body b into contiguous chunks and sum
 //   F = sum e_a [2 f~_a(x_f) + 6 w_a rho(x_f) e_-a . u_w(x_f + e_a)],
 //   T = sum (x_f + e_a / 2 - X) x F_link
-// over the body's links with f~ of step n (dst) and the state of step n.
+// with f~ of step n (dst) and the body state of step n, in FP64; each block
+// reduces with warp shuffles in a fixed order and writes its partial sums,
+// which the integrate kernel adds in block order (deterministic).
 template <typename T>
 __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, const StepPtrs sp) {
     const Domain d = dv.dom;
-    const int b = blockIdx.x;
+    const int b = blockIdx.y, kb = blockIdx.x;
     const BodyProps pb = dv.props[b];
     const BodyState sb = sp.body_cur[b];
     const int side = 2 * (pb.E + 1) + 1;
@@ -244,8 +271,10 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
     }
     __syncthreads();
     const int total = prefix[side];
+    const int chunk = (total + FORCE_BLOCKS - 1) / FORCE_BLOCKS;
+    const int j0 = kb * chunk, j1 = min(total, j0 + chunk);
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int j = threadIdx.x; j < total; j += FORCE_THREADS) {
+    for (int j = j0 + threadIdx.x; j < j1; j += FORCE_THREADS) {
         int lo = 0, hi = side - 1;       // segment k with prefix[k] <= j < prefix[k+1]
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -254,9 +283,15 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
         const Link lk = links[(long long)lo * dv.seg_cap + (j - prefix[lo])];
         const long long c = lk.cell;
         const int a = (int)lk.dir;
-        double rho = 1.0;
-        for (int q = 0; q < Q; ++q) rho += load_dev<T>(pop + q * C + c, s);
-        const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
+        double rho = 1.0, g_a = 0.0;
+        if constexpr (sizeof(T) == 8) {
+            for (int q = 0; q < Q; ++q) rho += load_dev<T>(pop + q * C + c, s);
+        } else {
+            float drho = 0.0f;          // FP32 sum of the stored deviations
+            for (int q = 0; q < Q; ++q) drho += (float)load_dev<T>(pop + q * C + c, s);
+            rho += (double)drho;
+        }
+        g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
         const int x = (int)(c % d.nx), y = (int)((c / d.nx) % d.ny),
                   z = (int)(c / ((long long)d.nx * d.ny));
         double u[3];
@@ -271,7 +306,6 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
         acc[4] += o[2] * fl[0] - o[0] * fl[2];
         acc[5] += o[0] * fl[1] - o[1] * fl[0];
     }
-    // fixed-order reduction: warp shuffles, then warp 0 over the warp sums
     __shared__ double part[FORCE_THREADS / 32][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -288,57 +322,58 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
             double v = lane < FORCE_THREADS / 32 ? part[lane][i] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) dv.fh[b * 6 + i] = v;
+            if (lane == 0) dv.fpart[((long long)b * FORCE_BLOCKS + kb) * 6 + i] = v;
         }
     }
 }
 
-// Rigid-body step (Algorithm 1, Eq. totalFSwimmer): thread b sums the
-// hydrodynamic force, g times the volume, its drive terms in order and its
-// springs in order, then advances by semi-implicit Euler (dt = 1).
-__global__ void integrate_kernel(const Device dv, const StepPtrs sp) {
+// Rigid-body step (Algorithm 1, Eq. totalFSwimmer): thread b adds the
+// momentum-exchange partial sums in block order, g times the volume, its
+// drive terms in term order and its springs in spring order, then advances
+// by semi-implicit Euler (dt = 1) in FP64.
+__global__ void __launch_bounds__(256) integrate_kernel(const Device dv, const StepPtrs sp, int with_fluid) {
     const int b = threadIdx.x;
     const long long tstep = *dv.t_dev;
     if (b < dv.nb) {
         const double t = (double)tstep;
         const BodyProps pb = dv.props[b];
-        BodyState s = sp.body_cur[b];
+        const BodyState s = sp.body_cur[b];
         double R[3][3];
         quat_to_matrix(s.q, R);
         double F[3], Tq[3];
-        for (int i = 0; i < 3; ++i) {
-            F[i] = dv.fh[b * 6 + i] + dv.g[i] * pb.volume;
-            Tq[i] = dv.fh[b * 6 + 3 + i];
+        for (int i = 0; i < 6; ++i) {
+            double v = 0.0;
+            if (with_fluid)
+                for (int k = 0; k < FORCE_BLOCKS; ++k) v += dv.fpart[((long long)b * FORCE_BLOCKS + k) * 6 + i];
+            dv.fh[b * 6 + i] = v;
+            if (i < 3) F[i] = v + dv.g[i] * pb.volume; else Tq[i - 3] = v;
         }
-        for (int k = 0; k < dv.nd; ++k) {
+        for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k) {
             const DriveTerm dt = dv.drives[k];
-            if (dt.body != b) continue;
-            const double omega = 2.0 * M_PI * dt.freq;
-            if (t < dt.phase / omega || t >= dt.t_off) continue;
-            const double f = dt.amp * sin(omega * t - dt.phase);
+            if (t < dt.t_on || t >= dt.t_off) continue;
+            const double f = dt.amp * sin(dt.omega * t - dt.phase);
             for (int i = 0; i < 3; ++i) F[i] += f * R[i][0];
         }
-        for (int k = 0; k < dv.ns; ++k) {
-            const Spring sp_ = dv.springs[k];
-            if (sp_.i != b && sp_.j != b) continue;
+        for (int kk = pb.spring_first; kk < pb.spring_first + pb.spring_count; ++kk) {
+            const Spring sp_ = dv.springs[dv.spring_list[kk]];
             const BodyState si = sp.body_cur[sp_.i], sj = sp.body_cur[sp_.j];
             const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
             const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+            const double inv_len = len > 0 ? 1.0 / len : 0.0;
             for (int i = 0; i < 3; ++i) {
-                const double dir = len > 0 ? dd[i] / len : 0.0;
-                const double fi = -sp_.k * (len - sp_.rest) * dir - sp_.gamma * (si.V[i] - sj.V[i]);
+                const double fi = -sp_.k * (len - sp_.rest) * (dd[i] * inv_len) - sp_.gamma * (si.V[i] - sj.V[i]);
                 F[i] += sp_.i == b ? fi : -fi;
             }
         }
         BodyState n = s;
         for (int i = 0; i < 3; ++i) {
-            n.V[i] = s.V[i] + F[i] / pb.m;
+            n.V[i] = s.V[i] + F[i] * pb.inv_m;
             n.X[i] = s.X[i] + n.V[i];
         }
         // Omega += R diag(1/I) R^T T
         double Tb[3], dW[3];
-        for (int i = 0; i < 3; ++i) Tb[i] = R[0][i] * Tq[0] + R[1][i] * Tq[1] + R[2][i] * Tq[2];
-        for (int i = 0; i < 3; ++i) Tb[i] /= pb.inertia[i];
+        for (int i = 0; i < 3; ++i)
+            Tb[i] = (R[0][i] * Tq[0] + R[1][i] * Tq[1] + R[2][i] * Tq[2]) * pb.inv_inertia[i];
         for (int i = 0; i < 3; ++i) dW[i] = R[i][0] * Tb[0] + R[i][1] * Tb[1] + R[i][2] * Tb[2];
         for (int i = 0; i < 3; ++i) n.W[i] = s.W[i] + dW[i];
         // q += 1/2 (0, Omega) (x) q, renormalised
@@ -348,8 +383,8 @@ __global__ void integrate_kernel(const Device dv, const StepPtrs sp) {
         double q4[4] = {w - 0.5 * (n.W[0] * v0 + n.W[1] * v1 + n.W[2] * v2),
                         v0 + 0.5 * (w * n.W[0] + c0), v1 + 0.5 * (w * n.W[1] + c1),
                         v2 + 0.5 * (w * n.W[2] + c2)};
-        const double nn = sqrt(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
-        for (int i = 0; i < 4; ++i) n.q[i] = q4[i] / nn;
+        const double inv_nn = rsqrt(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
+        for (int i = 0; i < 4; ++i) n.q[i] = q4[i] * inv_nn;
         bool finite = true;
         for (int i = 0; i < 3; ++i)
             finite = finite && isfinite(n.X[i]) && isfinite(n.V[i]) && isfinite(n.W[i]);
@@ -428,8 +463,8 @@ void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8
 
 void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s) {
     const long long side = dv.remap_side;
-    const unsigned bx = blocks_for(side * side * side, 256);
-    remap_kernel<<<dim3(bx, dv.nb), 256, 0, s>>>(dv, sp, init_mode);
+    const unsigned bx = blocks_for(side * side * side, REMAP_THREADS);
+    remap_kernel<<<dim3(bx, dv.nb), REMAP_THREADS, 0, s>>>(dv, sp, init_mode);
 }
 
 void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
@@ -437,16 +472,17 @@ void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
 }
 
 void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    const dim3 grid(FORCE_BLOCKS, dv.nb);
     switch (dv.precision) {
-    case 0: force_kernel<double><<<dv.nb, FORCE_THREADS, 0, s>>>(dv, sp); break;
-    case 1: force_kernel<float><<<dv.nb, FORCE_THREADS, 0, s>>>(dv, sp); break;
-    case 2: force_kernel<__half><<<dv.nb, FORCE_THREADS, 0, s>>>(dv, sp); break;
-    default: force_kernel<__nv_bfloat16><<<dv.nb, FORCE_THREADS, 0, s>>>(dv, sp); break;
+    case 0: force_kernel<double><<<grid, FORCE_THREADS, 0, s>>>(dv, sp); break;
+    case 1: force_kernel<float><<<grid, FORCE_THREADS, 0, s>>>(dv, sp); break;
+    case 2: force_kernel<__half><<<grid, FORCE_THREADS, 0, s>>>(dv, sp); break;
+    default: force_kernel<__nv_bfloat16><<<grid, FORCE_THREADS, 0, s>>>(dv, sp); break;
     }
 }
 
-void launch_integrate(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
-    integrate_kernel<<<1, 256, 0, s>>>(dv, sp);
+void launch_integrate(const Device &dv, const StepPtrs &sp, int with_fluid, cudaStream_t s) {
+    integrate_kernel<<<1, 256, 0, s>>>(dv, sp, with_fluid);
 }
 
 template <typename O>

@@ -61,12 +61,17 @@ constexpr int ST_OVERLAP = 1, ST_OUTSIDE = 2, ST_NAN = 4, ST_UNSTABLE = 8, ST_LI
 // whose flags can differ from the static value in either epoch buffer
 constexpr int REMAP_MARGIN = 4;
 constexpr double MAX_STEP = 0.5;
+constexpr int FORCE_BLOCKS = 8;     // blocks per body in the momentum-exchange sum
+constexpr int LBM_MAX_BODIES_DEV = 254;
 
 struct BodyProps {
     int shape;          // 0 sphere, 1 capsule
     int E;              // ceil(r + l/2) + 1: half-width of the box that holds every solid cell
     double r, l, m, volume;
     double inertia[3];      // body-frame principal moments of inertia
+    double inv_m, inv_inertia[3];
+    int drive_first, drive_count;   // this body's drive terms, in term order
+    int spring_first, spring_count; // this body's springs, in spring order (per-body list)
 };
 
 struct BodyState {      // 13 doubles, the layout of lbm_get_bodies
@@ -81,6 +86,7 @@ struct Spring {
 struct DriveTerm {
     int body;
     double amp, freq, phase, t_off;
+    double omega, t_on;     // 2 pi freq and phase / omega
 };
 
 struct Link {
@@ -92,6 +98,7 @@ struct Domain {
     int nx, ny, nz;
     int px, py, pz;     // periodic flags
     long long C;
+    double inx, iny, inz;   // 1 / n per axis
 };
 
 __host__ __device__ inline int wrap_axis(int i, int n) {
@@ -99,8 +106,10 @@ __host__ __device__ inline int wrap_axis(int i, int n) {
     return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
-__device__ inline double min_image(double d, int n, int periodic) {
-    return periodic ? d - n * rint(d / n) : d;
+// periodic minimum image d - n k with k the integer nearest to d / n
+// (a multiply and a floor: FP64 division is slow on this part)
+__device__ inline double min_image(double d, int n, double inv_n, int periodic) {
+    return periodic ? d - n * floor(d * inv_n + 0.5) : d;
 }
 
 __device__ inline void quat_to_matrix(const double q[4], double R[3][3]) {
@@ -113,9 +122,9 @@ __device__ inline void quat_to_matrix(const double q[4], double R[3][3]) {
 // offset of lattice point p from the body centre (periodic minimum image)
 __device__ inline void offset_from(const Domain &d, const BodyState &b, double px, double py,
                                    double pz, double o[3]) {
-    o[0] = min_image(px - b.X[0], d.nx, d.px);
-    o[1] = min_image(py - b.X[1], d.ny, d.py);
-    o[2] = min_image(pz - b.X[2], d.nz, d.pz);
+    o[0] = min_image(px - b.X[0], d.nx, d.inx, d.px);
+    o[1] = min_image(py - b.X[1], d.ny, d.iny, d.py);
+    o[2] = min_image(pz - b.X[2], d.nz, d.inz, d.pz);
 }
 
 // velocity of the body surface at lattice point p: V + Omega x (p - X)
@@ -143,6 +152,7 @@ struct StepPtrs {
 struct Device {
     Domain dom;
     int precision;          // LBM_PREC_*
+    int vec;                // cells per thread of the bulk stream-collide kernel
     int nb, ns, nd;
     double tau, omega, g[3];
     int forced;
@@ -150,7 +160,9 @@ struct Device {
     const BodyProps *props;
     const Spring *springs;
     const DriveTerm *drives;
+    const int *spring_list; // per-body spring indices (BodyProps::spring_first/count)
     double *fh;             // [nb][6] force, torque of the last step
+    double *fpart;          // [nb][FORCE_BLOCKS][6] per-block partial sums of the force kernel
     Link *links;            // [nb][link_side][seg_cap]
     int *seg_count;         // [nb][link_side]
     int link_side, seg_cap, remap_side;
@@ -166,12 +178,15 @@ void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8
                        uint8_t *bid1, cudaStream_t s);
 void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s);
 void launch_stream_collide(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+void launch_boundary_fix(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+bool needs_boundary_fix(const Device &dv);
+bool valid_vector_width(const Device &dv, int v);
+int default_vector_width(const Device &dv);
 void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s);
-void launch_integrate(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+void launch_integrate(const Device &dv, const StepPtrs &sp, int with_fluid, cudaStream_t s);
 void launch_export(const Device &dv, const void *pop, const uint8_t *flags, const uint8_t *bid,
                    int what, int mask_solid, void *out, int dtype, cudaStream_t s);
 void launch_import_pop(const Device &dv, void *pop, const double *in, cudaStream_t s);
-int stream_collide_vector_width(const Device &dv);
 
 }  // namespace lbm

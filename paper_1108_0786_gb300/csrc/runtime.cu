@@ -32,6 +32,7 @@ struct lbm_s {
     std::vector<Spring> springs;
     std::vector<DriveTerm> drives;
     int hist_cap = 0;
+    int tune_vec = 0;
     // device
     bool ready = false, graphs_ready = false;
     int device = 0;
@@ -124,22 +125,38 @@ lbm::StepPtrs step_ptrs(lbm_t *h, int p) {
     return sp;
 }
 
-// the kernels of one step of parity p, in Algorithm 2's order
-void enqueue_step(lbm_t *h, int p, cudaStream_t s) {
+// the kernels of one step of parity p, in Algorithm 2's order; `ev`
+// (optional) brackets each kernel slot with a pair of events
+void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bool *ran = nullptr) {
     const lbm::StepPtrs sp = step_ptrs(h, p);
-    const bool bodies = nb(h) > 0;
-    if (bodies && fluid(h)) lbm::launch_remap(h->dv, sp, 0, s);
-    if (fluid(h)) lbm::launch_stream_collide(h->dv, sp, s);
-    if (bodies && fluid(h)) {
-        lbm::launch_links(h->dv, sp, s);
-        lbm::launch_force(h->dv, sp, s);
+    const bool bodies = nb(h) > 0, fl = fluid(h);
+    auto run = [&](int slot, auto &&fn) {
+        if (ev) cudaEventRecord(ev[2 * slot], s);
+        fn();
+        if (ev) cudaEventRecord(ev[2 * slot + 1], s);
+        if (ran) ran[slot] = true;
+    };
+    if (bodies && fl) run(LBM_KERNEL_REMAP, [&] { lbm::launch_remap(h->dv, sp, 0, s); });
+    if (fl) run(LBM_KERNEL_STREAM_COLLIDE, [&] { lbm::launch_stream_collide(h->dv, sp, s); });
+    if (fl && lbm::needs_boundary_fix(h->dv))
+        run(LBM_KERNEL_BOUNDARY, [&] { lbm::launch_boundary_fix(h->dv, sp, s); });
+    if (bodies && fl) {
+        run(LBM_KERNEL_LINKS, [&] { lbm::launch_links(h->dv, sp, s); });
+        run(LBM_KERNEL_FORCE, [&] { lbm::launch_force(h->dv, sp, s); });
     }
-    if (bodies) lbm::launch_integrate(h->dv, sp, s);
+    if (bodies) run(LBM_KERNEL_INTEGRATE, [&] { lbm::launch_integrate(h->dv, sp, fl ? 1 : 0, s); });
 }
 
 int kernels_per_step(const lbm_t *h) {
-    const bool bodies = nb(h) > 0;
-    return (bodies && fluid(h) ? 1 : 0) + (fluid(h) ? 1 : 0) + (bodies && fluid(h) ? 2 : 0) + (bodies ? 1 : 0);
+    const bool bodies = nb(h) > 0, fl = fluid(h);
+    const bool walls = (h->bc & 7) != 7;
+    int n = 0;
+    if (bodies && fl) n += 1;                               // remap
+    if (fl) n += 1;                                         // bulk stream-collide
+    if (fl) n += (bodies ? 1 : 0) + (walls ? 1 : 0);        // boundary cells
+    if (bodies && fl) n += 2;                               // links, force
+    if (bodies) n += 1;                                     // integrate
+    return n;
 }
 
 // flags of the epoch before the first step: the mapping of state 0
@@ -172,7 +189,8 @@ int ensure_device(lbm_t *h) {
     int emax = 0;
     for (const auto &p : h->props) emax = std::max(emax, p.E);
     lbm::Device &dv = h->dv;
-    dv.dom = lbm::Domain{h->nx, h->ny, h->nz, (h->bc & 1) ? 1 : 0, (h->bc & 2) ? 1 : 0, (h->bc & 4) ? 1 : 0, C};
+    dv.dom = lbm::Domain{h->nx, h->ny, h->nz, (h->bc & 1) ? 1 : 0, (h->bc & 2) ? 1 : 0, (h->bc & 4) ? 1 : 0, C,
+                         1.0 / h->nx, 1.0 / h->ny, 1.0 / h->nz};
     dv.precision = h->precision;
     dv.nb = B;
     dv.ns = (int)h->springs.size();
@@ -187,6 +205,31 @@ int ensure_device(lbm_t *h) {
     dv.link_side = 2 * (emax + 1) + 1;
     dv.seg_cap = dv.link_side * dv.link_side * 18;
     dv.hist_cap = h->hist_cap;
+    dv.vec = h->tune_vec ? h->tune_vec : lbm::default_vector_width(dv);
+
+    // per-body reciprocals and term lists (drive terms and springs keep
+    // their creation order within a body)
+    std::vector<BodyProps> props_h = h->props;
+    std::vector<DriveTerm> drives_h;
+    std::vector<int> spring_list;
+    for (int b = 0; b < B; ++b) {
+        BodyProps &p = props_h[b];
+        p.inv_m = 1.0 / p.m;
+        for (int i = 0; i < 3; ++i) p.inv_inertia[i] = 1.0 / p.inertia[i];
+        p.drive_first = (int)drives_h.size();
+        for (const auto &d : h->drives)
+            if (d.body == b) {
+                DriveTerm t = d;
+                t.omega = 2.0 * M_PI * d.freq;
+                t.t_on = d.phase / t.omega;
+                drives_h.push_back(t);
+            }
+        p.drive_count = (int)drives_h.size() - p.drive_first;
+        p.spring_first = (int)spring_list.size();
+        for (size_t k = 0; k < h->springs.size(); ++k)
+            if (h->springs[k].i == b || h->springs[k].j == b) spring_list.push_back((int)k);
+        p.spring_count = (int)spring_list.size() - p.spring_first;
+    }
 
     for (int i = 0; i < 2; ++i) {
         if ((rc = alloc_into(h, &h->pop[i], es * lbm::Q * C))) return rc;
@@ -199,6 +242,10 @@ int ensure_device(lbm_t *h) {
     if ((rc = alloc_into(h, &springs, sizeof(Spring) * std::max<size_t>(h->springs.size(), 1)))) return rc;
     if ((rc = alloc_into(h, &drives, sizeof(DriveTerm) * std::max<size_t>(h->drives.size(), 1)))) return rc;
     if ((rc = alloc_into(h, &dv.fh, sizeof(double) * 6 * std::max(B, 1)))) return rc;
+    if ((rc = alloc_into(h, &dv.fpart, sizeof(double) * 6 * lbm::FORCE_BLOCKS * std::max(B, 1)))) return rc;
+    int *slist;
+    if ((rc = alloc_into(h, &slist, sizeof(int) * std::max<size_t>(spring_list.size(), 1)))) return rc;
+    dv.spring_list = slist;
     const size_t nlinks = (size_t)std::max(B, 1) * dv.link_side * dv.seg_cap;
     if ((rc = alloc_into(h, &dv.links, sizeof(lbm::Link) * (B > 0 && fluid(h) ? nlinks : 1)))) return rc;
     if ((rc = alloc_into(h, &dv.seg_count, sizeof(int) * std::max(B, 1) * dv.link_side))) return rc;
@@ -216,16 +263,21 @@ int ensure_device(lbm_t *h) {
     CK(cudaMemsetAsync(h->pop[0], 0, es * lbm::Q * C, s));   // deviation 0: fluid at rest
     CK(cudaMemsetAsync(h->pop[1], 0, es * lbm::Q * C, s));
     CK(cudaMemsetAsync(dv.fh, 0, sizeof(double) * 6 * std::max(B, 1), s));
+    CK(cudaMemsetAsync(dv.fpart, 0, sizeof(double) * 6 * lbm::FORCE_BLOCKS * std::max(B, 1), s));
+    if (!spring_list.empty())
+        CK(cudaMemcpyAsync(slist, spring_list.data(), sizeof(int) * spring_list.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dv.seg_count, 0, sizeof(int) * std::max(B, 1) * dv.link_side, s));
     const int st[4] = {0, 0, 1, 0};           // status, pad, changed[0] = 1, changed[1] = 0
     CK(cudaMemcpyAsync(dv.status, st, sizeof st, cudaMemcpyHostToDevice, s));
     const long long t0 = 0;
     CK(cudaMemcpyAsync(dv.t_dev, &t0, sizeof t0, cudaMemcpyHostToDevice, s));
-    if (B) CK(cudaMemcpyAsync(props, h->props.data(), sizeof(BodyProps) * B, cudaMemcpyHostToDevice, s));
+    if (B) CK(cudaMemcpyAsync(props, props_h.data(), sizeof(BodyProps) * B, cudaMemcpyHostToDevice, s));
     if (!h->springs.empty())
         CK(cudaMemcpyAsync(springs, h->springs.data(), sizeof(Spring) * h->springs.size(), cudaMemcpyHostToDevice, s));
-    if (!h->drives.empty())
-        CK(cudaMemcpyAsync(drives, h->drives.data(), sizeof(DriveTerm) * h->drives.size(), cudaMemcpyHostToDevice, s));
+    if (!drives_h.empty())
+        CK(cudaMemcpyAsync(drives, drives_h.data(), sizeof(DriveTerm) * drives_h.size(), cudaMemcpyHostToDevice, s));
+    // the staging vectors above go out of scope: finish the copies first
+    CK(cudaStreamSynchronize(s));
     if ((rc = upload_bodies(h))) return rc;
     if ((rc = init_flags(h))) return rc;
     CK(cudaStreamSynchronize(s));
@@ -393,7 +445,7 @@ int lbm_set_drive(lbm_t *h, int body, double amp, double freq, double phase) {
     if (h->ready) return fail(h, LBM_E_STATE, "drives must be added before the first step");
     if (body < 0 || body >= nb(h) || !(freq > 0) || !(phase >= 0) || !std::isfinite(amp))
         return fail(h, LBM_E_ARG, "bad drive");
-    h->drives.push_back(DriveTerm{body, amp, freq, phase, INFINITY});
+    h->drives.push_back(DriveTerm{body, amp, freq, phase, INFINITY, 0.0, 0.0});
     return (int)h->drives.size() - 1;
 }
 
@@ -659,30 +711,14 @@ int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots) {
     int rc = ensure_device(h);
     if (rc) return rc;
     if ((rc = sync_and_check(h))) return rc;
-    double total[LBM_NUM_KERNELS] = {0, 0, 0, 0, 0};
+    double total[LBM_NUM_KERNELS] = {0, 0, 0, 0, 0, 0};
     cudaEvent_t ev[2 * LBM_NUM_KERNELS];
     for (auto &e : ev) CK(cudaEventCreate(&e));
-    const bool bodies = nb(h) > 0, fl = fluid(h);
-    cudaStream_t s = h->stream;
     for (int it = 0; it < n; ++it) {
-        const int p = (int)(h->steps & 1);
-        const lbm::StepPtrs sp = step_ptrs(h, p);
-        bool ran[LBM_NUM_KERNELS] = {false, false, false, false, false};
-        auto run = [&](int slot, auto &&fn) {
-            cudaEventRecord(ev[2 * slot], s);
-            fn();
-            cudaEventRecord(ev[2 * slot + 1], s);
-            ran[slot] = true;
-        };
-        if (bodies && fl) run(LBM_KERNEL_REMAP, [&] { lbm::launch_remap(h->dv, sp, 0, s); });
-        if (fl) run(LBM_KERNEL_STREAM_COLLIDE, [&] { lbm::launch_stream_collide(h->dv, sp, s); });
-        if (bodies && fl) {
-            run(LBM_KERNEL_LINKS, [&] { lbm::launch_links(h->dv, sp, s); });
-            run(LBM_KERNEL_FORCE, [&] { lbm::launch_force(h->dv, sp, s); });
-        }
-        if (bodies) run(LBM_KERNEL_INTEGRATE, [&] { lbm::launch_integrate(h->dv, sp, s); });
+        bool ran[LBM_NUM_KERNELS] = {false, false, false, false, false, false};
+        enqueue_step(h, (int)(h->steps & 1), h->stream, ev, ran);
         h->steps += 1;
-        CK(cudaStreamSynchronize(s));
+        CK(cudaStreamSynchronize(h->stream));
         for (int k = 0; k < LBM_NUM_KERNELS; ++k) {
             if (!ran[k]) continue;
             float ms = 0;
@@ -691,8 +727,23 @@ int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots) {
         }
     }
     for (auto &e : ev) cudaEventDestroy(e);
-    for (int k = 0; k < slots && k < LBM_NUM_KERNELS; ++k) ms_out[k] = n ? total[k] / n : 0.0;
+    for (int k = 0; k < slots; ++k) ms_out[k] = (k < LBM_NUM_KERNELS && n) ? total[k] / n : 0.0;
     return check_status(h);
+}
+
+int lbm_tune(lbm_t *h, int cells_per_thread) {
+    if (!h) return LBM_E_ARG;
+    if (h->ready) return fail(h, LBM_E_STATE, "lbm_tune must come before the first step");
+    if (cells_per_thread != 0) {
+        lbm::Device probe{};
+        probe.dom.nx = h->nx;
+        probe.precision = h->precision;
+        if (!lbm::valid_vector_width(probe, cells_per_thread))
+            return fail(h, LBM_E_ARG, "%d cells per thread is not valid for nx = %d and this precision",
+                        cells_per_thread, h->nx);
+    }
+    h->tune_vec = cells_per_thread;
+    return LBM_OK;
 }
 
 int lbm_kernels_per_step(lbm_t *h) { return h ? kernels_per_step(h) : LBM_E_ARG; }

@@ -1,35 +1,43 @@
 // stream_collide.cu -- the fused D3Q19 stream + bounce-back + refill + LBGK
-// kernel of one coupled step (Eq. 1-4 of the paper and the moving-wall rule
-// and reconstruction of Sec. 2.3).  This kernel moves >99% of the bytes of a
-// step and is bound by HBM bandwidth: per cell it reads 19 populations and a
-// flag byte and writes 19 populations (2 * 19 * sizeof(T) + 1 bytes).
+// update of one coupled step (Eq. 1-4 of the paper, and the moving-wall rule
+// and the reconstruction of uncovered cells of Sec. 2.3).  It moves >99% of
+// the bytes of a step and is bound by HBM bandwidth: per cell it reads 19
+// populations and a flag byte and writes 19 populations
+// (2 * 19 * sizeof(T) + 1 bytes).
 //
-// Pull scheme, two grids (src = step n-1, dst = step n).  For a cell x that
-// is fluid at n:
-//   - fast path (flag byte 0): f_b(x) = f~_b(x - e_b) for all 19 b;
-//   - x was solid at n-1 (uncovered): f_b = f_eq(rho_avg, u_w(x; state n)),
-//     rho_avg the mean density of the D3Q19 neighbours that are fluid in both
-//     epochs (1 if none);
-//   - otherwise, for each b whose source y = x - e_b lies beyond a no-slip
-//     wall: f_b = f~_{-b}(x) (Eq. 4); if y was solid at n-1:
-//     f_b = f~_{-b}(x) + 6 w_b rho(x) e_b . u_w(y; state n-1), rho(x) the
-//     density of x at n-1;
-// then rho, u (Guo: u = (sum e f + g/2) / rho), LBGK relaxation to the
-// second-order equilibrium plus Guo's forcing term, and the store of
-// f~(x, n).  Solid cells store deviation 0.
+// Two kernels write the populations of step n (pull scheme, two grids: src =
+// step n-1, dst = step n):
+//
+//  bulk      every cell: f_b(x) = f~_b(x - e_b) for all 19 b, LBGK relaxation
+//            to the second-order equilibrium with Guo's forcing, store;
+//            solid cells store deviation 0.  No data-dependent branches, so
+//            the kernel stays small and register-light.
+//  boundary  afterwards, only the fluid cells whose flag byte is non-zero
+//            (they lie in the cubes around the bodies or on wall faces)
+//            are recomputed and overwritten:
+//              - x was solid at n-1 (uncovered): f_b = f_eq(rho_avg, u_w(x)),
+//                rho_avg the mean density of the D3Q19 neighbours that are
+//                fluid in both epochs (1 if none), u_w at the state of step n;
+//              - otherwise per b: if the source y = x - e_b lies beyond a
+//                no-slip wall, f_b = f~_{-b}(x) (Eq. 4); if y was solid at
+//                n-1, f_b = f~_{-b}(x) + 6 w_b rho(x) e_b . u_w(y) with rho(x)
+//                the density of x at n-1 and u_w at the state of step n-1;
+//            then the same LBGK collision.
 //
 // Populations are stored as deviations delta = f - w from the rest
-// equilibrium, so that FP32 and 16-bit storage keep the small velocity
-// signal; the collision runs in FP64 for FP64 storage and in FP32 otherwise.
+// equilibrium (16-bit formats: FP16 scaled by 2^10, BF16 unscaled), so the
+// small velocity signal survives FP32 and 16-bit storage; the collision runs
+// in FP64 for FP64 storage and in FP32 otherwise.
 //
-// Memory access: each thread handles V consecutive cells of an x row; every
-// population is fetched as one aligned V-wide vector per thread (coalesced
-// 128-bit loads for V * sizeof(T) = 16), and the +-1 x shift of the pull is
-// completed with a warp shuffle from the neighbouring lane (a scalar load at
-// row and warp ends).  Every population byte is read once and written once.
+// Memory access of the bulk kernel: thread (tx, ty) of block (bx, by, z)
+// handles V consecutive cells of row (y, z); each population is fetched as
+// one aligned V-wide vector, and the +-1 x shift of the pull is completed
+// with a warp shuffle from the neighbouring lane (a scalar load at row and
+// warp ends).  Every population byte is read once and written once.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "lbm_internal.cuh"
@@ -37,9 +45,8 @@
 namespace lbm {
 namespace {
 
-constexpr int SC_THREADS = 128;
-
 template <int BYTES> struct Raw;
+template <> struct Raw<1> { using type = unsigned char; };
 template <> struct Raw<2> { using type = unsigned short; };
 template <> struct Raw<4> { using type = unsigned int; };
 template <> struct Raw<8> { using type = uint2; };
@@ -84,250 +91,317 @@ __device__ __forceinline__ void store_vec(T *p, const T (&in)[V]) {
 }
 
 template <typename T>
-__device__ __forceinline__ T shfl_up1(T v) {
+__device__ __forceinline__ T shfl(T v, int delta, bool up) {
     if constexpr (sizeof(T) == 8) {
         unsigned long long b;
         memcpy(&b, &v, 8);
-        b = __shfl_up_sync(0xffffffffu, b, 1);
+        b = up ? __shfl_up_sync(0xffffffffu, b, delta) : __shfl_down_sync(0xffffffffu, b, delta);
         memcpy(&v, &b, 8);
     } else {
         unsigned int b = 0;
         memcpy(&b, &v, sizeof(T));
-        b = __shfl_up_sync(0xffffffffu, b, 1);
+        b = up ? __shfl_up_sync(0xffffffffu, b, delta) : __shfl_down_sync(0xffffffffu, b, delta);
         memcpy(&v, &b, sizeof(T));
     }
     return v;
 }
 
-template <typename T>
-__device__ __forceinline__ T shfl_down1(T v) {
-    if constexpr (sizeof(T) == 8) {
-        unsigned long long b;
-        memcpy(&b, &v, 8);
-        b = __shfl_down_sync(0xffffffffu, b, 1);
-        memcpy(&v, &b, 8);
-    } else {
-        unsigned int b = 0;
-        memcpy(&b, &v, sizeof(T));
-        b = __shfl_down_sync(0xffffffffu, b, 1);
-        memcpy(&v, &b, sizeof(T));
+// LBGK collision of one cell in place (deviation form):
+//   drho = sum delta, rho = 1 + drho, u = (sum e delta + g/2) / rho,
+//   delta_eq_b = w_b (drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)),
+//   delta~_b = delta_b - (delta_b - delta_eq_b) / tau
+//              + (1 - 1/(2 tau)) w_b (3 (e_b - u) . g + 9 (e_b . u)(e_b . g)).
+template <typename Cd>
+__device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
+    Cd s = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+        s += f[b];
+        if (ex(b)) jx += ex(b) > 0 ? f[b] : -f[b];
+        if (ey(b)) jy += ey(b) > 0 ? f[b] : -f[b];
+        if (ez(b)) jz += ez(b) > 0 ? f[b] : -f[b];
     }
-    return v;
+    const Cd rho = (Cd)1 + s;
+    const Cd inv = (Cd)1 / rho;
+    const Cd gx = (Cd)dv.g[0], gy = (Cd)dv.g[1], gz = (Cd)dv.g[2];
+    const Cd ux = (jx + (Cd)0.5 * gx) * inv, uy = (jy + (Cd)0.5 * gy) * inv, uz = (jz + (Cd)0.5 * gz) * inv;
+    const Cd usq = ux * ux + uy * uy + uz * uz;
+    const Cd om = (Cd)dv.omega;
+    const Cd guo = (Cd)(1.0 - 0.5 * dv.omega);
+    const Cd ug = ux * gx + uy * gy + uz * gz;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+        const Cd w = (Cd)wgt(b);
+        const Cd eu = (Cd)ex(b) * ux + (Cd)ey(b) * uy + (Cd)ez(b) * uz;
+        const Cd deq = w * (s + rho * ((Cd)3 * eu + (Cd)4.5 * eu * eu - (Cd)1.5 * usq));
+        Cd o = f[b] - om * (f[b] - deq);
+        if (dv.forced) {
+            const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
+            o += guo * w * ((Cd)3 * (eg - ug) + (Cd)9 * eu * eg);
+        }
+        f[b] = o;
+    }
 }
 
-template <typename T, int V>
-__global__ void __launch_bounds__(SC_THREADS)
-stream_collide_kernel(const Device dv, const StepPtrs sp) {
+template <typename T, int V, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+bulk_kernel(const Device dv, const StepPtrs sp) {
     using Cd = typename Codec<T>::C;
     const Domain d = dv.dom;
-    const long long C = d.C;
     const int nxq = d.nx / V;
-    const long long nq = C / V;
-    long long q = (long long)blockIdx.x * SC_THREADS + threadIdx.x;
-    const bool active = q < nq;
-    if (!active) q = nq - 1;             // keep the whole warp in the shuffles
+    int xq = blockIdx.x * BX + threadIdx.x;
+    int y = blockIdx.y * BY + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool active = xq < nxq && y < d.ny;
+    xq = min(xq, nxq - 1);              // inactive lanes still join the shuffles
+    y = min(y, d.ny - 1);
     const int lane = threadIdx.x & 31;
-    const int x0 = (int)(q % nxq) * V;
-    const long long row = q / nxq;
-    const int y = (int)(row % d.ny);
-    const int z = (int)(row / d.ny);
+    const int x0 = xq * V;
     const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? d.nz - 1 : z - 1, zp = z == d.nz - 1 ? 0 : z + 1;
-    const long long c0 = row * d.nx + x0;
+    const long long C = d.C;
+    const long long c0 = ((long long)z * d.ny + y) * d.nx + x0;
     const T *__restrict__ src = static_cast<const T *>(sp.src);
     T *__restrict__ dst = static_cast<T *>(sp.dst);
     const float inv_scale = dv.f16_inv_scale, scale = dv.f16_scale;
 
     uint8_t fl[V];
-    {
-        uint8_t raw[V];
-        if constexpr (V == 1) {
-            raw[0] = sp.flags_cur[c0];
-        } else {
-            load_vec<uint8_t, V>(sp.flags_cur + c0, raw);
-        }
-#pragma unroll
-        for (int i = 0; i < V; ++i) fl[i] = raw[i];
-    }
+    load_vec<uint8_t, V>(sp.flags_cur + c0, fl);
 
-    // ---- pull: f_b(x) = f~_b(x - e_b) -----------------------------------
     Cd f[Q][V];
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
         const int ys = ey(b) > 0 ? ym : (ey(b) < 0 ? yp : y);
         const int zs = ez(b) > 0 ? zm : (ez(b) < 0 ? zp : z);
-        const T *plane = src + (long long)b * C + ((long long)zs * d.ny + ys) * d.nx;
+        const T *row = src + (long long)b * C + ((long long)zs * d.ny + ys) * d.nx;
         T A[V];
-        load_vec<T, V>(plane + x0, A);
+        load_vec<T, V>(row + x0, A);
         if (ex(b) == 0) {
 #pragma unroll
             for (int i = 0; i < V; ++i) f[b][i] = Codec<T>::ld(A[i], inv_scale);
-        } else if (ex(b) > 0) {          // source at x - 1
-            T left = shfl_up1(A[V - 1]);
-            if (lane == 0 || x0 == 0) left = plane[x0 == 0 ? d.nx - 1 : x0 - 1];
+        } else if (ex(b) > 0) {          // pull from x - 1
+            T left = shfl(A[V - 1], 1, true);
+            if (lane == 0 || x0 == 0) left = row[x0 == 0 ? d.nx - 1 : x0 - 1];
             f[b][0] = Codec<T>::ld(left, inv_scale);
 #pragma unroll
             for (int i = 1; i < V; ++i) f[b][i] = Codec<T>::ld(A[i - 1], inv_scale);
-        } else {                          // source at x + 1
-            T right = shfl_down1(A[0]);
-            if (lane == 31 || x0 + V == d.nx) right = plane[x0 + V == d.nx ? 0 : x0 + V];
+        } else {                          // pull from x + 1
+            T right = shfl(A[0], 1, false);
+            if (lane == 31 || x0 + V == d.nx) right = row[x0 + V == d.nx ? 0 : x0 + V];
 #pragma unroll
             for (int i = 0; i < V - 1; ++i) f[b][i] = Codec<T>::ld(A[i + 1], inv_scale);
             f[b][V - 1] = Codec<T>::ld(right, inv_scale);
         }
     }
 
-    // ---- cells next to obstacles or walls ----------------------------------
-    unsigned solid_mask = 0;
-    unsigned any = 0;
-#pragma unroll
-    for (int i = 0; i < V; ++i) any |= fl[i];
-    if (any) {
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const uint8_t fc = fl[i];
-            if (fc == 0) continue;
-            if (fc & F_SOLID) {
-                solid_mask |= 1u << i;
-                continue;
-            }
-            const int xc = x0 + i;
-            const long long c = c0 + i;
-            if (fc & F_SOLID_PREV) {
-                // uncovered cell: f = f_eq(rho_avg, u_w(x)) with the state of step n
-                double sum = 0.0;
-                int cnt = 0;
-                for (int a = 1; a < Q; ++a) {
-                    int nx_ = xc + ex(a), ny_ = y + ey(a), nz_ = z + ez(a);
-                    if ((!d.px && (nx_ < 0 || nx_ >= d.nx)) || (!d.py && (ny_ < 0 || ny_ >= d.ny)) ||
-                        (!d.pz && (nz_ < 0 || nz_ >= d.nz)))
-                        continue;
-                    nx_ = wrap_axis(nx_, d.nx); ny_ = wrap_axis(ny_, d.ny); nz_ = wrap_axis(nz_, d.nz);
-                    const long long yc = ((long long)nz_ * d.ny + ny_) * d.nx + nx_;
-                    if (sp.flags_cur[yc] & (F_SOLID | F_SOLID_PREV)) continue;
-                    Cd drho = 0;
-                    for (int bb = 0; bb < Q; ++bb) drho += Codec<T>::ld(src[bb * C + yc], inv_scale);
-                    sum += 1.0 + (double)drho;
-                    ++cnt;
-                }
-                const double rho = cnt ? sum / cnt : 1.0;
-                const int k = sp.bid_prev[c];
-                double u[3] = {0.0, 0.0, 0.0};
-                if (k != NO_BODY) surface_velocity(d, sp.body_cur[k], xc, y, z, u);
-                const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-#pragma unroll
-                for (int b = 0; b < Q; ++b) {
-                    const double eu = ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2];
-                    f[b][i] = (Cd)(wgt(b) * (rho - 1.0) + wgt(b) * rho * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
-                }
-            } else {
-                // bounce-back at walls (Eq. 4) and at obstacles of step n-1
-                Cd rho_x = -1;
-#pragma unroll
-                for (int b = 1; b < Q; ++b) {
-                    int sx = xc - ex(b), sy = y - ey(b), sz = z - ez(b);
-                    const Cd back = Codec<T>::ld(src[(long long)opp(b) * C + c], inv_scale);
-                    if ((!d.px && (sx < 0 || sx >= d.nx)) || (!d.py && (sy < 0 || sy >= d.ny)) ||
-                        (!d.pz && (sz < 0 || sz >= d.nz))) {
-                        f[b][i] = back;
-                        continue;
-                    }
-                    sx = wrap_axis(sx, d.nx); sy = wrap_axis(sy, d.ny); sz = wrap_axis(sz, d.nz);
-                    const long long sc = ((long long)sz * d.ny + sy) * d.nx + sx;
-                    if (!(sp.flags_prev[sc] & F_SOLID)) continue;
-                    if (rho_x < 0) {
-                        Cd drho = 0;
-                        for (int a = 0; a < Q; ++a) drho += Codec<T>::ld(src[(long long)a * C + c], inv_scale);
-                        rho_x = (Cd)1 + drho;
-                    }
-                    const int k = sp.bid_prev[sc];
-                    double u[3] = {0.0, 0.0, 0.0};
-                    if (k != NO_BODY) surface_velocity(d, sp.body_prev[k], sx, sy, sz, u);
-                    const Cd eu = (Cd)(ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2]);
-                    f[b][i] = back + (Cd)(6.0 * wgt(b)) * rho_x * eu;
-                }
-            }
-        }
-    }
-
-    // ---- LBGK collision (Eq. 2) with Guo's forcing ---------------------------
-    Cd rho[V], drho[V], ux[V], uy[V], uz[V], usq[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) {
-        Cd s = 0, jx = 0, jy = 0, jz = 0;
+        Cd g[Q];
 #pragma unroll
-        for (int b = 0; b < Q; ++b) {
-            s += f[b][i];
-            if (ex(b)) jx += ex(b) > 0 ? f[b][i] : -f[b][i];
-            if (ey(b)) jy += ey(b) > 0 ? f[b][i] : -f[b][i];
-            if (ez(b)) jz += ez(b) > 0 ? f[b][i] : -f[b][i];
-        }
-        drho[i] = s;
-        rho[i] = (Cd)1 + s;
-        const Cd inv = (Cd)1 / rho[i];
-        ux[i] = (jx + (Cd)(0.5 * dv.g[0])) * inv;
-        uy[i] = (jy + (Cd)(0.5 * dv.g[1])) * inv;
-        uz[i] = (jz + (Cd)(0.5 * dv.g[2])) * inv;
-        usq[i] = ux[i] * ux[i] + uy[i] * uy[i] + uz[i] * uz[i];
+        for (int b = 0; b < Q; ++b) g[b] = f[b][i];
+        collide<Cd>(g, dv);
+        const bool solid = fl[i] & F_SOLID;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) f[b][i] = solid ? (Cd)0 : g[b];
     }
-    const Cd om = (Cd)dv.omega;
-    const Cd guo = (Cd)(1.0 - 0.5 * dv.omega);
-    const Cd gx = (Cd)dv.g[0], gy = (Cd)dv.g[1], gz = (Cd)dv.g[2];
+    if (!active) return;
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
-        const Cd w = (Cd)wgt(b);
         T out[V];
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const Cd eu = (Cd)ex(b) * ux[i] + (Cd)ey(b) * uy[i] + (Cd)ez(b) * uz[i];
-            const Cd deq = w * (drho[i] + rho[i] * ((Cd)3 * eu + (Cd)4.5 * eu * eu - (Cd)1.5 * usq[i]));
-            Cd o = f[b][i] - om * (f[b][i] - deq);
-            if (dv.forced) {
-                const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
-                const Cd ug = ux[i] * gx + uy[i] * gy + uz[i] * gz;
-                o += guo * w * ((Cd)3 * (eg - ug) + (Cd)9 * eu * eg);
-            }
-            if (solid_mask & (1u << i)) o = 0;
-            out[i] = Codec<T>::st(o, scale);
-        }
-        if (active) store_vec<T, V>(dst + (long long)b * C + c0, out);
+        for (int i = 0; i < V; ++i) out[i] = Codec<T>::st(f[b][i], scale);
+        store_vec<T, V>(dst + (long long)b * C + c0, out);
     }
 }
 
+// Cells with a non-zero flag byte: refill, bounce-back at walls and moving
+// obstacles, then LBGK.  mode 0: block row blockIdx.y = body b, the threads
+// cover the cube of side 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) (the
+// cube the remap wrote); mode 1: blockIdx.y = wall face (axis * 2 + side).
+template <typename T>
+__global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const StepPtrs sp, int mode) {
+    using Cd = typename Codec<T>::C;
+    const Domain d = dv.dom;
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int x, y, z;
+    if (mode == 0) {
+        const int b = blockIdx.y;
+        const BodyState sb = sp.body_cur[b];
+        const int half = dv.props[b].E + REMAP_MARGIN;
+        const int side = 2 * half + 1;
+        if (l >= (long long)side * side * side) return;
+        x = (int)floor(sb.X[0]) - half + (int)(l % side);
+        y = (int)floor(sb.X[1]) - half + (int)((l / side) % side);
+        z = (int)floor(sb.X[2]) - half + (int)(l / ((long long)side * side));
+        if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else if (x < 0 || x >= d.nx) return;
+        if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else if (y < 0 || y >= d.ny) return;
+        if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else if (z < 0 || z >= d.nz) return;
+    } else {
+        const int axis = blockIdx.y >> 1, hi = blockIdx.y & 1;
+        const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
+        if (per[axis]) return;
+        const int ua = axis == 0 ? 1 : 0, va = axis == 2 ? 1 : 2;
+        if (l >= (long long)n3[ua] * n3[va]) return;
+        int p[3];
+        p[axis] = hi ? n3[axis] - 1 : 0;
+        p[ua] = (int)(l % n3[ua]);
+        p[va] = (int)(l / n3[ua]);
+        x = p[0]; y = p[1]; z = p[2];
+    }
+    const long long C = d.C;
+    const long long c = ((long long)z * d.ny + y) * d.nx + x;
+    const uint8_t fc = sp.flags_cur[c];
+    if (fc == 0 || (fc & F_SOLID)) return;
+    const T *__restrict__ src = static_cast<const T *>(sp.src);
+    const float s = dv.f16_inv_scale;
+    Cd f[Q];
+    if (fc & F_SOLID_PREV) {
+        // uncovered cell: f = f_eq(rho_avg, u_w(x)) with the state of step n
+        double sum = 0.0;
+        int cnt = 0;
+        for (int a = 1; a < Q; ++a) {
+            int nx_ = x + ex(a), ny_ = y + ey(a), nz_ = z + ez(a);
+            if ((!d.px && (nx_ < 0 || nx_ >= d.nx)) || (!d.py && (ny_ < 0 || ny_ >= d.ny)) ||
+                (!d.pz && (nz_ < 0 || nz_ >= d.nz)))
+                continue;
+            nx_ = wrap_axis(nx_, d.nx); ny_ = wrap_axis(ny_, d.ny); nz_ = wrap_axis(nz_, d.nz);
+            const long long yc = ((long long)nz_ * d.ny + ny_) * d.nx + nx_;
+            if (sp.flags_cur[yc] & (F_SOLID | F_SOLID_PREV)) continue;
+            Cd drho = 0;
+            for (int bb = 0; bb < Q; ++bb) drho += Codec<T>::ld(src[bb * C + yc], s);
+            sum += 1.0 + (double)drho;
+            ++cnt;
+        }
+        const double rho = cnt ? sum / cnt : 1.0;
+        const int k = sp.bid_prev[c];
+        double u[3] = {0.0, 0.0, 0.0};
+        if (k != NO_BODY) surface_velocity(d, sp.body_cur[k], x, y, z, u);
+        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            const double eu = ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2];
+            f[b] = (Cd)(wgt(b) * (rho - 1.0) + wgt(b) * rho * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+        }
+    } else {
+        Cd rho_x = -1;
+        f[0] = Codec<T>::ld(src[c], s);
+#pragma unroll
+        for (int b = 1; b < Q; ++b) {
+            int sx = x - ex(b), sy = y - ey(b), sz = z - ez(b);
+            if ((!d.px && (sx < 0 || sx >= d.nx)) || (!d.py && (sy < 0 || sy >= d.ny)) ||
+                (!d.pz && (sz < 0 || sz >= d.nz))) {
+                f[b] = Codec<T>::ld(src[(long long)opp(b) * C + c], s);      // Eq. 4
+                continue;
+            }
+            sx = wrap_axis(sx, d.nx); sy = wrap_axis(sy, d.ny); sz = wrap_axis(sz, d.nz);
+            const long long sc = ((long long)sz * d.ny + sy) * d.nx + sx;
+            if (!(sp.flags_prev[sc] & F_SOLID)) {
+                f[b] = Codec<T>::ld(src[(long long)b * C + sc], s);          // plain pull
+                continue;
+            }
+            if (rho_x < 0) {
+                Cd drho = 0;
+                for (int a = 0; a < Q; ++a) drho += Codec<T>::ld(src[(long long)a * C + c], s);
+                rho_x = (Cd)1 + drho;
+            }
+            const int k = sp.bid_prev[sc];
+            double u[3] = {0.0, 0.0, 0.0};
+            if (k != NO_BODY) surface_velocity(d, sp.body_prev[k], sx, sy, sz, u);
+            const Cd eu = (Cd)(ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2]);
+            f[b] = Codec<T>::ld(src[(long long)opp(b) * C + c], s) + (Cd)(6.0 * wgt(b)) * rho_x * eu;
+        }
+    }
+    collide<Cd>(f, dv);
+    T *__restrict__ dst = static_cast<T *>(sp.dst);
+#pragma unroll
+    for (int b = 0; b < Q; ++b) dst[(long long)b * C + c] = Codec<T>::st(f[b], dv.f16_scale);
+}
+
+template <typename T, int V, int BX, int BY>
+void launch_bulk(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    const int nxq = dv.dom.nx / V;
+    dim3 grid((nxq + BX - 1) / BX, (dv.dom.ny + BY - 1) / BY, dv.dom.nz);
+    bulk_kernel<T, V, BX, BY><<<grid, dim3(BX, BY), 0, s>>>(dv, sp);
+}
+
+// launch shapes: V cells per thread, BX (a multiple of 32) x BY threads
 template <typename T, int V>
-void launch_typed(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
-    const long long nq = dv.dom.C / V;
-    const unsigned blocks = (unsigned)((nq + SC_THREADS - 1) / SC_THREADS);
-    stream_collide_kernel<T, V><<<blocks, SC_THREADS, 0, s>>>(dv, sp);
+void launch_shape(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    const int nxq = dv.dom.nx / V;
+    if (nxq >= 128) launch_bulk<T, V, 128, 2>(dv, sp, s);
+    else if (nxq >= 64) launch_bulk<T, V, 64, 4>(dv, sp, s);
+    else launch_bulk<T, V, 32, 8>(dv, sp, s);
+}
+
+template <typename T>
+void launch_boundary(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    if (dv.nb > 0) {
+        const long long side = dv.remap_side;
+        const unsigned bx = (unsigned)((side * side * side + 255) / 256);
+        boundary_kernel<T><<<dim3(bx, dv.nb), 256, 0, s>>>(dv, sp, 0);
+    }
+    if (!(dv.dom.px && dv.dom.py && dv.dom.pz)) {
+        const long long nx = dv.dom.nx, ny = dv.dom.ny, nz = dv.dom.nz;
+        const long long area = std::max(ny * nz, std::max(nx * nz, nx * ny));
+        boundary_kernel<T><<<dim3((unsigned)((area + 255) / 256), 6), 256, 0, s>>>(dv, sp, 1);
+    }
 }
 
 }  // namespace
 
-int stream_collide_vector_width(const Device &dv) {
-    const int nx = dv.dom.nx;
+bool valid_vector_width(const Device &dv, int v) {
+    if (v < 1 || dv.dom.nx % v) return false;
     switch (dv.precision) {
-    case 0: return nx % 2 == 0 ? 2 : 1;               // FP64: 16-byte vectors
-    case 1: return nx % 4 == 0 ? 4 : 1;               // FP32
-    default: return nx % 8 == 0 ? 8 : 1;              // FP16 / BF16
+    case 0: return v == 1 || v == 2;
+    case 1: return v == 1 || v == 2 || v == 4;
+    default: return v == 1 || v == 2 || v == 4 || v == 8;
     }
 }
 
+int default_vector_width(const Device &dv) {
+    const int pref = dv.precision == 0 ? 1 : (dv.precision == 1 ? 2 : 4);
+    for (int v = pref; v > 1; v >>= 1)
+        if (dv.dom.nx % v == 0) return v;
+    return 1;
+}
+
 void launch_stream_collide(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
-    const int v = stream_collide_vector_width(dv);
+    const int v = dv.vec;
     switch (dv.precision) {
     case 0:
-        if (v == 2) launch_typed<double, 2>(dv, sp, s); else launch_typed<double, 1>(dv, sp, s);
+        if (v == 2) launch_shape<double, 2>(dv, sp, s); else launch_shape<double, 1>(dv, sp, s);
         break;
     case 1:
-        if (v == 4) launch_typed<float, 4>(dv, sp, s); else launch_typed<float, 1>(dv, sp, s);
+        if (v == 4) launch_shape<float, 4>(dv, sp, s);
+        else if (v == 2) launch_shape<float, 2>(dv, sp, s);
+        else launch_shape<float, 1>(dv, sp, s);
         break;
     case 2:
-        if (v == 8) launch_typed<__half, 8>(dv, sp, s); else launch_typed<__half, 1>(dv, sp, s);
+        if (v == 8) launch_shape<__half, 8>(dv, sp, s);
+        else if (v == 4) launch_shape<__half, 4>(dv, sp, s);
+        else if (v == 2) launch_shape<__half, 2>(dv, sp, s);
+        else launch_shape<__half, 1>(dv, sp, s);
         break;
     default:
-        if (v == 8) launch_typed<__nv_bfloat16, 8>(dv, sp, s); else launch_typed<__nv_bfloat16, 1>(dv, sp, s);
+        if (v == 8) launch_shape<__nv_bfloat16, 8>(dv, sp, s);
+        else if (v == 4) launch_shape<__nv_bfloat16, 4>(dv, sp, s);
+        else if (v == 2) launch_shape<__nv_bfloat16, 2>(dv, sp, s);
+        else launch_shape<__nv_bfloat16, 1>(dv, sp, s);
         break;
     }
+}
+
+void launch_boundary_fix(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    switch (dv.precision) {
+    case 0: launch_boundary<double>(dv, sp, s); break;
+    case 1: launch_boundary<float>(dv, sp, s); break;
+    case 2: launch_boundary<__half>(dv, sp, s); break;
+    default: launch_boundary<__nv_bfloat16>(dv, sp, s); break;
+    }
+}
+
+bool needs_boundary_fix(const Device &dv) {
+    return dv.nb > 0 || !(dv.dom.px && dv.dom.py && dv.dom.pz);
 }
 
 }  // namespace lbm

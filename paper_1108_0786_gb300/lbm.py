@@ -29,7 +29,7 @@ PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = 0, 1, 2, 3
 OPT_NO_FLUID = 1
 FIELD_RHO, FIELD_U, FIELD_FLAGS, FIELD_POP = 0, 1, 2, 3
 DTYPE_F64, DTYPE_F32, DTYPE_U8 = 0, 1, 2
-KERNEL_NAMES = ("remap", "stream_collide", "links", "force", "integrate")
+KERNEL_NAMES = ("remap", "stream_collide", "boundary", "links", "force", "integrate")
 PRECISIONS = {"f64": PREC_F64, "f32": PREC_F32, "f16": PREC_F16, "bf16": PREC_BF16}
 
 EXPORTED = (
@@ -38,7 +38,7 @@ EXPORTED = (
     "lbm_set_body_state", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_steps_done",
     "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
-    "lbm_kernels_per_step", "lbm_bytes_per_cell", "lbm_last_error",
+    "lbm_tune", "lbm_kernels_per_step", "lbm_bytes_per_cell", "lbm_last_error",
 )
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -87,6 +87,7 @@ def load_library(path: Optional[str] = None):
         "lbm_save": ([P, ctypes.c_char_p], I),
         "lbm_load": ([P, ctypes.c_char_p], I),
         "lbm_time_kernels": ([P, I, DP, I], I),
+        "lbm_tune": ([P, I], I),
         "lbm_kernels_per_step": ([P], I),
         "lbm_bytes_per_cell": ([P], I),
         "lbm_last_error": ([P], ctypes.c_char_p),
@@ -208,6 +209,10 @@ class Lattice:
         assert p.size == 19 * self.cells
         return self._check(self._lib.lbm_set_fields(self._h, FIELD_POP, p.ctypes.data_as(ctypes.c_void_p),
                                                     DTYPE_F64))
+
+    def tune(self, cells_per_thread):
+        """Cells per thread of the bulk stream-collide kernel (0: default)."""
+        return self._check(self._lib.lbm_tune(self._h, int(cells_per_thread)))
 
     def enable_history(self, capacity):
         return self._check(self._lib.lbm_enable_history(self._h, int(capacity)))
