@@ -177,6 +177,12 @@ def workload(args, rank):
                             steps=args.steps)
 
 
+def job_mlups(cells_per_rank, steps, world, max_ms):
+    """Whole-job throughput: the cells all ranks advanced per second / 1e6,
+    over the slowest rank's time (weak scaling: every rank holds a replica)."""
+    return cells_per_rank * steps * world / (max_ms / 1e3) / 1e6
+
+
 def timed_steps(lat, steps, world, device):
     import torch
     stream = torch.cuda.current_stream()
@@ -300,7 +306,7 @@ def run_ours(args, world, rank, local):
     with ClockSampler(local) as clk:
         ms = timed_steps(lat, args.steps, world, device)
     clocks = clk.summary()
-    value = sc.cells * args.steps * world / (ms / 1e3) / 1e6
+    value = job_mlups(sc.cells, args.steps, world, ms)
     # dominant kernel: per-launch durations with CUDA events on the launching stream
     kms = lat.time_kernels(50)
     bpc = lat.bytes_per_cell

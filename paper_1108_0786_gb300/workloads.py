@@ -191,7 +191,11 @@ def capsule_swarm(nx=512, ny=256, nz=256, swimmers=8, seed=1108, mix=False,
     rest, r, l = 24.0, 4.0, 8.0
     reach = rest + r + 0.5 * l            # swimmer bounding-sphere radius
     centres = []
+    attempts = 0
     while len(centres) < swimmers:
+        attempts += 1
+        if attempts > 100000:
+            raise ValueError(f"cannot place {swimmers} swimmers in a {nx}x{ny}x{nz} box")
         c = (rng.uniform(0, nx), rng.uniform(0, ny), rng.uniform(0, nz))
         q = rng.quaternion()
         shapes = tuple(rng.choice((SPHERE, CAPSULE)) for _ in range(3)) if mix else (CAPSULE,) * 3
