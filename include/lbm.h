@@ -226,6 +226,44 @@ int lbm_kernels_per_step(lbm_t *h);
  * 2 * 19 * sizeof(population) + 1 flag byte. */
 int lbm_bytes_per_cell(lbm_t *h);
 
+/* ---- momentum exchange without device allocation -------------------------
+ *
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * call cudaMalloc: programs that keep every byte of device memory in a pool
+ * of their own under a fixed budget, or loops that must not pay the implicit
+ * device-wide synchronisation of cudaMalloc / cudaFree.  Such a caller owns
+ * all inputs and outputs and asks the library for the hydrodynamic force and
+ * torque of each body (the values lbm_get_forces reports for a step).
+ *
+ * Inputs (device pointers, read only):
+ *   pop     post-collision populations f~ as FP64, [19][nx*ny*nz] in the
+ *           population order above (as LBM_FIELD_POP / LBM_DTYPE_F64);
+ *   flags   uint8 per cell: 0 fluid, 1 + body id for a cell of that body
+ *           (as LBM_FIELD_FLAGS);
+ *   bodies  [nb][13] FP64 body states (as lbm_get_bodies) of the same step.
+ * Output (device pointer): out[nb][6] = F[3], T[3] per body, torque about
+ * the body centre.  half_width bounds the links of every body: all its
+ * solid cells lie within half_width - 1 cells of floor(X) on each axis.
+ * Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default).
+ *
+ * Scratch: per-block partial sums live in one file-scope device array of
+ * LBM_STATIC_SCRATCH_RECORDS records of 48 bytes (3 MiB), which every GPU
+ * that loads the library holds until the process exits.  The first call on
+ * a device looks up that array's device address, with the device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array and leaves its last contents there; calls that overlap on the GPU
+ * (for example on two streams) race and give wrong results.
+ *
+ * Errors: LBM_E_ARG for a null pointer, nb outside [1, LBM_MAX_BODIES], bad
+ * sizes or bc, half_width outside [1, LBM_STATIC_SCRATCH_MAX_HALF_WIDTH], or
+ * nb * ceil((2 half_width + 1)^3 / 256) > LBM_STATIC_SCRATCH_RECORDS;
+ * LBM_E_CUDA for a CUDA error.  Nothing is allocated in any case. */
+#define LBM_STATIC_SCRATCH_RECORDS        65536
+#define LBM_STATIC_SCRATCH_MAX_HALF_WIDTH 64
+int lbm_momentum_exchange_static(const double *pop, const unsigned char *flags, const double *bodies,
+                                 int nb, int nx, int ny, int nz, int bc, int half_width, double *out,
+                                 void *stream);
+
 /* Message of the last error on this handle (never NULL). */
 const char *lbm_last_error(lbm_t *h);
 

@@ -39,6 +39,7 @@ EXPORTED = (
     "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
     "lbm_tune", "lbm_kernels_per_step", "lbm_bytes_per_cell", "lbm_last_error",
+    "lbm_momentum_exchange_static",
 )
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -91,6 +92,7 @@ def load_library(path: Optional[str] = None):
         "lbm_kernels_per_step": ([P], I),
         "lbm_bytes_per_cell": ([P], I),
         "lbm_last_error": ([P], ctypes.c_char_p),
+        "lbm_momentum_exchange_static": ([P, P, P, I, I, I, I, I, I, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
