@@ -39,6 +39,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "lbm_internal.cuh"
 
@@ -109,9 +110,19 @@ __device__ __forceinline__ T shfl(T v, int delta, bool up) {
 // LBGK collision of one cell in place (deviation form):
 //   drho = sum delta, rho = 1 + drho, u = (sum e delta + g/2) / rho,
 //   delta_eq_b = w_b (drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)),
-//   delta~_b = delta_b - (delta_b - delta_eq_b) / tau
+//   delta~_b = delta_b + (delta_eq_b - delta_b) / tau
 //              + (1 - 1/(2 tau)) w_b (3 (e_b - u) . g + 9 (e_b . u)(e_b . g)).
-template <typename Cd>
+// In exact arithmetic the increments delta~_b - delta_b carry zero mass and
+// momentum exactly g.  With FP32 storage the rounded velocity that enters the
+// equilibrium would make each collision a small momentum source in every
+// cell, constant in a steady flow, and the slow viscous mode of a channel
+// integrates it into a ~1e-5 velocity error.  The FP32 update therefore sums
+// mass and momentum of the increments (small numbers, so the sums are
+// accurate) and moves the defect to the +-x, +-y, +-z pairs and the rest
+// population: only the value-dependent rounding of the final additions
+// remains.  FP64 keeps the plain update, as do the 16-bit formats, whose
+// storage rounding (2^-9 .. 2^-11 relative) dwarfs this effect.
+template <typename Cd, bool CLOSE>
 __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     Cd s = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -129,17 +140,38 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     const Cd om = (Cd)dv.omega;
     const Cd guo = (Cd)(1.0 - 0.5 * dv.omega);
     const Cd ug = ux * gx + uy * gy + uz * gz;
+    Cd m = 0, px = 0, py = 0, pz = 0;
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
         const Cd w = (Cd)wgt(b);
         const Cd eu = (Cd)ex(b) * ux + (Cd)ey(b) * uy + (Cd)ez(b) * uz;
         const Cd deq = w * (s + rho * ((Cd)3 * eu + (Cd)4.5 * eu * eu - (Cd)1.5 * usq));
-        Cd o = f[b] - om * (f[b] - deq);
-        if (dv.forced) {
-            const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
-            o += guo * w * ((Cd)3 * (eg - ug) + (Cd)9 * eu * eg);
+        if constexpr (CLOSE) {
+            Cd d = om * (deq - f[b]);
+            if (dv.forced) {
+                const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
+                d += guo * w * ((Cd)3 * (eg - ug) + (Cd)9 * eu * eg);
+            }
+            m += d;
+            if (ex(b)) px += ex(b) > 0 ? d : -d;
+            if (ey(b)) py += ey(b) > 0 ? d : -d;
+            if (ez(b)) pz += ez(b) > 0 ? d : -d;
+            f[b] += d;
+        } else {
+            Cd o = f[b] - om * (f[b] - deq);
+            if (dv.forced) {
+                const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
+                o += guo * w * ((Cd)3 * (eg - ug) + (Cd)9 * eu * eg);
+            }
+            f[b] = o;
         }
-        f[b] = o;
+    }
+    if constexpr (CLOSE) {
+        const Cd hx = (Cd)0.5 * (gx - px), hy = (Cd)0.5 * (gy - py), hz = (Cd)0.5 * (gz - pz);
+        f[1] += hx; f[2] -= hx;
+        f[3] += hy; f[4] -= hy;
+        f[5] += hz; f[6] -= hz;
+        f[0] -= m;
     }
 }
 
@@ -199,7 +231,7 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
         Cd g[Q];
 #pragma unroll
         for (int b = 0; b < Q; ++b) g[b] = f[b][i];
-        collide<Cd>(g, dv);
+        collide<Cd, std::is_same<T, float>::value>(g, dv);
         const bool solid = fl[i] & F_SOLID;
 #pragma unroll
         for (int b = 0; b < Q; ++b) f[b][i] = solid ? (Cd)0 : g[b];
@@ -311,7 +343,7 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
             f[b] = Codec<T>::ld(src[(long long)opp(b) * C + c], s) + (Cd)(6.0 * wgt(b)) * rho_x * eu;
         }
     }
-    collide<Cd>(f, dv);
+    collide<Cd, std::is_same<T, float>::value>(f, dv);
     T *__restrict__ dst = static_cast<T *>(sp.dst);
 #pragma unroll
     for (int b = 0; b < Q; ++b) dst[(long long)b * C + c] = Codec<T>::st(f[b], dv.f16_scale);
