@@ -99,8 +99,8 @@ extern "C" {
 #define LBM_KERNEL_STREAM_COLLIDE 1   /* bulk pull + LBGK over all cells */
 #define LBM_KERNEL_BOUNDARY       2   /* refill / bounce-back cells near bodies and walls */
 #define LBM_KERNEL_LINKS          3   /* per-body link lists */
-#define LBM_KERNEL_FORCE          4   /* momentum exchange */
-#define LBM_KERNEL_INTEGRATE      5   /* drive, springs, rigid-body step */
+#define LBM_KERNEL_FORCE          4   /* momentum exchange; with fluid it also runs the rigid-body step */
+#define LBM_KERNEL_INTEGRATE      5   /* drive, springs, rigid-body step when there is no fluid */
 #define LBM_NUM_KERNELS           6
 
 typedef struct lbm_s lbm_t;

@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
     const BodyState sb = sp.body_cur[b];
     const int half = pb.E + REMAP_MARGIN;
     const int side = 2 * half + 1;
-    const long long vol = (long long)side * side * side;
-    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int vol = side * side * side;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l == 0) {
         // a body may not cross a wall (its extent beyond the wall planes)
         double R[3][3];
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
         }
     }
     if (l >= vol) return;
-    const int lx = (int)(l % side), ly = (int)((l / side) % side), lz = (int)(l / ((long long)side * side));
+    const int lx = l % side, ly = (l / side) % side, lz = l / (side * side);
     int x = (int)floor(sb.X[0]) - half + lx;
     int y = (int)floor(sb.X[1]) - half + ly;
     int z = (int)floor(sb.X[2]) - half + lz;
@@ -126,18 +126,19 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
     if (!init_mode) {
         const uint8_t prev = sp.flags_prev[c] & F_SOLID;
         if (prev) flags |= F_SOLID_PREV;
-        // does any pull source x - e_a hold an obstacle of step n-1?
+        // does any pull source x - e_a hold an obstacle of step n-1?  (all
+        // 18 loads are independent; sources beyond a wall do not count)
+        uint8_t near = 0;
+#pragma unroll
         for (int a = 1; a < Q; ++a) {
-            int sx = x - ex(a), sy = y - ey(a), sz = z - ez(a);
-            if ((!d.px && (sx < 0 || sx >= d.nx)) || (!d.py && (sy < 0 || sy >= d.ny)) ||
-                (!d.pz && (sz < 0 || sz >= d.nz)))
-                continue;
-            sx = wrap_axis(sx, d.nx); sy = wrap_axis(sy, d.ny); sz = wrap_axis(sz, d.nz);
-            if (sp.flags_prev[((long long)sz * d.ny + sy) * d.nx + sx] & F_SOLID) {
-                flags |= F_NEAR;
-                break;
-            }
+            const int sx = x - ex(a), sy = y - ey(a), sz = z - ez(a);
+            const bool in = !((!d.px && (sx < 0 || sx >= d.nx)) || (!d.py && (sy < 0 || sy >= d.ny)) ||
+                              (!d.pz && (sz < 0 || sz >= d.nz)));
+            const uint8_t v = sp.flags_prev[((long long)wrap_axis(sz, d.nz) * d.ny + wrap_axis(sy, d.ny)) * d.nx +
+                                            wrap_axis(sx, d.nx)];
+            near |= in ? v : 0;
         }
+        if (near & F_SOLID) flags |= F_NEAR;
         if ((solid != 0) != (prev != 0) || (solid && sp.bid_prev[c] != id)) dv.changed[sp.parity] = 1;
     }
     sp.flags_cur[c] = flags;
@@ -240,102 +241,45 @@ template <> __device__ inline double load_dev<__nv_bfloat16>(const __nv_bfloat16
 constexpr int FORCE_THREADS = 256;
 constexpr int MAX_SEGMENTS = 1024;
 
-// Momentum exchange (Eq. hydroF): blocks (k, b), k < FORCE_BLOCKS, split the
-// links of body b into contiguous chunks and sum
-//   F = sum e_a [2 f~_a(x_f) + 6 w_a rho(x_f) e_-a . u_w(x_f + e_a)],
-//   T = sum (x_f + e_a / 2 - X) x F_link
-// with f~ of step n (dst) and the body state of step n, in FP64; each block
-// reduces with warp shuffles in a fixed order and writes its partial sums,
-// which the integrate kernel adds in block order (deterministic).
-template <typename T>
-__global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, const StepPtrs sp) {
-    const Domain d = dv.dom;
-    const int b = blockIdx.y, kb = blockIdx.x;
-    const BodyProps pb = dv.props[b];
-    const BodyState sb = sp.body_cur[b];
-    const int side = 2 * (pb.E + 1) + 1;
-    const int *counts = dv.seg_count + (long long)b * dv.link_side;
-    const Link *links = dv.links + (long long)b * dv.link_side * dv.seg_cap;
-    const T *pop = static_cast<const T *>(sp.dst);
-    const long long C = d.C;
-    const float s = dv.f16_inv_scale;
-
-    __shared__ int prefix[MAX_SEGMENTS + 1];
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int k = 0; k < side; ++k) {
-            prefix[k] = acc;
-            acc += counts[k];
-        }
-        prefix[side] = acc;
-    }
-    __syncthreads();
-    const int total = prefix[side];
-    const int chunk = (total + FORCE_BLOCKS - 1) / FORCE_BLOCKS;
-    const int j0 = kb * chunk, j1 = min(total, j0 + chunk);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int j = j0 + threadIdx.x; j < j1; j += FORCE_THREADS) {
-        int lo = 0, hi = side - 1;       // segment k with prefix[k] <= j < prefix[k+1]
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (prefix[mid] <= j) lo = mid; else hi = mid - 1;
-        }
-        const Link lk = links[(long long)lo * dv.seg_cap + (j - prefix[lo])];
-        const long long c = lk.cell;
-        const int a = (int)lk.dir;
-        double rho = 1.0, g_a = 0.0;
-        if constexpr (sizeof(T) == 8) {
-            for (int q = 0; q < Q; ++q) rho += load_dev<T>(pop + q * C + c, s);
-        } else {
-            float drho = 0.0f;          // FP32 sum of the stored deviations
-            for (int q = 0; q < Q; ++q) drho += (float)load_dev<T>(pop + q * C + c, s);
-            rho += (double)drho;
-        }
-        g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
-        const int x = (int)(c % d.nx), y = (int)((c / d.nx) % d.ny),
-                  z = (int)(c / ((long long)d.nx * d.ny));
-        double u[3];
-        surface_velocity(d, sb, x + ex(a), y + ey(a), z + ez(a), u);
-        const double eu = -(ex(a) * u[0] + ey(a) * u[1] + ez(a) * u[2]);   // e_-a . u_w
-        const double mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
-        const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
-        double o[3];
-        offset_from(d, sb, x + 0.5 * ex(a), y + 0.5 * ey(a), z + 0.5 * ez(a), o);
-        acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];
-        acc[3] += o[1] * fl[2] - o[2] * fl[1];
-        acc[4] += o[2] * fl[0] - o[0] * fl[2];
-        acc[5] += o[0] * fl[1] - o[1] * fl[0];
-    }
-    __shared__ double part[FORCE_THREADS / 32][6];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        double v = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) part[warp][i] = v;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            double v = lane < FORCE_THREADS / 32 ? part[lane][i] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) dv.fpart[((long long)b * FORCE_BLOCKS + kb) * 6 + i] = v;
-        }
-    }
+// periodic minimum image of d for |d| < 3n/2 (two compares, no FP64 floor)
+__device__ inline double wrap_near(double d, int n, int periodic) {
+    if (!periodic) return d;
+    const double h = 0.5 * n;
+    return d > h ? d - n : (d < -h ? d + n : d);
 }
 
-// Rigid-body step (Algorithm 1, Eq. totalFSwimmer): thread b adds the
-// momentum-exchange partial sums in block order, g times the volume, its
-// drive terms in term order and its springs in spring order, then advances
-// by semi-implicit Euler (dt = 1) in FP64.
-__global__ void __launch_bounds__(256) integrate_kernel(const Device dv, const StepPtrs sp, int with_fluid) {
-    const int b = threadIdx.x;
+// Rigid-body step (Algorithm 1, Eq. totalFSwimmer) for all bodies, run by
+// one block of 256 threads.  Phase 1 (threads over drive terms and springs)
+// evaluates every drive term (Eq. FB1-FB3) and spring force (Eq. osci_i,
+// osci_j) into scratch; phase 2 (thread b) adds, in order, the momentum-
+// exchange partial sums, g times the volume, its drive terms in term order
+// and its springs in spring order, then advances by semi-implicit Euler
+// (dt = 1) in FP64.
+__device__ void integrate_block(const Device &dv, const StepPtrs &sp, int with_fluid) {
     const long long tstep = *dv.t_dev;
+    const double t = (double)tstep;
+    for (int k = threadIdx.x; k < dv.nd; k += blockDim.x) {
+        const DriveTerm dt = dv.drives[k];
+        double f = 0.0;
+        if (!(t < dt.t_on || t >= dt.t_off)) f = dt.amp * sin(dt.omega * t - dt.phase);
+        const double *q = sp.body_cur[dt.body].q;     // body-frame x axis = first column of R(q)
+        const double w = q[0], x = q[1], y = q[2], z = q[3];
+        dv.drive_f[3 * k + 0] = f * (1 - 2 * (y * y + z * z));
+        dv.drive_f[3 * k + 1] = f * (2 * (x * y + w * z));
+        dv.drive_f[3 * k + 2] = f * (2 * (x * z - w * y));
+    }
+    for (int k = threadIdx.x; k < dv.ns; k += blockDim.x) {
+        const Spring sp_ = dv.springs[k];
+        const BodyState si = sp.body_cur[sp_.i], sj = sp.body_cur[sp_.j];
+        const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
+        const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        const double inv_len = len > 0 ? 1.0 / len : 0.0;
+        for (int i = 0; i < 3; ++i)
+            dv.spring_f[3 * k + i] = -sp_.k * (len - sp_.rest) * (dd[i] * inv_len) - sp_.gamma * (si.V[i] - sj.V[i]);
+    }
+    __syncthreads();
+    const int b = threadIdx.x;
     if (b < dv.nb) {
-        const double t = (double)tstep;
         const BodyProps pb = dv.props[b];
         const BodyState s = sp.body_cur[b];
         double R[3][3];
@@ -348,22 +292,12 @@ __global__ void __launch_bounds__(256) integrate_kernel(const Device dv, const S
             dv.fh[b * 6 + i] = v;
             if (i < 3) F[i] = v + dv.g[i] * pb.volume; else Tq[i - 3] = v;
         }
-        for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k) {
-            const DriveTerm dt = dv.drives[k];
-            if (t < dt.t_on || t >= dt.t_off) continue;
-            const double f = dt.amp * sin(dt.omega * t - dt.phase);
-            for (int i = 0; i < 3; ++i) F[i] += f * R[i][0];
-        }
+        for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k)
+            for (int i = 0; i < 3; ++i) F[i] += dv.drive_f[3 * k + i];
         for (int kk = pb.spring_first; kk < pb.spring_first + pb.spring_count; ++kk) {
-            const Spring sp_ = dv.springs[dv.spring_list[kk]];
-            const BodyState si = sp.body_cur[sp_.i], sj = sp.body_cur[sp_.j];
-            const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
-            const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-            const double inv_len = len > 0 ? 1.0 / len : 0.0;
-            for (int i = 0; i < 3; ++i) {
-                const double fi = -sp_.k * (len - sp_.rest) * (dd[i] * inv_len) - sp_.gamma * (si.V[i] - sj.V[i]);
-                F[i] += sp_.i == b ? fi : -fi;
-            }
+            const int k = dv.spring_list[kk];
+            const bool first = dv.springs[k].i == b;
+            for (int i = 0; i < 3; ++i) F[i] += first ? dv.spring_f[3 * k + i] : -dv.spring_f[3 * k + i];
         }
         BodyState n = s;
         for (int i = 0; i < 3; ++i) {
@@ -403,6 +337,119 @@ __global__ void __launch_bounds__(256) integrate_kernel(const Device dv, const S
         *dv.t_dev = tstep + 1;
         dv.changed[sp.parity ^ 1] = 0;
     }
+}
+
+// Momentum exchange (Eq. hydroF): blocks (k, b), k < FORCE_BLOCKS, split the
+// links of body b into contiguous chunks and sum
+//   F = sum e_a [2 f~_a(x_f) + 6 w_a rho(x_f) e_-a . u_w(x_f + e_a)],
+//   T = sum (x_f + e_a / 2 - X) x F_link
+// with f~ of step n (dst) and the body state of step n, in FP64; each block
+// reduces with warp shuffles in a fixed order and writes its partial sums.
+// The last block to finish then runs the rigid-body step for all bodies,
+// adding the partial sums in block order (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, const StepPtrs sp) {
+    const Domain d = dv.dom;
+    const int b = blockIdx.y, kb = blockIdx.x;
+    const BodyProps pb = dv.props[b];
+    const BodyState sb = sp.body_cur[b];
+    const int side = 2 * (pb.E + 1) + 1;
+    const int *counts = dv.seg_count + (long long)b * dv.link_side;
+    const Link *links = dv.links + (long long)b * dv.link_side * dv.seg_cap;
+    const T *pop = static_cast<const T *>(sp.dst);
+    const long long C = d.C;
+    const float s = dv.f16_inv_scale;
+    // body centre wrapped into the domain (once per block)
+    const double xw[3] = {d.px ? sb.X[0] - d.nx * floor(sb.X[0] * d.inx) : sb.X[0],
+                          d.py ? sb.X[1] - d.ny * floor(sb.X[1] * d.iny) : sb.X[1],
+                          d.pz ? sb.X[2] - d.nz * floor(sb.X[2] * d.inz) : sb.X[2]};
+
+    __shared__ int prefix[MAX_SEGMENTS + 1];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int k = 0; k < side; ++k) {
+            prefix[k] = acc;
+            acc += counts[k];
+        }
+        prefix[side] = acc;
+    }
+    __syncthreads();
+    const int total = prefix[side];
+    const int chunk = (total + FORCE_BLOCKS - 1) / FORCE_BLOCKS;
+    const int j0 = kb * chunk, j1 = min(total, j0 + chunk);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = j0 + threadIdx.x; j < j1; j += FORCE_THREADS) {
+        int lo = 0, hi = side - 1;       // segment k with prefix[k] <= j < prefix[k+1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const Link lk = links[(long long)lo * dv.seg_cap + (j - prefix[lo])];
+        const long long c = lk.cell;
+        const int a = (int)lk.dir;
+        double rho = 1.0;
+        if constexpr (sizeof(T) == 8) {
+            for (int q = 0; q < Q; ++q) rho += load_dev<T>(pop + q * C + c, s);
+        } else {
+            float drho = 0.0f;          // FP32 sum of the stored deviations
+            for (int q = 0; q < Q; ++q) drho += (float)load_dev<T>(pop + q * C + c, s);
+            rho += (double)drho;
+        }
+        const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
+        const int x = (int)(c % d.nx), y = (int)((c / d.nx) % d.ny),
+                  z = (int)(c / ((long long)d.nx * d.ny));
+        // offsets of the fluid cell, of the link end and of the link midpoint
+        const double o0 = wrap_near(x - xw[0], d.nx, d.px), o1 = wrap_near(y - xw[1], d.ny, d.py),
+                     o2 = wrap_near(z - xw[2], d.nz, d.pz);
+        const double e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
+        const double u0 = sb.V[0] + (sb.W[1] * e2 - sb.W[2] * e1);
+        const double u1 = sb.V[1] + (sb.W[2] * e0 - sb.W[0] * e2);
+        const double u2 = sb.V[2] + (sb.W[0] * e1 - sb.W[1] * e0);
+        const double eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);   // e_-a . u_w
+        const double mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
+        const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
+        const double m0 = o0 + 0.5 * ex(a), m1 = o1 + 0.5 * ey(a), m2 = o2 + 0.5 * ez(a);
+        acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];
+        acc[3] += m1 * fl[2] - m2 * fl[1];
+        acc[4] += m2 * fl[0] - m0 * fl[2];
+        acc[5] += m0 * fl[1] - m1 * fl[0];
+    }
+    __shared__ double part[FORCE_THREADS / 32][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) part[warp][i] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double v = lane < FORCE_THREADS / 32 ? part[lane][i] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) dv.fpart[((long long)b * FORCE_BLOCKS + kb) * 6 + i] = v;
+        }
+    }
+    // the last block to finish integrates the bodies
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(dv.blocks_done, 1u);
+        last = done == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    integrate_block(dv, sp, 1);
+    if (threadIdx.x == 0) *dv.blocks_done = 0u;
+}
+
+// the rigid-body step alone (bodies without fluid)
+__global__ void __launch_bounds__(256) integrate_kernel(const Device dv, const StepPtrs sp, int with_fluid) {
+    integrate_block(dv, sp, with_fluid);
 }
 
 // ---- field export / import -----------------------------------------------

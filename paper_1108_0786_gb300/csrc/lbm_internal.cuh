@@ -163,6 +163,9 @@ struct Device {
     const int *spring_list; // per-body spring indices (BodyProps::spring_first/count)
     double *fh;             // [nb][6] force, torque of the last step
     double *fpart;          // [nb][FORCE_BLOCKS][6] per-block partial sums of the force kernel
+    double *drive_f;        // [nd][3] drive forces of the current step (integrator scratch)
+    double *spring_f;       // [ns][3] spring forces on body i of each spring (integrator scratch)
+    unsigned *blocks_done;  // force blocks finished in the current step
     Link *links;            // [nb][link_side][seg_cap]
     int *seg_count;         // [nb][link_side]
     int link_side, seg_cap, remap_side;

@@ -36,7 +36,8 @@ struct lbm_s {
     // device
     bool ready = false, graphs_ready = false;
     int device = 0;
-    cudaStream_t stream = nullptr, cap = nullptr;
+    cudaStream_t stream = nullptr, cap = nullptr, side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     lbm_alloc_fn afn = nullptr;
     lbm_free_fn ffn = nullptr;
     void *actx = nullptr;
@@ -126,25 +127,38 @@ lbm::StepPtrs step_ptrs(lbm_t *h, int p) {
 }
 
 // the kernels of one step of parity p, in Algorithm 2's order; `ev`
-// (optional) brackets each kernel slot with a pair of events
-void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bool *ran = nullptr) {
+// (optional) brackets each kernel slot with a pair of events.  With `fork`
+// the boundary-cell kernel runs on a second stream concurrently with the
+// bulk kernel (they write disjoint cells) and joins before the force sums.
+void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bool *ran = nullptr,
+                  bool fork = false) {
     const lbm::StepPtrs sp = step_ptrs(h, p);
     const bool bodies = nb(h) > 0, fl = fluid(h);
-    auto run = [&](int slot, auto &&fn) {
-        if (ev) cudaEventRecord(ev[2 * slot], s);
+    auto run = [&](int slot, cudaStream_t st, auto &&fn) {
+        if (ev) cudaEventRecord(ev[2 * slot], st);
         fn();
-        if (ev) cudaEventRecord(ev[2 * slot + 1], s);
+        if (ev) cudaEventRecord(ev[2 * slot + 1], st);
         if (ran) ran[slot] = true;
     };
-    if (bodies && fl) run(LBM_KERNEL_REMAP, [&] { lbm::launch_remap(h->dv, sp, 0, s); });
-    if (fl) run(LBM_KERNEL_STREAM_COLLIDE, [&] { lbm::launch_stream_collide(h->dv, sp, s); });
-    if (fl && lbm::needs_boundary_fix(h->dv))
-        run(LBM_KERNEL_BOUNDARY, [&] { lbm::launch_boundary_fix(h->dv, sp, s); });
-    if (bodies && fl) {
-        run(LBM_KERNEL_LINKS, [&] { lbm::launch_links(h->dv, sp, s); });
-        run(LBM_KERNEL_FORCE, [&] { lbm::launch_force(h->dv, sp, s); });
+    if (bodies && fl) run(LBM_KERNEL_REMAP, s, [&] { lbm::launch_remap(h->dv, sp, 0, s); });
+    const bool boundary = fl && lbm::needs_boundary_fix(h->dv);
+    const bool forked = boundary && fork;
+    if (forked) {
+        cudaEventRecord(h->fork_ev, s);
+        cudaStreamWaitEvent(h->side, h->fork_ev, 0);
+        lbm::launch_boundary_fix(h->dv, sp, h->side);
+        cudaEventRecord(h->join_ev, h->side);
     }
-    if (bodies) run(LBM_KERNEL_INTEGRATE, [&] { lbm::launch_integrate(h->dv, sp, fl ? 1 : 0, s); });
+    if (fl) run(LBM_KERNEL_STREAM_COLLIDE, s, [&] { lbm::launch_stream_collide(h->dv, sp, s); });
+    if (boundary && !forked) run(LBM_KERNEL_BOUNDARY, s, [&] { lbm::launch_boundary_fix(h->dv, sp, s); });
+    if (bodies && fl) run(LBM_KERNEL_LINKS, s, [&] { lbm::launch_links(h->dv, sp, s); });
+    if (forked) cudaStreamWaitEvent(s, h->join_ev, 0);
+    if (bodies && fl) {
+        // momentum exchange; its last block runs the rigid-body step
+        run(LBM_KERNEL_FORCE, s, [&] { lbm::launch_force(h->dv, sp, s); });
+    } else if (bodies) {
+        run(LBM_KERNEL_INTEGRATE, s, [&] { lbm::launch_integrate(h->dv, sp, 0, s); });
+    }
 }
 
 int kernels_per_step(const lbm_t *h) {
@@ -154,8 +168,8 @@ int kernels_per_step(const lbm_t *h) {
     if (bodies && fl) n += 1;                               // remap
     if (fl) n += 1;                                         // bulk stream-collide
     if (fl) n += (bodies ? 1 : 0) + (walls ? 1 : 0);        // boundary cells
-    if (bodies && fl) n += 2;                               // links, force
-    if (bodies) n += 1;                                     // integrate
+    if (bodies && fl) n += 2;                               // links, force + rigid-body step
+    if (bodies && !fl) n += 1;                              // rigid-body step alone
     return n;
 }
 
@@ -246,6 +260,9 @@ int ensure_device(lbm_t *h) {
     int *slist;
     if ((rc = alloc_into(h, &slist, sizeof(int) * std::max<size_t>(spring_list.size(), 1)))) return rc;
     dv.spring_list = slist;
+    if ((rc = alloc_into(h, &dv.drive_f, sizeof(double) * 3 * std::max<size_t>(h->drives.size(), 1)))) return rc;
+    if ((rc = alloc_into(h, &dv.spring_f, sizeof(double) * 3 * std::max<size_t>(h->springs.size(), 1)))) return rc;
+    if ((rc = alloc_into(h, &dv.blocks_done, sizeof(unsigned) * 4))) return rc;
     const size_t nlinks = (size_t)std::max(B, 1) * dv.link_side * dv.seg_cap;
     if ((rc = alloc_into(h, &dv.links, sizeof(lbm::Link) * (B > 0 && fluid(h) ? nlinks : 1)))) return rc;
     if ((rc = alloc_into(h, &dv.seg_count, sizeof(int) * std::max(B, 1) * dv.link_side))) return rc;
@@ -264,6 +281,7 @@ int ensure_device(lbm_t *h) {
     CK(cudaMemsetAsync(h->pop[1], 0, es * lbm::Q * C, s));
     CK(cudaMemsetAsync(dv.fh, 0, sizeof(double) * 6 * std::max(B, 1), s));
     CK(cudaMemsetAsync(dv.fpart, 0, sizeof(double) * 6 * lbm::FORCE_BLOCKS * std::max(B, 1), s));
+    CK(cudaMemsetAsync(dv.blocks_done, 0, sizeof(unsigned) * 4, s));
     if (!spring_list.empty())
         CK(cudaMemcpyAsync(slist, spring_list.data(), sizeof(int) * spring_list.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dv.seg_count, 0, sizeof(int) * std::max(B, 1) * dv.link_side, s));
@@ -288,17 +306,20 @@ int ensure_device(lbm_t *h) {
 int build_graphs(lbm_t *h) {
     if (h->graphs_ready) return LBM_OK;
     if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+    if (!h->join_ev) CK(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
     for (int p = 0; p < 2; ++p) {
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-        enqueue_step(h, p, h->cap);
+        enqueue_step(h, p, h->cap, nullptr, nullptr, true);
         CK(cudaStreamEndCapture(h->cap, &g));
         CK(cudaGraphInstantiate(&h->single[p], g, 0));
         cudaGraphDestroy(g);
     }
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < CHUNK_STEPS; ++i) enqueue_step(h, i & 1, h->cap);
+    for (int i = 0; i < CHUNK_STEPS; ++i) enqueue_step(h, i & 1, h->cap, nullptr, nullptr, true);
     CK(cudaStreamEndCapture(h->cap, &g));
     CK(cudaGraphInstantiate(&h->chunk, g, 0));
     cudaGraphDestroy(g);
@@ -331,6 +352,9 @@ void release_device(lbm_t *h) {
         if (h->single[p]) cudaGraphExecDestroy(h->single[p]);
     if (h->chunk) cudaGraphExecDestroy(h->chunk);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     for (void *p : h->allocs) dfree(h, p);
     h->allocs.clear();
 }

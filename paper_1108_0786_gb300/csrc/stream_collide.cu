@@ -8,13 +8,13 @@
 // Two kernels write the populations of step n (pull scheme, two grids: src =
 // step n-1, dst = step n):
 //
-//  bulk      every cell: f_b(x) = f~_b(x - e_b) for all 19 b, LBGK relaxation
-//            to the second-order equilibrium with Guo's forcing, store;
-//            solid cells store deviation 0.  No data-dependent branches, so
-//            the kernel stays small and register-light.
-//  boundary  afterwards, only the fluid cells whose flag byte is non-zero
-//            (they lie in the cubes around the bodies or on wall faces)
-//            are recomputed and overwritten:
+//  bulk      every cell with a zero flag byte: f_b(x) = f~_b(x - e_b) for
+//            all 19 b, LBGK relaxation to the second-order equilibrium with
+//            Guo's forcing, store; solid cells store deviation 0.  No
+//            data-dependent paths, so the kernel stays small and light.
+//  boundary  only the fluid cells whose flag byte is non-zero (they lie in
+//            the cubes around the bodies or on wall faces; the bulk kernel
+//            leaves them alone, so the two kernels may run concurrently):
 //              - x was solid at n-1 (uncovered): f_b = f_eq(rho_avg, u_w(x)),
 //                rho_avg the mean density of the D3Q19 neighbours that are
 //                fluid in both epochs (1 if none), u_w at the state of step n;
@@ -237,12 +237,25 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
         for (int b = 0; b < Q; ++b) f[b][i] = solid ? (Cd)0 : g[b];
     }
     if (!active) return;
+    // fluid cells with a non-zero flag byte belong to the boundary kernel,
+    // which may run concurrently: leave them alone
+    unsigned mine = 0;
 #pragma unroll
-    for (int b = 0; b < Q; ++b) {
-        T out[V];
+    for (int i = 0; i < V; ++i) mine |= (fl[i] == 0 || (fl[i] & F_SOLID)) ? (1u << i) : 0u;
+    if (mine == (1u << V) - 1u) {
 #pragma unroll
-        for (int i = 0; i < V; ++i) out[i] = Codec<T>::st(f[b][i], scale);
-        store_vec<T, V>(dst + (long long)b * C + c0, out);
+        for (int b = 0; b < Q; ++b) {
+            T out[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) out[i] = Codec<T>::st(f[b][i], scale);
+            store_vec<T, V>(dst + (long long)b * C + c0, out);
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < Q; ++b)
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+                if (mine & (1u << i)) dst[(long long)b * C + c0 + i] = Codec<T>::st(f[b][i], scale);
     }
 }
 
@@ -250,21 +263,23 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
 // obstacles, then LBGK.  mode 0: block row blockIdx.y = body b, the threads
 // cover the cube of side 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) (the
 // cube the remap wrote); mode 1: blockIdx.y = wall face (axis * 2 + side).
+// Every load a cell needs is issued before any of them is used, so a thread
+// waits for memory about twice instead of once per direction.
 template <typename T>
 __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const StepPtrs sp, int mode) {
     using Cd = typename Codec<T>::C;
     const Domain d = dv.dom;
-    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
     int x, y, z;
     if (mode == 0) {
         const int b = blockIdx.y;
         const BodyState sb = sp.body_cur[b];
         const int half = dv.props[b].E + REMAP_MARGIN;
         const int side = 2 * half + 1;
-        if (l >= (long long)side * side * side) return;
-        x = (int)floor(sb.X[0]) - half + (int)(l % side);
-        y = (int)floor(sb.X[1]) - half + (int)((l / side) % side);
-        z = (int)floor(sb.X[2]) - half + (int)(l / ((long long)side * side));
+        if (l >= side * side * side) return;
+        x = (int)floor(sb.X[0]) - half + l % side;
+        y = (int)floor(sb.X[1]) - half + (l / side) % side;
+        z = (int)floor(sb.X[2]) - half + l / (side * side);
         if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else if (x < 0 || x >= d.nx) return;
         if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else if (y < 0 || y >= d.ny) return;
         if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else if (z < 0 || z >= d.nz) return;
@@ -273,11 +288,11 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
         const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
         if (per[axis]) return;
         const int ua = axis == 0 ? 1 : 0, va = axis == 2 ? 1 : 2;
-        if (l >= (long long)n3[ua] * n3[va]) return;
+        if (l >= n3[ua] * n3[va]) return;
         int p[3];
         p[axis] = hi ? n3[axis] - 1 : 0;
-        p[ua] = (int)(l % n3[ua]);
-        p[va] = (int)(l / n3[ua]);
+        p[ua] = l % n3[ua];
+        p[va] = l / n3[ua];
         x = p[0]; y = p[1]; z = p[2];
     }
     const long long C = d.C;
@@ -288,21 +303,30 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
     const float s = dv.f16_inv_scale;
     Cd f[Q];
     if (fc & F_SOLID_PREV) {
-        // uncovered cell: f = f_eq(rho_avg, u_w(x)) with the state of step n
+        // uncovered cell: f = f_eq(rho_avg, u_w(x)) with the state of step n;
+        // rho_avg over the D3Q19 neighbours fluid in both epochs (1 if none)
+        long long nc[Q];
+        bool ok[Q];
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            const int nx_ = x + ex(a), ny_ = y + ey(a), nz_ = z + ez(a);
+            ok[a] = !((!d.px && (nx_ < 0 || nx_ >= d.nx)) || (!d.py && (ny_ < 0 || ny_ >= d.ny)) ||
+                      (!d.pz && (nz_ < 0 || nz_ >= d.nz)));
+            nc[a] = ((long long)wrap_axis(nz_, d.nz) * d.ny + wrap_axis(ny_, d.ny)) * d.nx + wrap_axis(nx_, d.nx);
+        }
+#pragma unroll
+        for (int a = 1; a < Q; ++a) ok[a] = ok[a] && !(sp.flags_cur[nc[a]] & (F_SOLID | F_SOLID_PREV));
         double sum = 0.0;
         int cnt = 0;
+#pragma unroll
         for (int a = 1; a < Q; ++a) {
-            int nx_ = x + ex(a), ny_ = y + ey(a), nz_ = z + ez(a);
-            if ((!d.px && (nx_ < 0 || nx_ >= d.nx)) || (!d.py && (ny_ < 0 || ny_ >= d.ny)) ||
-                (!d.pz && (nz_ < 0 || nz_ >= d.nz)))
-                continue;
-            nx_ = wrap_axis(nx_, d.nx); ny_ = wrap_axis(ny_, d.ny); nz_ = wrap_axis(nz_, d.nz);
-            const long long yc = ((long long)nz_ * d.ny + ny_) * d.nx + nx_;
-            if (sp.flags_cur[yc] & (F_SOLID | F_SOLID_PREV)) continue;
             Cd drho = 0;
-            for (int bb = 0; bb < Q; ++bb) drho += Codec<T>::ld(src[bb * C + yc], s);
-            sum += 1.0 + (double)drho;
-            ++cnt;
+#pragma unroll
+            for (int bb = 0; bb < Q; ++bb) drho += Codec<T>::ld(src[bb * C + nc[a]], s);
+            if (ok[a]) {
+                sum += 1.0 + (double)drho;
+                ++cnt;
+            }
         }
         const double rho = cnt ? sum / cnt : 1.0;
         const int k = sp.bid_prev[c];
@@ -315,32 +339,36 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
             f[b] = (Cd)(wgt(b) * (rho - 1.0) + wgt(b) * rho * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
         }
     } else {
-        Cd rho_x = -1;
-        f[0] = Codec<T>::ld(src[c], s);
+        // bounce-back at walls (Eq. 4) and at obstacles of step n-1
+        Cd own[Q];
+        Cd drho = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            own[a] = Codec<T>::ld(src[(long long)a * C + c], s);
+            drho += own[a];
+        }
+        const Cd rho_x = (Cd)1 + drho;
+        f[0] = own[0];
 #pragma unroll
         for (int b = 1; b < Q; ++b) {
-            int sx = x - ex(b), sy = y - ey(b), sz = z - ez(b);
-            if ((!d.px && (sx < 0 || sx >= d.nx)) || (!d.py && (sy < 0 || sy >= d.ny)) ||
-                (!d.pz && (sz < 0 || sz >= d.nz))) {
-                f[b] = Codec<T>::ld(src[(long long)opp(b) * C + c], s);      // Eq. 4
-                continue;
+            const int sx = x - ex(b), sy = y - ey(b), sz = z - ez(b);
+            const bool wall = (!d.px && (sx < 0 || sx >= d.nx)) || (!d.py && (sy < 0 || sy >= d.ny)) ||
+                              (!d.pz && (sz < 0 || sz >= d.nz));
+            const long long sc = ((long long)wrap_axis(sz, d.nz) * d.ny + wrap_axis(sy, d.ny)) * d.nx +
+                                 wrap_axis(sx, d.nx);
+            const uint8_t fp = sp.flags_prev[sc];
+            const Cd pulled = Codec<T>::ld(src[(long long)b * C + sc], s);
+            Cd v = pulled;
+            if (wall) {
+                v = own[opp(b)];                                             // Eq. 4
+            } else if (fp & F_SOLID) {
+                const int k = sp.bid_prev[sc];
+                double u[3] = {0.0, 0.0, 0.0};
+                if (k != NO_BODY) surface_velocity(d, sp.body_prev[k], sx, sy, sz, u);
+                const Cd eu = (Cd)(ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2]);
+                v = own[opp(b)] + (Cd)(6.0 * wgt(b)) * rho_x * eu;          // moving wall
             }
-            sx = wrap_axis(sx, d.nx); sy = wrap_axis(sy, d.ny); sz = wrap_axis(sz, d.nz);
-            const long long sc = ((long long)sz * d.ny + sy) * d.nx + sx;
-            if (!(sp.flags_prev[sc] & F_SOLID)) {
-                f[b] = Codec<T>::ld(src[(long long)b * C + sc], s);          // plain pull
-                continue;
-            }
-            if (rho_x < 0) {
-                Cd drho = 0;
-                for (int a = 0; a < Q; ++a) drho += Codec<T>::ld(src[(long long)a * C + c], s);
-                rho_x = (Cd)1 + drho;
-            }
-            const int k = sp.bid_prev[sc];
-            double u[3] = {0.0, 0.0, 0.0};
-            if (k != NO_BODY) surface_velocity(d, sp.body_prev[k], sx, sy, sz, u);
-            const Cd eu = (Cd)(ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2]);
-            f[b] = Codec<T>::ld(src[(long long)opp(b) * C + c], s) + (Cd)(6.0 * wgt(b)) * rho_x * eu;
+            f[b] = v;
         }
     }
     collide<Cd, std::is_same<T, float>::value>(f, dv);
