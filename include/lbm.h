@@ -216,8 +216,17 @@ int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots);
 
 /* Launch shape of the bulk stream-collide kernel: cells_per_thread
  * consecutive x cells per thread (1, 2, 4; 8 for 16-bit storage; nx must be
- * a multiple), or 0 for the default.  Only before the first step. */
-int lbm_tune(lbm_t *h, int cells_per_thread);
+ * a multiple) and min_blocks_per_sm, a register cap that lets that many
+ * 256-thread blocks share an SM (0 for each: the defaults).  Only the
+ * compiled combinations are accepted (LBM_E_ARG otherwise).  Only before the
+ * first step.  Results do not depend on the shape. */
+int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm);
+
+/* Autotuner: time every compiled shape of the bulk kernel on this handle's
+ * lattice (`trials` launches each, on the populations of the next step,
+ * which that step rewrites) and keep the fastest for the following steps.
+ * Reports the choice through the optional outputs (synchronises). */
+int lbm_autotune(lbm_t *h, int trials, int *cells_per_thread, int *min_blocks_per_sm);
 
 /* Kernel launches one step makes (for launch accounting). */
 int lbm_kernels_per_step(lbm_t *h);

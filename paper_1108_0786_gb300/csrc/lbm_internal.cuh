@@ -153,6 +153,7 @@ struct Device {
     Domain dom;
     int precision;          // LBM_PREC_*
     int vec;                // cells per thread of the bulk stream-collide kernel
+    int minb;               // its minimum resident blocks per SM (0: the default variant)
     int nb, ns, nd;
     double tau, omega, g[3];
     int forced;
@@ -184,6 +185,8 @@ void launch_stream_collide(const Device &dv, const StepPtrs &sp, cudaStream_t s)
 void launch_boundary_fix(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 bool needs_boundary_fix(const Device &dv);
 bool valid_vector_width(const Device &dv, int v);
+bool valid_variant(const Device &dv, int v, int minb);
+int list_variants(const Device &dv, int *vec, int *minb, int max);
 int default_vector_width(const Device &dv);
 void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s);

@@ -32,7 +32,7 @@ struct lbm_s {
     std::vector<Spring> springs;
     std::vector<DriveTerm> drives;
     int hist_cap = 0;
-    int tune_vec = 0;
+    int tune_vec = 0, tune_minb = 0;
     // device
     bool ready = false, graphs_ready = false;
     int device = 0;
@@ -220,6 +220,7 @@ int ensure_device(lbm_t *h) {
     dv.seg_cap = dv.link_side * dv.link_side * 18;
     dv.hist_cap = h->hist_cap;
     dv.vec = h->tune_vec ? h->tune_vec : lbm::default_vector_width(dv);
+    dv.minb = h->tune_minb;
 
     // per-body reciprocals and term lists (drive terms and springs keep
     // their creation order within a body)
@@ -755,18 +756,64 @@ int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots) {
     return check_status(h);
 }
 
-int lbm_tune(lbm_t *h, int cells_per_thread) {
-    if (!h) return LBM_E_ARG;
+int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm) {
+    if (!h || min_blocks_per_sm < 0) return LBM_E_ARG;
     if (h->ready) return fail(h, LBM_E_STATE, "lbm_tune must come before the first step");
-    if (cells_per_thread != 0) {
+    if (cells_per_thread != 0 || min_blocks_per_sm != 0) {
         lbm::Device probe{};
         probe.dom.nx = h->nx;
         probe.precision = h->precision;
-        if (!lbm::valid_vector_width(probe, cells_per_thread))
-            return fail(h, LBM_E_ARG, "%d cells per thread is not valid for nx = %d and this precision",
-                        cells_per_thread, h->nx);
+        const int v = cells_per_thread ? cells_per_thread : lbm::default_vector_width(probe);
+        if (!lbm::valid_variant(probe, v, min_blocks_per_sm))
+            return fail(h, LBM_E_ARG, "no bulk kernel with %d cells per thread and %d blocks per SM for nx = %d",
+                        v, min_blocks_per_sm, h->nx);
     }
     h->tune_vec = cells_per_thread;
+    h->tune_minb = min_blocks_per_sm;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_t *h, int trials, int *best_cells, int *best_blocks) {
+    if (!h || trials < 1) return LBM_E_ARG;
+    int rc = ensure_device(h);
+    if (rc) return rc;
+    if ((rc = sync_and_check(h))) return rc;
+    if (fluid(h)) {
+        int vec[64], minb[64];
+        const int n = lbm::list_variants(h->dv, vec, minb, 64);
+        // time every variant on the buffers of the next step; its populations
+        // are rewritten in full by that step, so the state is unchanged
+        const lbm::StepPtrs sp = step_ptrs(h, (int)(h->steps & 1));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int bv = h->dv.vec, bm = h->dv.minb;
+        for (int i = 0; i < n; ++i) {
+            lbm::Device d = h->dv;
+            d.vec = vec[i];
+            d.minb = minb[i];
+            lbm::launch_stream_collide(d, sp, h->stream);
+            CK(cudaEventRecord(e0, h->stream));
+            for (int t = 0; t < trials; ++t) lbm::launch_stream_collide(d, sp, h->stream);
+            CK(cudaEventRecord(e1, h->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; bv = vec[i]; bm = minb[i]; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        h->dv.vec = h->tune_vec = bv;
+        h->dv.minb = h->tune_minb = bm;
+        // the step graphs bake in the launch shape: rebuild them
+        for (int p = 0; p < 2; ++p)
+            if (h->single[p]) { cudaGraphExecDestroy(h->single[p]); h->single[p] = nullptr; }
+        if (h->chunk) { cudaGraphExecDestroy(h->chunk); h->chunk = nullptr; }
+        h->graphs_ready = false;
+    }
+    if (best_cells) *best_cells = h->dv.vec;
+    if (best_blocks) *best_blocks = h->dv.minb;
     return LBM_OK;
 }
 

@@ -175,8 +175,23 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     }
 }
 
-template <typename T, int V, int BX, int BY>
-__global__ void __launch_bounds__(BX * BY)
+// stores of the cells of a thread that are not boundary cells (rare path,
+// kept out of line)
+template <typename T, int V, typename Cd>
+__device__ __noinline__ void store_partial(const Cd (&f)[Q][V], const uint8_t (&fl)[V], T *dst, long long C,
+                                           long long c0, float scale) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        if (!(fl[i] == 0 || (fl[i] & F_SOLID))) continue;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + i] = Codec<T>::st(f[b][i], scale);
+    }
+}
+
+// MINB == 1 leaves the register budget to the compiler (an explicit minimum
+// of one block lets it spend far more registers than it needs)
+template <typename T, int V, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB)
 bulk_kernel(const Device dv, const StepPtrs sp) {
     using Cd = typename Codec<T>::C;
     const Domain d = dv.dom;
@@ -239,10 +254,10 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
     if (!active) return;
     // fluid cells with a non-zero flag byte belong to the boundary kernel,
     // which may run concurrently: leave them alone
-    unsigned mine = 0;
+    bool all_mine = true;
 #pragma unroll
-    for (int i = 0; i < V; ++i) mine |= (fl[i] == 0 || (fl[i] & F_SOLID)) ? (1u << i) : 0u;
-    if (mine == (1u << V) - 1u) {
+    for (int i = 0; i < V; ++i) all_mine = all_mine && (fl[i] == 0 || (fl[i] & F_SOLID));
+    if (all_mine) {
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
             T out[V];
@@ -250,13 +265,9 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
             for (int i = 0; i < V; ++i) out[i] = Codec<T>::st(f[b][i], scale);
             store_vec<T, V>(dst + (long long)b * C + c0, out);
         }
-    } else {
-#pragma unroll
-        for (int b = 0; b < Q; ++b)
-#pragma unroll
-            for (int i = 0; i < V; ++i)
-                if (mine & (1u << i)) dst[(long long)b * C + c0 + i] = Codec<T>::st(f[b][i], scale);
+        return;
     }
+    store_partial<T, V>(f, fl, dst, C, c0, scale);
 }
 
 // Cells with a non-zero flag byte: refill, bounce-back at walls and moving
@@ -377,20 +388,56 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
     for (int b = 0; b < Q; ++b) dst[(long long)b * C + c] = Codec<T>::st(f[b], dv.f16_scale);
 }
 
-template <typename T, int V, int BX, int BY>
+template <typename T, int V, int BX, int BY, int MINB>
 void launch_bulk(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     const int nxq = dv.dom.nx / V;
     dim3 grid((nxq + BX - 1) / BX, (dv.dom.ny + BY - 1) / BY, dv.dom.nz);
-    bulk_kernel<T, V, BX, BY><<<grid, dim3(BX, BY), 0, s>>>(dv, sp);
+    bulk_kernel<T, V, BX, BY, MINB><<<grid, dim3(BX, BY), 0, s>>>(dv, sp);
 }
 
-// launch shapes: V cells per thread, BX (a multiple of 32) x BY threads
-template <typename T, int V>
+// launch shapes: V cells per thread in blocks of 256 threads (BX a multiple
+// of 32 along x); MINB > 1 caps the registers so that MINB blocks fit an SM
+template <typename T, int V, int MINB>
 void launch_shape(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     const int nxq = dv.dom.nx / V;
-    if (nxq >= 128) launch_bulk<T, V, 128, 2>(dv, sp, s);
-    else if (nxq >= 64) launch_bulk<T, V, 64, 4>(dv, sp, s);
-    else launch_bulk<T, V, 32, 8>(dv, sp, s);
+    if (nxq >= 128) launch_bulk<T, V, 128, 2, MINB>(dv, sp, s);
+    else launch_bulk<T, V, 32, 8, MINB>(dv, sp, s);
+}
+
+using Launcher = void (*)(const Device &, const StepPtrs &, cudaStream_t);
+struct Variant {
+    int precision, vec, minb;
+    Launcher fn;
+};
+
+// the compiled variants of the bulk kernel; the first entry of a precision
+// and width is its default
+const Variant kVariants[] = {
+    {0, 1, 1, launch_shape<double, 1, 1>},
+    {0, 2, 1, launch_shape<double, 2, 1>},
+    {1, 2, 1, launch_shape<float, 2, 1>},
+    {1, 2, 4, launch_shape<float, 2, 4>},
+    {1, 1, 1, launch_shape<float, 1, 1>},
+    {1, 4, 1, launch_shape<float, 4, 1>},
+    {2, 4, 1, launch_shape<__half, 4, 1>},
+    {2, 2, 1, launch_shape<__half, 2, 1>},
+    {2, 2, 3, launch_shape<__half, 2, 3>},
+    {2, 8, 1, launch_shape<__half, 8, 1>},
+    {2, 1, 1, launch_shape<__half, 1, 1>},
+    {3, 4, 1, launch_shape<__nv_bfloat16, 4, 1>},
+    {3, 2, 1, launch_shape<__nv_bfloat16, 2, 1>},
+    {3, 2, 3, launch_shape<__nv_bfloat16, 2, 3>},
+    {3, 8, 1, launch_shape<__nv_bfloat16, 8, 1>},
+    {3, 1, 1, launch_shape<__nv_bfloat16, 1, 1>},
+};
+const Variant *find_variant(int precision, int vec, int minb) {
+    const Variant *first = nullptr;
+    for (const Variant &v : kVariants) {
+        if (v.precision != precision || v.vec != vec) continue;
+        if (!first) first = &v;
+        if (minb == 0 || v.minb == minb) return minb == 0 ? first : &v;
+    }
+    return nullptr;
 }
 
 template <typename T>
@@ -410,12 +457,11 @@ void launch_boundary(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
 }  // namespace
 
 bool valid_vector_width(const Device &dv, int v) {
-    if (v < 1 || dv.dom.nx % v) return false;
-    switch (dv.precision) {
-    case 0: return v == 1 || v == 2;
-    case 1: return v == 1 || v == 2 || v == 4;
-    default: return v == 1 || v == 2 || v == 4 || v == 8;
-    }
+    return v >= 1 && dv.dom.nx % v == 0 && find_variant(dv.precision, v, 0) != nullptr;
+}
+
+bool valid_variant(const Device &dv, int v, int minb) {
+    return valid_vector_width(dv, v) && find_variant(dv.precision, v, minb) != nullptr;
 }
 
 int default_vector_width(const Device &dv) {
@@ -425,30 +471,21 @@ int default_vector_width(const Device &dv) {
     return 1;
 }
 
+int list_variants(const Device &dv, int *vec, int *minb, int max) {
+    int n = 0;
+    for (const Variant &v : kVariants)
+        if (v.precision == dv.precision && dv.dom.nx % v.vec == 0 && n < max) {
+            vec[n] = v.vec;
+            minb[n] = v.minb;
+            ++n;
+        }
+    return n;
+}
+
 void launch_stream_collide(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
-    const int v = dv.vec;
-    switch (dv.precision) {
-    case 0:
-        if (v == 2) launch_shape<double, 2>(dv, sp, s); else launch_shape<double, 1>(dv, sp, s);
-        break;
-    case 1:
-        if (v == 4) launch_shape<float, 4>(dv, sp, s);
-        else if (v == 2) launch_shape<float, 2>(dv, sp, s);
-        else launch_shape<float, 1>(dv, sp, s);
-        break;
-    case 2:
-        if (v == 8) launch_shape<__half, 8>(dv, sp, s);
-        else if (v == 4) launch_shape<__half, 4>(dv, sp, s);
-        else if (v == 2) launch_shape<__half, 2>(dv, sp, s);
-        else launch_shape<__half, 1>(dv, sp, s);
-        break;
-    default:
-        if (v == 8) launch_shape<__nv_bfloat16, 8>(dv, sp, s);
-        else if (v == 4) launch_shape<__nv_bfloat16, 4>(dv, sp, s);
-        else if (v == 2) launch_shape<__nv_bfloat16, 2>(dv, sp, s);
-        else launch_shape<__nv_bfloat16, 1>(dv, sp, s);
-        break;
-    }
+    const Variant *v = find_variant(dv.precision, dv.vec, dv.minb);
+    if (!v) v = find_variant(dv.precision, 1, 0);
+    v->fn(dv, sp, s);
 }
 
 void launch_boundary_fix(const Device &dv, const StepPtrs &sp, cudaStream_t s) {

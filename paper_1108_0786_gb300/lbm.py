@@ -38,7 +38,7 @@ EXPORTED = (
     "lbm_set_body_state", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_steps_done",
     "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
-    "lbm_tune", "lbm_kernels_per_step", "lbm_bytes_per_cell", "lbm_last_error",
+    "lbm_tune", "lbm_autotune", "lbm_kernels_per_step", "lbm_bytes_per_cell", "lbm_last_error",
     "lbm_momentum_exchange_static",
 )
 
@@ -88,7 +88,8 @@ def load_library(path: Optional[str] = None):
         "lbm_save": ([P, ctypes.c_char_p], I),
         "lbm_load": ([P, ctypes.c_char_p], I),
         "lbm_time_kernels": ([P, I, DP, I], I),
-        "lbm_tune": ([P, I], I),
+        "lbm_tune": ([P, I, I], I),
+        "lbm_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "lbm_kernels_per_step": ([P], I),
         "lbm_bytes_per_cell": ([P], I),
         "lbm_last_error": ([P], ctypes.c_char_p),
@@ -212,9 +213,16 @@ class Lattice:
         return self._check(self._lib.lbm_set_fields(self._h, FIELD_POP, p.ctypes.data_as(ctypes.c_void_p),
                                                     DTYPE_F64))
 
-    def tune(self, cells_per_thread):
-        """Cells per thread of the bulk stream-collide kernel (0: default)."""
-        return self._check(self._lib.lbm_tune(self._h, int(cells_per_thread)))
+    def tune(self, cells_per_thread, min_blocks_per_sm=0):
+        """Launch shape of the bulk stream-collide kernel (0: default)."""
+        return self._check(self._lib.lbm_tune(self._h, int(cells_per_thread), int(min_blocks_per_sm)))
+
+    def autotune(self, trials=5):
+        """Time the compiled bulk-kernel shapes and keep the fastest;
+        returns (cells_per_thread, min_blocks_per_sm)."""
+        v, m = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self._lib.lbm_autotune(self._h, int(trials), ctypes.byref(v), ctypes.byref(m)))
+        return v.value, m.value
 
     def enable_history(self, capacity):
         return self._check(self._lib.lbm_enable_history(self._h, int(capacity)))

@@ -68,6 +68,16 @@ def test_create_rejects_bad_arguments(lib, args):
     assert lib.lbm_create(*args, ctypes.byref(h)) == lbm.E_ARG
 
 
+def test_tune_accepts_only_compiled_shapes(lib):
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(16, 8, 8, 1.0, 7, ctypes.byref(h)) == 0
+    assert lib.lbm_tune(h, 2, 4) == 0
+    assert lib.lbm_tune(h, 2, 7) == lbm.E_ARG
+    assert lib.lbm_tune(h, 3, 0) == lbm.E_ARG          # 16 is not a multiple of 3
+    assert lib.lbm_tune(h, 0, 0) == 0
+    lib.lbm_destroy(h)
+
+
 def test_bytes_per_cell_by_precision(lib):
     for prec, es in ((lbm.PREC_F64, 8), (lbm.PREC_F32, 4), (lbm.PREC_F16, 2), (lbm.PREC_BF16, 2)):
         h = ctypes.c_void_p()

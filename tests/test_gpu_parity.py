@@ -276,17 +276,26 @@ def test_graph_steps_equal_eager_steps():
     assert np.array_equal(a.bodies(), b.bodies())
 
 
-@pytest.mark.parametrize("precision,widths", [("f64", (1, 2)), ("f32", (1, 2, 4)),
-                                              ("f16", (1, 2, 4, 8)), ("bf16", (1, 2, 4, 8))])
-def test_launch_shapes_are_bitwise_identical(precision, widths):
-    """The bulk kernel's cells-per-thread setting changes only the memory
-    access pattern: every setting gives the same bits."""
+@pytest.mark.parametrize("precision,shapes", [
+    ("f64", ((1, 0), (2, 0))),
+    ("f32", ((1, 0), (2, 0), (2, 4), (4, 0))),
+    ("f16", ((1, 0), (2, 0), (2, 3), (4, 0), (8, 0))),
+    ("bf16", ((1, 0), (2, 0), (2, 3), (4, 0), (8, 0)))])
+def test_launch_shapes_are_bitwise_identical(precision, shapes):
+    """The bulk kernel's launch shape changes only the memory access
+    pattern and register budget: every shape gives the same bits, and so
+    does the autotuner's pick."""
     sc = wl.three_sphere_periodic()
     ref_pop = None
-    for v in widths:
+    for v, mb in list(shapes) + [("auto", 0)]:
         lat = lbm.from_scenario(sc, precision=precision)
-        lat.tune(v)
-        lat.step(40)
+        if v == "auto":
+            lat.step(1)
+            lat.autotune(2)
+            lat.step(39)
+        else:
+            lat.tune(v, mb)
+            lat.step(40)
         pop = lat.pop()
         if ref_pop is None:
             ref_pop = pop
