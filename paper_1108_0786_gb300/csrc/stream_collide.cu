@@ -175,19 +175,6 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     }
 }
 
-// stores of the cells of a thread that are not boundary cells (rare path,
-// kept out of line)
-template <typename T, int V, typename Cd>
-__device__ __noinline__ void store_partial(const Cd (&f)[Q][V], const uint8_t (&fl)[V], T *dst, long long C,
-                                           long long c0, float scale) {
-#pragma unroll
-    for (int i = 0; i < V; ++i) {
-        if (!(fl[i] == 0 || (fl[i] & F_SOLID))) continue;
-#pragma unroll
-        for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + i] = Codec<T>::st(f[b][i], scale);
-    }
-}
-
 // MINB == 1 leaves the register budget to the compiler (an explicit minimum
 // of one block lets it spend far more registers than it needs)
 template <typename T, int V, int BX, int BY, int MINB>
@@ -267,7 +254,11 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
         }
         return;
     }
-    store_partial<T, V>(f, fl, dst, C, c0, scale);
+#pragma unroll
+    for (int b = 0; b < Q; ++b)
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+            if (fl[i] == 0 || (fl[i] & F_SOLID)) dst[(long long)b * C + c0 + i] = Codec<T>::st(f[b][i], scale);
 }
 
 // Cells with a non-zero flag byte: refill, bounce-back at walls and moving
