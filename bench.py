@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--nz", type=int, default=256)
     ap.add_argument("--no-variants", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--shape", default="auto",
+                    help="bulk-kernel shape 'cells_per_thread,min_blocks_per_sm', or 'auto' for the autotuner")
     return ap.parse_args()
 
 
@@ -303,8 +305,12 @@ def run_ours(args, world, rank, local):
     device = torch.device("cuda", local)
     sc = workload(args, rank)
     lat = lbm.from_scenario(sc, precision=args.precision)
+    if args.shape != "auto":
+        shape = tuple(int(v) for v in args.shape.split(","))
+        lat.tune(*shape)               # a fixed bulk-kernel shape must be set before the first step
     lat.step(1)
-    shape = lat.autotune(5)            # the library's autotuner picks the bulk-kernel shape
+    if args.shape == "auto":
+        shape = lat.autotune(5)        # the library's autotuner picks the bulk-kernel shape
     lat.step(args.warmup)
     lat.sync()
     with ClockSampler(local) as clk:

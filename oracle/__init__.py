@@ -75,6 +75,9 @@ def _load():
     lib.lbm_ref_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), DP]
     lib.lbm_ref_equilibrium.argtypes = [D, DP, DP]
     lib.lbm_ref_body_props.argtypes = [P, I, DP]
+    lib.lbm_ref_adjoint.argtypes = [P, I, DP, DP, DP, DP, DP, DP, DP]
+    lib.lbm_ref_flag_digest.argtypes = [P]
+    lib.lbm_ref_flag_digest.restype = ctypes.c_ulonglong
     lib.lbm_ref_last_error.argtypes = [P]
     lib.lbm_ref_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -143,6 +146,8 @@ class Oracle:
             raise OracleError(rc, "create failed")
         self._h = h
         self.nbodies = 0
+        self.nsprings = 0
+        self.ndrives = 0
 
     def _check(self, rc):
         if rc < 0:
@@ -165,12 +170,16 @@ class Oracle:
         return b
 
     def add_spring(self, i, j, k, rest, damping):
-        return self._check(self._lib.lbm_ref_add_spring(self._h, i, j, float(k), float(rest),
-                                                        float(damping)))
+        s = self._check(self._lib.lbm_ref_add_spring(self._h, i, j, float(k), float(rest),
+                                                     float(damping)))
+        self.nsprings += 1
+        return s
 
     def set_drive(self, body, amp, freq, phase):
-        return self._check(self._lib.lbm_ref_set_drive(self._h, body, float(amp), float(freq),
-                                                       float(phase)))
+        d = self._check(self._lib.lbm_ref_set_drive(self._h, body, float(amp), float(freq),
+                                                    float(phase)))
+        self.ndrives += 1
+        return d
 
     def set_drive_window(self, term, t_off):
         return self._check(self._lib.lbm_ref_set_drive_window(self._h, term, float(t_off)))
@@ -222,6 +231,26 @@ class Oracle:
             raise ValueError(what)
         self._check(self._lib.lbm_ref_get_fields(self._h, int(what), out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    def adjoint(self, n, seed):
+        """Advance n steps and return the gradient of sum(seed * final body
+        states) (seed: nbodies x 13) as a dict: ``state``, ``prev``, ``pop``,
+        ``drive`` (nd x 2: amp, phase), ``spring`` (ns x 3: k, rest,
+        damping), ``body`` (nb x 5: mass, I1, I2, I3, volume)."""
+        sd = np.ascontiguousarray(seed, dtype=np.float64).reshape(self.nbodies, 13)
+        nz, ny, nx = self.shape
+        out = {"state": np.zeros((self.nbodies, 13)), "prev": np.zeros((self.nbodies, 13)),
+               "pop": np.zeros((19, nz, ny, nx)), "drive": np.zeros((self.ndrives, 2)),
+               "spring": np.zeros((self.nsprings, 3)), "body": np.zeros((self.nbodies, 5))}
+        ptr = [_dp(out[k]) if out[k].size else None
+               for k in ("state", "prev", "pop", "drive", "spring", "body")]
+        self._check(self._lib.lbm_ref_adjoint(self._h, int(n), _dp(sd), *ptr))
+        return out
+
+    @property
+    def flag_digest(self):
+        """Running digest of the obstacle map of every step taken so far."""
+        return int(self._lib.lbm_ref_flag_digest(self._h))
 
     def rho(self):
         return self.field(FIELD_RHO)

@@ -116,6 +116,8 @@ struct ref_lbm {
     double Fh[MAX_BODIES][3], Th[MAX_BODIES][3];
     long step;
     int started;
+    unsigned long long flag_digest;   /* running digest of every step's obstacle map */
+    struct tape *tape;                /* recording for the reverse sweep, or NULL */
     char err[256];
 };
 
@@ -623,6 +625,33 @@ static int integrate_bodies(ref_lbm *h)
     return REF_OK;
 }
 
+/* ---- recording for the reverse sweep ------------------------------------ */
+
+/* Everything the reverse sweep reads, for each recorded step j (forward step
+ * n = t0 + j): the post-collision populations entering the step (G^{n-1}),
+ * the pre-collision populations it forms (stream + refill), the obstacle
+ * map of epoch n-1, the body states n-1 and n and the hydrodynamic force and
+ * torque of the step.  Index n of Gin and bid holds the final ones, index
+ * n + 1 of state the final body states. */
+struct tape {
+    int n, cap;
+    long t0;
+    double *Gin, *Fpre, *fh;
+    short *bid;
+    body_t *state;
+};
+
+/* FNV-1a digest of the obstacle map of a step, folded into a running value */
+static unsigned long long digest_map(unsigned long long d, const short *bid, long C)
+{
+    if (d == 0) d = 1469598103934665603ULL;
+    for (long c = 0; c < C; ++c) {
+        d ^= (unsigned long long)(unsigned short)bid[c];
+        d *= 1099511628211ULL;
+    }
+    return d;
+}
+
 /* ---- one coupled step (Algorithm 2) ------------------------------------- */
 
 static int one_step(ref_lbm *h)
@@ -635,16 +664,33 @@ static int one_step(ref_lbm *h)
         for (int k = 0; k < h->nb; ++k) h->body_prev[k] = h->body[k];
         h->started = 1;
     }
+    struct tape *tp = h->tape;
+    const long QC = (long)Q * h->C;
     int rc = map_bodies(h, h->bid_now);             /* 1. map */
     if (rc) return rc;
+    h->flag_digest = digest_map(h->flag_digest, h->bid_now, h->C);
+    if (tp) {
+        const int j = tp->n;
+        memcpy(tp->Gin + j * QC, h->G, sizeof(double) * QC);
+        memcpy(tp->bid + j * h->C, h->bid_prev, sizeof(short) * h->C);
+        memcpy(tp->state + (long)j * h->nb, h->body_prev, sizeof(body_t) * h->nb);
+        memcpy(tp->state + (long)(j + 1) * h->nb, h->body, sizeof(body_t) * h->nb);
+    }
     stream(h);                                       /* 2. stream + bounce-back */
     refill(h);                                       /*    uncovered cells */
+    if (tp) memcpy(tp->Fpre + tp->n * QC, h->F, sizeof(double) * QC);
     collide(h);                                      /*    LBGK */
     hydro_force(h);                                  /* 3. F_hydro, T_hydro */
+    if (tp) {
+        double *f = tp->fh + (long)tp->n * h->nb * 6;
+        for (int k = 0; k < h->nb; ++k)
+            for (int i = 0; i < 3; ++i) { f[6 * k + i] = h->Fh[k][i]; f[6 * k + 3 + i] = h->Th[k][i]; }
+    }
     rc = integrate_bodies(h);                        /* 4.-5. drive, springs, pe */
     if (rc) return rc;
     short *t = h->bid_prev; h->bid_prev = h->bid_now; h->bid_now = t;
     h->step++;
+    if (tp) tp->n++;
     return REF_OK;
 }
 
@@ -756,3 +802,462 @@ int lbm_ref_num_threads(void)
 }
 
 const char *lbm_ref_last_error(ref_lbm *h) { return h ? h->err : "null handle"; }
+
+/* ==========================================================================
+ * Reverse mode.  The gradient of J = sum_b seed_b . S_b(n0 + n), a linear
+ * function of the body states after n steps, with respect to the drive
+ * amplitudes and phases, the spring constants, rest lengths and dampings,
+ * the body masses, principal moments of inertia and volumes, and the body
+ * states and populations the run starts from.
+ *
+ * The obstacle maps of the recorded run are held fixed (the cell-centre test
+ * of Sec. 2.3 is piecewise constant in the body positions), so J is the
+ * smooth function of the parameters that the recorded map sequence defines.
+ * The sweep applies, step by step in reverse, the transposed Jacobian of
+ * each part of the step in reverse order: rigid-body step, momentum-exchange
+ * force, collision, refill, stream with bounce-back.  The recording keeps
+ * every step (no checkpoints): this is the plain version.
+ * ========================================================================== */
+
+/* adjoint of the surface velocity u_w = V + Omega x (p - X) of body b, for
+ * the scalar uh . u_w: adds to the adjoint sa[13] of the body state */
+static void adj_surface_velocity(const ref_lbm *h, const body_t *b, const double p[3], const double uh[3],
+                                 double *sa)
+{
+    double o[3], c[3];
+    body_offset(h, b, p, o);
+    for (int i = 0; i < 3; ++i) sa[7 + i] += uh[i];
+    cross(o, uh, c);                       /* uh . (Om x o) = Om . (o x uh) */
+    for (int i = 0; i < 3; ++i) sa[10 + i] += c[i];
+    cross(b->Om, uh, c);                   /* d/dX = -(uh x Om) = Om x uh */
+    for (int i = 0; i < 3; ++i) sa[i] += c[i];
+}
+
+/* adjoint of R(q) (rot_matrix): qh += sum_ij Rh_ij dR_ij/dq */
+static void adj_rot_matrix(const double q[4], const double Rh[3][3], double qh[4])
+{
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    qh[2] += -4 * y * Rh[0][0]; qh[3] += -4 * z * Rh[0][0];
+    qh[1] += 2 * y * Rh[0][1]; qh[2] += 2 * x * Rh[0][1]; qh[0] += -2 * z * Rh[0][1]; qh[3] += -2 * w * Rh[0][1];
+    qh[1] += 2 * z * Rh[0][2]; qh[3] += 2 * x * Rh[0][2]; qh[0] += 2 * y * Rh[0][2]; qh[2] += 2 * w * Rh[0][2];
+    qh[1] += 2 * y * Rh[1][0]; qh[2] += 2 * x * Rh[1][0]; qh[0] += 2 * z * Rh[1][0]; qh[3] += 2 * w * Rh[1][0];
+    qh[1] += -4 * x * Rh[1][1]; qh[3] += -4 * z * Rh[1][1];
+    qh[2] += 2 * z * Rh[1][2]; qh[3] += 2 * y * Rh[1][2]; qh[0] += -2 * x * Rh[1][2]; qh[1] += -2 * w * Rh[1][2];
+    qh[1] += 2 * z * Rh[2][0]; qh[3] += 2 * x * Rh[2][0]; qh[0] += -2 * y * Rh[2][0]; qh[2] += -2 * w * Rh[2][0];
+    qh[2] += 2 * z * Rh[2][1]; qh[3] += 2 * y * Rh[2][1]; qh[0] += 2 * x * Rh[2][1]; qh[1] += 2 * w * Rh[2][1];
+    qh[1] += -4 * x * Rh[2][2]; qh[2] += -4 * y * Rh[2][2];
+}
+
+/* Reverse of integrate_bodies at step t from the states S (state n) and the
+ * hydrodynamic loads fhyd (nb x 6).  Sn: adjoint of state n + 1 (input);
+ * Sc: adjoint of state n (added to); Fa: adjoint of the hydrodynamic force
+ * and torque (output); gd, gs, gb: parameter gradients (added to). */
+static void integrate_adjoint(const ref_lbm *h, const body_t *S, const double *fhyd, long t,
+                              const double (*Sn)[13], double (*Sc)[13], double (*Fa)[6],
+                              double *gd, double *gs, double *gb)
+{
+    const int nb = h->nb;
+    double (*Ftot)[3] = calloc(nb, sizeof *Ftot);
+    double (*Fh)[3] = calloc(nb, sizeof *Fh);
+    double (*Rh)[3][3] = calloc(nb, sizeof *Rh);
+    /* the total force of the forward step, in the same order */
+    for (int k = 0; k < nb; ++k)
+        for (int i = 0; i < 3; ++i) Ftot[k][i] = fhyd[6 * k + i] + h->g[i] * S[k].volume;
+    for (int d = 0; d < h->nd; ++d) {
+        const drive_t *dr = &h->drive[d];
+        double omega = 2.0 * M_PI * dr->freq;
+        if ((double)t < dr->phase / omega || (double)t >= dr->t_off) continue;
+        double R[3][3];
+        rot_matrix(S[dr->body].q, R);
+        double f = dr->amp * sin(omega * t - dr->phase);
+        for (int i = 0; i < 3; ++i) Ftot[dr->body][i] += f * R[i][0];
+    }
+    for (int s = 0; s < h->ns; ++s) {
+        const spring_t *sp = &h->spring[s];
+        const body_t *bi = &S[sp->i], *bj = &S[sp->j];
+        double d[3] = {bi->X[0] - bj->X[0], bi->X[1] - bj->X[1], bi->X[2] - bj->X[2]};
+        double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int i = 0; i < 3; ++i) {
+            double dir = len > 0 ? d[i] / len : 0.0;
+            double fi = -sp->k * (len - sp->rest) * dir - sp->gamma * (bi->V[i] - bj->V[i]);
+            Ftot[sp->i][i] += fi;
+            Ftot[sp->j][i] -= fi;
+        }
+    }
+    /* semi-implicit Euler, body by body */
+    for (int k = 0; k < nb; ++k) {
+        const body_t *b = &S[k];
+        const double *sn = Sn[k];
+        double R[3][3];
+        rot_matrix(b->q, R);
+        const double *T = fhyd + 6 * k + 3;
+        double beta[3], Tb[3], Om1[3];
+        for (int i = 0; i < 3; ++i) beta[i] = R[0][i] * T[0] + R[1][i] * T[1] + R[2][i] * T[2];
+        for (int i = 0; i < 3; ++i) Tb[i] = beta[i] / b->inertia[i];
+        for (int i = 0; i < 3; ++i) Om1[i] = b->Om[i] + R[i][0] * Tb[0] + R[i][1] * Tb[1] + R[i][2] * Tb[2];
+        const double w = b->q[0], v[3] = {b->q[1], b->q[2], b->q[3]};
+        double c[3];
+        cross(Om1, v, c);
+        double q4[4] = {w - 0.5 * (Om1[0] * v[0] + Om1[1] * v[1] + Om1[2] * v[2]),
+                        v[0] + 0.5 * (w * Om1[0] + c[0]), v[1] + 0.5 * (w * Om1[1] + c[1]),
+                        v[2] + 0.5 * (w * Om1[2] + c[2])};
+        double nn = sqrt(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
+        double q1[4] = {q4[0] / nn, q4[1] / nn, q4[2] / nn, q4[3] / nn};
+        /* q1 = q4 / |q4| */
+        double dot = 0.0, qh4[4];
+        for (int i = 0; i < 4; ++i) dot += q1[i] * sn[3 + i];
+        for (int i = 0; i < 4; ++i) qh4[i] = (sn[3 + i] - q1[i] * dot) / nn;
+        /* q4 = q + (0, Om1) (x) q / 2 */
+        const double qv[3] = {qh4[1], qh4[2], qh4[3]};
+        double t1[3], t2[3];
+        Sc[k][3] += qh4[0] + 0.5 * (qv[0] * Om1[0] + qv[1] * Om1[1] + qv[2] * Om1[2]);
+        cross(qv, Om1, t1);
+        for (int i = 0; i < 3; ++i) Sc[k][4 + i] += qv[i] - 0.5 * qh4[0] * Om1[i] + 0.5 * t1[i];
+        double Oh1[3];
+        cross(v, qv, t2);
+        for (int i = 0; i < 3; ++i) Oh1[i] = sn[10 + i] - 0.5 * qh4[0] * v[i] + 0.5 * w * qv[i] + 0.5 * t2[i];
+        /* Om1 = Om + R diag(1/I) R^T T */
+        double alpha[3];
+        for (int i = 0; i < 3; ++i) alpha[i] = R[0][i] * Oh1[0] + R[1][i] * Oh1[1] + R[2][i] * Oh1[2];
+        for (int i = 0; i < 3; ++i) {
+            Sc[k][10 + i] += Oh1[i];
+            Fa[k][3 + i] = R[i][0] * alpha[0] / b->inertia[0] + R[i][1] * alpha[1] / b->inertia[1] +
+                           R[i][2] * alpha[2] / b->inertia[2];
+            gb[5 * k + 1 + i] += -beta[i] * alpha[i] / (b->inertia[i] * b->inertia[i]);
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int jj = 0; jj < 3; ++jj)
+                Rh[k][i][jj] += Oh1[i] * beta[jj] / b->inertia[jj] + T[i] * alpha[jj] / b->inertia[jj];
+        /* X1 = X + V1, V1 = V + F / m */
+        double Vh1[3], F2 = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            Vh1[i] = sn[7 + i] + sn[i];
+            Sc[k][i] += sn[i];
+            Sc[k][7 + i] += Vh1[i];
+            Fh[k][i] = Vh1[i] / b->m;
+            Fa[k][i] = Fh[k][i];
+            F2 += Vh1[i] * Ftot[k][i];
+            gb[5 * k + 4] += h->g[i] * Fh[k][i];
+        }
+        gb[5 * k] += -F2 / (b->m * b->m);
+    }
+    /* drive terms */
+    for (int d = 0; d < h->nd; ++d) {
+        const drive_t *dr = &h->drive[d];
+        double omega = 2.0 * M_PI * dr->freq;
+        if ((double)t < dr->phase / omega || (double)t >= dr->t_off) continue;
+        double R[3][3];
+        rot_matrix(S[dr->body].q, R);
+        const double sn_ = sin(omega * t - dr->phase), cs = cos(omega * t - dr->phase);
+        const double *fh_ = Fh[dr->body];
+        double proj = fh_[0] * R[0][0] + fh_[1] * R[1][0] + fh_[2] * R[2][0];
+        gd[2 * d] += sn_ * proj;
+        gd[2 * d + 1] += -dr->amp * cs * proj;
+        for (int i = 0; i < 3; ++i) Rh[dr->body][i][0] += dr->amp * sn_ * fh_[i];
+    }
+    /* springs */
+    for (int s = 0; s < h->ns; ++s) {
+        const spring_t *sp = &h->spring[s];
+        const body_t *bi = &S[sp->i], *bj = &S[sp->j];
+        double d[3] = {bi->X[0] - bj->X[0], bi->X[1] - bj->X[1], bi->X[2] - bj->X[2]};
+        double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double fh_[3], dv = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            fh_[i] = Fh[sp->i][i] - Fh[sp->j][i];
+            dv += fh_[i] * (bi->V[i] - bj->V[i]);
+            Sc[sp->i][7 + i] += -sp->gamma * fh_[i];
+            Sc[sp->j][7 + i] += sp->gamma * fh_[i];
+        }
+        gs[3 * s + 2] += -dv;
+        if (!(len > 0)) continue;
+        double dir[3] = {d[0] / len, d[1] / len, d[2] / len};
+        double fd = fh_[0] * dir[0] + fh_[1] * dir[1] + fh_[2] * dir[2];
+        gs[3 * s] += -(len - sp->rest) * fd;
+        gs[3 * s + 1] += sp->k * fd;
+        for (int i = 0; i < 3; ++i) {
+            double da = -sp->k * (fd * dir[i] + (len - sp->rest) / len * (fh_[i] - fd * dir[i]));
+            Sc[sp->i][i] += da;
+            Sc[sp->j][i] -= da;
+        }
+    }
+    for (int k = 0; k < nb; ++k) adj_rot_matrix(S[k].q, Rh[k], Sc[k] + 3);
+    free(Ftot); free(Fh); free(Rh);
+}
+
+/* Reverse of hydro_force for the populations G (step n), map bid and body
+ * states S of step n: adds to Ga (adjoint of G) and Sc (adjoint of S). */
+static void hydro_force_adjoint(const ref_lbm *h, const double *G, const short *bid, const body_t *S,
+                                const double (*Fa)[6], double *Ga, double (*Sc)[13])
+{
+    const long C = h->C;
+    int per[3] = {h->bc & REF_BC_PERIODIC_X, h->bc & REF_BC_PERIODIC_Y, h->bc & REF_BC_PERIODIC_Z};
+    for (int k = 0; k < h->nb; ++k) {
+        const body_t *b = &S[k];
+        const double *Fk = Fa[k], *Tk = Fa[k] + 3;
+        double ext = b->r + 0.5 * b->l;
+        int lo[3], hi[3], n[3] = {h->nx, h->ny, h->nz};
+        for (int i = 0; i < 3; ++i) {
+            lo[i] = (int)floor(b->X[i] - ext) - 2;
+            hi[i] = (int)ceil(b->X[i] + ext) + 2;
+            if (per[i] && hi[i] - lo[i] + 1 > n[i]) { lo[i] = 0; hi[i] = n[i] - 1; }
+        }
+        for (int iz = lo[2]; iz <= hi[2]; ++iz) {
+            int z = wrap(iz, h->nz, per[2]);
+            if (z < 0) continue;
+            for (int iy = lo[1]; iy <= hi[1]; ++iy) {
+                int y = wrap(iy, h->ny, per[1]);
+                if (y < 0) continue;
+                for (int ix = lo[0]; ix <= hi[0]; ++ix) {
+                    int x = wrap(ix, h->nx, per[0]);
+                    if (x < 0) continue;
+                    long c = cell(h, x, y, z);
+                    if (bid[c] >= 0) continue;
+                    double rho = 0.0;
+                    for (int q = 0; q < Q; ++q) rho += G[q * C + c];
+                    for (int a = 1; a < Q; ++a) {
+                        long nbr = neighbour(h, x, y, z, a);
+                        if (nbr < 0 || bid[nbr] != k) continue;
+                        int ab = OPP[a];
+                        double p[3] = {x + EX[a], y + EY[a], z + EZ[a]}, uw[3];
+                        wall_velocity(h, b, p, uw);
+                        double eu = EX[ab] * uw[0] + EY[ab] * uw[1] + EZ[ab] * uw[2];
+                        double mag = 2.0 * G[a * C + c] + 6.0 * W[a] * rho * eu;
+                        double e[3] = {EX[a], EY[a], EZ[a]};
+                        double mid[3] = {x + 0.5 * EX[a], y + 0.5 * EY[a], z + 0.5 * EZ[a]}, d[3], de[3];
+                        body_offset(h, b, mid, d);
+                        cross(d, e, de);
+                        /* F_link = e mag, T_link = d x e mag */
+                        double mh = e[0] * Fk[0] + e[1] * Fk[1] + e[2] * Fk[2] +
+                                    de[0] * Tk[0] + de[1] * Tk[1] + de[2] * Tk[2];
+                        Ga[a * C + c] += 2.0 * mh;
+                        for (int q = 0; q < Q; ++q) Ga[q * C + c] += 6.0 * W[a] * eu * mh;
+                        double s = 6.0 * W[a] * rho * mh;
+                        double uh[3] = {EX[ab] * s, EY[ab] * s, EZ[ab] * s};
+                        adj_surface_velocity(h, b, p, uh, Sc[k]);
+                        /* the lever arm d = mid - X: Xh += Th x F_link */
+                        double fl[3] = {e[0] * mag, e[1] * mag, e[2] * mag}, tf[3];
+                        cross(Tk, fl, tf);
+                        for (int i = 0; i < 3; ++i) Sc[k][i] += tf[i];
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* Reverse of the LBGK collision with Guo's term at one cell: f holds the
+ * pre-collision populations, gh the adjoint of the post-collision ones. */
+static void collide_adjoint_cell(const ref_lbm *h, const double *f, const double *gh, double *fh)
+{
+    const double tau = h->tau, *g = h->g, om = 1.0 / tau;
+    const int forced = g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0;
+    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < Q; ++a) {
+        rho += f[a];
+        m[0] += EX[a] * f[a]; m[1] += EY[a] * f[a]; m[2] += EZ[a] * f[a];
+    }
+    double u[3] = {(m[0] + 0.5 * g[0]) / rho, (m[1] + 0.5 * g[1]) / rho, (m[2] + 0.5 * g[2]) / rho};
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double sr = 0.0, su[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < Q; ++b) {
+        double e[3] = {EX[b], EY[b], EZ[b]};
+        double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+        sr += gh[b] * om * W[b] * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+        for (int i = 0; i < 3; ++i) su[i] += gh[b] * om * W[b] * rho * (3.0 * e[i] + 9.0 * eu * e[i] - 3.0 * u[i]);
+        if (forced) {
+            double eg = e[0] * g[0] + e[1] * g[1] + e[2] * g[2];
+            for (int i = 0; i < 3; ++i) su[i] += gh[b] * (1.0 - 0.5 / tau) * W[b] * (-3.0 * g[i] + 9.0 * e[i] * eg);
+        }
+    }
+    for (int a = 0; a < Q; ++a) {
+        double e[3] = {EX[a], EY[a], EZ[a]};
+        fh[a] = (1.0 - om) * gh[a] + sr;
+        for (int i = 0; i < 3; ++i) fh[a] += su[i] * (e[i] - u[i]) / rho;
+    }
+}
+
+/* Reverse of refill: Fa adjoint of the pre-collision populations of step n,
+ * G the populations entering the step, bid_prev / bid_now the maps of epochs
+ * n-1 and n, S the body states of step n.  Adds to Gp (adjoint of G) and Sc. */
+static void refill_adjoint(const ref_lbm *h, const double *Fa, const double *G, const short *bid_prev,
+                           const short *bid_now, const body_t *S, double *Gp, double (*Sc)[13])
+{
+    const long C = h->C;
+    for (int z = 0; z < h->nz; ++z)
+        for (int y = 0; y < h->ny; ++y)
+            for (int x = 0; x < h->nx; ++x) {
+                long c = cell(h, x, y, z);
+                if (!(bid_prev[c] >= 0 && bid_now[c] < 0)) continue;
+                double sum = 0.0;
+                int cnt = 0;
+                for (int a = 1; a < Q; ++a) {
+                    long n = neighbour(h, x, y, z, a);
+                    if (n < 0 || bid_prev[n] >= 0 || bid_now[n] >= 0) continue;
+                    for (int b = 0; b < Q; ++b) sum += G[b * C + n];
+                    ++cnt;
+                }
+                double rho_avg = cnt ? sum / cnt : 1.0;
+                const body_t *b = &S[bid_prev[c]];
+                double p[3] = {x, y, z}, uw[3];
+                wall_velocity(h, b, p, uw);
+                double uu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+                double rh = 0.0, uh[3] = {0.0, 0.0, 0.0};
+                for (int a = 0; a < Q; ++a) {
+                    double e[3] = {EX[a], EY[a], EZ[a]};
+                    double eu = e[0] * uw[0] + e[1] * uw[1] + e[2] * uw[2];
+                    double fa = Fa[a * C + c];
+                    rh += fa * W[a] * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+                    for (int i = 0; i < 3; ++i) uh[i] += fa * W[a] * rho_avg * (3.0 * e[i] + 9.0 * eu * e[i] - 3.0 * uw[i]);
+                }
+                if (cnt) {
+                    for (int a = 1; a < Q; ++a) {
+                        long n = neighbour(h, x, y, z, a);
+                        if (n < 0 || bid_prev[n] >= 0 || bid_now[n] >= 0) continue;
+                        for (int q = 0; q < Q; ++q) Gp[q * C + n] += rh / cnt;
+                    }
+                }
+                adj_surface_velocity(h, b, p, uh, Sc[bid_prev[c]]);
+            }
+}
+
+/* Reverse of stream: Fa adjoint of the pre-collision populations of step n,
+ * G the populations entering the step, bid_prev the map of epoch n-1, Sp
+ * the body states n-1.  Adds to Gp (adjoint of G) and Spa (adjoint of Sp). */
+static void stream_adjoint(const ref_lbm *h, const double *Fa, const double *G, const short *bid_prev,
+                           const body_t *Sp, double *Gp, double (*Spa)[13])
+{
+    const long C = h->C;
+    for (int z = 0; z < h->nz; ++z)
+        for (int y = 0; y < h->ny; ++y)
+            for (int x = 0; x < h->nx; ++x) {
+                long c = cell(h, x, y, z);
+                if (bid_prev[c] >= 0) continue;
+                double rho = 0.0;
+                for (int a = 0; a < Q; ++a) rho += G[a * C + c];
+                double cr = 0.0;
+                Gp[0 * C + c] += Fa[0 * C + c];
+                for (int a = 1; a < Q; ++a) {
+                    long n = neighbour(h, x, y, z, a);
+                    int ab = OPP[a];
+                    if (n < 0) {
+                        Gp[a * C + c] += Fa[ab * C + c];
+                    } else if (bid_prev[n] >= 0) {
+                        const body_t *b = &Sp[bid_prev[n]];
+                        double p[3] = {x + EX[a], y + EY[a], z + EZ[a]}, uw[3];
+                        wall_velocity(h, b, p, uw);
+                        double eu = EX[ab] * uw[0] + EY[ab] * uw[1] + EZ[ab] * uw[2];
+                        double fa = Fa[ab * C + c];
+                        Gp[a * C + c] += fa;
+                        cr += 6.0 * W[a] * eu * fa;
+                        double s = 6.0 * W[a] * rho * fa;
+                        double uh[3] = {EX[ab] * s, EY[ab] * s, EZ[ab] * s};
+                        adj_surface_velocity(h, b, p, uh, Spa[bid_prev[n]]);
+                    } else {
+                        Gp[a * C + c] += Fa[a * C + n];
+                    }
+                }
+                for (int q = 0; q < Q; ++q) Gp[q * C + c] += cr;
+            }
+}
+
+static void free_tape(struct tape *tp)
+{
+    if (!tp) return;
+    free(tp->Gin); free(tp->Fpre); free(tp->fh); free(tp->bid); free(tp->state);
+    free(tp);
+}
+
+int lbm_ref_adjoint(ref_lbm *h, int n, const double *seed, double *grad_state, double *grad_prev,
+                    double *grad_pop, double *grad_drive, double *grad_spring, double *grad_body)
+{
+    if (!h || n < 1 || !seed) return REF_E_ARG;
+    const long C = h->C, QC = (long)Q * C;
+    const int nb = h->nb;
+    const int first_run = !h->started;
+    struct tape *tp = calloc(1, sizeof *tp);
+    if (!tp) return REF_E_OOM;
+    tp->cap = n;
+    tp->t0 = h->step;
+    tp->Gin = malloc(sizeof(double) * (size_t)(n + 1) * QC);
+    tp->Fpre = malloc(sizeof(double) * (size_t)n * QC);
+    tp->fh = malloc(sizeof(double) * (size_t)n * (nb ? nb : 1) * 6);
+    tp->bid = malloc(sizeof(short) * (size_t)(n + 1) * C);
+    tp->state = malloc(sizeof(body_t) * (size_t)(n + 2) * (nb ? nb : 1));
+    if (!tp->Gin || !tp->Fpre || !tp->fh || !tp->bid || !tp->state) {
+        free_tape(tp);
+        return REF_E_OOM;
+    }
+    /* forward, recorded */
+    h->tape = tp;
+    int rc = lbm_ref_step(h, n);
+    h->tape = NULL;
+    if (rc) { free_tape(tp); return rc; }
+    memcpy(tp->Gin + (long)n * QC, h->G, sizeof(double) * QC);
+    memcpy(tp->bid + (long)n * C, h->bid_prev, sizeof(short) * C);
+    memcpy(tp->state + (long)(n + 1) * nb, h->body, sizeof(body_t) * nb);
+
+    double *Ga = calloc(QC, sizeof(double));      /* adjoint of G^n */
+    double *Gp = calloc(QC, sizeof(double));      /* adjoint of G^{n-1} */
+    double *Fa = calloc(QC, sizeof(double));      /* adjoint of the pre-collision populations */
+    double (*Sn)[13] = calloc(nb ? nb : 1, sizeof *Sn);   /* adjoint of state n + 1 */
+    double (*Sc)[13] = calloc(nb ? nb : 1, sizeof *Sc);   /* adjoint of state n */
+    double (*Sq)[13] = calloc(nb ? nb : 1, sizeof *Sq);   /* adjoint of state n - 1 (bounce-back) */
+    double (*Fh)[6] = calloc(nb ? nb : 1, sizeof *Fh);
+    double *gd = calloc(2 * (h->nd ? h->nd : 1), sizeof(double));
+    double *gs = calloc(3 * (h->ns ? h->ns : 1), sizeof(double));
+    double *gb = calloc(5 * (nb ? nb : 1), sizeof(double));
+    if (!Ga || !Gp || !Fa || !Sn || !Sc || !Sq || !Fh || !gd || !gs || !gb) {
+        rc = REF_E_OOM;
+        goto done;
+    }
+    for (int k = 0; k < nb; ++k)
+        for (int i = 0; i < 13; ++i) Sn[k][i] = seed[13 * k + i];
+    const int with_fluid = !(h->options & REF_OPT_NO_FLUID);
+    for (int j = n - 1; j >= 0; --j) {
+        const body_t *Sprev = tp->state + (long)j * nb, *Scur = tp->state + (long)(j + 1) * nb;
+        const double *Gin = tp->Gin + (long)j * QC, *Gout = tp->Gin + (long)(j + 1) * QC;
+        const double *Fpre = tp->Fpre + (long)j * QC;
+        const short *bprev = tp->bid + (long)j * C, *bnow = tp->bid + (long)(j + 1) * C;
+        /* Sc starts with the bounce-back terms of step n + 1 (held in Sq) */
+        memcpy(Sc, Sq, sizeof(double) * 13 * nb);
+        integrate_adjoint(h, Scur, tp->fh + (long)j * nb * 6, tp->t0 + j, (const double (*)[13])Sn, Sc, Fh,
+                          gd, gs, gb);
+        memset(Sq, 0, sizeof(double) * 13 * nb);
+        memset(Gp, 0, sizeof(double) * QC);
+        if (with_fluid) {
+            hydro_force_adjoint(h, Gout, bnow, Scur, (const double (*)[6])Fh, Ga, Sc);
+            for (long c = 0; c < C; ++c) {
+                double f[Q], gh[Q], fh[Q];
+                if (bnow[c] >= 0) {
+                    for (int a = 0; a < Q; ++a) Fa[a * C + c] = 0.0;
+                    continue;
+                }
+                for (int a = 0; a < Q; ++a) { f[a] = Fpre[a * C + c]; gh[a] = Ga[a * C + c]; }
+                collide_adjoint_cell(h, f, gh, fh);
+                for (int a = 0; a < Q; ++a) Fa[a * C + c] = fh[a];
+            }
+            refill_adjoint(h, Fa, Gin, bprev, bnow, Scur, Gp, Sc);
+            stream_adjoint(h, Fa, Gin, bprev, Sprev, Gp, Sq);
+        }
+        memcpy(Sn, Sc, sizeof(double) * 13 * nb);
+        double *t = Ga; Ga = Gp; Gp = t;
+    }
+    /* Sn: adjoint of the first state; Sq: of the state before it, which is
+     * the same state when the run began at the very first step */
+    if (first_run)
+        for (int k = 0; k < nb; ++k)
+            for (int i = 0; i < 13; ++i) { Sn[k][i] += Sq[k][i]; Sq[k][i] = 0.0; }
+    if (grad_state) memcpy(grad_state, Sn, sizeof(double) * 13 * nb);
+    if (grad_prev) memcpy(grad_prev, Sq, sizeof(double) * 13 * nb);
+    if (grad_pop) memcpy(grad_pop, Ga, sizeof(double) * QC);
+    if (grad_drive) memcpy(grad_drive, gd, sizeof(double) * 2 * h->nd);
+    if (grad_spring) memcpy(grad_spring, gs, sizeof(double) * 3 * h->ns);
+    if (grad_body) memcpy(grad_body, gb, sizeof(double) * 5 * nb);
+    rc = REF_OK;
+done:
+    free(Ga); free(Gp); free(Fa); free(Sn); free(Sc); free(Sq); free(Fh); free(gd); free(gs); free(gb);
+    free_tape(tp);
+    return rc;
+}
+
+unsigned long long lbm_ref_flag_digest(ref_lbm *h) { return h ? h->flag_digest : 0; }

@@ -77,6 +77,21 @@ int  lbm_ref_lattice(int *e /* [19][3] */, double *w /* [19] */);
 int  lbm_ref_equilibrium(double rho, const double u[3], double *out /* [19] */);
 int  lbm_ref_body_props(ref_lbm *h, int b, double *out /* volume, I1, I2, I3 */);
 int  lbm_ref_num_threads(void);
+/* Reverse mode: advances n steps (recording every one), then returns the
+ * gradient of J = sum_b seed[b] . state_b(after the n steps) (seed: nb x 13)
+ * with respect to the body states at the start (grad_state, nb x 13) and the
+ * state before it (grad_prev: the wall velocities of the first stream; zero
+ * and folded into grad_state when the run starts at the first step), the
+ * populations entering the first step (grad_pop, 19 x cells), the drive
+ * terms (grad_drive, nd x 2: amp, phase), the springs (grad_spring, ns x 3:
+ * k, rest, damping) and the bodies (grad_body, nb x 5: mass, the three
+ * principal moments of inertia, volume), with the obstacle maps of the run
+ * held fixed.  Any output may be NULL. */
+int  lbm_ref_adjoint(ref_lbm *h, int n, const double *seed, double *grad_state,
+                     double *grad_prev, double *grad_pop, double *grad_drive,
+                     double *grad_spring, double *grad_body);
+/* running digest of the obstacle map of every step taken so far */
+unsigned long long lbm_ref_flag_digest(ref_lbm *h);
 const char *lbm_ref_last_error(ref_lbm *h);
 
 #ifdef __cplusplus
