@@ -228,6 +228,53 @@ int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm);
  * Reports the choice through the optional outputs (synchronises). */
 int lbm_autotune(lbm_t *h, int trials, int *cells_per_thread, int *min_blocks_per_sm);
 
+/* ---- reverse mode ---------------------------------------------------------
+ *
+ * Gradients of J = sum_b seed[b] . state_b(n0 + n), a linear function of the
+ * body states (the layout of lbm_get_bodies) after n steps, with respect to
+ * the parameters of the swimmers: drive terms (Eq. FB1-FB3), springs
+ * (Eq. osci_i, osci_j), body mass, inertia and volume (Algorithm 1), and the
+ * state the run starts from.  The obstacle maps of the recorded run are held
+ * fixed: the cell-centre test of Sec. 2.3 is piecewise constant in the body
+ * positions, so J is the smooth function of the parameters that the recorded
+ * map sequence defines.  A gradient with respect to a capsule length is the
+ * chain rule through mass, inertia and volume (the cell map held fixed).
+ * The paper has no reverse mode; it is the differentiation path of the
+ * swimmer design study.
+ *
+ * lbm_adjoint_record advances the handle by n steps from its current step n0
+ * (like lbm_step, through the same kernels) and keeps: the body state and the
+ * hydrodynamic force and torque of every step (13 + 6 doubles per body and
+ * step), and every `segment` steps a checkpoint of the populations and the
+ * flags entering the step (19 populations + 2 bytes per cell).  Device memory
+ * comes from the handle's allocator and is held until the next recording or
+ * lbm_destroy.  FP64 and FP32 storage only (LBM_E_ARG otherwise); at least
+ * one body.  Synchronises.
+ *
+ * lbm_adjoint_backward runs the reverse sweep over the recording: segment by
+ * segment, last first, it recomputes the segment's populations and flags from
+ * its checkpoint (segment + 1 population and flag slots), then applies the
+ * transposed step in reverse order.  The adjoint populations are kept in the
+ * storage precision (FP64, or FP32 for FP32 storage); body adjoints and
+ * parameter gradients in FP64.  It does not change the handle's state.
+ * Outputs (host, caller-owned, each may be NULL):
+ *   grad_state   [nb][13]  dJ/d state n0
+ *   grad_prev    [nb][13]  dJ/d state n0 - 1 (the moving-wall velocities of
+ *                          the first stream); when n0 = 0 these two are one
+ *                          state: the sum is reported in grad_state and
+ *                          grad_prev is zero
+ *   grad_drive   [nd][2]   dJ/d amp, dJ/d phase of each drive term (the
+ *                          switch-on step phase / (2 pi freq) held fixed)
+ *   grad_spring  [ns][3]   dJ/d k, dJ/d rest, dJ/d damping
+ *   grad_body    [nb][5]   dJ/d mass, dJ/d I_1, I_2, I_3 (body-frame
+ *                          principal moments), dJ/d volume (body force g)
+ *   grad_pop     [19][C]   dJ/d populations entering step n0 (FP64)
+ * Allocates and frees its own working buffers (through the allocator hook);
+ * LBM_E_STATE without a recording.  Synchronises. */
+int lbm_adjoint_record(lbm_t *h, int n, int segment);
+int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, double *grad_prev,
+                         double *grad_drive, double *grad_spring, double *grad_body, double *grad_pop);
+
 /* Kernel launches one step makes (for launch accounting). */
 int lbm_kernels_per_step(lbm_t *h);
 

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
 HEADER = os.path.join(ROOT, "include", "lbm.h")
-SOURCES = ["stream_collide.cu", "kernels.cu", "runtime.cu", "static_scratch.cu"]
+SOURCES = ["stream_collide.cu", "kernels.cu", "runtime.cu", "static_scratch.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

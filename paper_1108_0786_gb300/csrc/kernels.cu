@@ -326,6 +326,16 @@ __device__ void integrate_block(const Device &dv, const StepPtrs &sp, int with_f
         else if (fabs(n.V[0]) > MAX_STEP || fabs(n.V[1]) > MAX_STEP || fabs(n.V[2]) > MAX_STEP)
             atomicOr(dv.status, ST_UNSTABLE);
         sp.body_next[b] = n;
+        if (dv.tape) {
+            const TapeCtl tc = *dv.tape;
+            const long long j = tstep - tc.t0;
+            if (tc.on && j >= 0 && j < tc.cap) {
+                const double *src = &n.X[0];
+                double *st = tc.state + ((j + 2) * dv.nb + b) * 13;
+                for (int i = 0; i < 13; ++i) st[i] = src[i];
+                for (int i = 0; i < 6; ++i) tc.force[(j * dv.nb + b) * 6 + i] = dv.fh[b * 6 + i];
+            }
+        }
         if (dv.hist) {
             double *h = dv.hist + ((tstep % dv.hist_cap) * dv.nb + b) * 13;
             const double *src = &n.X[0];

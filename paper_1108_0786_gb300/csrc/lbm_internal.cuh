@@ -137,6 +137,16 @@ __device__ inline void surface_velocity(const Domain &d, const BodyState &b, dou
     u[2] = b.V[2] + (b.W[0] * o[1] - b.W[1] * o[0]);
 }
 
+// Recording of a forward run for the reverse sweep: when `on`, the rigid-body
+// step t writes the state t + 1 and the hydrodynamic load of step t.
+struct TapeCtl {
+    double *state;      // [cap + 2][nb][13]: index t - t0 + 1 holds the state of step t
+    double *force;      // [cap][nb][6]: index t - t0 holds force and torque of step t
+    long long t0;       // first recorded step
+    int cap;            // steps the buffers hold
+    int on;
+};
+
 // kernel launch parameters of one step
 struct StepPtrs {
     const void *src;        // populations of step n-1
@@ -175,9 +185,40 @@ struct Device {
     long long *t_dev;       // step counter seen by the drive
     double *hist;           // [hist_cap][nb][13] or null
     int hist_cap;
+    TapeCtl *tape;          // recording switch of the reverse sweep, or null
 };
 
-// ---- launch wrappers (kernels.cu / stream_collide.cu) ----------------------
+// pointers of one reverse step n of the cell part (adjoint.cu)
+struct AdjPtrs {
+    const void *G;                  // post-collision populations of step n (storage type)
+    const uint8_t *flags_cur;       // flags of epoch n
+    const uint8_t *bid_cur;         // body ids of epoch n
+    const uint8_t *bid_prev;        // body ids of epoch n-1 (the body an uncovered cell left)
+    const uint8_t *flags_next;      // flags of epoch n+1
+    const void *ain;                // [19][C] adjoint of the pre-collision populations of step n+1
+    const void *rin;                // [C] density adjoint of the cells uncovered at step n+1
+    void *aout;                     // [19][C] adjoint of the pre-collision populations of step n
+    void *rout;                     // [C] density adjoint of the cells uncovered at step n
+    const BodyState *body;          // state n
+    const double *fadj;             // [nb][6] adjoint of force and torque of step n
+    double *part;                   // [nb][part_stride][9] per-block body sums (X, V, W)
+    int part_stride;
+};
+
+// pointers of the reversed rigid-body step n (adjoint.cu)
+struct AdjBody {
+    const BodyState *state;         // state n
+    const double *fh;               // [nb][6] hydrodynamic force and torque of step n
+    double *sa_next;                // [nb][13] adjoint of state n+1 (completed in place)
+    double *sa_cur;                 // [nb][13] adjoint of state n (written)
+    double *fadj;                   // [nb][6] adjoint of the hydrodynamic load (written)
+    const double *part;             // cell sums of reverse step n+1
+    int part_stride, part_count;
+    double *grad_drive, *grad_spring, *grad_body;   // [nd][2], [ns][3], [nb][5] (added to)
+    long long t;                    // step n
+};
+
+// ---- launch wrappers (kernels.cu / stream_collide.cu / adjoint.cu) ---------
 void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8_t *bid0,
                        uint8_t *bid1, cudaStream_t s);
 void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s);
@@ -194,5 +235,9 @@ void launch_integrate(const Device &dv, const StepPtrs &sp, int with_fluid, cuda
 void launch_export(const Device &dv, const void *pop, const uint8_t *flags, const uint8_t *bid,
                    int what, int mask_solid, void *out, int dtype, cudaStream_t s);
 void launch_import_pop(const Device &dv, void *pop, const double *in, cudaStream_t s);
+int adjoint_part_stride(const Device &dv);
+void launch_adj_integrate(const Device &dv, const AdjBody &ab, cudaStream_t s);
+void launch_adj_cells(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s);
+void launch_adj_reduce(const Device &dv, const double *part, int stride, int count, double *sa, cudaStream_t s);
 
 }  // namespace lbm

@@ -33,6 +33,7 @@ struct lbm_s {
     std::vector<DriveTerm> drives;
     int hist_cap = 0;
     int tune_vec = 0, tune_minb = 0;
+    std::vector<int> drive_slot;        // creation index of each device drive term (grouped by body)
     // device
     bool ready = false, graphs_ready = false;
     int device = 0;
@@ -49,6 +50,19 @@ struct lbm_s {
     long long steps = 0;
     cudaGraphExec_t single[2] = {nullptr, nullptr};
     cudaGraphExec_t chunk = nullptr;
+    // reverse sweep: the recording of the last lbm_adjoint_record
+    struct Tape {
+        bool recorded = false;
+        int n = 0, seg = 0, nseg = 0;
+        long long n0 = 0;
+        lbm::TapeCtl *ctl = nullptr;        // device switch read by the rigid-body step
+        lbm::TapeCtl ctl_host{};
+        double *state = nullptr;            // [n + 2][nb][13]: states n0 - 1 ... n0 + n
+        double *force = nullptr;            // [n][nb][6]
+        void *ckpt_pop = nullptr;           // [nseg][19][C]: populations entering each segment
+        uint8_t *ckpt_flags = nullptr, *ckpt_bid = nullptr;   // [nseg][C]: epoch before each segment
+        std::vector<void *> allocs;
+    } tape;
     std::string err;
 };
 
@@ -232,13 +246,16 @@ int ensure_device(lbm_t *h) {
         p.inv_m = 1.0 / p.m;
         for (int i = 0; i < 3; ++i) p.inv_inertia[i] = 1.0 / p.inertia[i];
         p.drive_first = (int)drives_h.size();
-        for (const auto &d : h->drives)
+        for (size_t k = 0; k < h->drives.size(); ++k) {
+            const DriveTerm &d = h->drives[k];
             if (d.body == b) {
                 DriveTerm t = d;
                 t.omega = 2.0 * M_PI * d.freq;
                 t.t_on = d.phase / t.omega;
                 drives_h.push_back(t);
+                h->drive_slot.push_back((int)k);
             }
+        }
         p.drive_count = (int)drives_h.size() - p.drive_first;
         p.spring_first = (int)spring_list.size();
         for (size_t k = 0; k < h->springs.size(); ++k)
@@ -276,6 +293,8 @@ int ensure_device(lbm_t *h) {
     dv.props = props;
     dv.springs = springs;
     dv.drives = drives;
+    if ((rc = alloc_into(h, &h->tape.ctl, sizeof(lbm::TapeCtl)))) return rc;
+    dv.tape = h->tape.ctl;
 
     cudaStream_t s = h->stream;
     CK(cudaMemsetAsync(h->pop[0], 0, es * lbm::Q * C, s));   // deviation 0: fluid at rest
@@ -290,6 +309,7 @@ int ensure_device(lbm_t *h) {
     CK(cudaMemcpyAsync(dv.status, st, sizeof st, cudaMemcpyHostToDevice, s));
     const long long t0 = 0;
     CK(cudaMemcpyAsync(dv.t_dev, &t0, sizeof t0, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(h->tape.ctl, 0, sizeof(lbm::TapeCtl), s));
     if (B) CK(cudaMemcpyAsync(props, props_h.data(), sizeof(BodyProps) * B, cudaMemcpyHostToDevice, s));
     if (!h->springs.empty())
         CK(cudaMemcpyAsync(springs, h->springs.data(), sizeof(Spring) * h->springs.size(), cudaMemcpyHostToDevice, s));
@@ -356,9 +376,29 @@ void release_device(lbm_t *h) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->join_ev) cudaEventDestroy(h->join_ev);
+    for (void *p : h->tape.allocs) dfree(h, p);
+    h->tape.allocs.clear();
     for (void *p : h->allocs) dfree(h, p);
     h->allocs.clear();
 }
+
+// ---- reverse sweep helpers ---------------------------------------------------
+
+template <typename T>
+int alloc_list(lbm_t *h, std::vector<void *> &list, T **out, size_t bytes) {
+    void *p = dalloc(h, bytes);
+    if (!p) return fail(h, LBM_E_OOM, "device allocation of %zu bytes failed", bytes);
+    list.push_back(p);
+    *out = static_cast<T *>(p);
+    return LBM_OK;
+}
+
+void free_list(lbm_t *h, std::vector<void *> &list) {
+    for (void *p : list) dfree(h, p);
+    list.clear();
+}
+
+size_t adj_bytes(int precision) { return precision == LBM_PREC_F64 ? 8 : 4; }
 
 int last_parity(const lbm_t *h) { return (int)((h->steps + 1) & 1); }
 
@@ -814,6 +854,275 @@ int lbm_autotune(lbm_t *h, int trials, int *best_cells, int *best_blocks) {
     }
     if (best_cells) *best_cells = h->dv.vec;
     if (best_blocks) *best_blocks = h->dv.minb;
+    return LBM_OK;
+}
+
+int lbm_adjoint_record(lbm_t *h, int n, int segment) {
+    if (!h || n < 1 || segment < 1) return LBM_E_ARG;
+    if (h->precision != LBM_PREC_F64 && h->precision != LBM_PREC_F32)
+        return fail(h, LBM_E_ARG, "the reverse sweep needs FP64 or FP32 storage");
+    if (nb(h) == 0) return fail(h, LBM_E_ARG, "the reverse sweep needs at least one body");
+    int rc = ensure_device(h);
+    if (rc) return rc;
+    if ((rc = build_graphs(h))) return rc;
+    if ((rc = sync_and_check(h))) return rc;
+    auto &tp = h->tape;
+    free_list(h, tp.allocs);
+    tp.recorded = false;
+    const int B = nb(h);
+    const long long C = h->C;
+    const int nseg = (n + segment - 1) / segment;
+    const size_t pop_sz = pop_bytes(h->precision) * lbm::Q * C;
+    if ((rc = alloc_list(h, tp.allocs, &tp.state, sizeof(double) * 13 * B * ((size_t)n + 2)))) return rc;
+    if ((rc = alloc_list(h, tp.allocs, &tp.force, sizeof(double) * 6 * B * (size_t)n))) return rc;
+    if (fluid(h)) {
+        if ((rc = alloc_list(h, tp.allocs, &tp.ckpt_pop, pop_sz * nseg))) return rc;
+        if ((rc = alloc_list(h, tp.allocs, &tp.ckpt_flags, (size_t)C * nseg))) return rc;
+        if ((rc = alloc_list(h, tp.allocs, &tp.ckpt_bid, (size_t)C * nseg))) return rc;
+    }
+    const long long n0 = h->steps;
+    const int p0 = (int)(n0 & 1);
+    cudaStream_t s = h->stream;
+    const size_t bs = sizeof(BodyState) * B;
+    CK(cudaMemcpyAsync(tp.state, h->bodies[p0 ^ 1], bs, cudaMemcpyDeviceToDevice, s));     // state n0 - 1
+    CK(cudaMemcpyAsync(tp.state + 13 * B, h->bodies[p0], bs, cudaMemcpyDeviceToDevice, s)); // state n0
+    tp.ctl_host = lbm::TapeCtl{tp.state, tp.force, n0, n, 1};
+    CK(cudaMemcpyAsync(tp.ctl, &tp.ctl_host, sizeof(lbm::TapeCtl), cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < nseg; ++k) {
+        const long long m = n0 + (long long)k * segment;
+        const int q = (int)((m & 1) ^ 1);           // buffers of epoch m - 1
+        if (fluid(h)) {
+            CK(cudaMemcpyAsync(static_cast<char *>(tp.ckpt_pop) + pop_sz * k, h->pop[q], pop_sz,
+                               cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(tp.ckpt_flags + C * k, h->flags[q], (size_t)C, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(tp.ckpt_bid + C * k, h->bid[q], (size_t)C, cudaMemcpyDeviceToDevice, s));
+        }
+        if ((rc = lbm_step(h, std::min(segment, n - k * segment)))) return rc;
+    }
+    tp.ctl_host.on = 0;
+    CK(cudaMemcpyAsync(tp.ctl, &tp.ctl_host, sizeof(lbm::TapeCtl), cudaMemcpyHostToDevice, s));
+    if ((rc = sync_and_check(h))) return rc;
+    tp.n = n;
+    tp.seg = segment;
+    tp.nseg = nseg;
+    tp.n0 = n0;
+    tp.recorded = true;
+    return LBM_OK;
+}
+
+int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, double *grad_prev,
+                         double *grad_drive, double *grad_spring, double *grad_body, double *grad_pop) {
+    if (!h || !seed) return LBM_E_ARG;
+    auto &tp = h->tape;
+    if (!tp.recorded) return fail(h, LBM_E_STATE, "lbm_adjoint_backward needs a recording (lbm_adjoint_record)");
+    int rc = sync_and_check(h);
+    if (rc) return rc;
+    const int B = nb(h), ND = (int)h->drives.size(), NS = (int)h->springs.size();
+    const long long C = h->C;
+    const bool fl = fluid(h);
+    const size_t es = pop_bytes(h->precision), as = adj_bytes(h->precision);
+    const size_t pop_sz = es * lbm::Q * C;
+    const int K = tp.seg;
+    std::vector<void *> bk;         // this call's buffers
+    struct Guard {
+        lbm_t *h;
+        std::vector<void *> &list;
+        ~Guard() {
+            cudaStreamSynchronize(h->stream);
+            free_list(h, list);
+        }
+    } guard{h, bk};
+    // recompute and adjoint buffers
+    void *seg_pop = nullptr, *A[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
+    uint8_t *seg_flags = nullptr, *seg_bid = nullptr, *carry = nullptr;
+    double *sa[2], *fadj, *part, *grads, *r_fh;
+    BodyState *scratch;
+    lbm::Link *r_links = nullptr;
+    int *r_seg = nullptr, *r_changed = nullptr;
+    long long *r_t = nullptr;
+    const lbm::Device &dv = h->dv;
+    const int stride = fl ? lbm::adjoint_part_stride(dv) : 1;
+    if ((rc = alloc_list(h, bk, &sa[0], sizeof(double) * 13 * B))) return rc;
+    if ((rc = alloc_list(h, bk, &sa[1], sizeof(double) * 13 * B))) return rc;
+    if ((rc = alloc_list(h, bk, &fadj, sizeof(double) * 6 * B))) return rc;
+    if ((rc = alloc_list(h, bk, &part, sizeof(double) * 9 * B * (size_t)stride))) return rc;
+    const size_t ngrad = 2 * (size_t)ND + 3 * (size_t)NS + 5 * (size_t)B;
+    if ((rc = alloc_list(h, bk, &grads, sizeof(double) * ngrad))) return rc;
+    if (fl) {
+        if ((rc = alloc_list(h, bk, &seg_pop, pop_sz * (K + 1)))) return rc;
+        if ((rc = alloc_list(h, bk, &seg_flags, (size_t)C * (K + 2)))) return rc;
+        if ((rc = alloc_list(h, bk, &seg_bid, (size_t)C * (K + 2)))) return rc;
+        if ((rc = alloc_list(h, bk, &carry, (size_t)C))) return rc;
+        for (int i = 0; i < 2; ++i) {
+            if ((rc = alloc_list(h, bk, &A[i], as * lbm::Q * C))) return rc;
+            if ((rc = alloc_list(h, bk, &R[i], as * C))) return rc;
+        }
+        if ((rc = alloc_list(h, bk, &scratch, sizeof(BodyState) * B))) return rc;
+        if ((rc = alloc_list(h, bk, &r_fh, sizeof(double) * 6 * B))) return rc;
+        if ((rc = alloc_list(h, bk, &r_links, sizeof(lbm::Link) * (size_t)B * dv.link_side * dv.seg_cap))) return rc;
+        if ((rc = alloc_list(h, bk, &r_seg, sizeof(int) * B * dv.link_side))) return rc;
+        if ((rc = alloc_list(h, bk, &r_changed, sizeof(int) * 2))) return rc;
+        if ((rc = alloc_list(h, bk, &r_t, sizeof(long long)))) return rc;
+    }
+    cudaStream_t s = h->stream;
+    double *gd = grads, *gs = grads + 2 * ND, *gb = grads + 2 * ND + 3 * NS;
+    CK(cudaMemsetAsync(grads, 0, sizeof(double) * ngrad, s));
+    CK(cudaMemsetAsync(part, 0, sizeof(double) * 9 * B * (size_t)stride, s));
+    CK(cudaMemcpyAsync(sa[0], seed, sizeof(double) * 13 * B, cudaMemcpyHostToDevice, s));
+    int cur = 0;                    // sa[cur]: adjoint of state n + 1
+    int ai = 0;                     // A[ai], R[ai]: adjoint entering reverse step n
+    // the recomputation runs the forward kernels on its own link lists,
+    // change flags, clock and force output
+    lbm::Device dr = dv;
+    dr.hist = nullptr;
+    dr.tape = nullptr;
+    if (fl) {
+        dr.fh = r_fh;
+        dr.links = r_links;
+        dr.seg_count = r_seg;
+        dr.changed = r_changed;
+        dr.t_dev = r_t;
+        CK(cudaMemsetAsync(A[0], 0, as * lbm::Q * C, s));
+        CK(cudaMemsetAsync(R[0], 0, as * C, s));
+        CK(cudaMemsetAsync(r_seg, 0, sizeof(int) * B * dv.link_side, s));
+    }
+    const BodyState *states = reinterpret_cast<const BodyState *>(tp.state);
+    auto S = [&](long long t) { return states + (t - (tp.n0 - 1)) * B; };     // state t
+    auto slot_pop = [&](int j) { return static_cast<void *>(static_cast<char *>(seg_pop) + pop_sz * j); };
+    const int ones[2] = {1, 1};
+    for (int k = tp.nseg - 1; k >= 0; --k) {
+        const long long m = tp.n0 + (long long)k * K;
+        const int L = std::min(K, tp.n - k * K);
+        if (fl) {
+            if (k < tp.nseg - 1)            // epoch m + L, recomputed with the later segment
+                CK(cudaMemcpyAsync(carry, seg_flags + C, (size_t)C, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(seg_pop, static_cast<char *>(tp.ckpt_pop) + pop_sz * k, pop_sz,
+                               cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(seg_flags, tp.ckpt_flags + C * k, (size_t)C, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(seg_bid, tp.ckpt_bid + C * k, (size_t)C, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(r_t, &m, sizeof m, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(r_changed, ones, sizeof ones, cudaMemcpyHostToDevice, s));
+            for (int j = 0; j <= L; ++j) {
+                // the remap rewrites only the cubes around the bodies: the
+                // slot starts from the epoch before it, as the forward's
+                // ping-pong buffers do
+                CK(cudaMemcpyAsync(seg_flags + C * (j + 1), seg_flags + C * j, (size_t)C, cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(seg_bid + C * (j + 1), seg_bid + C * j, (size_t)C, cudaMemcpyDeviceToDevice, s));
+                lbm::StepPtrs sp{};
+                sp.src = slot_pop(j);
+                sp.dst = slot_pop(j + 1);
+                sp.flags_prev = seg_flags + C * j;
+                sp.bid_prev = seg_bid + C * j;
+                sp.flags_cur = seg_flags + C * (j + 1);
+                sp.bid_cur = seg_bid + C * (j + 1);
+                sp.body_prev = S(m + j - 1);
+                sp.body_cur = S(m + j);
+                sp.body_next = scratch;
+                sp.parity = j & 1;
+                if (j == L) {
+                    // the flags of the epoch after the run: the last reverse
+                    // step needs them (its bounce-back and link cells)
+                    if (k == tp.nseg - 1) lbm::launch_remap(dr, sp, 0, s);
+                    break;
+                }
+                lbm::launch_remap(dr, sp, 0, s);
+                lbm::launch_stream_collide(dr, sp, s);
+                if (lbm::needs_boundary_fix(dr)) lbm::launch_boundary_fix(dr, sp, s);
+                lbm::launch_links(dr, sp, s);
+                lbm::launch_force(dr, sp, s);
+            }
+            CK(cudaGetLastError());
+        }
+        for (int j = L - 1; j >= 0; --j) {
+            const long long n = m + j;
+            lbm::AdjBody ab{};
+            ab.state = S(n);
+            ab.fh = tp.force + (n - tp.n0) * 6 * B;
+            ab.sa_next = sa[cur];
+            ab.sa_cur = sa[cur ^ 1];
+            ab.fadj = fadj;
+            ab.part = part;
+            ab.part_stride = stride;
+            ab.part_count = fl ? stride : 0;
+            ab.grad_drive = gd;
+            ab.grad_spring = gs;
+            ab.grad_body = gb;
+            ab.t = n;
+            lbm::launch_adj_integrate(dv, ab, s);
+            if (fl) {
+                lbm::AdjPtrs ap{};
+                ap.G = slot_pop(j + 1);
+                ap.flags_cur = seg_flags + C * (j + 1);
+                ap.bid_cur = seg_bid + C * (j + 1);
+                ap.bid_prev = seg_bid + C * j;
+                ap.flags_next = (j + 1 < L || k == tp.nseg - 1) ? seg_flags + C * (j + 2) : carry;
+                ap.ain = A[ai];
+                ap.rin = R[ai];
+                ap.aout = A[ai ^ 1];
+                ap.rout = R[ai ^ 1];
+                ap.body = S(n);
+                ap.fadj = fadj;
+                ap.part = part;
+                ap.part_stride = stride;
+                lbm::launch_adj_cells(dv, ap, false, s);
+                ai ^= 1;
+            }
+            cur ^= 1;
+        }
+        CK(cudaGetLastError());
+    }
+    // sa[cur]: adjoint of state n0 without the cell sums of reverse step n0
+    if (fl) {
+        lbm::launch_adj_reduce(dv, part, stride, stride, sa[cur], s);
+        // the stream of step n0 itself: adjoint of the populations entering
+        // the run and of the state n0 - 1 (its moving-wall velocities)
+        CK(cudaMemsetAsync(fadj, 0, sizeof(double) * 6 * B, s));
+        lbm::AdjPtrs ap{};
+        ap.G = slot_pop(0);
+        ap.flags_cur = seg_flags;
+        ap.bid_cur = seg_bid;
+        ap.bid_prev = seg_bid;
+        ap.flags_next = seg_flags + C;
+        ap.ain = A[ai];
+        ap.rin = R[ai];
+        ap.aout = A[ai ^ 1];
+        ap.rout = R[ai ^ 1];
+        ap.body = S(tp.n0 - 1);
+        ap.fadj = fadj;
+        ap.part = part;
+        ap.part_stride = stride;
+        lbm::launch_adj_cells(dv, ap, true, s);
+        CK(cudaMemsetAsync(sa[cur ^ 1], 0, sizeof(double) * 13 * B, s));
+        lbm::launch_adj_reduce(dv, part, stride, stride, sa[cur ^ 1], s);
+        ai ^= 1;
+    } else {
+        CK(cudaMemsetAsync(sa[cur ^ 1], 0, sizeof(double) * 13 * B, s));
+    }
+    CK(cudaGetLastError());
+    std::vector<double> st(13 * B), pv(13 * B), gh(ngrad);
+    CK(cudaMemcpyAsync(st.data(), sa[cur], sizeof(double) * 13 * B, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pv.data(), sa[cur ^ 1], sizeof(double) * 13 * B, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(gh.data(), grads, sizeof(double) * ngrad, cudaMemcpyDeviceToHost, s));
+    if (grad_pop && fl) {
+        if (as == 8) {
+            CK(cudaMemcpyAsync(grad_pop, A[ai], sizeof(double) * lbm::Q * C, cudaMemcpyDeviceToHost, s));
+        } else {
+            std::vector<float> tmp((size_t)lbm::Q * C);
+            CK(cudaMemcpyAsync(tmp.data(), A[ai], sizeof(float) * lbm::Q * C, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (size_t i = 0; i < tmp.size(); ++i) grad_pop[i] = tmp[i];
+        }
+    }
+    if ((rc = sync_and_check(h))) return rc;
+    if (tp.n0 == 0)             // state -1 is state 0: one input
+        for (int i = 0; i < 13 * B; ++i) { st[i] += pv[i]; pv[i] = 0.0; }
+    if (grad_state) std::memcpy(grad_state, st.data(), sizeof(double) * 13 * B);
+    if (grad_prev) std::memcpy(grad_prev, pv.data(), sizeof(double) * 13 * B);
+    if (grad_drive)             // device terms are grouped by body: back to creation order
+        for (int k = 0; k < ND; ++k)
+            for (int i = 0; i < 2; ++i) grad_drive[2 * h->drive_slot[k] + i] = gh[2 * k + i];
+    if (grad_spring) std::memcpy(grad_spring, gh.data() + 2 * ND, sizeof(double) * 3 * NS);
+    if (grad_body) std::memcpy(grad_body, gh.data() + 2 * ND + 3 * NS, sizeof(double) * 5 * B);
     return LBM_OK;
 }
 

@@ -39,7 +39,7 @@ EXPORTED = (
     "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
     "lbm_tune", "lbm_autotune", "lbm_kernels_per_step", "lbm_bytes_per_cell", "lbm_last_error",
-    "lbm_momentum_exchange_static",
+    "lbm_momentum_exchange_static", "lbm_adjoint_record", "lbm_adjoint_backward",
 )
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -94,6 +94,8 @@ def load_library(path: Optional[str] = None):
         "lbm_bytes_per_cell": ([P], I),
         "lbm_last_error": ([P], ctypes.c_char_p),
         "lbm_momentum_exchange_static": ([P, P, P, I, I, I, I, I, I, P, P], I),
+        "lbm_adjoint_record": ([P, I, I], I),
+        "lbm_adjoint_backward": ([P, DP, DP, DP, DP, DP, DP, DP], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -139,6 +141,8 @@ class Lattice:
             raise LbmError(rc, "lbm_create_ex failed")
         self._h = h
         self.nbodies = 0
+        self.nsprings = 0
+        self.ndrives = 0
         self._callbacks = None
         if torch_memory:
             self._use_torch()
@@ -192,12 +196,16 @@ class Lattice:
         return b
 
     def add_spring(self, i, j, k, rest, damping):
-        return self._check(self._lib.lbm_add_spring(self._h, int(i), int(j), float(k), float(rest),
-                                                    float(damping)))
+        s = self._check(self._lib.lbm_add_spring(self._h, int(i), int(j), float(k), float(rest),
+                                                 float(damping)))
+        self.nsprings += 1
+        return s
 
     def set_drive(self, body, amp, freq, phase):
-        return self._check(self._lib.lbm_set_drive(self._h, int(body), float(amp), float(freq),
-                                                   float(phase)))
+        d = self._check(self._lib.lbm_set_drive(self._h, int(body), float(amp), float(freq),
+                                                float(phase)))
+        self.ndrives += 1
+        return d
 
     def set_drive_window(self, term, t_off):
         return self._check(self._lib.lbm_set_drive_window(self._h, int(term), float(t_off)))
@@ -292,6 +300,30 @@ class Lattice:
 
     def load(self, path):
         return self._check(self._lib.lbm_load(self._h, os.fsencode(path)))
+
+    # -- reverse mode ---------------------------------------------------------
+    def adjoint_record(self, n, segment=64):
+        """Advance n steps keeping the recording the reverse sweep needs
+        (checkpoints every ``segment`` steps)."""
+        return self._check(self._lib.lbm_adjoint_record(self._h, int(n), int(segment)))
+
+    def adjoint_backward(self, seed, want_pop=False):
+        """Gradient of sum(seed * body states after the recorded run) (seed:
+        nbodies x 13) as a dict: ``state``, ``prev``, ``drive`` (nd x 2: amp,
+        phase), ``spring`` (ns x 3: k, rest, damping), ``body`` (nb x 5:
+        mass, I1, I2, I3, volume) and, with ``want_pop``, ``pop`` (19 x
+        cells)."""
+        sd = np.ascontiguousarray(seed, dtype=np.float64).reshape(self.nbodies, 13)
+        out = {"state": np.zeros((self.nbodies, 13)), "prev": np.zeros((self.nbodies, 13)),
+               "drive": np.zeros((self.ndrives, 2)), "spring": np.zeros((self.nsprings, 3)),
+               "body": np.zeros((self.nbodies, 5))}
+        if want_pop:
+            nz, ny, nx = self.shape
+            out["pop"] = np.zeros((19, nz, ny, nx))
+        keys = ("state", "prev", "drive", "spring", "body", "pop")
+        ptr = [_dp(out[k]) if k in out and out[k].size else None for k in keys]
+        self._check(self._lib.lbm_adjoint_backward(self._h, _dp(sd), *ptr))
+        return out
 
     def time_kernels(self, n):
         """Average per-kernel duration in ms over n eagerly launched steps."""

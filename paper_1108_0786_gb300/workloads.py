@@ -217,6 +217,29 @@ def capsule_swarm(nx=512, ny=256, nz=256, swimmers=8, seed=1108, mix=False,
     return sc
 
 
+def design_swimmer(capsules: bool = False, seed: int = 1108, steps: int = 4000) -> Scenario:
+    """96 x 48 x 48 periodic box with one swimmer for the gradient study.
+
+    Spheres of radius 4, rest length 14 centre to centre, k = 0.015,
+    damping 0.005, amplitude 5e-4, period 500 steps, density 1, tau = 1,
+    4000 steps (8 periods).  With ``capsules``, three parallel capsules of
+    radius 3 and cylinder length 4 (half-extent 5 along the axis, a 4-cell
+    gap at rest 14).  The middle body starts at the box centre with every
+    coordinate jittered by U[-0.1, 0.1].
+    """
+    rng = SplitMix64(seed)
+    name = "design swimmer 96x48x48 " + ("capsules" if capsules else "spheres")
+    sc = Scenario(name, 96, 48, 48, 1.0, steps=steps)
+    centre = tuple(v + rng.uniform(-0.1, 0.1) for v in (48.0, 24.0, 24.0))
+    if capsules:
+        add_swimmer(sc, centre, (1.0, 0.0, 0.0, 0.0), (CAPSULE,) * 3, 3.0, 4.0, 14.0, 0.015, 0.005,
+                    5e-4, 500.0)
+    else:
+        add_swimmer(sc, centre, (1.0, 0.0, 0.0, 0.0), (SPHERE,) * 3, 4.0, 0.0, 14.0, 0.015, 0.005,
+                    5e-4, 500.0)
+    return sc
+
+
 def scaled_copy(sc: Scenario, steps: int) -> Scenario:
     """The same scenario with a different step count."""
     import copy

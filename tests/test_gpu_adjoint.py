@@ -1,0 +1,215 @@
+"""GPU reverse sweep against the oracle's reverse mode and central differences.
+
+FP64 parity: the gradients the CUDA path returns through the C ABI
+(lbm_adjoint_record + lbm_adjoint_backward, checkpoints every `segment`
+steps and recomputation) are compared element by element with the oracle's
+plain reverse sweep on the same seeded scenario: periodic, and with walls,
+Guo forcing and a capsule; segments that do not divide the run (a ragged
+last segment); a run that starts after some steps.  The tolerance is 1e-9
+of each array's largest magnitude (the FP64 trajectories agree to 1e-10).
+
+FP32 storage: the same gradients within 1e-3.  The 96 x 48 x 48 gradient
+study (4000 steps, 63 segments of 64) is checked against central
+differences of FP64 forward runs for the drive amplitude a, the phase, the
+spring constant k and the capsule length, with steps small enough (1e-5
+relative) that no cell of the obstacle maps flips.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from adjoint_helpers import N_STEPS, SEED, scenario, set_motion, start
+from paper_1108_0786_gb300 import lbm, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1108_0786_gb300 import _build
+    _build.build()
+    return torch
+
+
+def gpu_gradients(sc, precision="f64", n=N_STEPS, segment=16, pre=0, seed=SEED, want_pop=True):
+    lat = set_motion(lbm.from_scenario(sc, precision=precision))
+    if pre:
+        lat.step(pre)
+    lat.adjoint_record(n, segment)
+    g = lat.adjoint_backward(seed, want_pop=want_pop)
+    g["final"] = lat.bodies()
+    lat.close()
+    return g
+
+
+def oracle_gradients(sc, n=N_STEPS, pre=0, seed=SEED):
+    o = start(sc)
+    if pre:
+        o.step(pre)
+    g = o.adjoint(n, seed)
+    g["final"] = o.bodies()
+    return g
+
+
+def assert_close(got, ref, rel, keys=("state", "prev", "drive", "spring", "body", "pop")):
+    for k in keys:
+        scale = max(np.abs(ref[k]).max(), 1e-300)
+        err = np.abs(got[k] - ref[k]).max()
+        assert err <= rel * scale, (k, err, scale)
+
+
+@pytest.mark.parametrize("variant", ["periodic", "walls-force-capsule"])
+def test_fp64_gradients_match_the_oracle(gpu, variant):
+    if variant == "periodic":
+        sc = scenario()
+    else:
+        sc = scenario(bc=wl.PERIODIC_X, g=(2e-6, 0.0, 0.0), cap_len=3.0)
+    got = gpu_gradients(sc)
+    ref = oracle_gradients(sc)
+    np.testing.assert_allclose(got["final"], ref["final"], rtol=1e-10, atol=1e-12)
+    assert_close(got, ref, 1e-9)
+    assert np.abs(ref["pop"]).max() > 0 and np.abs(ref["body"][:, 4]).max() >= 0
+
+
+def test_segment_length_does_not_change_the_gradients(gpu):
+    sc = scenario()
+    ref = gpu_gradients(sc, segment=N_STEPS)
+    for seg in (1, 7, 13):
+        got = gpu_gradients(sc, segment=seg)
+        for k in ("state", "drive", "spring", "body", "pop"):
+            assert np.array_equal(got[k], ref[k]), (seg, k)
+
+
+def test_run_starting_after_some_steps(gpu):
+    """n0 > 0: the state before the first recorded step is its own input."""
+    sc = scenario()
+    got = gpu_gradients(sc, n=40, pre=11, segment=9)
+    ref = oracle_gradients(sc, n=40, pre=11)
+    assert np.abs(ref["prev"]).max() > 0
+    assert_close(got, ref, 1e-9)
+
+
+def test_seed_on_every_state_component(gpu):
+    """A dense seed (every component of every body) exercises every output."""
+    sc = scenario()
+    seed = np.random.default_rng(7).standard_normal((3, 13))
+    got = gpu_gradients(sc, seed=seed, n=30, segment=8)
+    ref = oracle_gradients(sc, seed=seed, n=30)
+    assert_close(got, ref, 1e-9)
+
+
+def test_fp32_gradients_close_to_fp64(gpu):
+    sc = scenario()
+    got = gpu_gradients(sc, precision="f32")
+    ref = oracle_gradients(sc)
+    assert_close(got, ref, 1e-3, keys=("state", "drive", "spring", "body"))
+
+
+def test_adjoint_needs_a_recording_and_supported_storage(gpu):
+    sc = scenario()
+    lat = lbm.from_scenario(sc, precision="f64")
+    with pytest.raises(lbm.LbmError) as e:
+        lat.adjoint_backward(SEED)
+    assert e.value.code == lbm.E_STATE
+    lat.close()
+    lat = lbm.from_scenario(sc, precision="f16")
+    with pytest.raises(lbm.LbmError) as e:
+        lat.adjoint_record(10, 4)
+    assert e.value.code == lbm.E_ARG
+    lat.close()
+
+
+# ---- the 96 x 48 x 48 gradient study against central differences ----------
+
+def design(capsules, **kw):
+    sc = wl.design_swimmer(capsules=capsules)
+    for key, v in kw.items():
+        if key == "a":
+            sc.drives = [dataclasses.replace(d, amp=math.copysign(v, d.amp)) for d in sc.drives]
+        elif key == "phase":
+            sc.drives = [dataclasses.replace(d, phase=v) if d.phase > 0 else d for d in sc.drives]
+        elif key == "k":
+            sc.springs = [dataclasses.replace(s, k=v) for s in sc.springs]
+        elif key == "l":
+            sc.bodies = [dataclasses.replace(b, length=v, mass=wl.capsule_volume(b.radius, v))
+                         for b in sc.bodies]
+    return sc
+
+
+def displacement(sc, precision="f64"):
+    """x displacement of the middle body and a digest of the obstacle map
+    every 64 steps (a flipped cell between two difference runs shows up in
+    the digests, or as a jump the gradient check rejects)."""
+    import hashlib
+    lat = lbm.from_scenario(sc, precision=precision)
+    x0 = lat.bodies()[1, 0]
+    maps = hashlib.sha256()
+    for _ in range(sc.steps // 64):
+        lat.step(64)
+        maps.update(lat.field(lbm.FIELD_FLAGS).tobytes())
+    lat.step(sc.steps % 64)
+    maps.update(lat.field(lbm.FIELD_FLAGS).tobytes())
+    x = lat.bodies()[1, 0]
+    lat.close()
+    return x - x0, maps.hexdigest()
+
+
+def capsule_chain(sc, gb):
+    """dJ/dl through mass (density 1 x volume), inertia and volume of the
+    three capsules, by automatic differentiation of the body formulas the
+    library uses (uniform solid capsule: cylinder plus two hemispheres)."""
+    import torch
+    r = torch.tensor(sc.bodies[0].radius, dtype=torch.float64)
+    l = torch.tensor(sc.bodies[0].length, dtype=torch.float64, requires_grad=True)
+    vc = math.pi * r * r * l
+    vh = 2.0 / 3.0 * math.pi * r ** 3
+    vol = vc + 2 * vh
+    m = vol
+    mc, mh = m * vc / vol, m * vh / vol
+    i1 = 0.5 * mc * r * r + 2 * (0.4 * mh * r * r)
+    i2 = mc * (r * r / 4 + l * l / 12) + 2 * mh * (0.4 * r * r + l * l / 4 + 3 * l * r / 8)
+    props = torch.stack([m, i1, i2, i2, vol])
+    jac = torch.stack([torch.autograd.grad(p, l, retain_graph=True)[0] for p in props]).numpy()
+    return float((gb * jac[None, :]).sum())
+
+
+@pytest.mark.parametrize("precision,rel", [("f64", 2e-4), ("f32", 1e-2)])
+def test_design_swimmer_gradients_against_central_differences(gpu, precision, rel):
+    for capsules in (False, True):
+        sc = design(capsules)
+        lat = lbm.from_scenario(sc, precision=precision)
+        seed = np.zeros((3, 13))
+        seed[1, 0] = 1.0
+        lat.adjoint_record(sc.steps, 64)
+        g = lat.adjoint_backward(seed)
+        lat.close()
+        a0, ph0, k0 = 5e-4, math.pi / 2, 0.015
+        signs = np.array([math.copysign(1.0, d.amp) for d in sc.drives])
+        # difference steps: 1e-5 relative (a step of 1e-3 moves the bodies by
+        # ~1e-6 cells, enough to flip cells of the map within 4000 steps)
+        checks = {
+            "a": (float((g["drive"][:, 0] * signs).sum()), a0 * 1e-5),
+            "k": (float(g["spring"][:, 0].sum()), k0 * 1e-5),
+            # the switch-on step of the delayed terms sits on the step grid
+            # (phase / omega = T / 4): difference just below it, where it is fixed
+            "phase": (float(sum(g["drive"][i, 1] for i, d in enumerate(sc.drives) if d.phase > 0)), 1e-5),
+        }
+        if capsules:
+            checks["l"] = (capsule_chain(sc, g["body"]), 4e-5)
+        for key, (ad, h) in checks.items():
+            x0 = {"a": a0, "k": k0, "phase": ph0, "l": sc.bodies[0].length}[key]
+            if key == "phase":
+                (jp, fp), (jm, fm) = displacement(design(capsules, phase=x0 - h)), \
+                    displacement(design(capsules, phase=x0 - 3 * h))
+            else:
+                (jp, fp), (jm, fm) = displacement(design(capsules, **{key: x0 + h})), \
+                    displacement(design(capsules, **{key: x0 - h}))
+            assert fp == fm, f"{key}: the difference step changed an obstacle map"
+            fd = (jp - jm) / (2 * h)
+            assert abs(ad - fd) <= rel * abs(fd), (capsules, key, ad, fd)
