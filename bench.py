@@ -354,10 +354,54 @@ def run_ours(args, world, rank, local):
     }
     if not args.no_variants and rank == 0 and world == 1:
         line["storage_variants"] = variant_runs(workload(args, 0), args, 200)
+    if not args.no_variants and rank == 0 and world == 1:
+        line["adjoint"] = adjoint_run()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def adjoint_run(precision="f32", segment=64):
+    """Reverse sweep against the forward run on the 96 x 48 x 48 gradient
+    study (one three-sphere swimmer, 4000 steps): wall-clock of the forward
+    steps alone, of the recorded forward (lbm_adjoint_record) and of the
+    reverse sweep (lbm_adjoint_backward: recomputation from checkpoints every
+    `segment` steps plus the transposed steps), each bracketed by a device
+    synchronisation."""
+    import numpy as np
+    from paper_1108_0786_gb300 import lbm, workloads as wl
+    sc = wl.design_swimmer(capsules=False)
+    seed = np.zeros((len(sc.bodies), 13))
+    seed[1, 0] = 1.0                    # x of the middle body: its displacement
+    times = {}
+    lat = lbm.from_scenario(sc, precision=precision)
+    lat.step(64)
+    lat.sync()
+    t0 = time.perf_counter()
+    lat.step(sc.steps)
+    lat.sync()
+    times["forward"] = time.perf_counter() - t0
+    lat.close()
+    lat = lbm.from_scenario(sc, precision=precision)
+    lat.step(0)                                 # device buffers and step graphs
+    lat.sync()
+    t0 = time.perf_counter()
+    lat.adjoint_record(sc.steps, segment)
+    times["record"] = time.perf_counter() - t0
+    lat.adjoint_backward(seed)                  # warm-up of the reverse kernels
+    t0 = time.perf_counter()
+    g = lat.adjoint_backward(seed)
+    times["backward"] = time.perf_counter() - t0
+    lat.close()
+    signs = np.sign([d.amp for d in sc.drives])
+    return {"workload": f"{sc.name}, {sc.steps} steps, {precision} storage, checkpoints every {segment} steps",
+            "forward_ms": round(times["forward"] * 1e3, 2), "record_ms": round(times["record"] * 1e3, 2),
+            "backward_ms": round(times["backward"] * 1e3, 2),
+            "backward_over_forward": round(times["backward"] / times["forward"], 3),
+            "record_plus_backward_over_forward": round((times["record"] + times["backward"]) / times["forward"], 3),
+            "d_displacement_d_amplitude": float((g["drive"][:, 0] * signs).sum()),
+            "d_displacement_d_k": float(g["spring"][:, 0].sum())}
 
 
 def run_reference(args, world, rank):

@@ -1,0 +1,127 @@
+"""PyTorch autograd binding of the reverse sweep.
+
+``swimmer_run`` returns the body states after ``steps`` coupled steps of a
+scenario as a differentiable function of the swimmer parameters: drive
+amplitudes and phases (Eq. FB1-FB3), spring constants, rest lengths and
+dampings (Eq. osci_i, osci_j), body masses, capsule lengths and the start
+state of the bodies.  The forward pass runs the GPU library with a
+recording (``lbm_adjoint_record``, checkpoints every ``segment`` steps); the
+backward pass runs its reverse sweep (``lbm_adjoint_backward``) on the
+incoming gradient of the final states.  The obstacle maps of the recorded
+run are held fixed, so a capsule length acts through the body's mass
+distribution (principal moments of inertia) and volume only.
+
+Argument marshalling only: both passes run in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import copy
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import lbm, workloads as wl
+
+
+def body_properties(shape, radius, length, mass):
+    """Principal moments of inertia (body frame) and volume of a uniform
+    solid sphere or capsule (a cylinder of length ``length`` plus two
+    hemispheres) -- the formulas the library applies in lbm_add_body --
+    as torch expressions, so that their derivatives follow."""
+    r, l, m = radius, length, mass
+    if shape == wl.SPHERE:
+        vol = 4.0 / 3.0 * math.pi * r ** 3 + 0.0 * l
+        i0 = 0.4 * m * r * r
+        return torch.stack([i0, i0, i0]), vol
+    vc = math.pi * r * r * l
+    vh = 2.0 / 3.0 * math.pi * r ** 3
+    vol = vc + 2.0 * vh
+    mc, mh = m * vc / vol, m * vh / vol
+    i0 = 0.5 * mc * r * r + 2.0 * (0.4 * mh * r * r)
+    i1 = mc * (r * r / 4.0 + l * l / 12.0) + 2.0 * mh * (0.4 * r * r + l * l / 4.0 + 3.0 * l * r / 8.0)
+    return torch.stack([i0, i1, i1]), vol
+
+
+def _scenario_with(sc, amp, phase, k, rest, damping, mass, length):
+    out = copy.deepcopy(sc)
+    out.drives = [dataclasses.replace(d, amp=float(a), phase=float(p))
+                  for d, a, p in zip(sc.drives, amp, phase)]
+    out.springs = [dataclasses.replace(s, k=float(kk), rest=float(rr), damping=float(dd))
+                   for s, kk, rr, dd in zip(sc.springs, k, rest, damping)]
+    out.bodies = [dataclasses.replace(b, mass=float(m), length=float(l) if b.shape == wl.CAPSULE else 0.0)
+                  for b, m, l in zip(sc.bodies, mass, length)]
+    return out
+
+
+class _SwimmerRun(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, amp, phase, k, rest, damping, mass, length, state0, sc, steps, segment, precision):
+        run = _scenario_with(sc, amp.tolist(), phase.tolist(), k.tolist(), rest.tolist(),
+                             damping.tolist(), mass.tolist(), length.tolist())
+        lat = lbm.from_scenario(run, precision=precision)
+        s0 = state0.detach().cpu().double().numpy()
+        for b in range(len(run.bodies)):
+            lat.set_body_state(b, s0[b])
+        lat.adjoint_record(int(steps), int(segment))
+        final = torch.from_numpy(lat.bodies())
+        ctx.lat = lat
+        ctx.run = run
+        ctx.save_for_backward(mass, length)
+        return final.to(state0.dtype)
+
+    @staticmethod
+    def backward(ctx, grad_final):
+        mass, length = ctx.saved_tensors
+        g = ctx.lat.adjoint_backward(grad_final.detach().cpu().double().numpy())
+        ctx.lat.close()
+        ctx.lat = None
+        nb = len(ctx.run.bodies)
+        d_mass = np.zeros(nb)
+        d_length = np.zeros(nb)
+        for b, body in enumerate(ctx.run.bodies):
+            m = torch.tensor(float(mass[b]), dtype=torch.float64, requires_grad=True)
+            l = torch.tensor(float(length[b]) if body.shape == wl.CAPSULE else 0.0, dtype=torch.float64,
+                             requires_grad=True)
+            inertia, vol = body_properties(body.shape, body.radius, l, m)
+            # J depends on (m, I, V): d/dm and d/dl through I(m, l) and V(l)
+            total = (float(g["body"][b, 0]) * m + (torch.from_numpy(g["body"][b, 1:4]) * inertia).sum() +
+                     float(g["body"][b, 4]) * vol)
+            dm, dl = torch.autograd.grad(total, (m, l), allow_unused=True)
+            d_mass[b] = float(dm)
+            d_length[b] = float(dl) if (dl is not None and body.shape == wl.CAPSULE) else 0.0
+        t = lambda a, like: torch.as_tensor(a, dtype=like.dtype, device=like.device)
+        return (t(g["drive"][:, 0], mass), t(g["drive"][:, 1], mass), t(g["spring"][:, 0], mass),
+                t(g["spring"][:, 1], mass), t(g["spring"][:, 2], mass), t(d_mass, mass),
+                t(d_length, length), t(g["state"], grad_final), None, None, None, None)
+
+
+def swimmer_run(sc, steps, amp, phase, k, rest, damping, mass, length, state0, segment=64,
+                precision="f64"):
+    """Final body states [nbodies, 13] after ``steps`` steps of scenario
+    ``sc`` with the given parameter tensors (CPU, float64):
+
+    amp, phase        [ndrives]   per drive term, in the scenario's order
+    k, rest, damping  [nsprings]
+    mass, length      [nbodies]   (length is ignored for spheres)
+    state0            [nbodies, 13] start states (lbm_get_bodies layout)
+
+    Differentiable in every tensor argument (a unit quaternion in state0 is
+    taken as given).  ``precision``: "f64" or "f32" storage."""
+    return _SwimmerRun.apply(amp, phase, k, rest, damping, mass, length, state0, sc, steps, segment,
+                             precision)
+
+
+def scenario_parameters(sc):
+    """The parameter tensors of ``swimmer_run`` for a scenario as it stands."""
+    f = lambda v: torch.tensor(v, dtype=torch.float64)
+    state0 = np.zeros((len(sc.bodies), 13))
+    for i, b in enumerate(sc.bodies):
+        state0[i, 0:3] = b.pos
+        q = np.asarray(b.orient, dtype=np.float64)
+        state0[i, 3:7] = q / np.linalg.norm(q)
+    return dict(amp=f([d.amp for d in sc.drives]), phase=f([d.phase for d in sc.drives]),
+                k=f([s.k for s in sc.springs]), rest=f([s.rest for s in sc.springs]),
+                damping=f([s.damping for s in sc.springs]), mass=f([b.mass for b in sc.bodies]),
+                length=f([b.length for b in sc.bodies]), state0=torch.from_numpy(state0))

@@ -334,25 +334,43 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
     const long long t = ab.t;
     const double tt = (double)t;
     const BodyState *S = ab.state;
-    // 1. complete Sh^{n+1}
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        double *sn = ab.sa_next + 13 * b;
-        for (int k = 0; k < ab.part_count; ++k) {
+    // 1. complete Sh^{n+1}: warp w adds body b's block sums, lanes over the
+    //    blocks, then a fixed shuffle tree
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int b = warp; b < nb; b += nwarps) {
+        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = lane; k < ab.part_count; k += 32) {
             const double *p = ab.part + ((long long)b * ab.part_stride + k) * 9;
-            for (int i = 0; i < 3; ++i) { sn[i] += p[i]; sn[7 + i] += p[3 + i]; sn[10 + i] += p[6 + i]; }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) acc[i] += p[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
+        }
+        if (lane == 0) {
+            double *sn = ab.sa_next + 13 * b;
+            for (int i = 0; i < 3; ++i) { sn[i] += acc[i]; sn[7 + i] += acc[3 + i]; sn[10 + i] += acc[6 + i]; }
         }
     }
     // drive-term and spring forces of the forward step (the order of the
-    // forward's sums is kept below)
+    // forward's sums is kept below); each drive term's sine and cosine once
     for (int k = threadIdx.x; k < dv.nd; k += blockDim.x) {
         const DriveTerm dt = dv.drives[k];
-        double f = 0.0;
-        if (!(tt < dt.t_on || tt >= dt.t_off)) f = dt.amp * sin(dt.omega * tt - dt.phase);
+        double f = 0.0, sn_ = 0.0, cs = 0.0;
+        if (!(tt < dt.t_on || tt >= dt.t_off)) {
+            sincos(dt.omega * tt - dt.phase, &sn_, &cs);
+            f = dt.amp * sn_;
+        }
         const double *q = S[dt.body].q;
         const double w = q[0], x = q[1], y = q[2], z = q[3];
         dv.drive_f[3 * k + 0] = f * (1 - 2 * (y * y + z * z));
         dv.drive_f[3 * k + 1] = f * (2 * (x * y + w * z));
         dv.drive_f[3 * k + 2] = f * (2 * (x * z - w * y));
+        ab.drive_sc[3 * k + 0] = f;
+        ab.drive_sc[3 * k + 1] = sn_;
+        ab.drive_sc[3 * k + 2] = cs;
     }
     for (int k = threadIdx.x; k < dv.ns; k += blockDim.x) {
         const Spring sp_ = dv.springs[k];
@@ -434,9 +452,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
         out[2] += Th[0] * fh[1] - Th[1] * fh[0];
         // drive terms of this body (their axis is the first column of R)
         for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k) {
-            const DriveTerm dt = dv.drives[k];
-            if (tt < dt.t_on || tt >= dt.t_off) continue;
-            const double f = dt.amp * sin(dt.omega * tt - dt.phase);
+            const double f = ab.drive_sc[3 * k];         // zero outside the drive window
             for (int i = 0; i < 3; ++i) Rh[i][0] += f * Fh[i];
         }
         double qh[4] = {0, 0, 0, 0};
@@ -452,7 +468,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
     for (int k = threadIdx.x; k < dv.nd; k += blockDim.x) {
         const DriveTerm dt = dv.drives[k];
         if (tt < dt.t_on || tt >= dt.t_off) continue;
-        const double sn_ = sin(dt.omega * tt - dt.phase), cs = cos(dt.omega * tt - dt.phase);
+        const double sn_ = ab.drive_sc[3 * k + 1], cs = ab.drive_sc[3 * k + 2];
         const double *fa = ab.fadj + 6 * dt.body;
         const double *q = S[dt.body].q;
         const double w = q[0], x = q[1], y = q[2], z = q[3];
@@ -511,10 +527,14 @@ __global__ void adj_reduce_kernel(int nb, const double *part, int stride, int co
 }
 
 template <typename A, typename T, bool FIRST>
-void launch_cells(const Device &dv, const AdjPtrs &ap, cudaStream_t s) {
+void launch_bulk_cells(const Device &dv, const AdjPtrs &ap, cudaStream_t s) {
     const dim3 blk(128, 2);
     const dim3 grid((dv.dom.nx + 127) / 128, (dv.dom.ny + 1) / 2, dv.dom.nz);
     adj_bulk_kernel<A, T, FIRST><<<grid, blk, 0, s>>>(dv, ap);
+}
+
+template <typename A, typename T, bool FIRST>
+void launch_boundary_cells(const Device &dv, const AdjPtrs &ap, cudaStream_t s) {
     if (dv.nb > 0)
         adj_boundary_kernel<A, T, FIRST><<<dim3(ap.part_stride, dv.nb), ADJ_THREADS, 0, s>>>(dv, ap, 0);
     if (!(dv.dom.px && dv.dom.py && dv.dom.pz)) {
@@ -536,13 +556,23 @@ void launch_adj_integrate(const Device &dv, const AdjBody &ab, cudaStream_t s) {
     adj_integrate_kernel<<<1, ADJ_THREADS, 0, s>>>(dv, ab);
 }
 
-void launch_adj_cells(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s) {
+void launch_adj_bulk(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s) {
     if (dv.precision == LBM_PREC_F64) {
-        if (first) launch_cells<double, double, true>(dv, ap, s);
-        else launch_cells<double, double, false>(dv, ap, s);
+        if (first) launch_bulk_cells<double, double, true>(dv, ap, s);
+        else launch_bulk_cells<double, double, false>(dv, ap, s);
     } else {
-        if (first) launch_cells<float, float, true>(dv, ap, s);
-        else launch_cells<float, float, false>(dv, ap, s);
+        if (first) launch_bulk_cells<float, float, true>(dv, ap, s);
+        else launch_bulk_cells<float, float, false>(dv, ap, s);
+    }
+}
+
+void launch_adj_boundary(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s) {
+    if (dv.precision == LBM_PREC_F64) {
+        if (first) launch_boundary_cells<double, double, true>(dv, ap, s);
+        else launch_boundary_cells<double, double, false>(dv, ap, s);
+    } else {
+        if (first) launch_boundary_cells<float, float, true>(dv, ap, s);
+        else launch_boundary_cells<float, float, false>(dv, ap, s);
     }
 }
 

@@ -215,6 +215,7 @@ struct AdjBody {
     const double *part;             // cell sums of reverse step n+1
     int part_stride, part_count;
     double *grad_drive, *grad_spring, *grad_body;   // [nd][2], [ns][3], [nb][5] (added to)
+    double *drive_sc;               // [nd][3] scratch: drive value, sine, cosine of step n
     long long t;                    // step n
 };
 
@@ -237,7 +238,8 @@ void launch_export(const Device &dv, const void *pop, const uint8_t *flags, cons
 void launch_import_pop(const Device &dv, void *pop, const double *in, cudaStream_t s);
 int adjoint_part_stride(const Device &dv);
 void launch_adj_integrate(const Device &dv, const AdjBody &ab, cudaStream_t s);
-void launch_adj_cells(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s);
+void launch_adj_bulk(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s);
+void launch_adj_boundary(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s);
 void launch_adj_reduce(const Device &dv, const double *part, int stride, int count, double *sa, cudaStream_t s);
 
 }  // namespace lbm

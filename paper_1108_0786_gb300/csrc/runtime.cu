@@ -935,7 +935,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     // recompute and adjoint buffers
     void *seg_pop = nullptr, *A[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
     uint8_t *seg_flags = nullptr, *seg_bid = nullptr, *carry = nullptr;
-    double *sa[2], *fadj, *part, *grads, *r_fh;
+    double *sa[2], *fadj, *part, *grads, *r_fh, *drive_sc;
     BodyState *scratch;
     lbm::Link *r_links = nullptr;
     int *r_seg = nullptr, *r_changed = nullptr;
@@ -948,6 +948,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     if ((rc = alloc_list(h, bk, &part, sizeof(double) * 9 * B * (size_t)stride))) return rc;
     const size_t ngrad = 2 * (size_t)ND + 3 * (size_t)NS + 5 * (size_t)B;
     if ((rc = alloc_list(h, bk, &grads, sizeof(double) * ngrad))) return rc;
+    if ((rc = alloc_list(h, bk, &drive_sc, sizeof(double) * 3 * std::max(ND, 1)))) return rc;
     if (fl) {
         if ((rc = alloc_list(h, bk, &seg_pop, pop_sz * (K + 1)))) return rc;
         if ((rc = alloc_list(h, bk, &seg_flags, (size_t)C * (K + 2)))) return rc;
@@ -965,6 +966,19 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         if ((rc = alloc_list(h, bk, &r_t, sizeof(long long)))) return rc;
     }
     cudaStream_t s = h->stream;
+    if ((rc = build_graphs(h))) return rc;        // creates the side stream
+    // the bulk part of each reverse step needs no body adjoint: it runs on
+    // the side stream, concurrently with the rigid-body and boundary parts
+    cudaStream_t side = h->side;
+    cudaEvent_t ev_main = nullptr, ev_side = nullptr;
+    CK(cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming));
+    struct Events {
+        cudaEvent_t &a, &b;
+        ~Events() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } events{ev_main, ev_side};
+    CK(cudaEventRecord(ev_main, s));
+    CK(cudaEventRecord(ev_side, s));
     double *gd = grads, *gs = grads + 2 * ND, *gb = grads + 2 * ND + 3 * NS;
     CK(cudaMemsetAsync(grads, 0, sizeof(double) * ngrad, s));
     CK(cudaMemsetAsync(part, 0, sizeof(double) * 9 * B * (size_t)stride, s));
@@ -994,6 +1008,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         const long long m = tp.n0 + (long long)k * K;
         const int L = std::min(K, tp.n - k * K);
         if (fl) {
+            CK(cudaStreamWaitEvent(s, ev_side, 0));     // the bulk adjoint read the slots
             if (k < tp.nseg - 1)            // epoch m + L, recomputed with the later segment
                 CK(cudaMemcpyAsync(carry, seg_flags + C, (size_t)C, cudaMemcpyDeviceToDevice, s));
             CK(cudaMemcpyAsync(seg_pop, static_cast<char *>(tp.ckpt_pop) + pop_sz * k, pop_sz,
@@ -1032,6 +1047,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
                 lbm::launch_force(dr, sp, s);
             }
             CK(cudaGetLastError());
+            CK(cudaEventRecord(ev_main, s));        // the segment's slots are ready
         }
         for (int j = L - 1; j >= 0; --j) {
             const long long n = m + j;
@@ -1047,6 +1063,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
             ab.grad_drive = gd;
             ab.grad_spring = gs;
             ab.grad_body = gb;
+            ab.drive_sc = drive_sc;
             ab.t = n;
             lbm::launch_adj_integrate(dv, ab, s);
             if (fl) {
@@ -1064,7 +1081,12 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
                 ap.fadj = fadj;
                 ap.part = part;
                 ap.part_stride = stride;
-                lbm::launch_adj_cells(dv, ap, false, s);
+                CK(cudaStreamWaitEvent(side, ev_main, 0));     // Ph^{n+1} of the boundary cells
+                lbm::launch_adj_bulk(dv, ap, false, side);
+                CK(cudaStreamWaitEvent(s, ev_side, 0));        // Ph^{n+1} of the bulk cells
+                CK(cudaEventRecord(ev_side, side));
+                lbm::launch_adj_boundary(dv, ap, false, s);
+                CK(cudaEventRecord(ev_main, s));
                 ai ^= 1;
             }
             cur ^= 1;
@@ -1073,6 +1095,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     }
     // sa[cur]: adjoint of state n0 without the cell sums of reverse step n0
     if (fl) {
+        CK(cudaStreamWaitEvent(s, ev_side, 0));
         lbm::launch_adj_reduce(dv, part, stride, stride, sa[cur], s);
         // the stream of step n0 itself: adjoint of the populations entering
         // the run and of the state n0 - 1 (its moving-wall velocities)
@@ -1091,7 +1114,8 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         ap.fadj = fadj;
         ap.part = part;
         ap.part_stride = stride;
-        lbm::launch_adj_cells(dv, ap, true, s);
+        lbm::launch_adj_bulk(dv, ap, true, s);
+        lbm::launch_adj_boundary(dv, ap, true, s);
         CK(cudaMemsetAsync(sa[cur ^ 1], 0, sizeof(double) * 13 * B, s));
         lbm::launch_adj_reduce(dv, part, stride, stride, sa[cur ^ 1], s);
         ai ^= 1;

@@ -9,10 +9,11 @@ last segment); a run that starts after some steps.  The tolerance is 1e-9
 of each array's largest magnitude (the FP64 trajectories agree to 1e-10).
 
 FP32 storage: the same gradients within 1e-3.  The 96 x 48 x 48 gradient
-study (4000 steps, 63 segments of 64) is checked against central
+study (4000 steps, 63 segments of 64; the capsule variant over one period)
+is checked against central
 differences of FP64 forward runs for the drive amplitude a, the phase, the
-spring constant k and the capsule length, with steps small enough (1e-5
-relative) that no cell of the obstacle maps flips.
+spring constant k and the capsule length, with steps small enough (bodies
+moved by ~1e-9 cells) that no cell of the obstacle maps flips.
 """
 import dataclasses
 import math
@@ -127,8 +128,8 @@ def test_adjoint_needs_a_recording_and_supported_storage(gpu):
 
 # ---- the 96 x 48 x 48 gradient study against central differences ----------
 
-def design(capsules, **kw):
-    sc = wl.design_swimmer(capsules=capsules)
+def design(capsules, steps, **kw):
+    sc = wl.design_swimmer(capsules=capsules, steps=steps)
     for key, v in kw.items():
         if key == "a":
             sc.drives = [dataclasses.replace(d, amp=math.copysign(v, d.amp)) for d in sc.drives]
@@ -179,10 +180,14 @@ def capsule_chain(sc, gb):
     return float((gb * jac[None, :]).sum())
 
 
-@pytest.mark.parametrize("precision,rel", [("f64", 2e-4), ("f32", 1e-2)])
+@pytest.mark.parametrize("precision,rel", [("f64", 2e-3), ("f32", 1e-2)])
 def test_design_swimmer_gradients_against_central_differences(gpu, precision, rel):
-    for capsules in (False, True):
-        sc = design(capsules)
+    # the capsule swimmer loses its axial alignment after about two periods
+    # (a rotational instability seeded by round-off: Omega grows from 1e-16
+    # to 1e-3); past it J is too sensitive for difference quotients to
+    # converge, so the capsule variant is checked over one period
+    for capsules, steps in ((False, 4000), (True, 500)):
+        sc = design(capsules, steps)
         lat = lbm.from_scenario(sc, precision=precision)
         seed = np.zeros((3, 13))
         seed[1, 0] = 1.0
@@ -191,25 +196,79 @@ def test_design_swimmer_gradients_against_central_differences(gpu, precision, re
         lat.close()
         a0, ph0, k0 = 5e-4, math.pi / 2, 0.015
         signs = np.array([math.copysign(1.0, d.amp) for d in sc.drives])
-        # difference steps: 1e-5 relative (a step of 1e-3 moves the bodies by
-        # ~1e-6 cells, enough to flip cells of the map within 4000 steps)
-        checks = {
-            "a": (float((g["drive"][:, 0] * signs).sum()), a0 * 1e-5),
-            "k": (float(g["spring"][:, 0].sum()), k0 * 1e-5),
+        # difference steps sized to move the bodies by about 1e-9 cells
+        # (larger steps flip cells of the map within 4000 steps; the FP64
+        # round-off of a run limits the difference to ~1e-4 relative)
+        grads = {
+            "a": float((g["drive"][:, 0] * signs).sum()),
+            "k": float(g["spring"][:, 0].sum()),
             # the switch-on step of the delayed terms sits on the step grid
             # (phase / omega = T / 4): difference just below it, where it is fixed
-            "phase": (float(sum(g["drive"][i, 1] for i, d in enumerate(sc.drives) if d.phase > 0)), 1e-5),
+            "phase": float(sum(g["drive"][i, 1] for i, d in enumerate(sc.drives) if d.phase > 0)),
         }
         if capsules:
-            checks["l"] = (capsule_chain(sc, g["body"]), 4e-5)
+            grads["l"] = capsule_chain(sc, g["body"])
+        checks = {key: (ad, 1e-9 / max(abs(ad), 1e-6)) for key, ad in grads.items()}
         for key, (ad, h) in checks.items():
             x0 = {"a": a0, "k": k0, "phase": ph0, "l": sc.bodies[0].length}[key]
             if key == "phase":
-                (jp, fp), (jm, fm) = displacement(design(capsules, phase=x0 - h)), \
-                    displacement(design(capsules, phase=x0 - 3 * h))
+                (jp, fp), (jm, fm) = displacement(design(capsules, steps, phase=x0 - h)), \
+                    displacement(design(capsules, steps, phase=x0 - 3 * h))
             else:
-                (jp, fp), (jm, fm) = displacement(design(capsules, **{key: x0 + h})), \
-                    displacement(design(capsules, **{key: x0 - h}))
+                (jp, fp), (jm, fm) = displacement(design(capsules, steps, **{key: x0 + h})), \
+                    displacement(design(capsules, steps, **{key: x0 - h}))
             assert fp == fm, f"{key}: the difference step changed an obstacle map"
             fd = (jp - jm) / (2 * h)
             assert abs(ad - fd) <= rel * abs(fd), (capsules, key, ad, fd)
+
+
+def test_autograd_function_matches_the_oracle(gpu):
+    """swimmer_run (torch.autograd.Function over the C ABI) against the
+    oracle's reverse mode, including the chain rule of mass and capsule
+    length through the inertia and volume formulas."""
+    import torch
+    from adjoint_helpers import V0, W0
+    from paper_1108_0786_gb300 import autograd as ag
+    sc = scenario(bc=wl.PERIODIC_X, g=(2e-6, 0.0, 0.0), cap_len=3.0)
+    p = ag.scenario_parameters(sc)
+    for b in range(3):
+        p["state0"][b, 7:10] = torch.tensor(V0[b])
+        p["state0"][b, 10:13] = torch.tensor(W0[b])
+    for v in p.values():
+        v.requires_grad_(True)
+    final = ag.swimmer_run(sc, N_STEPS, segment=16, precision="f64", **p)
+    (final * torch.from_numpy(SEED)).sum().backward()
+    ref = oracle_gradients(sc)
+    np.testing.assert_allclose(final.detach().numpy(), ref["final"], rtol=1e-10, atol=1e-12)
+
+    def close(got, want):
+        want = np.asarray(want)
+        assert np.abs(got.detach().numpy() - want).max() <= 1e-9 * max(np.abs(want).max(), 1e-300)
+    close(p["amp"].grad, ref["drive"][:, 0])
+    close(p["phase"].grad, ref["drive"][:, 1])
+    close(p["k"].grad, ref["spring"][:, 0])
+    close(p["rest"].grad, ref["spring"][:, 1])
+    close(p["damping"].grad, ref["spring"][:, 2])
+    close(p["state0"].grad, ref["state"])
+    # mass and length: the oracle's (m, I, V) gradients through differences
+    # of the oracle's own body properties
+    o = oracle.from_scenario(sc)
+    dmass, dlen = np.zeros(3), np.zeros(3)
+    for b, body in enumerate(sc.bodies):
+        def props(m, l):
+            s2 = dataclasses.replace(body, mass=m, length=l)
+            o2 = oracle.Oracle(sc.nx, sc.ny, sc.nz, sc.tau, sc.bc, sc.g)
+            o2.add_body(s2.shape, s2.radius, s2.length, s2.mass, s2.pos, s2.orient)
+            vi = o2.body_props(0)
+            return np.concatenate(([m], vi[1:], vi[:1]))
+        hm = 1e-4 * body.mass
+        dmass[b] = (ref["body"][b] * (props(body.mass + hm, body.length) - props(body.mass - hm, body.length))
+                    / (2 * hm)).sum()
+        if body.shape == wl.CAPSULE:
+            hl = 1e-4
+            dlen[b] = (ref["body"][b] * (props(body.mass, body.length + hl) - props(body.mass, body.length - hl))
+                       / (2 * hl)).sum()
+    assert np.abs(p["mass"].grad.numpy() - dmass).max() <= 1e-7 * np.abs(dmass).max()
+    assert abs(p["length"].grad[2].item() - dlen[2]) <= 1e-7 * abs(dlen[2])
+    assert dlen[2] != 0.0
+    del o
