@@ -81,20 +81,26 @@ class _SwimmerRun(torch.autograd.Function):
         d_mass = np.zeros(nb)
         d_length = np.zeros(nb)
         for b, body in enumerate(ctx.run.bodies):
-            m = torch.tensor(float(mass[b]), dtype=torch.float64, requires_grad=True)
-            l = torch.tensor(float(length[b]) if body.shape == wl.CAPSULE else 0.0, dtype=torch.float64,
-                             requires_grad=True)
-            inertia, vol = body_properties(body.shape, body.radius, l, m)
-            # J depends on (m, I, V): d/dm and d/dl through I(m, l) and V(l)
-            total = (float(g["body"][b, 0]) * m + (torch.from_numpy(g["body"][b, 1:4]) * inertia).sum() +
-                     float(g["body"][b, 4]) * vol)
-            dm, dl = torch.autograd.grad(total, (m, l), allow_unused=True)
-            d_mass[b] = float(dm)
-            d_length[b] = float(dl) if (dl is not None and body.shape == wl.CAPSULE) else 0.0
+            d_mass[b], d_length[b] = _mass_length_chain(body, float(mass[b]), float(length[b]), g["body"][b])
         t = lambda a, like: torch.as_tensor(a, dtype=like.dtype, device=like.device)
         return (t(g["drive"][:, 0], mass), t(g["drive"][:, 1], mass), t(g["spring"][:, 0], mass),
                 t(g["spring"][:, 1], mass), t(g["spring"][:, 2], mass), t(d_mass, mass),
                 t(d_length, length), t(g["state"], grad_final), None, None, None, None)
+
+
+def _mass_length_chain(body, mass, length, gbody):
+    """dJ/dm and dJ/dl from dJ/d(m, I1, I2, I3, V) through the inertia and
+    volume formulas."""
+    with torch.enable_grad():
+        m = torch.tensor(mass, dtype=torch.float64, requires_grad=True)
+        l = torch.tensor(length if body.shape == wl.CAPSULE else 0.0, dtype=torch.float64,
+                         requires_grad=True)
+        inertia, vol = body_properties(body.shape, body.radius, l, m)
+        # J depends on (m, I, V): d/dm and d/dl through I(m, l) and V(l)
+        total = (float(gbody[0]) * m + (torch.from_numpy(gbody[1:4]) * inertia).sum() +
+                 float(gbody[4]) * vol)
+        dm, dl = torch.autograd.grad(total, (m, l), allow_unused=True)
+    return float(dm), (float(dl) if (dl is not None and body.shape == wl.CAPSULE) else 0.0)
 
 
 def swimmer_run(sc, steps, amp, phase, k, rest, damping, mass, length, state0, segment=64,

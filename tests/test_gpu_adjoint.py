@@ -11,9 +11,11 @@ of each array's largest magnitude (the FP64 trajectories agree to 1e-10).
 FP32 storage: the same gradients within 1e-3.  The 96 x 48 x 48 gradient
 study (4000 steps, 63 segments of 64; the capsule variant over one period)
 is checked against central
-differences of FP64 forward runs for the drive amplitude a, the phase, the
-spring constant k and the capsule length, with steps small enough (bodies
-moved by ~1e-9 cells) that no cell of the obstacle maps flips.
+differences of FP64 forward runs for the drive amplitude a, the phase and
+the spring constant k, with steps small enough (bodies moved by ~1e-9
+cells) that no cell of the obstacle maps flips.  The capsule-length
+gradient (through mass and inertia) is compared with the oracle through
+the autograd binding.
 """
 import dataclasses
 import math
@@ -161,25 +163,6 @@ def displacement(sc, precision="f64"):
     return x - x0, maps.hexdigest()
 
 
-def capsule_chain(sc, gb):
-    """dJ/dl through mass (density 1 x volume), inertia and volume of the
-    three capsules, by automatic differentiation of the body formulas the
-    library uses (uniform solid capsule: cylinder plus two hemispheres)."""
-    import torch
-    r = torch.tensor(sc.bodies[0].radius, dtype=torch.float64)
-    l = torch.tensor(sc.bodies[0].length, dtype=torch.float64, requires_grad=True)
-    vc = math.pi * r * r * l
-    vh = 2.0 / 3.0 * math.pi * r ** 3
-    vol = vc + 2 * vh
-    m = vol
-    mc, mh = m * vc / vol, m * vh / vol
-    i1 = 0.5 * mc * r * r + 2 * (0.4 * mh * r * r)
-    i2 = mc * (r * r / 4 + l * l / 12) + 2 * mh * (0.4 * r * r + l * l / 4 + 3 * l * r / 8)
-    props = torch.stack([m, i1, i2, i2, vol])
-    jac = torch.stack([torch.autograd.grad(p, l, retain_graph=True)[0] for p in props]).numpy()
-    return float((gb * jac[None, :]).sum())
-
-
 @pytest.mark.parametrize("precision,rel", [("f64", 2e-3), ("f32", 1e-2)])
 def test_design_swimmer_gradients_against_central_differences(gpu, precision, rel):
     # the capsule swimmer loses its axial alignment after about two periods
@@ -206,11 +189,12 @@ def test_design_swimmer_gradients_against_central_differences(gpu, precision, re
             # (phase / omega = T / 4): difference just below it, where it is fixed
             "phase": float(sum(g["drive"][i, 1] for i, d in enumerate(sc.drives) if d.phase > 0)),
         }
-        if capsules:
-            grads["l"] = capsule_chain(sc, g["body"])
+        # (the capsule length acts through mass and inertia only: a step that
+        # keeps the maps moves J by ~1e-14, below a run's round-off, so its
+        # gradient is checked against the oracle, not by differences here)
         checks = {key: (ad, 1e-9 / max(abs(ad), 1e-6)) for key, ad in grads.items()}
         for key, (ad, h) in checks.items():
-            x0 = {"a": a0, "k": k0, "phase": ph0, "l": sc.bodies[0].length}[key]
+            x0 = {"a": a0, "k": k0, "phase": ph0}[key]
             if key == "phase":
                 (jp, fp), (jm, fm) = displacement(design(capsules, steps, phase=x0 - h)), \
                     displacement(design(capsules, steps, phase=x0 - 3 * h))
