@@ -211,13 +211,10 @@ def test_autograd_function_matches_the_oracle(gpu):
     oracle's reverse mode, including the chain rule of mass and capsule
     length through the inertia and volume formulas."""
     import torch
-    from adjoint_helpers import V0, W0
     from paper_1108_0786_gb300 import autograd as ag
     sc = scenario(bc=wl.PERIODIC_X, g=(2e-6, 0.0, 0.0), cap_len=3.0)
     p = ag.scenario_parameters(sc)
-    for b in range(3):
-        p["state0"][b, 7:10] = torch.tensor(V0[b])
-        p["state0"][b, 10:13] = torch.tensor(W0[b])
+    p["state0"] = torch.from_numpy(start(sc).bodies())    # the oracle's start state, bit for bit
     for v in p.values():
         v.requires_grad_(True)
     final = ag.swimmer_run(sc, N_STEPS, segment=16, precision="f64", **p)
