@@ -356,6 +356,7 @@ def run_ours(args, world, rank, local):
         line["storage_variants"] = variant_runs(workload(args, 0), args, 200)
     if not args.no_variants and rank == 0 and world == 1:
         line["adjoint"] = adjoint_run()
+        line["ensemble"] = ensemble_run()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
@@ -402,6 +403,53 @@ def adjoint_run(precision="f32", segment=64):
             "record_plus_backward_over_forward": round((times["record"] + times["backward"]) / times["forward"], 3),
             "d_displacement_d_amplitude": float((g["drive"][:, 0] * signs).sum()),
             "d_displacement_d_k": float(g["spring"][:, 0].sum())}
+
+
+def ensemble_run(precision="f32", reference_edge=48):
+    """The 96-box ensemble (one swimmer per periodic box, edges 48-96, 1000 /
+    2000 / 4000 steps): every member autotunes its bulk-kernel shape, then
+    the whole ensemble runs to completion; aggregate MLUPS = sum of cells x
+    steps over the wall-clock between two device synchronisations.  Member
+    error: the members of edge `reference_edge` rerun alone with FP64
+    storage; relative error of each body's displacement."""
+    import numpy as np
+    from paper_1108_0786_gb300 import lbm, workloads as wl
+    scs = wl.ensemble_members()
+    lats = [lbm.from_scenario(sc, precision=precision) for sc in scs]
+    shapes = []
+    for lat in lats:
+        lat.step(0)
+        shapes.append(lat.autotune(3))
+    x0 = [lat.bodies()[:, 0:3].copy() for lat in lats]
+    ens = lbm.Ensemble(lats)
+    ens.step([16] * len(lats))                  # builds the graphs; members then restart their count
+    ens.sync()
+    steps = [sc.steps - 16 for sc in scs]
+    t0 = time.perf_counter()
+    ens.step(steps)
+    ens.sync()
+    dt = time.perf_counter() - t0
+    updates = sum(sc.cells * n for sc, n in zip(scs, steps))
+    final = [lat.bodies() for lat in lats]
+    ens.close()
+    for lat in lats:
+        lat.close()
+    errors = []
+    for i, sc in enumerate(scs):
+        if sc.nx != reference_edge:
+            continue
+        ref = lbm.from_scenario(sc, precision="f64")
+        ref.step(sc.steps)
+        d_ref = np.linalg.norm(ref.bodies()[:, 0:3] - x0[i], axis=1)
+        d = np.linalg.norm(final[i][:, 0:3] - x0[i], axis=1)
+        errors.append(float(np.abs(d - d_ref).max() / d_ref.max()))
+        ref.close()
+    return {"workload": f"{len(scs)} periodic boxes (edges 48-96, {sum(sc.cells for sc in scs) / 1e6:.1f} M cells), "
+                        f"one three-body swimmer each, 1000/2000/4000 steps, {precision} storage",
+            "mlups": round(updates / dt / 1e6, 1), "wall_s": round(dt, 3), "cell_updates": updates,
+            "bulk_kernel_shapes": sorted({f"{v}x{m}" for v, m in shapes}),
+            "member_displacement_rel_err_vs_f64": {"members": len(errors), "max": max(errors) if errors else None,
+                                                   "median": float(np.median(errors)) if errors else None}}
 
 
 def run_reference(args, world, rank):

@@ -275,6 +275,33 @@ int lbm_adjoint_record(lbm_t *h, int n, int segment);
 int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, double *grad_prev,
                          double *grad_drive, double *grad_spring, double *grad_body, double *grad_pop);
 
+/* ---- ensembles ------------------------------------------------------------
+ *
+ * Many independent lattices (ensemble members, e.g. one swimmer design per
+ * member on its own periodic box, of uneven sizes and step counts) stepped
+ * together.  One CUDA graph holds, as parallel branches, CHUNK (16) steps of
+ * every member of a set; one launch of it advances the whole set, and the
+ * GPU's block scheduler spreads the members' kernels over the SMs.  Members
+ * whose step budget runs out drop out of the set (a graph per set is built
+ * on first use and kept).  There is no dependency between members: no
+ * kernel waits on another.  The paper runs one simulation per design study
+ * point; the ensemble is the throughput path for a set of such points.
+ *
+ * lbm_ensemble_create: members (n handles, not owned) must share one stream
+ * (lbm_set_stream); each keeps its own buffers, bodies, bulk-kernel shape
+ * (lbm_tune / lbm_autotune before the first lbm_ensemble_step) and status
+ * word.  lbm_ensemble_step advances member i by steps[i] steps (host array
+ * of n counts, >= 0): whole chunks through the ensemble graphs, the rest
+ * through the member's own step graphs.  Asynchronous, like lbm_step.
+ * lbm_ensemble_sync synchronises and returns the first member error.
+ * lbm_ensemble_destroy releases the graphs, not the members. */
+typedef struct lbm_ensemble_s lbm_ensemble_t;
+int lbm_ensemble_create(lbm_t *const *members, int n, lbm_ensemble_t **out);
+int lbm_ensemble_step(lbm_ensemble_t *e, const int *steps);
+int lbm_ensemble_sync(lbm_ensemble_t *e);
+int lbm_ensemble_destroy(lbm_ensemble_t *e);
+const char *lbm_ensemble_last_error(lbm_ensemble_t *e);
+
 /* Kernel launches one step makes (for launch accounting). */
 int lbm_kernels_per_step(lbm_t *h);
 

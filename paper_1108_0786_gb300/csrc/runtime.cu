@@ -1150,6 +1150,168 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     return LBM_OK;
 }
 
+}  // extern "C"
+
+// ---- ensembles ---------------------------------------------------------------
+
+struct lbm_ensemble_s {
+    std::vector<lbm_t *> members;
+    cudaStream_t stream = nullptr;          // the members' common stream
+    cudaStream_t cap = nullptr;             // capture origin
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;          // one per member
+    // one graph per set of members advanced together: CHUNK_STEPS steps of
+    // each as parallel branches
+    std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> graphs;
+    std::string err;
+};
+
+namespace {
+
+int ens_fail(lbm_ensemble_t *e, int code, const char *msg) {
+    if (e) e->err = msg;
+    return code;
+}
+
+void ens_release(lbm_ensemble_t *e) {
+    for (auto &g : e->graphs) cudaGraphExecDestroy(g.second);
+    e->graphs.clear();
+    for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
+    e->join.clear();
+    if (e->fork) cudaEventDestroy(e->fork);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    e->fork = nullptr;
+    e->cap = nullptr;
+}
+
+// the graph advancing the members `set` by CHUNK_STEPS steps each (built on
+// first use): fork from the capture origin to every member's capture
+// stream, its chunk of steps, join back
+int ens_graph(lbm_ensemble_t *e, const std::vector<int> &set, cudaGraphExec_t *out) {
+    for (auto &g : e->graphs)
+        if (g.first == set) { *out = g.second; return LBM_OK; }
+    cudaGraph_t g = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
+    cudaEventRecord(e->fork, e->cap);
+    for (int i : set) {
+        lbm_t *h = e->members[i];
+        cudaStreamWaitEvent(h->cap, e->fork, 0);
+        for (int k = 0; k < CHUNK_STEPS; ++k) enqueue_step(h, k & 1, h->cap, nullptr, nullptr, true);
+        cudaEventRecord(e->join[i], h->cap);
+        cudaStreamWaitEvent(e->cap, e->join[i], 0);
+    }
+    err = cudaStreamEndCapture(e->cap, &g);
+    if (err != cudaSuccess) return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
+    cudaGraphExec_t x = nullptr;
+    err = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
+    e->graphs.emplace_back(set, x);
+    *out = x;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_ensemble_create(lbm_t *const *members, int n, lbm_ensemble_t **out) {
+    if (!out) return LBM_E_ARG;
+    *out = nullptr;
+    if (!members || n < 1) return LBM_E_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!members[i]) return LBM_E_ARG;
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return fail(members[i], LBM_E_ARG, "a handle is twice in the ensemble");
+        if (members[i]->stream != members[0]->stream)
+            return fail(members[i], LBM_E_ARG, "ensemble members must share one stream");
+    }
+    lbm_ensemble_t *e = new (std::nothrow) lbm_ensemble_s();
+    if (!e) return LBM_E_OOM;
+    e->members.assign(members, members + n);
+    e->stream = members[0]->stream;
+    cudaError_t err = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && err == cudaSuccess; ++i) {
+        cudaEvent_t ev = nullptr;
+        err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (err == cudaSuccess) e->join.push_back(ev);
+    }
+    if (err != cudaSuccess) {
+        ens_release(e);
+        delete e;
+        return LBM_E_CUDA;
+    }
+    *out = e;
+    return LBM_OK;
+}
+
+int lbm_ensemble_destroy(lbm_ensemble_t *e) {
+    if (!e) return LBM_OK;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    ens_release(e);
+    delete e;
+    return LBM_OK;
+}
+
+int lbm_ensemble_step(lbm_ensemble_t *e, const int *steps) {
+    if (!e || !steps) return LBM_E_ARG;
+    const int n = (int)e->members.size();
+    std::vector<long long> left(n);
+    for (int i = 0; i < n; ++i) {
+        if (steps[i] < 0) return ens_fail(e, LBM_E_ARG, "negative step count");
+        left[i] = steps[i];
+        lbm_t *h = e->members[i];
+        int rc = ensure_device(h);
+        if (rc == LBM_OK) rc = build_graphs(h);
+        if (rc != LBM_OK) return ens_fail(e, rc, h->err.c_str());
+        // members enter a chunk at an even step (the chunk starts with parity 0)
+        if (left[i] > 0 && (h->steps & 1)) {
+            if ((rc = lbm_step(h, 1))) return ens_fail(e, rc, h->err.c_str());
+            --left[i];
+        }
+    }
+    for (;;) {
+        std::vector<int> set;
+        for (int i = 0; i < n; ++i)
+            if (left[i] >= CHUNK_STEPS) set.push_back(i);
+        if (set.empty()) break;
+        cudaGraphExec_t x = nullptr;
+        int rc = ens_graph(e, set, &x);
+        if (rc) return rc;
+        // members whose step budget runs out drop from the set: launch this
+        // graph as often as every member of the set has whole chunks left
+        long long chunks = left[set[0]] / CHUNK_STEPS;
+        for (int i : set) chunks = std::min(chunks, left[i] / CHUNK_STEPS);
+        for (long long c = 0; c < chunks; ++c) {
+            cudaError_t err = cudaGraphLaunch(x, e->stream);
+            if (err != cudaSuccess) return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
+        }
+        for (int i : set) {
+            e->members[i]->steps += chunks * CHUNK_STEPS;
+            left[i] -= chunks * CHUNK_STEPS;
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        if (left[i] > 0) {
+            int rc = lbm_step(e->members[i], (int)left[i]);
+            if (rc) return ens_fail(e, rc, e->members[i]->err.c_str());
+        }
+    return LBM_OK;
+}
+
+int lbm_ensemble_sync(lbm_ensemble_t *e) {
+    if (!e) return LBM_E_ARG;
+    for (lbm_t *h : e->members) {
+        int rc = sync_and_check(h);
+        if (rc) return ens_fail(e, rc, h->err.c_str());
+    }
+    return LBM_OK;
+}
+
+const char *lbm_ensemble_last_error(lbm_ensemble_t *e) { return e ? e->err.c_str() : "null handle"; }
+
 int lbm_kernels_per_step(lbm_t *h) { return h ? kernels_per_step(h) : LBM_E_ARG; }
 
 int lbm_bytes_per_cell(lbm_t *h) { return h ? (int)(2 * lbm::Q * pop_bytes(h->precision) + 1) : LBM_E_ARG; }

@@ -40,6 +40,8 @@ EXPORTED = (
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
     "lbm_tune", "lbm_autotune", "lbm_kernels_per_step", "lbm_bytes_per_cell", "lbm_last_error",
     "lbm_momentum_exchange_static", "lbm_adjoint_record", "lbm_adjoint_backward",
+    "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_sync", "lbm_ensemble_destroy",
+    "lbm_ensemble_last_error",
 )
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -96,6 +98,11 @@ def load_library(path: Optional[str] = None):
         "lbm_momentum_exchange_static": ([P, P, P, I, I, I, I, I, I, P, P], I),
         "lbm_adjoint_record": ([P, I, I], I),
         "lbm_adjoint_backward": ([P, DP, DP, DP, DP, DP, DP, DP], I),
+        "lbm_ensemble_create": ([ctypes.POINTER(P), I, PP], I),
+        "lbm_ensemble_step": ([P, ctypes.POINTER(I)], I),
+        "lbm_ensemble_sync": ([P], I),
+        "lbm_ensemble_destroy": ([P], I),
+        "lbm_ensemble_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -354,3 +361,47 @@ def from_scenario(sc, precision="f32", torch_memory=True, options=0, history=0):
         if math.isfinite(d.t_off):
             lat.set_drive_window(t, d.t_off)
     return lat
+
+
+class Ensemble:
+    """Independent lattices stepped together (``lbm_ensemble_*``): one CUDA
+    graph launch advances every member that still has whole 16-step chunks
+    left.  Members must share a stream (lattices created with torch_memory
+    use torch's current stream)."""
+
+    def __init__(self, lattices):
+        self._lib = load_library()
+        self.members = list(lattices)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        h = ctypes.c_void_p()
+        rc = self._lib.lbm_ensemble_create(arr, len(self.members), ctypes.byref(h))
+        if rc != OK:
+            raise LbmError(rc, "lbm_ensemble_create failed: " +
+                           self.members[0]._lib.lbm_last_error(self.members[0]._h).decode())
+        self._h = h
+
+    def _check(self, rc):
+        if rc < 0:
+            raise LbmError(rc, self._lib.lbm_ensemble_last_error(self._h).decode())
+        return rc
+
+    def step(self, steps):
+        """Advance member i by steps[i] steps (an int applies to all)."""
+        if isinstance(steps, int):
+            steps = [steps] * len(self.members)
+        arr = (ctypes.c_int * len(self.members))(*[int(v) for v in steps])
+        return self._check(self._lib.lbm_ensemble_step(self._h, arr))
+
+    def sync(self):
+        return self._check(self._lib.lbm_ensemble_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -240,6 +240,50 @@ def design_swimmer(capsules: bool = False, seed: int = 1108, steps: int = 4000) 
     return sc
 
 
+def ensemble_members(n: int = 96, seed: int = 1108, density: float = 2.0):
+    """``n`` independent periodic cubic boxes, one three-body swimmer each.
+
+    Edge U{48, 64, 80, 96}; each body a sphere of radius 3 or a capsule of
+    radius 3 and cylinder length 6 (p = 1/2), density 2 (radius-3 bodies at
+    density 1 sit on the explicit coupling's rotational instability); rest
+    lengths the two half-extents along the axis plus a 4-cell gap; k = 0.01,
+    damping 0.005, amplitude U[1e-4, 1e-3], phase U[pi/4, 3pi/4], period in
+    {200, 400, 800} and 5 periods of steps; the middle body at the box centre
+    jittered by U[-0.5, 0.5], orientation uniform.
+    """
+    rng = SplitMix64(seed)
+    out = []
+    for i in range(n):
+        L = rng.choice((48, 64, 80, 96))
+        period = rng.choice((200, 400, 800))
+        sc = Scenario(f"ensemble member {i}: {L}^3 periodic", L, L, L, 1.0, steps=5 * period)
+        shapes = tuple(rng.choice((SPHERE, CAPSULE)) for _ in range(3))
+        amp = rng.uniform(1e-4, 1e-3)
+        phase = rng.uniform(math.pi / 4, 3 * math.pi / 4)
+        q = rng.quaternion()
+        centre = tuple(L / 2 + rng.uniform(-0.5, 0.5) for _ in range(3))
+        half = [3.0 + (3.0 if sh == CAPSULE else 0.0) for sh in shapes]     # half-extent along the axis
+        rest_a = half[0] + half[1] + 4.0
+        rest_b = half[1] + half[2] + 4.0
+        ax = _axis(q)
+        offsets = (-rest_a, 0.0, rest_b)
+        freq = 1.0 / period
+        for sh, off in zip(shapes, offsets):
+            l = 6.0 if sh == CAPSULE else 0.0
+            vol = capsule_volume(3.0, l) if sh == CAPSULE else sphere_volume(3.0)
+            pos = tuple(centre[k] + off * ax[k] for k in range(3))
+            sc.bodies.append(Body(sh, 3.0, l, density * vol, pos, q))
+        b2, b1, b3 = 0, 1, 2
+        sc.springs.append(Spring(b2, b1, 0.01, rest_a, 0.005))
+        sc.springs.append(Spring(b3, b1, 0.01, rest_b, 0.005))
+        sc.drives.append(Drive(b2, -amp, freq, 0.0))
+        sc.drives.append(Drive(b1, amp, freq, 0.0))
+        sc.drives.append(Drive(b3, amp, freq, phase))
+        sc.drives.append(Drive(b1, -amp, freq, phase))
+        out.append(sc)
+    return out
+
+
 def scaled_copy(sc: Scenario, steps: int) -> Scenario:
     """The same scenario with a different step count."""
     import copy
