@@ -63,6 +63,7 @@ def _load():
     lib.lbm_ref_add_spring.argtypes = [P, I, I, D, D, D]
     lib.lbm_ref_set_drive.argtypes = [P, I, D, D, D]
     lib.lbm_ref_set_drive_window.argtypes = [P, I, D]
+    lib.lbm_ref_set_drive_axis.argtypes = [P, I, DP]
     lib.lbm_ref_set_body_state.argtypes = [P, I, DP]
     lib.lbm_ref_step.argtypes = [P, I]
     lib.lbm_ref_get_bodies.argtypes = [P, DP]
@@ -118,6 +119,9 @@ def from_scenario(sc, options=0):
         t = o.set_drive(d.body, d.amp, d.freq, d.phase)
         if math.isfinite(d.t_off):
             o.set_drive_window(t, d.t_off)
+        axis = tuple(getattr(d, "axis", (1.0, 0.0, 0.0)))
+        if axis != (1.0, 0.0, 0.0):
+            o.set_drive_axis(t, axis)
     return o
 
 
@@ -183,6 +187,10 @@ class Oracle:
 
     def set_drive_window(self, term, t_off):
         return self._check(self._lib.lbm_ref_set_drive_window(self._h, term, float(t_off)))
+
+    def set_drive_axis(self, term, axis):
+        a = np.ascontiguousarray(axis, dtype=np.float64)
+        return self._check(self._lib.lbm_ref_set_drive_axis(self._h, term, _dp(a)))
 
     def set_body_state(self, body, state):
         s = np.ascontiguousarray(state, dtype=np.float64)

@@ -44,9 +44,9 @@
  *   - cells that become solid drop their populations;
  *   - bodies advance by semi-implicit Euler with dt = 1: V += F/m, X += V,
  *     Omega += I_world^-1 T, q += (0,Omega) q / 2 then renormalised;
- *   - drive term: F = amp sin(2 pi freq t - phase) along the body x axis for
- *     phase/(2 pi freq) <= t < t_off, zero otherwise (the paper delays the
- *     third body by T/4, Sec. 3.3 and 5.1);
+ *   - drive term: F = amp sin(2 pi freq t - phase) along a body-frame axis
+ *     (default the body x axis) for phase/(2 pi freq) <= t < t_off, zero
+ *     otherwise (the paper delays the third body by T/4, Sec. 3.3 and 5.1);
  *   - body force g (a force density) enters the fluid through Guo's forcing
  *     term and the bodies as g times their volume.
  *
@@ -99,7 +99,7 @@ typedef struct {
 } body_t;
 
 typedef struct { int i, j; double k, rest, gamma; } spring_t;
-typedef struct { int body; double amp, freq, phase, t_off; } drive_t;
+typedef struct { int body; double amp, freq, phase, t_off, axis[3]; } drive_t;
 
 struct ref_lbm {
     int nx, ny, nz, bc, options;
@@ -318,8 +318,16 @@ int lbm_ref_set_drive(ref_lbm *h, int body, double amp, double freq, double phas
     drive_t *d = realloc(h->drive, sizeof *d * (h->nd + 1));
     if (!d) return REF_E_OOM;
     h->drive = d;
-    d[h->nd] = (drive_t){body, amp, freq, phase, INFINITY};
+    d[h->nd] = (drive_t){body, amp, freq, phase, INFINITY, {1.0, 0.0, 0.0}};
     return h->nd++;
+}
+
+int lbm_ref_set_drive_axis(ref_lbm *h, int term, const double axis[3])
+{
+    if (!h || !axis || term < 0 || term >= h->nd) return REF_E_ARG;
+    if (h->started) return fail(h, REF_E_STATE, "drive axes must be set before the first step");
+    for (int i = 0; i < 3; ++i) h->drive[term].axis[i] = axis[i];
+    return REF_OK;
 }
 
 int lbm_ref_set_drive_window(ref_lbm *h, int term, double t_off)
@@ -576,7 +584,9 @@ static int integrate_bodies(ref_lbm *h)
         double R[3][3];
         rot_matrix(h->body[dr->body].q, R);
         double f = dr->amp * sin(omega * t - dr->phase);
-        for (int i = 0; i < 3; ++i) Ftot[dr->body][i] += f * R[i][0];
+        /* the drive direction is a body-frame axis (default the body x axis) */
+        for (int i = 0; i < 3; ++i)
+            Ftot[dr->body][i] += f * (R[i][0] * dr->axis[0] + R[i][1] * dr->axis[1] + R[i][2] * dr->axis[2]);
     }
     /* damped harmonic springs (Eq. spring_i, damp_i, osci_i, osci_j) */
     for (int s = 0; s < h->ns; ++s) {
@@ -870,7 +880,8 @@ static void integrate_adjoint(const ref_lbm *h, const body_t *S, const double *f
         double R[3][3];
         rot_matrix(S[dr->body].q, R);
         double f = dr->amp * sin(omega * t - dr->phase);
-        for (int i = 0; i < 3; ++i) Ftot[dr->body][i] += f * R[i][0];
+        for (int i = 0; i < 3; ++i)
+            Ftot[dr->body][i] += f * (R[i][0] * dr->axis[0] + R[i][1] * dr->axis[1] + R[i][2] * dr->axis[2]);
     }
     for (int s = 0; s < h->ns; ++s) {
         const spring_t *sp = &h->spring[s];
@@ -949,11 +960,17 @@ static void integrate_adjoint(const ref_lbm *h, const body_t *S, const double *f
         double R[3][3];
         rot_matrix(S[dr->body].q, R);
         const double sn_ = sin(omega * t - dr->phase), cs = cos(omega * t - dr->phase);
-        const double *fh_ = Fh[dr->body];
-        double proj = fh_[0] * R[0][0] + fh_[1] * R[1][0] + fh_[2] * R[2][0];
+        const double *fh_ = Fh[dr->body], *a = dr->axis;
+        double dir[3], proj = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            dir[i] = R[i][0] * a[0] + R[i][1] * a[1] + R[i][2] * a[2];
+            proj += fh_[i] * dir[i];
+        }
         gd[2 * d] += sn_ * proj;
         gd[2 * d + 1] += -dr->amp * cs * proj;
-        for (int i = 0; i < 3; ++i) Rh[dr->body][i][0] += dr->amp * sn_ * fh_[i];
+        /* F = f R a: dF_i / dR_ij = f a_j */
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Rh[dr->body][i][j] += dr->amp * sn_ * fh_[i] * a[j];
     }
     /* springs */
     for (int s = 0; s < h->ns; ++s) {

@@ -66,6 +66,9 @@ int  lbm_ref_add_spring(ref_lbm *h, int i, int j, double k, double rest,
 int  lbm_ref_set_drive(ref_lbm *h, int body, double amp, double freq,
                        double phase);
 int  lbm_ref_set_drive_window(ref_lbm *h, int term, double t_off);
+/* direction of a drive term as a body-frame vector (default 1, 0, 0: the
+ * body x axis), used unnormalised; before the first step */
+int  lbm_ref_set_drive_axis(ref_lbm *h, int term, const double axis[3]);
 int  lbm_ref_set_body_state(ref_lbm *h, int body, const double state[13]);
 int  lbm_ref_step(ref_lbm *h, int n);
 int  lbm_ref_get_bodies(ref_lbm *h, double *out);

@@ -76,6 +76,7 @@ class Drive:
     freq: float
     phase: float
     t_off: float = math.inf
+    axis: Tuple[float, float, float] = (1.0, 0.0, 0.0)    # body-frame direction
 
 
 @dataclass
