@@ -147,11 +147,17 @@ int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass,
 int lbm_add_spring(lbm_t *h, int i, int j, double k, double rest, double damping);
 
 /* Add a drive term on `body` (Eq. FB1-FB3): the force
- * amp * sin(2 pi freq t - phase) along the body x axis for
- * t >= phase / (2 pi freq), zero before; t is the step index.  Terms on one
- * body add up, so the middle body's -(F2 + F3) is two terms.  Only before
- * the first step.  Returns the term id. */
+ * amp * sin(2 pi freq t - phase) along the body x axis (or the axis set by
+ * lbm_set_drive_axis) for t >= phase / (2 pi freq), zero before; t is the
+ * step index.  Terms on one body add up, so the middle body's -(F2 + F3) is
+ * two terms.  Only before the first step.  Returns the term id. */
 int lbm_set_drive(lbm_t *h, int body, double amp, double freq, double phase);
+
+/* Direction of drive term `term` as a body-frame vector (used as given, not
+ * normalised; default 1, 0, 0): the world-frame force is amp sin(...) R(q) a.
+ * The paper's perpendicular capsules (Sec. 5.1) are driven along the
+ * swimming direction, across their own axis.  Only before the first step. */
+int lbm_set_drive_axis(lbm_t *h, int term, const double axis[3]);
 
 /* Switch drive term `term` off for t >= t_off (the paper's protocol stops
  * the drives at t1 and t2, Sec. 5.1). */

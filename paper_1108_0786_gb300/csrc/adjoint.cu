@@ -363,11 +363,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
             sincos(dt.omega * tt - dt.phase, &sn_, &cs);
             f = dt.amp * sn_;
         }
-        const double *q = S[dt.body].q;
-        const double w = q[0], x = q[1], y = q[2], z = q[3];
-        dv.drive_f[3 * k + 0] = f * (1 - 2 * (y * y + z * z));
-        dv.drive_f[3 * k + 1] = f * (2 * (x * y + w * z));
-        dv.drive_f[3 * k + 2] = f * (2 * (x * z - w * y));
+        double R[3][3];
+        quat_to_matrix(S[dt.body].q, R);
+        for (int i = 0; i < 3; ++i)
+            dv.drive_f[3 * k + i] = f * (R[i][0] * dt.axis[0] + R[i][1] * dt.axis[1] + R[i][2] * dt.axis[2]);
         ab.drive_sc[3 * k + 0] = f;
         ab.drive_sc[3 * k + 1] = sn_;
         ab.drive_sc[3 * k + 2] = cs;
@@ -453,7 +452,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
         // drive terms of this body (their axis is the first column of R)
         for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k) {
             const double f = ab.drive_sc[3 * k];         // zero outside the drive window
-            for (int i = 0; i < 3; ++i) Rh[i][0] += f * Fh[i];
+            const double *a = dv.drives[k].axis;         // F = f R a: dF_i / dR_ij = f a_j
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) Rh[i][j] += f * Fh[i] * a[j];
         }
         double qh[4] = {0, 0, 0, 0};
         adj_rot_matrix(s.q, Rh, qh);
@@ -470,9 +471,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
         if (tt < dt.t_on || tt >= dt.t_off) continue;
         const double sn_ = ab.drive_sc[3 * k + 1], cs = ab.drive_sc[3 * k + 2];
         const double *fa = ab.fadj + 6 * dt.body;
-        const double *q = S[dt.body].q;
-        const double w = q[0], x = q[1], y = q[2], z = q[3];
-        const double proj = fa[0] * (1 - 2 * (y * y + z * z)) + fa[1] * (2 * (x * y + w * z)) + fa[2] * (2 * (x * z - w * y));
+        double R[3][3];
+        quat_to_matrix(S[dt.body].q, R);
+        double proj = 0.0;
+        for (int i = 0; i < 3; ++i)
+            proj += fa[i] * (R[i][0] * dt.axis[0] + R[i][1] * dt.axis[1] + R[i][2] * dt.axis[2]);
         ab.grad_drive[2 * k] += sn_ * proj;
         ab.grad_drive[2 * k + 1] += -dt.amp * cs * proj;
     }

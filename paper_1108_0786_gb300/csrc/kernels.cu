@@ -262,11 +262,10 @@ __device__ void integrate_block(const Device &dv, const StepPtrs &sp, int with_f
         const DriveTerm dt = dv.drives[k];
         double f = 0.0;
         if (!(t < dt.t_on || t >= dt.t_off)) f = dt.amp * sin(dt.omega * t - dt.phase);
-        const double *q = sp.body_cur[dt.body].q;     // body-frame x axis = first column of R(q)
-        const double w = q[0], x = q[1], y = q[2], z = q[3];
-        dv.drive_f[3 * k + 0] = f * (1 - 2 * (y * y + z * z));
-        dv.drive_f[3 * k + 1] = f * (2 * (x * y + w * z));
-        dv.drive_f[3 * k + 2] = f * (2 * (x * z - w * y));
+        double R[3][3];                                 // the drive acts along R(q) axis
+        quat_to_matrix(sp.body_cur[dt.body].q, R);
+        for (int i = 0; i < 3; ++i)
+            dv.drive_f[3 * k + i] = f * (R[i][0] * dt.axis[0] + R[i][1] * dt.axis[1] + R[i][2] * dt.axis[2]);
     }
     for (int k = threadIdx.x; k < dv.ns; k += blockDim.x) {
         const Spring sp_ = dv.springs[k];
@@ -374,14 +373,38 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
                           d.py ? sb.X[1] - d.ny * floor(sb.X[1] * d.iny) : sb.X[1],
                           d.pz ? sb.X[2] - d.nz * floor(sb.X[2] * d.inz) : sb.X[2]};
 
+    // exclusive prefix of the segment counts: thread t holds segments
+    // [t per, (t+1) per), per <= 4 (side <= MAX_SEGMENTS), block scan
     __shared__ int prefix[MAX_SEGMENTS + 1];
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int k = 0; k < side; ++k) {
-            prefix[k] = acc;
-            acc += counts[k];
+    __shared__ int seg_warp[FORCE_THREADS / 32];
+    {
+        const int per = (side + FORCE_THREADS - 1) / FORCE_THREADS;
+        const int k0 = threadIdx.x * per;
+        int loc[MAX_SEGMENTS / FORCE_THREADS], sum = 0;
+#pragma unroll
+        for (int i = 0; i < MAX_SEGMENTS / FORCE_THREADS; ++i) {
+            const int k = k0 + i;
+            loc[i] = (i < per && k < side) ? counts[k] : 0;
+            sum += loc[i];
         }
-        prefix[side] = acc;
+        const int ln = threadIdx.x & 31, wp = threadIdx.x >> 5;
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (ln >= o) incl += v;
+        }
+        if (ln == 31) seg_warp[wp] = incl;
+        __syncthreads();
+        int acc = incl - sum;
+        for (int w = 0; w < wp; ++w) acc += seg_warp[w];
+#pragma unroll
+        for (int i = 0; i < MAX_SEGMENTS / FORCE_THREADS; ++i) {
+            const int k = k0 + i;
+            if (i < per && k < side) prefix[k] = acc;
+            acc += loc[i];
+        }
+        if (threadIdx.x == FORCE_THREADS - 1) prefix[side] = acc;
     }
     __syncthreads();
     const int total = prefix[side];

@@ -87,6 +87,7 @@ struct DriveTerm {
     int body;
     double amp, freq, phase, t_off;
     double omega, t_on;     // 2 pi freq and phase / omega
+    double axis[3];         // body-frame direction (default the body x axis)
 };
 
 struct Link {

@@ -510,8 +510,18 @@ int lbm_set_drive(lbm_t *h, int body, double amp, double freq, double phase) {
     if (h->ready) return fail(h, LBM_E_STATE, "drives must be added before the first step");
     if (body < 0 || body >= nb(h) || !(freq > 0) || !(phase >= 0) || !std::isfinite(amp))
         return fail(h, LBM_E_ARG, "bad drive");
-    h->drives.push_back(DriveTerm{body, amp, freq, phase, INFINITY, 0.0, 0.0});
+    h->drives.push_back(DriveTerm{body, amp, freq, phase, INFINITY, 0.0, 0.0, {1.0, 0.0, 0.0}});
     return (int)h->drives.size() - 1;
+}
+
+int lbm_set_drive_axis(lbm_t *h, int term, const double axis[3]) {
+    if (!h || !axis || term < 0 || term >= (int)h->drives.size()) return LBM_E_ARG;
+    if (h->ready) return fail(h, LBM_E_STATE, "drive axes must be set before the first step");
+    for (int i = 0; i < 3; ++i) {
+        if (!std::isfinite(axis[i])) return fail(h, LBM_E_ARG, "non-finite drive axis");
+        h->drives[term].axis[i] = axis[i];
+    }
+    return LBM_OK;
 }
 
 int lbm_set_drive_window(lbm_t *h, int term, double t_off) {

@@ -261,6 +261,28 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
             if (fl[i] == 0 || (fl[i] & F_SOLID)) dst[(long long)b * C + c0 + i] = Codec<T>::st(f[b][i], scale);
 }
 
+// Velocity of body b's surface at lattice point p in the compute type R:
+// FP64 throughout for FP64 storage; otherwise the offset p - X in FP64 (one
+// subtraction per axis) and the minimum image and V + W x offset in R (the
+// moving-wall term is ~1e-4 and its R rounding sits below the storage's)
+template <typename R>
+__device__ inline void wall_velocity(const Domain &d, const BodyState &b, int px, int py, int pz, R (&u)[3]) {
+    if constexpr (sizeof(R) == 8) {
+        double w[3];
+        surface_velocity(d, b, px, py, pz, w);
+        u[0] = w[0]; u[1] = w[1]; u[2] = w[2];
+    } else {
+        R o0 = (R)((double)px - b.X[0]), o1 = (R)((double)py - b.X[1]), o2 = (R)((double)pz - b.X[2]);
+        if (d.px) o0 -= (R)d.nx * floor(o0 * (R)d.inx + (R)0.5);
+        if (d.py) o1 -= (R)d.ny * floor(o1 * (R)d.iny + (R)0.5);
+        if (d.pz) o2 -= (R)d.nz * floor(o2 * (R)d.inz + (R)0.5);
+        const R w0 = (R)b.W[0], w1 = (R)b.W[1], w2 = (R)b.W[2];
+        u[0] = (R)b.V[0] + (w1 * o2 - w2 * o1);
+        u[1] = (R)b.V[1] + (w2 * o0 - w0 * o2);
+        u[2] = (R)b.V[2] + (w0 * o1 - w1 * o0);
+    }
+}
+
 // Cells with a non-zero flag byte: refill, bounce-back at walls and moving
 // obstacles, then LBGK.  mode 0: block row blockIdx.y = body b, the threads
 // cover the cube of side 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) (the
@@ -365,9 +387,9 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
                 v = own[opp(b)];                                             // Eq. 4
             } else if (fp & F_SOLID) {
                 const int k = sp.bid_prev[sc];
-                double u[3] = {0.0, 0.0, 0.0};
-                if (k != NO_BODY) surface_velocity(d, sp.body_prev[k], sx, sy, sz, u);
-                const Cd eu = (Cd)(ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2]);
+                Cd u[3] = {0, 0, 0};
+                if (k != NO_BODY) wall_velocity<Cd>(d, sp.body_prev[k], sx, sy, sz, u);
+                const Cd eu = (Cd)ex(b) * u[0] + (Cd)ey(b) * u[1] + (Cd)ez(b) * u[2];
                 v = own[opp(b)] + (Cd)(6.0 * wgt(b)) * rho_x * eu;          // moving wall
             }
             f[b] = v;

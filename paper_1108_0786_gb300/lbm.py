@@ -34,7 +34,7 @@ PRECISIONS = {"f64": PREC_F64, "f32": PREC_F32, "f16": PREC_F16, "bf16": PREC_BF
 
 EXPORTED = (
     "lbm_create", "lbm_create_ex", "lbm_destroy", "lbm_set_allocator", "lbm_set_stream",
-    "lbm_add_body", "lbm_add_spring", "lbm_set_drive", "lbm_set_drive_window",
+    "lbm_add_body", "lbm_add_spring", "lbm_set_drive", "lbm_set_drive_window", "lbm_set_drive_axis",
     "lbm_set_body_state", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_steps_done",
     "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
@@ -76,6 +76,7 @@ def load_library(path: Optional[str] = None):
         "lbm_add_spring": ([P, I, I, D, D, D], I),
         "lbm_set_drive": ([P, I, D, D, D], I),
         "lbm_set_drive_window": ([P, I, D], I),
+        "lbm_set_drive_axis": ([P, I, DP], I),
         "lbm_set_body_state": ([P, I, DP], I),
         "lbm_set_fields": ([P, I, P, I], I),
         "lbm_step": ([P, I], I),
@@ -216,6 +217,10 @@ class Lattice:
 
     def set_drive_window(self, term, t_off):
         return self._check(self._lib.lbm_set_drive_window(self._h, int(term), float(t_off)))
+
+    def set_drive_axis(self, term, axis):
+        a = np.ascontiguousarray(axis, dtype=np.float64)
+        return self._check(self._lib.lbm_set_drive_axis(self._h, int(term), _dp(a)))
 
     def set_body_state(self, body, state):
         s = np.ascontiguousarray(state, dtype=np.float64)
@@ -360,6 +365,9 @@ def from_scenario(sc, precision="f32", torch_memory=True, options=0, history=0):
         t = lat.set_drive(d.body, d.amp, d.freq, d.phase)
         if math.isfinite(d.t_off):
             lat.set_drive_window(t, d.t_off)
+        axis = tuple(getattr(d, "axis", (1.0, 0.0, 0.0)))
+        if axis != (1.0, 0.0, 0.0):
+            lat.set_drive_axis(t, axis)
     return lat
 
 

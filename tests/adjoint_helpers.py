@@ -1,6 +1,8 @@
 """The three-body scenario the reverse-mode tests share (oracle pins and GPU
 parity): two spheres and a tilted capsule joined by two springs, moving and
 turning from the first step so that cells are covered and uncovered."""
+import dataclasses
+
 import numpy as np
 
 from paper_1108_0786_gb300 import workloads as wl
@@ -57,3 +59,26 @@ def start(sc, options=0, dstate=None):
     return set_motion(oracle.from_scenario(sc, options), dstate)
 
 
+
+
+def rot(q):
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def axis_swimmer(q, axis_world, n=32):
+    """Three spheres along x with the four drive terms; every body turned by
+    q and driven along the body-frame axis that q maps to axis_world."""
+    q = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
+    a = rot(q).T @ np.asarray(axis_world, dtype=np.float64)
+    sc = wl.Scenario("axis", n, n, n, 0.9)
+    m = 2.0 * wl.sphere_volume(2.5)
+    for x in (n / 2 - 8.2, n / 2 + 0.1, n / 2 + 8.3):
+        sc.bodies.append(wl.Body(wl.SPHERE, 2.5, 0.0, m, (x, n / 2 + 0.2, n / 2 - 0.3), tuple(q)))
+    sc.springs += [wl.Spring(0, 1, 0.02, 8.3, 0.01), wl.Spring(2, 1, 0.02, 8.2, 0.01)]
+    amp, f = 3e-3, 1 / 50.0
+    sc.drives += [wl.Drive(0, -amp, f, 0.0, axis=tuple(a)), wl.Drive(1, amp, f, 0.0, axis=tuple(a)),
+                  wl.Drive(2, amp, f, 1.1, axis=tuple(a)), wl.Drive(1, -amp, f, 1.1, axis=tuple(a))]
+    return sc
