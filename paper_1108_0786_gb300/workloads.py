@@ -19,6 +19,8 @@ from typing import List, Tuple
 SPHERE, CAPSULE = 0, 1
 PERIODIC_ALL = 7
 PERIODIC_X = 1
+PERIODIC_Y = 2
+PERIODIC_Z = 4
 
 _MASK = (1 << 64) - 1
 
