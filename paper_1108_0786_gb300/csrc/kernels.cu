@@ -32,6 +32,39 @@ __device__ inline bool cell_inside(const Domain &d, const BodyProps &p, const Bo
     return e0 * e0 + e1 * e1 + e2 * e2 <= p.r * p.r;
 }
 
+// minimum image of d for |d| < 3n/2 by two compares (no FP64 floor)
+__device__ inline double wrap_near_d(double d, int n, int periodic) {
+    if (!periodic) return d;
+    const double h = 0.5 * n;
+    return d > h ? d - n : (d < -h ? d + n : d);
+}
+
+// The inside test in FP32: the minimum-image offset to the wrapped centre in
+// FP64 (a difference and two compares per axis), then the distance in FP32
+// from that small offset.  Returns 1 (inside) or 0 (outside) when the squared
+// distance is farther than 2e-2 max(r^2, 1) from r^2 -- orders of magnitude
+// above its FP32 error -- and -1 otherwise (the FP64 test decides), so the
+// map is the FP64 map bit for bit.
+__device__ inline int inside_screen(const Domain &d, const BodyProps &p, const double (&cw)[3],
+                                    const float (&a)[3], int x, int y, int z) {
+    const float o0 = (float)wrap_near_d((double)x - cw[0], d.nx, d.px);
+    const float o1 = (float)wrap_near_d((double)y - cw[1], d.ny, d.py);
+    const float o2 = (float)wrap_near_d((double)z - cw[2], d.nz, d.pz);
+    float d2;
+    if (p.shape == 0) {
+        d2 = o0 * o0 + o1 * o1 + o2 * o2;
+    } else {
+        const float h = (float)(0.5 * p.l);
+        float sp = o0 * a[0] + o1 * a[1] + o2 * a[2];
+        sp = sp > h ? h : (sp < -h ? -h : sp);
+        const float e0 = o0 - sp * a[0], e1 = o1 - sp * a[1], e2 = o2 - sp * a[2];
+        d2 = e0 * e0 + e1 * e1 + e2 * e2;
+    }
+    const float r2 = (float)(p.r * p.r);
+    const float margin = 2e-2f * fmaxf(r2, 1.0f);
+    return d2 < r2 - margin ? 1 : (d2 > r2 + margin ? 0 : -1);
+}
+
 __device__ inline uint8_t wall_bit(const Domain &d, int x, int y, int z) {
     const bool w = (!d.px && (x == 0 || x == d.nx - 1)) || (!d.py && (y == 0 || y == d.ny - 1)) ||
                    (!d.pz && (z == 0 || z == d.nz - 1));
@@ -63,11 +96,20 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
     const Domain d = dv.dom;
     const int b = blockIdx.y;
     __shared__ int box[LBM_MAX_BODIES_DEV][6];     // wrapped lower corner, width per axis
+    __shared__ double cw[LBM_MAX_BODIES_DEV][3];   // wrapped centre
+    __shared__ float ax[LBM_MAX_BODIES_DEV][3];    // body x axis
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
     for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) {
         const BodyState sk = sp.body_cur[k];
         const BodyProps pk = dv.props[k];
         const double reach = pk.r + 0.5 * pk.l;
+        cw[k][0] = d.px ? sk.X[0] - d.nx * floor(sk.X[0] * d.inx) : sk.X[0];
+        cw[k][1] = d.py ? sk.X[1] - d.ny * floor(sk.X[1] * d.iny) : sk.X[1];
+        cw[k][2] = d.pz ? sk.X[2] - d.nz * floor(sk.X[2] * d.inz) : sk.X[2];
+        const double w = sk.q[0], qx = sk.q[1], qy = sk.q[2], qz = sk.q[3];
+        ax[k][0] = (float)(1 - 2 * (qy * qy + qz * qz));
+        ax[k][1] = (float)(2 * (qx * qy + w * qz));
+        ax[k][2] = (float)(2 * (qx * qz - w * qy));
         for (int a = 0; a < 3; ++a) {
             int lo = (int)floor(sk.X[a] - reach), hi = (int)floor(sk.X[a] + reach);
             int width = hi - lo + 1;
@@ -117,7 +159,10 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
             in = o >= 0 && o < box[k][3 + a];
         }
         if (!in) continue;
-        if (!cell_inside(d, dv.props[k], sp.body_cur[k], x, y, z)) continue;
+        // FP32 screen; cells within its margin of the surface take the FP64 test
+        const BodyProps pk = dv.props[k];
+        const int screen = inside_screen(d, pk, cw[k], ax[k], x, y, z);
+        if (screen == 0 || (screen < 0 && !cell_inside(d, pk, sp.body_cur[k], x, y, z))) continue;
         if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
         id = k;
     }
@@ -247,6 +292,11 @@ __device__ inline double wrap_near(double d, int n, int periodic) {
     const double h = 0.5 * n;
     return d > h ? d - n : (d < -h ? d + n : d);
 }
+__device__ inline float wrap_near_f(float d, int n, int periodic) {
+    if (!periodic) return d;
+    const float h = 0.5f * n;
+    return d > h ? d - n : (d < -h ? d + n : d);
+}
 
 // Rigid-body step (Algorithm 1, Eq. totalFSwimmer) for all bodies, run by
 // one block of 256 threads.  Phase 1 (threads over drive terms and springs)
@@ -372,6 +422,8 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
     const double xw[3] = {d.px ? sb.X[0] - d.nx * floor(sb.X[0] * d.inx) : sb.X[0],
                           d.py ? sb.X[1] - d.ny * floor(sb.X[1] * d.iny) : sb.X[1],
                           d.pz ? sb.X[2] - d.nz * floor(sb.X[2] * d.inz) : sb.X[2]};
+    const float vf[3] = {(float)sb.V[0], (float)sb.V[1], (float)sb.V[2]};
+    const float wf[3] = {(float)sb.W[0], (float)sb.W[1], (float)sb.W[2]};
 
     // exclusive prefix of the segment counts: thread t holds segments
     // [t per, (t+1) per), per <= 4 (side <= MAX_SEGMENTS), block scan
@@ -420,32 +472,52 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
         const Link lk = links[(long long)lo * dv.seg_cap + (j - prefix[lo])];
         const long long c = lk.cell;
         const int a = (int)lk.dir;
-        double rho = 1.0;
+        // cells are 32-bit indices (C < 2^31): 32-bit division
+        const unsigned cu = lk.cell, nxu = (unsigned)d.nx, nyu = (unsigned)d.ny;
+        const int x = (int)(cu % nxu), y = (int)((cu / nxu) % nyu), z = (int)(cu / (nxu * nyu));
         if constexpr (sizeof(T) == 8) {
+            double rho = 1.0;
             for (int q = 0; q < Q; ++q) rho += load_dev<T>(pop + q * C + c, s);
+            const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
+            // offsets of the fluid cell, of the link end and of the link midpoint
+            const double o0 = wrap_near(x - xw[0], d.nx, d.px), o1 = wrap_near(y - xw[1], d.ny, d.py),
+                         o2 = wrap_near(z - xw[2], d.nz, d.pz);
+            const double e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
+            const double u0 = sb.V[0] + (sb.W[1] * e2 - sb.W[2] * e1);
+            const double u1 = sb.V[1] + (sb.W[2] * e0 - sb.W[0] * e2);
+            const double u2 = sb.V[2] + (sb.W[0] * e1 - sb.W[1] * e0);
+            const double eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);   // e_-a . u_w
+            const double mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
+            const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
+            const double m0 = o0 + 0.5 * ex(a), m1 = o1 + 0.5 * ey(a), m2 = o2 + 0.5 * ez(a);
+            acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];
+            acc[3] += m1 * fl[2] - m2 * fl[1];
+            acc[4] += m2 * fl[0] - m0 * fl[2];
+            acc[5] += m0 * fl[1] - m1 * fl[0];
         } else {
-            float drho = 0.0f;          // FP32 sum of the stored deviations
+            // 32/16-bit storage: the link terms in FP32 (the populations are
+            // FP32 or coarser), their sum in FP64; the offsets from one FP64
+            // difference each
+            float drho = 0.0f;
             for (int q = 0; q < Q; ++q) drho += (float)load_dev<T>(pop + q * C + c, s);
-            rho += (double)drho;
+            const float rho = 1.0f + drho;
+            const float g_a = (float)wgt(a) + (float)load_dev<T>(pop + a * C + c, s);
+            const float o0 = wrap_near_f((float)(x - xw[0]), d.nx, d.px),
+                        o1 = wrap_near_f((float)(y - xw[1]), d.ny, d.py),
+                        o2 = wrap_near_f((float)(z - xw[2]), d.nz, d.pz);
+            const float e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
+            const float u0 = vf[0] + (wf[1] * e2 - wf[2] * e1);
+            const float u1 = vf[1] + (wf[2] * e0 - wf[0] * e2);
+            const float u2 = vf[2] + (wf[0] * e1 - wf[1] * e0);
+            const float eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);
+            const float mag = 2.0f * g_a + (float)(6.0 * wgt(a)) * rho * eu;
+            const float fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
+            const float m0 = o0 + 0.5f * ex(a), m1 = o1 + 0.5f * ey(a), m2 = o2 + 0.5f * ez(a);
+            acc[0] += (double)fl[0]; acc[1] += (double)fl[1]; acc[2] += (double)fl[2];
+            acc[3] += (double)(m1 * fl[2] - m2 * fl[1]);
+            acc[4] += (double)(m2 * fl[0] - m0 * fl[2]);
+            acc[5] += (double)(m0 * fl[1] - m1 * fl[0]);
         }
-        const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
-        const int x = (int)(c % d.nx), y = (int)((c / d.nx) % d.ny),
-                  z = (int)(c / ((long long)d.nx * d.ny));
-        // offsets of the fluid cell, of the link end and of the link midpoint
-        const double o0 = wrap_near(x - xw[0], d.nx, d.px), o1 = wrap_near(y - xw[1], d.ny, d.py),
-                     o2 = wrap_near(z - xw[2], d.nz, d.pz);
-        const double e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
-        const double u0 = sb.V[0] + (sb.W[1] * e2 - sb.W[2] * e1);
-        const double u1 = sb.V[1] + (sb.W[2] * e0 - sb.W[0] * e2);
-        const double u2 = sb.V[2] + (sb.W[0] * e1 - sb.W[1] * e0);
-        const double eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);   // e_-a . u_w
-        const double mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
-        const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
-        const double m0 = o0 + 0.5 * ex(a), m1 = o1 + 0.5 * ey(a), m2 = o2 + 0.5 * ez(a);
-        acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];
-        acc[3] += m1 * fl[2] - m2 * fl[1];
-        acc[4] += m2 * fl[0] - m0 * fl[2];
-        acc[5] += m0 * fl[1] - m1 * fl[0];
     }
     __shared__ double part[FORCE_THREADS / 32][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

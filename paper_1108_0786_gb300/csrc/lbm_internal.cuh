@@ -54,7 +54,7 @@ constexpr uint8_t F_WALL = 8;       // some neighbour lies beyond a no-slip wall
 constexpr uint8_t NO_BODY = 0xFF;
 
 // device status word bits
-constexpr int ST_OVERLAP = 1, ST_OUTSIDE = 2, ST_NAN = 4, ST_UNSTABLE = 8, ST_LINKS = 16;
+constexpr int ST_OVERLAP = 1, ST_OUTSIDE = 2, ST_NAN = 4, ST_UNSTABLE = 8, ST_LINKS = 16, ST_TIMEOUT = 32;
 
 // cells added around a body's extent in the remap region; with at most
 // MAX_STEP lattice units of motion per step the region covers every cell
@@ -231,6 +231,7 @@ bool valid_vector_width(const Device &dv, int v);
 bool valid_variant(const Device &dv, int v, int minb);
 int list_variants(const Device &dv, int *vec, int *minb, int max);
 int default_vector_width(const Device &dv);
+void prepare_bulk_variants();           // host: shared-memory opt-in of the staged variants (once)
 void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_integrate(const Device &dv, const StepPtrs &sp, int with_fluid, cudaStream_t s);

@@ -210,6 +210,7 @@ int upload_bodies(lbm_t *h) {
 int ensure_device(lbm_t *h) {
     if (h->ready) return LBM_OK;
     CK(cudaGetDevice(&h->device));
+    lbm::prepare_bulk_variants();
     int rc;
     const size_t es = pop_bytes(h->precision);
     const long long C = h->C;
@@ -357,6 +358,7 @@ int check_status(lbm_t *h) {
     if (st & lbm::ST_UNSTABLE)
         return fail(h, LBM_E_UNSTABLE, "a body moved more than %g lattice units in one step", LBM_MAX_BODY_STEP);
     if (st & lbm::ST_LINKS) return fail(h, LBM_E_LINKS, "link list capacity exceeded");
+    if (st & lbm::ST_TIMEOUT) return fail(h, LBM_E_TIMEOUT, "a bounded wait on a bulk copy ran out");
     return LBM_OK;
 }
 

@@ -401,6 +401,182 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
     for (int b = 0; b < Q; ++b) dst[(long long)b * C + c] = Codec<T>::st(f[b], dv.f16_scale);
 }
 
+// ---- TMA row-staged variant ---------------------------------------------------
+//
+// Persistent blocks walk the x-rows (y, z) of the lattice (row r = blockIdx.x
+// + i gridDim.x).  For each row one thread issues 20 bulk copies
+// (cp.async.bulk, completed on an mbarrier with the byte count): the 19
+// source rows, direction b from the neighbour row (y - ey_b, z - ez_b) of
+// plane b, and the row's flag bytes, into one of NSTAGE shared-memory stages;
+// NSTAGE rows are in flight.  The threads then pull f_b(x) = row_b[x - ex_b]
+// from shared memory, collide with the same code as the register variant
+// and store -- the same arithmetic, the same bits.  Every wait on an
+// mbarrier is bounded: past the limit the block records ST_TIMEOUT, waits
+// (bounded again) for its copies in flight and returns.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bulk copy global -> shared of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned), completing `bytes` transactions on bar
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+constexpr int TMA_THREADS = 256;
+constexpr long long TMA_WAIT_CYCLES = 1LL << 31;     // ~1 s of SM clock before a block gives up
+constexpr int TMA_HEADER = 128;                      // mbarriers, ahead of the stages
+
+__host__ __device__ constexpr size_t tma_stage_bytes(int nx, int elem) { return (size_t)Q * nx * elem + (size_t)nx; }
+
+template <typename T, int NSTAGE>
+__global__ void __launch_bounds__(TMA_THREADS) bulk_tma_kernel(const Device dv, const StepPtrs sp) {
+    using Cd = typename Codec<T>::C;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Domain d = dv.dom;
+    const int nx = d.nx;
+    const unsigned row_bytes = (unsigned)(nx * sizeof(T));
+    const unsigned flag_off = Q * row_bytes;
+    const unsigned stage_bytes = (unsigned)tma_stage_bytes(nx, sizeof(T));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    unsigned char *stages = smem + TMA_HEADER;
+    const long long rows = (long long)d.ny * d.nz;
+    const long long first = blockIdx.x;
+    const long long nmine = rows > first ? (rows - 1 - first) / gridDim.x + 1 : 0;
+    const T *__restrict__ src = static_cast<const T *>(sp.src);
+    T *__restrict__ dst = static_cast<T *>(sp.dst);
+    const long long C = d.C;
+    const float inv_scale = dv.f16_inv_scale, scale = dv.f16_scale;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < NSTAGE; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](long long i) {          // thread 0: row i of this block into stage i % NSTAGE
+        const int st = (int)(i % NSTAGE);
+        const long long r = first + i * gridDim.x;
+        const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+        unsigned char *buf = stages + (size_t)st * stage_bytes;
+        mbar_expect_tx(&bar[st], stage_bytes);
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            const int ys = wrap_axis(y - ey(b), d.ny), zs = wrap_axis(z - ez(b), d.nz);
+            bulk_copy(buf + b * row_bytes, src + (long long)b * C + ((long long)zs * d.ny + ys) * nx, row_bytes,
+                      &bar[st]);
+        }
+        bulk_copy(buf + flag_off, sp.flags_cur + r * nx, (unsigned)nx, &bar[st]);
+    };
+    if (threadIdx.x == 0)
+        for (long long i = 0; i < nmine && i < NSTAGE; ++i) issue(i);
+
+    long long i = 0;
+    bool ok = true;
+    for (; i < nmine; ++i) {
+        const int st = (int)(i % NSTAGE);
+        const unsigned parity = (unsigned)((i / NSTAGE) & 1);
+        const long long t0 = clock64();
+        bool ready = false;
+        while (!(ready = mbar_try_wait(&bar[st], parity)) && clock64() - t0 < TMA_WAIT_CYCLES) {
+        }
+        ok = __syncthreads_and(ready);
+        if (!ok) break;
+        const unsigned char *buf = stages + (size_t)st * stage_bytes;
+        const T *rowb = reinterpret_cast<const T *>(buf);
+        const uint8_t *fl = buf + flag_off;
+        const long long c0 = (first + i * gridDim.x) * nx;
+        for (int x = threadIdx.x; x < nx; x += TMA_THREADS) {
+            const uint8_t f8 = fl[x];
+            if (f8 != 0 && !(f8 & F_SOLID)) continue;      // the boundary kernel's cell
+            if (f8 & F_SOLID) {
+#pragma unroll
+                for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = Codec<T>::st((Cd)0, scale);
+                continue;
+            }
+            Cd g[Q];
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+                int xs = x - ex(b);
+                xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+                g[b] = Codec<T>::ld(rowb[b * nx + xs], inv_scale);
+            }
+            collide<Cd, std::is_same<T, float>::value>(g, dv);
+#pragma unroll
+            for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = Codec<T>::st(g[b], scale);
+        }
+        __syncthreads();                         // stage st is free again
+        if (threadIdx.x == 0 && i + NSTAGE < nmine) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(i + NSTAGE);
+        }
+    }
+    if (!ok && threadIdx.x == 0) {
+        atomicOr(dv.status, ST_TIMEOUT);
+        // the copies still in flight target this block's shared memory
+        for (long long j = i; j < nmine && j < i + NSTAGE; ++j) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&bar[j % NSTAGE], (unsigned)((j / NSTAGE) & 1)) &&
+                   clock64() - t0 < TMA_WAIT_CYCLES) {
+            }
+        }
+    }
+}
+
+template <typename T, int NSTAGE, int PER_SM>
+size_t tma_smem_bytes(int nx) { return TMA_HEADER + (size_t)NSTAGE * tma_stage_bytes(nx, sizeof(T)); }
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <typename T, int NSTAGE, int PER_SM>
+void launch_tma(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    const size_t bytes = tma_smem_bytes<T, NSTAGE, PER_SM>(dv.dom.nx);
+    const long long rows = (long long)dv.dom.ny * dv.dom.nz;
+    const long long grid = std::min<long long>(rows, (long long)sm_count() * PER_SM);
+    bulk_tma_kernel<T, NSTAGE><<<(unsigned)grid, TMA_THREADS, bytes, s>>>(dv, sp);
+}
+
+template <typename T, int NSTAGE, int PER_SM>
+bool tma_fits(int nx) {
+    return nx % 16 == 0 && tma_smem_bytes<T, NSTAGE, PER_SM>(nx) * PER_SM <= 227u * 1024u;
+}
+
+template <typename T, int NSTAGE, int PER_SM>
+void tma_prepare() {
+    cudaFuncSetAttribute(bulk_tma_kernel<T, NSTAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 template <typename T, int V, int BX, int BY, int MINB>
 void launch_bulk(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     const int nxq = dv.dom.nx / V;
@@ -419,8 +595,9 @@ void launch_shape(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
 
 using Launcher = void (*)(const Device &, const StepPtrs &, cudaStream_t);
 struct Variant {
-    int precision, vec, minb;
+    int precision, vec, minb;       // vec -1: TMA row-staged, minb = resident blocks per SM
     Launcher fn;
+    bool (*fits)(int nx);           // staged variants: shared memory and alignment for this nx
 };
 
 // the compiled variants of the bulk kernel; the first entry of a precision
@@ -442,6 +619,13 @@ const Variant kVariants[] = {
     {3, 2, 3, launch_shape<__nv_bfloat16, 2, 3>},
     {3, 8, 1, launch_shape<__nv_bfloat16, 8, 1>},
     {3, 1, 1, launch_shape<__nv_bfloat16, 1, 1>},
+    {0, -1, 1, launch_tma<double, 2, 1>, tma_fits<double, 2, 1>},
+    {1, -1, 1, launch_tma<float, 4, 1>, tma_fits<float, 4, 1>},
+    {1, -1, 2, launch_tma<float, 2, 2>, tma_fits<float, 2, 2>},
+    {2, -1, 1, launch_tma<__half, 4, 1>, tma_fits<__half, 4, 1>},
+    {2, -1, 2, launch_tma<__half, 3, 2>, tma_fits<__half, 3, 2>},
+    {3, -1, 1, launch_tma<__nv_bfloat16, 4, 1>, tma_fits<__nv_bfloat16, 4, 1>},
+    {3, -1, 2, launch_tma<__nv_bfloat16, 3, 2>, tma_fits<__nv_bfloat16, 3, 2>},
 };
 const Variant *find_variant(int precision, int vec, int minb) {
     const Variant *first = nullptr;
@@ -470,11 +654,30 @@ void launch_boundary(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
 }  // namespace
 
 bool valid_vector_width(const Device &dv, int v) {
+    if (v == -1) {
+        const Variant *x = find_variant(dv.precision, -1, 0);
+        return x && x->fits(dv.dom.nx);
+    }
     return v >= 1 && dv.dom.nx % v == 0 && find_variant(dv.precision, v, 0) != nullptr;
 }
 
 bool valid_variant(const Device &dv, int v, int minb) {
-    return valid_vector_width(dv, v) && find_variant(dv.precision, v, minb) != nullptr;
+    if (!valid_vector_width(dv, v)) return false;
+    const Variant *x = find_variant(dv.precision, v, minb);
+    return x && (!x->fits || x->fits(dv.dom.nx));
+}
+
+void prepare_bulk_variants() {
+    static bool done = false;
+    if (done) return;
+    tma_prepare<double, 2, 1>();
+    tma_prepare<float, 4, 1>();
+    tma_prepare<float, 2, 2>();
+    tma_prepare<__half, 4, 1>();
+    tma_prepare<__half, 3, 2>();
+    tma_prepare<__nv_bfloat16, 4, 1>();
+    tma_prepare<__nv_bfloat16, 3, 2>();
+    done = true;
 }
 
 int default_vector_width(const Device &dv) {
@@ -487,7 +690,7 @@ int default_vector_width(const Device &dv) {
 int list_variants(const Device &dv, int *vec, int *minb, int max) {
     int n = 0;
     for (const Variant &v : kVariants)
-        if (v.precision == dv.precision && dv.dom.nx % v.vec == 0 && n < max) {
+        if (v.precision == dv.precision && (v.fits ? v.fits(dv.dom.nx) : dv.dom.nx % v.vec == 0) && n < max) {
             vec[n] = v.vec;
             minb[n] = v.minb;
             ++n;
