@@ -223,7 +223,12 @@ int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots);
 /* Launch shape of the bulk stream-collide kernel: cells_per_thread
  * consecutive x cells per thread (1, 2, 4; 8 for 16-bit storage; nx must be
  * a multiple) and min_blocks_per_sm, a register cap that lets that many
- * 256-thread blocks share an SM (0 for each: the defaults).  Only the
+ * 256-thread blocks share an SM (0 for each: the defaults).
+ * cells_per_thread = -1 selects the row-staged kernel: persistent blocks
+ * (min_blocks_per_sm of them per SM: 1 or 2) copy each x-row's 19 source rows
+ * and flags into shared memory with bulk asynchronous copies (TMA) and
+ * collide from there; it needs nx a multiple of 16 and the stages within the
+ * shared memory of an SM (FP32: nx <= 1472 for 2 blocks per SM).  Only the
  * compiled combinations are accepted (LBM_E_ARG otherwise).  Only before the
  * first step.  Results do not depend on the shape. */
 int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm);
