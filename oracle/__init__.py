@@ -25,6 +25,7 @@ LIB = os.path.join(OUT_DIR, "liblbm_oracle.so")
 BC_PERIODIC_X, BC_PERIODIC_Y, BC_PERIODIC_Z = 1, 2, 4
 SHAPE_SPHERE, SHAPE_CAPSULE = 0, 1
 OPT_NO_FLUID = 1
+OPT_AVERAGE_FORCE = 2
 FIELD_RHO, FIELD_U, FIELD_FLAGS, FIELD_POP = 0, 1, 2, 3
 
 # error codes returned by the oracle (same numeric values as the GPU library)

@@ -48,7 +48,11 @@
  *     (default the body x axis) for phase/(2 pi freq) <= t < t_off, zero
  *     otherwise (the paper delays the third body by T/4, Sec. 3.3 and 5.1);
  *   - body force g (a force density) enters the fluid through Guo's forcing
- *     term and the bodies as g times their volume.
+ *     term and the bodies as g times their volume;
+ *   - option REF_OPT_AVERAGE_FORCE (not in the paper): the rigid-body step
+ *     takes the mean hydrodynamic force and torque of steps n and n-1, a
+ *     stabiliser of the explicit coupling for bodies near or below the
+ *     fluid's density.
  *
  * Collision, stream and field exports are parallel over cells with OpenMP
  * when compiled with -fopenmp; every loop that sums in a particular order
@@ -114,6 +118,7 @@ struct ref_lbm {
     spring_t *spring;
     drive_t *drive;
     double Fh[MAX_BODIES][3], Th[MAX_BODIES][3];
+    double Fh_prev[MAX_BODIES][3], Th_prev[MAX_BODIES][3];   /* load of the previous step */
     long step;
     int started;
     unsigned long long flag_digest;   /* running digest of every step's obstacle map */
@@ -219,7 +224,8 @@ int lbm_ref_create_ex(int nx, int ny, int nz, double tau, int bc,
     if (!out) return REF_E_ARG;
     *out = NULL;
     fill_opposite();
-    if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5) || bc < 0 || bc > 7)
+    if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5) || bc < 0 || bc > 7 ||
+        (options & ~(REF_OPT_NO_FLUID | REF_OPT_AVERAGE_FORCE)))
         return REF_E_ARG;
     ref_lbm *h = calloc(1, sizeof *h);
     if (!h) return REF_E_OOM;
@@ -570,12 +576,21 @@ static void hydro_force(ref_lbm *h)
 
 static int integrate_bodies(ref_lbm *h)
 {
-    double Ftot[MAX_BODIES][3];
+    double Ftot[MAX_BODIES][3], Tq[MAX_BODIES][3];
     double t = (double)h->step;
+    /* with REF_OPT_AVERAGE_FORCE the step takes the mean hydrodynamic load
+     * of this step and the previous one (from the second step on) */
+    const int avg = (h->options & REF_OPT_AVERAGE_FORCE) && h->step > 0;
     for (int k = 0; k < h->nb; ++k) {
         const body_t *b = &h->body[k];
-        for (int i = 0; i < 3; ++i) Ftot[k][i] = h->Fh[k][i] + h->g[i] * b->volume;
+        for (int i = 0; i < 3; ++i) {
+            const double f = avg ? 0.5 * (h->Fh[k][i] + h->Fh_prev[k][i]) : h->Fh[k][i];
+            Tq[k][i] = avg ? 0.5 * (h->Th[k][i] + h->Th_prev[k][i]) : h->Th[k][i];
+            Ftot[k][i] = f + h->g[i] * b->volume;
+        }
     }
+    memcpy(h->Fh_prev, h->Fh, sizeof h->Fh);
+    memcpy(h->Th_prev, h->Th, sizeof h->Th);
     /* driving forces of the cycling strategy (Eq. FB1-FB3) along body x */
     for (int d = 0; d < h->nd; ++d) {
         const drive_t *dr = &h->drive[d];
@@ -613,7 +628,7 @@ static int integrate_bodies(ref_lbm *h)
         double R[3][3], Tb[3], dW[3];
         rot_matrix(b->q, R);
         for (int i = 0; i < 3; ++i)
-            Tb[i] = R[0][i] * h->Th[k][0] + R[1][i] * h->Th[k][1] + R[2][i] * h->Th[k][2];
+            Tb[i] = R[0][i] * Tq[k][0] + R[1][i] * Tq[k][1] + R[2][i] * Tq[k][2];
         for (int i = 0; i < 3; ++i) Tb[i] /= b->inertia[i];
         for (int i = 0; i < 3; ++i) dW[i] = R[i][0] * Tb[0] + R[i][1] * Tb[1] + R[i][2] * Tb[2];
         for (int i = 0; i < 3; ++i) b->Om[i] += dW[i];
@@ -1188,6 +1203,7 @@ int lbm_ref_adjoint(ref_lbm *h, int n, const double *seed, double *grad_state, d
                     double *grad_pop, double *grad_drive, double *grad_spring, double *grad_body)
 {
     if (!h || n < 1 || !seed) return REF_E_ARG;
+    if (h->options & REF_OPT_AVERAGE_FORCE) return fail(h, REF_E_ARG, "no reverse mode with the averaged load");
     const long C = h->C, QC = (long)Q * C;
     const int nb = h->nb;
     const int first_run = !h->started;

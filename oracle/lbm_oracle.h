@@ -47,6 +47,7 @@ extern "C" {
 #define REF_SHAPE_CAPSULE 1
 
 #define REF_OPT_NO_FLUID  1   /* bodies only: no mapping, no hydrodynamic force */
+#define REF_OPT_AVERAGE_FORCE 2  /* rigid-body step with the mean load of steps n and n-1 */
 
 #define REF_FIELD_RHO   0     /* double[cells] */
 #define REF_FIELD_U     1     /* double[3][cells] */
