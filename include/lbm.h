@@ -81,6 +81,9 @@ extern "C" {
 #define LBM_PREC_BF16 3
 
 #define LBM_OPT_NO_FLUID  1   /* bodies only: no mapping, no hydrodynamic force */
+#define LBM_OPT_AVERAGE_FORCE 2   /* rigid-body step with the mean hydrodynamic load of steps n and n-1
+                                     (not in the paper: a stabiliser of the explicit coupling for
+                                     light bodies; lbm_get_forces still reports step n's load) */
 
 #define LBM_FIELD_RHO   0     /* density, cells */
 #define LBM_FIELD_U     1     /* velocity, [3][cells] */

@@ -338,7 +338,9 @@ __device__ void integrate_block(const Device &dv, const StepPtrs &sp, int with_f
             double v = 0.0;
             if (with_fluid)
                 for (int k = 0; k < FORCE_BLOCKS; ++k) v += dv.fpart[((long long)b * FORCE_BLOCKS + k) * 6 + i];
+            const double prev = dv.fh[b * 6 + i];
             dv.fh[b * 6 + i] = v;
+            if (dv.avg_force && tstep > 0) v = 0.5 * (v + prev);
             if (i < 3) F[i] = v + dv.g[i] * pb.volume; else Tq[i - 3] = v;
         }
         for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k)

@@ -168,6 +168,7 @@ struct Device {
     int nb, ns, nd;
     double tau, omega, g[3];
     int forced;
+    int avg_force;          // the rigid-body step uses the mean load of steps n and n-1
     float f16_scale, f16_inv_scale;
     const BodyProps *props;
     const Spring *springs;

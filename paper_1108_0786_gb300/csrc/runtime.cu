@@ -228,6 +228,7 @@ int ensure_device(lbm_t *h) {
     dv.omega = 1.0 / h->tau;
     for (int i = 0; i < 3; ++i) dv.g[i] = h->g[i];
     dv.forced = (h->g[0] != 0.0 || h->g[1] != 0.0 || h->g[2] != 0.0) ? 1 : 0;
+    dv.avg_force = (h->options & LBM_OPT_AVERAGE_FORCE) ? 1 : 0;
     dv.f16_scale = h->precision == LBM_PREC_F16 ? 1024.0f : 1.0f;
     dv.f16_inv_scale = 1.0f / dv.f16_scale;
     dv.remap_side = 2 * (emax + lbm::REMAP_MARGIN) + 1;
@@ -415,7 +416,7 @@ int lbm_create_ex(int nx, int ny, int nz, double tau, int bc, int precision, con
     if (!out) return LBM_E_ARG;
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5) || bc < 0 || bc > 7 || precision < 0 || precision > 3 ||
-        (options & ~LBM_OPT_NO_FLUID))
+        (options & ~(LBM_OPT_NO_FLUID | LBM_OPT_AVERAGE_FORCE)))
         return LBM_E_ARG;
     const long long C = (long long)nx * ny * nz;
     if (C > (1LL << 31) - 1) return LBM_E_ARG;   // link cells are 32-bit indices
@@ -874,6 +875,8 @@ int lbm_adjoint_record(lbm_t *h, int n, int segment) {
     if (h->precision != LBM_PREC_F64 && h->precision != LBM_PREC_F32)
         return fail(h, LBM_E_ARG, "the reverse sweep needs FP64 or FP32 storage");
     if (nb(h) == 0) return fail(h, LBM_E_ARG, "the reverse sweep needs at least one body");
+    if (h->options & LBM_OPT_AVERAGE_FORCE)
+        return fail(h, LBM_E_ARG, "the reverse sweep does not cover LBM_OPT_AVERAGE_FORCE");
     int rc = ensure_device(h);
     if (rc) return rc;
     if ((rc = build_graphs(h))) return rc;

@@ -321,3 +321,18 @@ def test_bf16_storage_channel_swimmer_accuracy():
     rel_l2, disp_err, _, _ = channel_run("bf16")
     assert disp_err < 0.3, disp_err
     assert rel_l2 < 0.2, rel_l2
+
+
+def test_averaged_load_option_matches_the_oracle():
+    """LBM_OPT_AVERAGE_FORCE (the rigid-body step takes the mean load of
+    steps n and n-1): FP64 GPU against the oracle with the same option."""
+    import oracle
+    sc = wl.three_sphere_periodic()
+    o = oracle.from_scenario(sc, oracle.OPT_AVERAGE_FORCE)
+    lat = lbm.from_scenario(sc, precision="f64", options=lbm.OPT_AVERAGE_FORCE)
+    o.step(300)
+    lat.step(300)
+    np.testing.assert_allclose(lat.bodies(), o.bodies(), rtol=1e-10, atol=1e-12)
+    assert np.abs(lat.pop() - o.pop()).max() <= 1e-12
+    np.testing.assert_allclose(lat.forces(), o.forces(), rtol=1e-9, atol=1e-13)
+    lat.close()
