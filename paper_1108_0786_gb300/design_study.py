@@ -66,6 +66,33 @@ DESIGNS = {
 }
 
 
+# the paper's results per design (Tables 2, 4, 5, 6): u_swim and u_GA in
+# 1e-6 lattice units per step, the error bound in %, efficiency in 1e-4
+PAPER_RESULTS = {
+    "a": (9.05, 8.98, 1, 10.44), "q": (2.02, 2.45, 18, 0.88),
+    "b": (7.32, 7.21, 2, 7.77), "c": (6.66, 6.31, 6, 5.86), "d": (7.11, 7.16, 1, 7.37),
+    "e": (5.68, 5.48, 4, 5.31), "f": (4.78, 4.50, 7, 3.69),
+    "g": (6.40, 6.82, 7, 5.97), "h": (5.71, 6.50, 13, 4.24), "i": (6.23, 6.75, 8, 5.74),
+    "j": (4.21, 4.66, 10, 3.08), "k": (3.69, 3.95, 7, 2.12),
+    "l": (6.75, 7.66, 12, 6.47), "m": (6.30, 8.96, 30, 4.76), "n": (6.44, 7.74, 17, 5.93),
+    "o": (5.05, 6.63, 24, 4.08), "p": (4.90, 6.70, 27, 3.63),
+}
+
+
+def markdown_table(res):
+    """The results beside the paper's (u in 1e-6, efficiency in 1e-4)."""
+    lines = ["| design | u_swim | paper | u_GA | paper | error % | paper | efficiency | paper | d1 | d2 | sin dphi |",
+             "|---|---|---|---|---|---|---|---|---|---|---|---|"]
+    for lab in DESIGNS:
+        if lab not in res:
+            continue
+        r, p = res[lab], PAPER_RESULTS[lab]
+        lines.append(f"| ({lab}) | {r['u_swim'] * 1e6:.2f} | {p[0]:.2f} | {r['u_ga'] * 1e6:.2f} | {p[1]:.2f} | "
+                     f"{r['error_pct']:.1f} | < {p[2]} | {r['efficiency'] * 1e4:.2f} | {p[3]:.2f} | "
+                     f"{r['d1']:.2f} | {r['d2']:.2f} | {r['sin_dphi']:.2f} |")
+    return "\n".join(lines)
+
+
 def lattice_parameters():
     """The protocol's physical parameters in lattice units (dx = dt = 1)."""
     u = analysis.lattice_units(SI["dx"], PERIOD, OMEGA_SI, SI["mass_unit"])
@@ -195,9 +222,15 @@ def main(argv=None):
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--designs", default="".join(DESIGNS))
     ap.add_argument("--json", default=None, help="write the results as JSON to this file")
+    ap.add_argument("--from-json", default=None, help="format results written earlier instead of running")
     args = ap.parse_args(argv)
-    res = run(list(args.designs), precision=args.precision)
+    if args.from_json:
+        with open(args.from_json) as fh:
+            res = json.load(fh)
+    else:
+        res = run(list(args.designs), precision=args.precision)
     print(json.dumps(res, indent=1))
+    print(markdown_table(res))
     if args.json:
         with open(args.json, "w") as fh:
             json.dump(res, fh, indent=1)
