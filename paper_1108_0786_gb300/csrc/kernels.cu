@@ -32,24 +32,24 @@ __device__ inline bool cell_inside(const Domain &d, const BodyProps &p, const Bo
     return e0 * e0 + e1 * e1 + e2 * e2 <= p.r * p.r;
 }
 
-// minimum image of d for |d| < 3n/2 by two compares (no FP64 floor)
-__device__ inline double wrap_near_d(double d, int n, int periodic) {
-    if (!periodic) return d;
-    const double h = 0.5 * n;
-    return d > h ? d - n : (d < -h ? d + n : d);
-}
-
-// The inside test in FP32: the minimum-image offset to the wrapped centre in
-// FP64 (a difference and two compares per axis), then the distance in FP32
-// from that small offset.  Returns 1 (inside) or 0 (outside) when the squared
-// distance is farther than 2e-2 max(r^2, 1) from r^2 -- orders of magnitude
-// above its FP32 error -- and -1 otherwise (the FP64 test decides), so the
-// map is the FP64 map bit for bit.
-__device__ inline int inside_screen(const Domain &d, const BodyProps &p, const double (&cw)[3],
+// The inside test in FP32: the minimum-image offset as an integer difference
+// of cells (wrapped by compares) minus the centre's offset within its cell,
+// then the distance in FP32 from that small, nearly exact offset.  Returns 1
+// (inside) or 0 (outside) when the squared distance is farther than
+// 2e-2 max(r^2, 1) from r^2 -- orders of magnitude above its FP32 error --
+// and -1 otherwise (the FP64 test decides), so the map is the FP64 map bit
+// for bit.
+__device__ inline int inside_screen(const Domain &d, const BodyProps &p, const int (&ci)[3], const float (&cf)[3],
                                     const float (&a)[3], int x, int y, int z) {
-    const float o0 = (float)wrap_near_d((double)x - cw[0], d.nx, d.px);
-    const float o1 = (float)wrap_near_d((double)y - cw[1], d.ny, d.py);
-    const float o2 = (float)wrap_near_d((double)z - cw[2], d.nz, d.pz);
+    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz}, q3[3] = {x, y, z};
+    float o[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        int io = q3[i] - ci[i];
+        if (per[i]) io = 2 * io > n3[i] ? io - n3[i] : (2 * io < -n3[i] ? io + n3[i] : io);
+        o[i] = (float)io - cf[i];
+    }
+    const float o0 = o[0], o1 = o[1], o2 = o[2];
     float d2;
     if (p.shape == 0) {
         d2 = o0 * o0 + o1 * o1 + o2 * o2;
@@ -91,21 +91,34 @@ __global__ void init_flags_kernel(const Domain d, uint8_t *f0, uint8_t *f1, uint
 // culled with integer boxes first, so the FP64 inside test runs only for
 // the bodies whose box holds the cell.
 constexpr int REMAP_THREADS = 256;
+// A cell farther than this from a body's bounding box [floor(X - reach),
+// floor(X + reach)] can hold no flag of that body in epochs n-2 .. n: solid
+// cells of epoch n-3 lie within 1.5 cells of the current extent, NEAR adds a
+// neighbour's 1.42 cells, and the floor of the upper bound loses up to one.
+constexpr int STATIC_REACH = 4;
 
 __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
     const Domain d = dv.dom;
     const int b = blockIdx.y;
     __shared__ int box[LBM_MAX_BODIES_DEV][6];     // wrapped lower corner, width per axis
-    __shared__ double cw[LBM_MAX_BODIES_DEV][3];   // wrapped centre
+    __shared__ int ebox[LBM_MAX_BODIES_DEV][6];    // the same grown by STATIC_REACH cells
+    __shared__ int cwi[LBM_MAX_BODIES_DEV][3];     // wrapped centre: cell
+    __shared__ float cwf[LBM_MAX_BODIES_DEV][3];   // and offset within it
     __shared__ float ax[LBM_MAX_BODIES_DEV][3];    // body x axis
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
     for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) {
         const BodyState sk = sp.body_cur[k];
         const BodyProps pk = dv.props[k];
         const double reach = pk.r + 0.5 * pk.l;
-        cw[k][0] = d.px ? sk.X[0] - d.nx * floor(sk.X[0] * d.inx) : sk.X[0];
-        cw[k][1] = d.py ? sk.X[1] - d.ny * floor(sk.X[1] * d.iny) : sk.X[1];
-        cw[k][2] = d.pz ? sk.X[2] - d.nz * floor(sk.X[2] * d.inz) : sk.X[2];
+        {
+            const double inv[3] = {d.inx, d.iny, d.inz};
+            for (int a = 0; a < 3; ++a) {
+                const double c = per[a] ? sk.X[a] - n3[a] * floor(sk.X[a] * inv[a]) : sk.X[a];
+                const double fc = floor(c);
+                cwi[k][a] = (int)fc;
+                cwf[k][a] = (float)(c - fc);
+            }
+        }
         const double w = sk.q[0], qx = sk.q[1], qy = sk.q[2], qz = sk.q[3];
         ax[k][0] = (float)(1 - 2 * (qy * qy + qz * qz));
         ax[k][1] = (float)(2 * (qx * qy + w * qz));
@@ -113,13 +126,19 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
         for (int a = 0; a < 3; ++a) {
             int lo = (int)floor(sk.X[a] - reach), hi = (int)floor(sk.X[a] + reach);
             int width = hi - lo + 1;
+            int elo = lo - STATIC_REACH, ewidth = width + 2 * STATIC_REACH;
             if (per[a]) {
                 lo %= n3[a];
                 if (lo < 0) lo += n3[a];
                 if (width > n3[a]) width = n3[a];
+                elo %= n3[a];
+                if (elo < 0) elo += n3[a];
+                if (ewidth > n3[a]) ewidth = n3[a];
             }
             box[k][a] = lo;
             box[k][3 + a] = width;
+            ebox[k][a] = elo;
+            ebox[k][3 + a] = ewidth;
         }
     }
     __syncthreads();
@@ -151,8 +170,16 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
     const int p3[3] = {x, y, z};
 
     int id = NO_BODY;
+    bool reached = false;           // within STATIC_REACH cells of some body's box
     for (int k = 0; k < dv.nb; ++k) {
         bool in = true;
+        for (int a = 0; a < 3 && in; ++a) {
+            int o = p3[a] - ebox[k][a];
+            if (per[a] && o < 0) o += n3[a];
+            in = o >= 0 && o < ebox[k][3 + a];
+        }
+        if (!in) continue;
+        reached = true;
         for (int a = 0; a < 3 && in; ++a) {
             int o = p3[a] - box[k][a];
             if (per[a] && o < 0) o += n3[a];
@@ -161,11 +188,15 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
         if (!in) continue;
         // FP32 screen; cells within its margin of the surface take the FP64 test
         const BodyProps pk = dv.props[k];
-        const int screen = inside_screen(d, pk, cw[k], ax[k], x, y, z);
+        const int screen = inside_screen(d, pk, cwi[k], cwf[k], ax[k], x, y, z);
         if (screen == 0 || (screen < 0 && !cell_inside(d, pk, sp.body_cur[k], x, y, z))) continue;
         if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
         id = k;
     }
+    // farther than STATIC_REACH from every body's box: the cell holds its
+    // static flags in both epoch buffers already (nothing within reach was
+    // solid in the last three steps, at most 0.5 cells of motion per step)
+    if (!reached) return;
     const uint8_t solid = id != NO_BODY ? F_SOLID : 0;
     uint8_t flags = solid | wall_bit(d, x, y, z);
     if (!init_mode) {
@@ -290,11 +321,6 @@ constexpr int MAX_SEGMENTS = 1024;
 __device__ inline double wrap_near(double d, int n, int periodic) {
     if (!periodic) return d;
     const double h = 0.5 * n;
-    return d > h ? d - n : (d < -h ? d + n : d);
-}
-__device__ inline float wrap_near_f(float d, int n, int periodic) {
-    if (!periodic) return d;
-    const float h = 0.5f * n;
     return d > h ? d - n : (d < -h ? d + n : d);
 }
 
@@ -424,8 +450,6 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
     const double xw[3] = {d.px ? sb.X[0] - d.nx * floor(sb.X[0] * d.inx) : sb.X[0],
                           d.py ? sb.X[1] - d.ny * floor(sb.X[1] * d.iny) : sb.X[1],
                           d.pz ? sb.X[2] - d.nz * floor(sb.X[2] * d.inz) : sb.X[2]};
-    const float vf[3] = {(float)sb.V[0], (float)sb.V[1], (float)sb.V[2]};
-    const float wf[3] = {(float)sb.W[0], (float)sb.W[1], (float)sb.W[2]};
 
     // exclusive prefix of the segment counts: thread t holds segments
     // [t per, (t+1) per), per <= 4 (side <= MAX_SEGMENTS), block scan
@@ -477,49 +501,32 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
         // cells are 32-bit indices (C < 2^31): 32-bit division
         const unsigned cu = lk.cell, nxu = (unsigned)d.nx, nyu = (unsigned)d.ny;
         const int x = (int)(cu % nxu), y = (int)((cu / nxu) % nyu), z = (int)(cu / (nxu * nyu));
+        double rho = 1.0;
         if constexpr (sizeof(T) == 8) {
-            double rho = 1.0;
             for (int q = 0; q < Q; ++q) rho += load_dev<T>(pop + q * C + c, s);
-            const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
-            // offsets of the fluid cell, of the link end and of the link midpoint
-            const double o0 = wrap_near(x - xw[0], d.nx, d.px), o1 = wrap_near(y - xw[1], d.ny, d.py),
-                         o2 = wrap_near(z - xw[2], d.nz, d.pz);
-            const double e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
-            const double u0 = sb.V[0] + (sb.W[1] * e2 - sb.W[2] * e1);
-            const double u1 = sb.V[1] + (sb.W[2] * e0 - sb.W[0] * e2);
-            const double u2 = sb.V[2] + (sb.W[0] * e1 - sb.W[1] * e0);
-            const double eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);   // e_-a . u_w
-            const double mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
-            const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
-            const double m0 = o0 + 0.5 * ex(a), m1 = o1 + 0.5 * ey(a), m2 = o2 + 0.5 * ez(a);
-            acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];
-            acc[3] += m1 * fl[2] - m2 * fl[1];
-            acc[4] += m2 * fl[0] - m0 * fl[2];
-            acc[5] += m0 * fl[1] - m1 * fl[0];
         } else {
-            // 32/16-bit storage: the link terms in FP32 (the populations are
-            // FP32 or coarser), their sum in FP64; the offsets from one FP64
-            // difference each
-            float drho = 0.0f;
+            float drho = 0.0f;          // FP32 sum of the stored deviations
             for (int q = 0; q < Q; ++q) drho += (float)load_dev<T>(pop + q * C + c, s);
-            const float rho = 1.0f + drho;
-            const float g_a = (float)wgt(a) + (float)load_dev<T>(pop + a * C + c, s);
-            const float o0 = wrap_near_f((float)(x - xw[0]), d.nx, d.px),
-                        o1 = wrap_near_f((float)(y - xw[1]), d.ny, d.py),
-                        o2 = wrap_near_f((float)(z - xw[2]), d.nz, d.pz);
-            const float e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
-            const float u0 = vf[0] + (wf[1] * e2 - wf[2] * e1);
-            const float u1 = vf[1] + (wf[2] * e0 - wf[0] * e2);
-            const float u2 = vf[2] + (wf[0] * e1 - wf[1] * e0);
-            const float eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);
-            const float mag = 2.0f * g_a + (float)(6.0 * wgt(a)) * rho * eu;
-            const float fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
-            const float m0 = o0 + 0.5f * ex(a), m1 = o1 + 0.5f * ey(a), m2 = o2 + 0.5f * ez(a);
-            acc[0] += (double)fl[0]; acc[1] += (double)fl[1]; acc[2] += (double)fl[2];
-            acc[3] += (double)(m1 * fl[2] - m2 * fl[1]);
-            acc[4] += (double)(m2 * fl[0] - m0 * fl[2]);
-            acc[5] += (double)(m0 * fl[1] - m1 * fl[0]);
+            rho += (double)drho;
         }
+        // the link terms in FP64: the force is a small difference of ~1e3
+        // terms of size ~0.1 (2 f~_a), which FP32 terms would not keep
+        const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
+        // offsets of the fluid cell, of the link end and of the link midpoint
+        const double o0 = wrap_near(x - xw[0], d.nx, d.px), o1 = wrap_near(y - xw[1], d.ny, d.py),
+                     o2 = wrap_near(z - xw[2], d.nz, d.pz);
+        const double e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
+        const double u0 = sb.V[0] + (sb.W[1] * e2 - sb.W[2] * e1);
+        const double u1 = sb.V[1] + (sb.W[2] * e0 - sb.W[0] * e2);
+        const double u2 = sb.V[2] + (sb.W[0] * e1 - sb.W[1] * e0);
+        const double eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);   // e_-a . u_w
+        const double mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
+        const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
+        const double m0 = o0 + 0.5 * ex(a), m1 = o1 + 0.5 * ey(a), m2 = o2 + 0.5 * ez(a);
+        acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];
+        acc[3] += m1 * fl[2] - m2 * fl[1];
+        acc[4] += m2 * fl[0] - m0 * fl[2];
+        acc[5] += m0 * fl[1] - m1 * fl[0];
     }
     __shared__ double part[FORCE_THREADS / 32][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

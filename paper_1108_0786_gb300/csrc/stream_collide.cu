@@ -262,9 +262,9 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
 }
 
 // Velocity of body b's surface at lattice point p in the compute type R:
-// FP64 throughout for FP64 storage; otherwise the offset p - X in FP64 (one
-// subtraction per axis) and the minimum image and V + W x offset in R (the
-// moving-wall term is ~1e-4 and its R rounding sits below the storage's)
+// FP64 throughout for FP64 storage; otherwise the minimum-image offset in
+// FP64 and V + W x offset in R (the moving-wall term is ~1e-4 and its R
+// rounding sits below the storage's)
 template <typename R>
 __device__ inline void wall_velocity(const Domain &d, const BodyState &b, int px, int py, int pz, R (&u)[3]) {
     if constexpr (sizeof(R) == 8) {
@@ -272,15 +272,55 @@ __device__ inline void wall_velocity(const Domain &d, const BodyState &b, int px
         surface_velocity(d, b, px, py, pz, w);
         u[0] = w[0]; u[1] = w[1]; u[2] = w[2];
     } else {
-        R o0 = (R)((double)px - b.X[0]), o1 = (R)((double)py - b.X[1]), o2 = (R)((double)pz - b.X[2]);
-        if (d.px) o0 -= (R)d.nx * floor(o0 * (R)d.inx + (R)0.5);
-        if (d.py) o1 -= (R)d.ny * floor(o1 * (R)d.iny + (R)0.5);
-        if (d.pz) o2 -= (R)d.nz * floor(o2 * (R)d.inz + (R)0.5);
+        double od[3];
+        offset_from(d, b, (double)px, (double)py, (double)pz, od);
+        const R o0 = (R)od[0], o1 = (R)od[1], o2 = (R)od[2];
         const R w0 = (R)b.W[0], w1 = (R)b.W[1], w2 = (R)b.W[2];
         u[0] = (R)b.V[0] + (w1 * o2 - w2 * o1);
         u[1] = (R)b.V[1] + (w2 * o0 - w0 * o2);
         u[2] = (R)b.V[2] + (w0 * o1 - w1 * o0);
     }
+}
+
+// a body for the moving-wall term: the centre wrapped into the domain and
+// split into its cell (int) and the offset within it (FP32), velocity and
+// angular velocity in FP32
+struct WallBody {
+    int ic[3];
+    float frac[3], v[3], w[3];
+};
+
+__device__ inline WallBody wall_body(const Domain &d, const BodyState &b) {
+    WallBody r;
+    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
+    const double inv[3] = {d.inx, d.iny, d.inz};
+    for (int i = 0; i < 3; ++i) {
+        const double c = per[i] ? b.X[i] - n3[i] * floor(b.X[i] * inv[i]) : b.X[i];
+        const double fc = floor(c);
+        r.ic[i] = (int)fc;
+        r.frac[i] = (float)(c - fc);
+        r.v[i] = (float)b.V[i];
+        r.w[i] = (float)b.W[i];
+    }
+    return r;
+}
+
+__device__ inline int near_cell(int o, int n, int periodic) {
+    if (!periodic) return o;
+    return 2 * o > n ? o - n : (2 * o < -n ? o + n : o);
+}
+
+// V + W x (p - X) in FP32; the minimum-image offset is an integer difference
+// of cells wrapped by compares minus the centre's fraction (exact to FP32
+// rounding of a few-cell offset)
+__device__ inline void wall_velocity_wrapped(const Domain &d, const WallBody &b, int px, int py, int pz,
+                                             float (&u)[3]) {
+    const float o0 = (float)near_cell(px - b.ic[0], d.nx, d.px) - b.frac[0];
+    const float o1 = (float)near_cell(py - b.ic[1], d.ny, d.py) - b.frac[1];
+    const float o2 = (float)near_cell(pz - b.ic[2], d.nz, d.pz) - b.frac[2];
+    u[0] = b.v[0] + (b.w[1] * o2 - b.w[2] * o1);
+    u[1] = b.v[1] + (b.w[2] * o0 - b.w[0] * o2);
+    u[2] = b.v[2] + (b.w[0] * o1 - b.w[1] * o0);
 }
 
 // Cells with a non-zero flag byte: refill, bounce-back at walls and moving
@@ -294,6 +334,14 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
     using Cd = typename Codec<T>::C;
     const Domain d = dv.dom;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    // 32/16-bit storage: the bodies of step n-1 with their centres wrapped
+    // into the domain (one FP64 floor per body and block), so that a link's
+    // minimum-image offset is an FP64 difference and two compares
+    __shared__ WallBody wb[sizeof(T) == 8 ? 1 : LBM_MAX_BODIES_DEV];
+    if constexpr (sizeof(T) != 8) {
+        for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) wb[k] = wall_body(d, sp.body_prev[k]);
+        __syncthreads();
+    }
     int x, y, z;
     if (mode == 0) {
         const int b = blockIdx.y;
@@ -388,7 +436,10 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
             } else if (fp & F_SOLID) {
                 const int k = sp.bid_prev[sc];
                 Cd u[3] = {0, 0, 0};
-                if (k != NO_BODY) wall_velocity<Cd>(d, sp.body_prev[k], sx, sy, sz, u);
+                if (k != NO_BODY) {
+                    if constexpr (sizeof(T) == 8) wall_velocity<Cd>(d, sp.body_prev[k], sx, sy, sz, u);
+                    else wall_velocity_wrapped(d, wb[k], sx, sy, sz, u);
+                }
                 const Cd eu = (Cd)ex(b) * u[0] + (Cd)ey(b) * u[1] + (Cd)ez(b) * u[2];
                 v = own[opp(b)] + (Cd)(6.0 * wgt(b)) * rho_x * eu;          // moving wall
             }
@@ -452,8 +503,8 @@ constexpr int TMA_HEADER = 128;                      // mbarriers, ahead of the 
 
 __host__ __device__ constexpr size_t tma_stage_bytes(int nx, int elem) { return (size_t)Q * nx * elem + (size_t)nx; }
 
-template <typename T, int NSTAGE>
-__global__ void __launch_bounds__(TMA_THREADS) bulk_tma_kernel(const Device dv, const StepPtrs sp) {
+template <typename T, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Device dv, const StepPtrs sp) {
     using Cd = typename Codec<T>::C;
     extern __shared__ __align__(128) unsigned char smem[];
     const Domain d = dv.dom;
@@ -564,7 +615,7 @@ void launch_tma(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     const size_t bytes = tma_smem_bytes<T, NSTAGE, PER_SM>(dv.dom.nx);
     const long long rows = (long long)dv.dom.ny * dv.dom.nz;
     const long long grid = std::min<long long>(rows, (long long)sm_count() * PER_SM);
-    bulk_tma_kernel<T, NSTAGE><<<(unsigned)grid, TMA_THREADS, bytes, s>>>(dv, sp);
+    bulk_tma_kernel<T, NSTAGE, PER_SM><<<(unsigned)grid, TMA_THREADS, bytes, s>>>(dv, sp);
 }
 
 template <typename T, int NSTAGE, int PER_SM>
@@ -574,7 +625,8 @@ bool tma_fits(int nx) {
 
 template <typename T, int NSTAGE, int PER_SM>
 void tma_prepare() {
-    cudaFuncSetAttribute(bulk_tma_kernel<T, NSTAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(bulk_tma_kernel<T, NSTAGE, PER_SM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
 }
 
 template <typename T, int V, int BX, int BY, int MINB>
@@ -624,8 +676,10 @@ const Variant kVariants[] = {
     {1, -1, 2, launch_tma<float, 2, 2>, tma_fits<float, 2, 2>},
     {2, -1, 1, launch_tma<__half, 4, 1>, tma_fits<__half, 4, 1>},
     {2, -1, 2, launch_tma<__half, 3, 2>, tma_fits<__half, 3, 2>},
+    {2, -1, 4, launch_tma<__half, 2, 4>, tma_fits<__half, 2, 4>},
     {3, -1, 1, launch_tma<__nv_bfloat16, 4, 1>, tma_fits<__nv_bfloat16, 4, 1>},
     {3, -1, 2, launch_tma<__nv_bfloat16, 3, 2>, tma_fits<__nv_bfloat16, 3, 2>},
+    {3, -1, 4, launch_tma<__nv_bfloat16, 2, 4>, tma_fits<__nv_bfloat16, 2, 4>},
 };
 const Variant *find_variant(int precision, int vec, int minb) {
     const Variant *first = nullptr;
@@ -675,8 +729,10 @@ void prepare_bulk_variants() {
     tma_prepare<float, 2, 2>();
     tma_prepare<__half, 4, 1>();
     tma_prepare<__half, 3, 2>();
+    tma_prepare<__half, 2, 4>();
     tma_prepare<__nv_bfloat16, 4, 1>();
     tma_prepare<__nv_bfloat16, 3, 2>();
+    tma_prepare<__nv_bfloat16, 2, 4>();
     done = true;
 }
 
