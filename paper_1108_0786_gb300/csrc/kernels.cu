@@ -105,7 +105,13 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
     __shared__ int cwi[LBM_MAX_BODIES_DEV][3];     // wrapped centre: cell
     __shared__ float cwf[LBM_MAX_BODIES_DEV][3];   // and offset within it
     __shared__ float ax[LBM_MAX_BODIES_DEV][3];    // body x axis
+    __shared__ int origin[3];                      // cell of this block's cube corner
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
+    if (threadIdx.x == 0) {
+        const BodyState sb0 = sp.body_cur[blockIdx.y];
+        const int half0 = dv.props[blockIdx.y].E + REMAP_MARGIN;
+        for (int a = 0; a < 3; ++a) origin[a] = (int)floor(sb0.X[a]) - half0;
+    }
     for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) {
         const BodyState sk = sp.body_cur[k];
         const BodyProps pk = dv.props[k];
@@ -160,9 +166,9 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
     }
     if (l >= vol) return;
     const int lx = l % side, ly = (l / side) % side, lz = l / (side * side);
-    int x = (int)floor(sb.X[0]) - half + lx;
-    int y = (int)floor(sb.X[1]) - half + ly;
-    int z = (int)floor(sb.X[2]) - half + lz;
+    int x = origin[0] + lx;
+    int y = origin[1] + ly;
+    int z = origin[2] + lz;
     if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else if (x < 0 || x >= d.nx) return;
     if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else if (y < 0 || y >= d.ny) return;
     if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else if (z < 0 || z >= d.nz) return;
@@ -317,6 +323,12 @@ template <> __device__ inline double load_dev<__nv_bfloat16>(const __nv_bfloat16
 constexpr int FORCE_THREADS = 256;
 constexpr int MAX_SEGMENTS = 1024;
 
+// minimum image of a cell difference o (|o| < n + 1) by integer compares
+__device__ inline int near_cell_k(int o, int n, int periodic) {
+    if (!periodic) return o;
+    return 2 * o > n ? o - n : (2 * o < -n ? o + n : o);
+}
+
 // periodic minimum image of d for |d| < 3n/2 (two compares, no FP64 floor)
 __device__ inline double wrap_near(double d, int n, int periodic) {
     if (!periodic) return d;
@@ -450,6 +462,10 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
     const double xw[3] = {d.px ? sb.X[0] - d.nx * floor(sb.X[0] * d.inx) : sb.X[0],
                           d.py ? sb.X[1] - d.ny * floor(sb.X[1] * d.iny) : sb.X[1],
                           d.pz ? sb.X[2] - d.nz * floor(sb.X[2] * d.inz) : sb.X[2]};
+    const int ci[3] = {(int)floor(xw[0]), (int)floor(xw[1]), (int)floor(xw[2])};
+    const double cfr[3] = {xw[0] - ci[0], xw[1] - ci[1], xw[2] - ci[2]};
+    const float vf[3] = {(float)sb.V[0], (float)sb.V[1], (float)sb.V[2]};
+    const float wf[3] = {(float)sb.W[0], (float)sb.W[1], (float)sb.W[2]};
 
     // exclusive prefix of the segment counts: thread t holds segments
     // [t per, (t+1) per), per <= 4 (side <= MAX_SEGMENTS), block scan
@@ -512,15 +528,31 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
         // the link terms in FP64: the force is a small difference of ~1e3
         // terms of size ~0.1 (2 f~_a), which FP32 terms would not keep
         const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
-        // offsets of the fluid cell, of the link end and of the link midpoint
-        const double o0 = wrap_near(x - xw[0], d.nx, d.px), o1 = wrap_near(y - xw[1], d.ny, d.py),
-                     o2 = wrap_near(z - xw[2], d.nz, d.pz);
-        const double e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
-        const double u0 = sb.V[0] + (sb.W[1] * e2 - sb.W[2] * e1);
-        const double u1 = sb.V[1] + (sb.W[2] * e0 - sb.W[0] * e2);
-        const double u2 = sb.V[2] + (sb.W[0] * e1 - sb.W[1] * e0);
-        const double eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);   // e_-a . u_w
-        const double mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
+        double o0, o1, o2, mag;
+        if constexpr (sizeof(T) == 8) {
+            // offsets of the fluid cell, of the link end and of the link midpoint
+            o0 = wrap_near(x - xw[0], d.nx, d.px);
+            o1 = wrap_near(y - xw[1], d.ny, d.py);
+            o2 = wrap_near(z - xw[2], d.nz, d.pz);
+            const double e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
+            const double u0 = sb.V[0] + (sb.W[1] * e2 - sb.W[2] * e1);
+            const double u1 = sb.V[1] + (sb.W[2] * e0 - sb.W[0] * e2);
+            const double u2 = sb.V[2] + (sb.W[0] * e1 - sb.W[1] * e0);
+            const double eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);   // e_-a . u_w
+            mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
+        } else {
+            // offsets from the centre's cell (integer minimum image) and its
+            // FP64 fraction; the moving-wall term (~1e-3 of the link) in FP32
+            o0 = (double)near_cell_k(x - ci[0], d.nx, d.px) - cfr[0];
+            o1 = (double)near_cell_k(y - ci[1], d.ny, d.py) - cfr[1];
+            o2 = (double)near_cell_k(z - ci[2], d.nz, d.pz) - cfr[2];
+            const float e0 = (float)o0 + ex(a), e1 = (float)o1 + ey(a), e2 = (float)o2 + ez(a);
+            const float u0 = vf[0] + (wf[1] * e2 - wf[2] * e1);
+            const float u1 = vf[1] + (wf[2] * e0 - wf[0] * e2);
+            const float u2 = vf[2] + (wf[0] * e1 - wf[1] * e0);
+            const float eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);
+            mag = 2.0 * g_a + (double)((float)(6.0 * wgt(a)) * (float)rho * eu);
+        }
         const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
         const double m0 = o0 + 0.5 * ex(a), m1 = o1 + 0.5 * ey(a), m2 = o2 + 0.5 * ez(a);
         acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];

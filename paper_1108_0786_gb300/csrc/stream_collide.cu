@@ -338,20 +338,24 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
     // into the domain (one FP64 floor per body and block), so that a link's
     // minimum-image offset is an FP64 difference and two compares
     __shared__ WallBody wb[sizeof(T) == 8 ? 1 : LBM_MAX_BODIES_DEV];
-    if constexpr (sizeof(T) != 8) {
+    __shared__ int origin[3];               // mode 0: the cube corner (one FP64 floor per axis and block)
+    if constexpr (sizeof(T) != 8)
         for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) wb[k] = wall_body(d, sp.body_prev[k]);
-        __syncthreads();
+    if (mode == 0 && threadIdx.x == 0) {
+        const BodyState sb = sp.body_cur[blockIdx.y];
+        const int half = dv.props[blockIdx.y].E + REMAP_MARGIN;
+        for (int a = 0; a < 3; ++a) origin[a] = (int)floor(sb.X[a]) - half;
     }
+    __syncthreads();
     int x, y, z;
     if (mode == 0) {
         const int b = blockIdx.y;
-        const BodyState sb = sp.body_cur[b];
         const int half = dv.props[b].E + REMAP_MARGIN;
         const int side = 2 * half + 1;
         if (l >= side * side * side) return;
-        x = (int)floor(sb.X[0]) - half + l % side;
-        y = (int)floor(sb.X[1]) - half + (l / side) % side;
-        z = (int)floor(sb.X[2]) - half + l / (side * side);
+        x = origin[0] + l % side;
+        y = origin[1] + (l / side) % side;
+        z = origin[2] + l / (side * side);
         if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else if (x < 0 || x >= d.nx) return;
         if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else if (y < 0 || y >= d.ny) return;
         if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else if (z < 0 || z >= d.nz) return;
