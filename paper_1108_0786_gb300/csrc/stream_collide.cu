@@ -122,7 +122,13 @@ __device__ __forceinline__ T shfl(T v, int delta, bool up) {
 // population: only the value-dependent rounding of the final additions
 // remains.  FP64 keeps the plain update, as do the 16-bit formats, whose
 // storage rounding (2^-9 .. 2^-11 relative) dwarfs this effect.
-template <typename Cd, bool CLOSE>
+// CLOSE selects that closure.  PAIRED evaluates opposite directions (b, b + 1)
+// together: they share w, (e.u)^2 and e.g up to sign, so
+// deq = w (base + 4.5 rho (e.u)^2 +- 3 rho e.u) saves a fifth of the
+// arithmetic; otherwise one direction at a time.  Both forms compute the
+// same expression (FP32 takes the paired one; the 16-bit kernels schedule
+// the per-direction one better).
+template <typename Cd, bool CLOSE, bool PAIRED = CLOSE>
 __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     Cd s = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -140,18 +146,14 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     const Cd om = (Cd)dv.omega;
     const Cd guo = (Cd)(1.0 - 0.5 * dv.omega);
     const Cd ug = ux * gx + uy * gy + uz * gz;
+    const Cd base = s - (Cd)1.5 * rho * usq;    // deviation of f_eq without the e.u terms, over w
     Cd m = 0, px = 0, py = 0, pz = 0;
-#pragma unroll
-    for (int b = 0; b < Q; ++b) {
-        const Cd w = (Cd)wgt(b);
-        const Cd eu = (Cd)ex(b) * ux + (Cd)ey(b) * uy + (Cd)ez(b) * uz;
-        const Cd deq = w * (s + rho * ((Cd)3 * eu + (Cd)4.5 * eu * eu - (Cd)1.5 * usq));
+    // one relaxation: the increment of direction b towards deq (+ Guo's term
+    // gt), kept for the conservation closure or applied directly
+    auto relax = [&](int b, Cd deq, Cd gt) {
         if constexpr (CLOSE) {
             Cd d = om * (deq - f[b]);
-            if (dv.forced) {
-                const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
-                d += guo * w * ((Cd)3 * (eg - ug) + (Cd)9 * eu * eg);
-            }
+            if (dv.forced) d += gt;
             m += d;
             if (ex(b)) px += ex(b) > 0 ? d : -d;
             if (ey(b)) py += ey(b) > 0 ? d : -d;
@@ -159,12 +161,45 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
             f[b] += d;
         } else {
             Cd o = f[b] - om * (f[b] - deq);
-            if (dv.forced) {
-                const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
-                o += guo * w * ((Cd)3 * (eg - ug) + (Cd)9 * eu * eg);
-            }
+            if (dv.forced) o += gt;
             f[b] = o;
         }
+    };
+    if constexpr (!PAIRED) {
+        // one direction at a time (the form the 16-bit kernels schedule best)
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            const Cd w = (Cd)wgt(b);
+            const Cd eu = (Cd)ex(b) * ux + (Cd)ey(b) * uy + (Cd)ez(b) * uz;
+            const Cd deq = w * (s + rho * ((Cd)3 * eu + (Cd)4.5 * eu * eu - (Cd)1.5 * usq));
+            Cd gt = 0;
+            if (dv.forced) {
+                const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
+                gt = guo * w * ((Cd)3 * (eg - ug) + (Cd)9 * eu * eg);
+            }
+            relax(b, deq, gt);
+        }
+    } else {
+    {
+        const Cd w = (Cd)wgt(0);
+        relax(0, w * base, dv.forced ? guo * w * ((Cd)(-3) * ug) : (Cd)0);
+    }
+#pragma unroll
+    for (int b = 1; b < Q; b += 2) {
+        const Cd w = (Cd)wgt(b);
+        const Cd eu = (Cd)ex(b) * ux + (Cd)ey(b) * uy + (Cd)ez(b) * uz;
+        const Cd a = base + (Cd)4.5 * rho * eu * eu;
+        const Cd c = (Cd)3 * rho * eu;
+        Cd g1 = 0, g2 = 0;
+        if (dv.forced) {
+            const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
+            const Cd sym = (Cd)9 * eu * eg - (Cd)3 * ug, asym = (Cd)3 * eg;
+            g1 = guo * w * (sym + asym);
+            g2 = guo * w * (sym - asym);
+        }
+        relax(b, w * (a + c), g1);
+        relax(b + 1, w * (a - c), g2);
+    }
     }
     if constexpr (CLOSE) {
         const Cd hx = (Cd)0.5 * (gx - px), hy = (Cd)0.5 * (gy - py), hz = (Cd)0.5 * (gz - pz);
@@ -507,7 +542,7 @@ constexpr int TMA_HEADER = 128;                      // mbarriers, ahead of the 
 
 __host__ __device__ constexpr size_t tma_stage_bytes(int nx, int elem) { return (size_t)Q * nx * elem + (size_t)nx; }
 
-template <typename T, int NSTAGE, int MINB>
+template <typename T, int NSTAGE, int MINB, int ROWS>
 __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Device dv, const StepPtrs sp) {
     using Cd = typename Codec<T>::C;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -515,12 +550,14 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
     const int nx = d.nx;
     const unsigned row_bytes = (unsigned)(nx * sizeof(T));
     const unsigned flag_off = Q * row_bytes;
-    const unsigned stage_bytes = (unsigned)tma_stage_bytes(nx, sizeof(T));
+    const unsigned row_stage = (unsigned)tma_stage_bytes(nx, sizeof(T));     // one x-row's sources + flags
+    const unsigned stage_bytes = ROWS * row_stage;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     unsigned char *stages = smem + TMA_HEADER;
     const long long rows = (long long)d.ny * d.nz;
     const long long first = blockIdx.x;
     const long long nmine = rows > first ? (rows - 1 - first) / gridDim.x + 1 : 0;
+    const long long ngroups = (nmine + ROWS - 1) / ROWS;     // a stage holds ROWS of this block's rows
     const T *__restrict__ src = static_cast<const T *>(sp.src);
     T *__restrict__ dst = static_cast<T *>(sp.dst);
     const long long C = d.C;
@@ -531,67 +568,74 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    auto issue = [&](long long i) {          // thread 0: row i of this block into stage i % NSTAGE
-        const int st = (int)(i % NSTAGE);
-        const long long r = first + i * gridDim.x;
-        const int y = (int)(r % d.ny), z = (int)(r / d.ny);
-        unsigned char *buf = stages + (size_t)st * stage_bytes;
-        mbar_expect_tx(&bar[st], stage_bytes);
+    auto issue = [&](long long g) {          // thread 0: rows of group g into stage g % NSTAGE
+        const int st = (int)(g % NSTAGE);
+        const int nr = (int)min((long long)ROWS, nmine - g * ROWS);
+        unsigned char *buf0 = stages + (size_t)st * stage_bytes;
+        mbar_expect_tx(&bar[st], nr * row_stage);
+        for (int rr = 0; rr < nr; ++rr) {
+            const long long r = first + (g * ROWS + rr) * gridDim.x;
+            const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+            unsigned char *buf = buf0 + (size_t)rr * row_stage;
 #pragma unroll
-        for (int b = 0; b < Q; ++b) {
-            const int ys = wrap_axis(y - ey(b), d.ny), zs = wrap_axis(z - ez(b), d.nz);
-            bulk_copy(buf + b * row_bytes, src + (long long)b * C + ((long long)zs * d.ny + ys) * nx, row_bytes,
-                      &bar[st]);
+            for (int b = 0; b < Q; ++b) {
+                const int ys = wrap_axis(y - ey(b), d.ny), zs = wrap_axis(z - ez(b), d.nz);
+                bulk_copy(buf + b * row_bytes, src + (long long)b * C + ((long long)zs * d.ny + ys) * nx,
+                          row_bytes, &bar[st]);
+            }
+            bulk_copy(buf + flag_off, sp.flags_cur + r * nx, (unsigned)nx, &bar[st]);
         }
-        bulk_copy(buf + flag_off, sp.flags_cur + r * nx, (unsigned)nx, &bar[st]);
     };
     if (threadIdx.x == 0)
-        for (long long i = 0; i < nmine && i < NSTAGE; ++i) issue(i);
+        for (long long g = 0; g < ngroups && g < NSTAGE; ++g) issue(g);
 
-    long long i = 0;
+    long long g = 0;
     bool ok = true;
-    for (; i < nmine; ++i) {
-        const int st = (int)(i % NSTAGE);
-        const unsigned parity = (unsigned)((i / NSTAGE) & 1);
+    for (; g < ngroups; ++g) {
+        const int st = (int)(g % NSTAGE);
+        const unsigned parity = (unsigned)((g / NSTAGE) & 1);
         const long long t0 = clock64();
         bool ready = false;
         while (!(ready = mbar_try_wait(&bar[st], parity)) && clock64() - t0 < TMA_WAIT_CYCLES) {
         }
         ok = __syncthreads_and(ready);
         if (!ok) break;
-        const unsigned char *buf = stages + (size_t)st * stage_bytes;
-        const T *rowb = reinterpret_cast<const T *>(buf);
-        const uint8_t *fl = buf + flag_off;
-        const long long c0 = (first + i * gridDim.x) * nx;
-        for (int x = threadIdx.x; x < nx; x += TMA_THREADS) {
-            const uint8_t f8 = fl[x];
-            if (f8 != 0 && !(f8 & F_SOLID)) continue;      // the boundary kernel's cell
-            if (f8 & F_SOLID) {
+        const int nr = (int)min((long long)ROWS, nmine - g * ROWS);
+        for (int rr = 0; rr < nr; ++rr) {
+            const unsigned char *buf = stages + (size_t)st * stage_bytes + (size_t)rr * row_stage;
+            const T *rowb = reinterpret_cast<const T *>(buf);
+            const uint8_t *fl = buf + flag_off;
+            const long long c0 = (first + (g * ROWS + rr) * gridDim.x) * nx;
+            for (int x = threadIdx.x; x < nx; x += TMA_THREADS) {
+                const uint8_t f8 = fl[x];
+                if (f8 != 0 && !(f8 & F_SOLID)) continue;      // the boundary kernel's cell
+                if (f8 & F_SOLID) {
 #pragma unroll
-                for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = Codec<T>::st((Cd)0, scale);
-                continue;
+                    for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = Codec<T>::st((Cd)0, scale);
+                    continue;
+                }
+                Cd f[Q];
+#pragma unroll
+                for (int b = 0; b < Q; ++b) {
+                    int xs = x - ex(b);
+                    xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+                    f[b] = Codec<T>::ld(rowb[b * nx + xs], inv_scale);
+                }
+                collide<Cd, std::is_same<T, float>::value>(f, dv);
+#pragma unroll
+                for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = Codec<T>::st(f[b], scale);
             }
-            Cd g[Q];
-#pragma unroll
-            for (int b = 0; b < Q; ++b) {
-                int xs = x - ex(b);
-                xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-                g[b] = Codec<T>::ld(rowb[b * nx + xs], inv_scale);
-            }
-            collide<Cd, std::is_same<T, float>::value>(g, dv);
-#pragma unroll
-            for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = Codec<T>::st(g[b], scale);
         }
         __syncthreads();                         // stage st is free again
-        if (threadIdx.x == 0 && i + NSTAGE < nmine) {
+        if (threadIdx.x == 0 && g + NSTAGE < ngroups) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(i + NSTAGE);
+            issue(g + NSTAGE);
         }
     }
     if (!ok && threadIdx.x == 0) {
         atomicOr(dv.status, ST_TIMEOUT);
         // the copies still in flight target this block's shared memory
-        for (long long j = i; j < nmine && j < i + NSTAGE; ++j) {
+        for (long long j = g; j < ngroups && j < g + NSTAGE; ++j) {
             const long long t0 = clock64();
             while (!mbar_try_wait(&bar[j % NSTAGE], (unsigned)((j / NSTAGE) & 1)) &&
                    clock64() - t0 < TMA_WAIT_CYCLES) {
@@ -600,8 +644,8 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
     }
 }
 
-template <typename T, int NSTAGE, int PER_SM>
-size_t tma_smem_bytes(int nx) { return TMA_HEADER + (size_t)NSTAGE * tma_stage_bytes(nx, sizeof(T)); }
+template <typename T, int NSTAGE, int PER_SM, int ROWS = 1>
+size_t tma_smem_bytes(int nx) { return TMA_HEADER + (size_t)NSTAGE * ROWS * tma_stage_bytes(nx, sizeof(T)); }
 
 int sm_count() {
     static int n = 0;
@@ -614,22 +658,22 @@ int sm_count() {
     return n;
 }
 
-template <typename T, int NSTAGE, int PER_SM>
+template <typename T, int NSTAGE, int PER_SM, int ROWS = 1>
 void launch_tma(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
-    const size_t bytes = tma_smem_bytes<T, NSTAGE, PER_SM>(dv.dom.nx);
+    const size_t bytes = tma_smem_bytes<T, NSTAGE, PER_SM, ROWS>(dv.dom.nx);
     const long long rows = (long long)dv.dom.ny * dv.dom.nz;
     const long long grid = std::min<long long>(rows, (long long)sm_count() * PER_SM);
-    bulk_tma_kernel<T, NSTAGE, PER_SM><<<(unsigned)grid, TMA_THREADS, bytes, s>>>(dv, sp);
+    bulk_tma_kernel<T, NSTAGE, PER_SM, ROWS><<<(unsigned)grid, TMA_THREADS, bytes, s>>>(dv, sp);
 }
 
-template <typename T, int NSTAGE, int PER_SM>
+template <typename T, int NSTAGE, int PER_SM, int ROWS = 1>
 bool tma_fits(int nx) {
-    return nx % 16 == 0 && tma_smem_bytes<T, NSTAGE, PER_SM>(nx) * PER_SM <= 227u * 1024u;
+    return nx % 16 == 0 && tma_smem_bytes<T, NSTAGE, PER_SM, ROWS>(nx) * PER_SM <= 227u * 1024u;
 }
 
-template <typename T, int NSTAGE, int PER_SM>
+template <typename T, int NSTAGE, int PER_SM, int ROWS = 1>
 void tma_prepare() {
-    cudaFuncSetAttribute(bulk_tma_kernel<T, NSTAGE, PER_SM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(bulk_tma_kernel<T, NSTAGE, PER_SM, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          227 * 1024);
 }
 
@@ -678,11 +722,11 @@ const Variant kVariants[] = {
     {0, -1, 1, launch_tma<double, 2, 1>, tma_fits<double, 2, 1>},
     {1, -1, 1, launch_tma<float, 4, 1>, tma_fits<float, 4, 1>},
     {1, -1, 2, launch_tma<float, 2, 2>, tma_fits<float, 2, 2>},
-    {2, -1, 1, launch_tma<__half, 4, 1>, tma_fits<__half, 4, 1>},
-    {2, -1, 2, launch_tma<__half, 3, 2>, tma_fits<__half, 3, 2>},
+    {2, -1, 2, launch_tma<__half, 2, 2, 2>, tma_fits<__half, 2, 2, 2>},
+    {2, -1, 3, launch_tma<__half, 2, 3>, tma_fits<__half, 2, 3>},
     {2, -1, 4, launch_tma<__half, 2, 4>, tma_fits<__half, 2, 4>},
-    {3, -1, 1, launch_tma<__nv_bfloat16, 4, 1>, tma_fits<__nv_bfloat16, 4, 1>},
-    {3, -1, 2, launch_tma<__nv_bfloat16, 3, 2>, tma_fits<__nv_bfloat16, 3, 2>},
+    {3, -1, 2, launch_tma<__nv_bfloat16, 2, 2, 2>, tma_fits<__nv_bfloat16, 2, 2, 2>},
+    {3, -1, 3, launch_tma<__nv_bfloat16, 2, 3>, tma_fits<__nv_bfloat16, 2, 3>},
     {3, -1, 4, launch_tma<__nv_bfloat16, 2, 4>, tma_fits<__nv_bfloat16, 2, 4>},
 };
 const Variant *find_variant(int precision, int vec, int minb) {
@@ -731,11 +775,11 @@ void prepare_bulk_variants() {
     tma_prepare<double, 2, 1>();
     tma_prepare<float, 4, 1>();
     tma_prepare<float, 2, 2>();
-    tma_prepare<__half, 4, 1>();
-    tma_prepare<__half, 3, 2>();
+    tma_prepare<__half, 2, 2, 2>();
+    tma_prepare<__half, 2, 3>();
     tma_prepare<__half, 2, 4>();
-    tma_prepare<__nv_bfloat16, 4, 1>();
-    tma_prepare<__nv_bfloat16, 3, 2>();
+    tma_prepare<__nv_bfloat16, 2, 2, 2>();
+    tma_prepare<__nv_bfloat16, 2, 3>();
     tma_prepare<__nv_bfloat16, 2, 4>();
     done = true;
 }
