@@ -316,7 +316,10 @@ int lbm_ensemble_sync(lbm_ensemble_t *e);
 int lbm_ensemble_destroy(lbm_ensemble_t *e);
 const char *lbm_ensemble_last_error(lbm_ensemble_t *e);
 
-/* Kernel launches one step makes (for launch accounting). */
+/* Kernel launches one step makes (for launch accounting): with bodies and
+ * fluid, body preparation, remap, bulk stream-collide, boundary cells (one
+ * more launch with walls), link lists, drive and spring loads, and the
+ * momentum exchange with the rigid-body step. */
 int lbm_kernels_per_step(lbm_t *h);
 
 /* Algorithmic bytes per cell the stream-collide kernel moves:

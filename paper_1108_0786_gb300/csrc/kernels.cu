@@ -39,29 +39,27 @@ __device__ inline bool cell_inside(const Domain &d, const BodyProps &p, const Bo
 // 2e-2 max(r^2, 1) from r^2 -- orders of magnitude above its FP32 error --
 // and -1 otherwise (the FP64 test decides), so the map is the FP64 map bit
 // for bit.
-__device__ inline int inside_screen(const Domain &d, const BodyProps &p, const int (&ci)[3], const float (&cf)[3],
-                                    const float (&a)[3], int x, int y, int z) {
+__device__ inline int inside_screen(const Domain &d, const BodyGeom *__restrict__ g, int x, int y, int z) {
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz}, q3[3] = {x, y, z};
     float o[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        int io = q3[i] - ci[i];
+        int io = q3[i] - g->ci[i];
         if (per[i]) io = 2 * io > n3[i] ? io - n3[i] : (2 * io < -n3[i] ? io + n3[i] : io);
-        o[i] = (float)io - cf[i];
+        o[i] = (float)io - g->cf[i];
     }
     const float o0 = o[0], o1 = o[1], o2 = o[2];
     float d2;
-    if (p.shape == 0) {
+    if (g->shape == 0) {
         d2 = o0 * o0 + o1 * o1 + o2 * o2;
     } else {
-        const float h = (float)(0.5 * p.l);
-        float sp = o0 * a[0] + o1 * a[1] + o2 * a[2];
+        const float h = g->h;
+        float sp = o0 * g->ax[0] + o1 * g->ax[1] + o2 * g->ax[2];
         sp = sp > h ? h : (sp < -h ? -h : sp);
-        const float e0 = o0 - sp * a[0], e1 = o1 - sp * a[1], e2 = o2 - sp * a[2];
+        const float e0 = o0 - sp * g->ax[0], e1 = o1 - sp * g->ax[1], e2 = o2 - sp * g->ax[2];
         d2 = e0 * e0 + e1 * e1 + e2 * e2;
     }
-    const float r2 = (float)(p.r * p.r);
-    const float margin = 2e-2f * fmaxf(r2, 1.0f);
+    const float r2 = g->r2, margin = g->margin;
     return d2 < r2 - margin ? 1 : (d2 > r2 + margin ? 0 : -1);
 }
 
@@ -84,147 +82,312 @@ __global__ void init_flags_kernel(const Domain d, uint8_t *f0, uint8_t *f1, uint
     b1[c] = NO_BODY;
 }
 
-// Remap: block row blockIdx.y = body b; the threads cover the cube of side
-// 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) at state n.  Every covered
-// cell gets its epoch-n flags from the geometry of all bodies and the
-// epoch-(n-1) buffer; overlapping cubes write identical values.  Bodies are
-// culled with integer boxes first, so the FP64 inside test runs only for
-// the bodies whose box holds the cell.
-constexpr int REMAP_THREADS = 256;
 // A cell farther than this from a body's bounding box [floor(X - reach),
 // floor(X + reach)] can hold no flag of that body in epochs n-2 .. n: solid
 // cells of epoch n-3 lie within 1.5 cells of the current extent, NEAR adds a
 // neighbour's 1.42 cells, and the floor of the upper bound loses up to one.
 constexpr int STATIC_REACH = 4;
 
-__global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
-    const Domain d = dv.dom;
-    const int b = blockIdx.y;
-    __shared__ int box[LBM_MAX_BODIES_DEV][6];     // wrapped lower corner, width per axis
-    __shared__ int ebox[LBM_MAX_BODIES_DEV][6];    // the same grown by STATIC_REACH cells
-    __shared__ int cwi[LBM_MAX_BODIES_DEV][3];     // wrapped centre: cell
-    __shared__ float cwf[LBM_MAX_BODIES_DEV][3];   // and offset within it
-    __shared__ float ax[LBM_MAX_BODIES_DEV][3];    // body x axis
-    __shared__ int origin[3];                      // cell of this block's cube corner
-    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
-    if (threadIdx.x == 0) {
-        const BodyState sb0 = sp.body_cur[blockIdx.y];
-        const int half0 = dv.props[blockIdx.y].E + REMAP_MARGIN;
-        for (int a = 0; a < 3; ++a) origin[a] = (int)floor(sb0.X[a]) - half0;
+// Axis a of a body's geometry record from that axis' centre coordinate,
+// velocity, angular velocity and the body x axis' component.  Every FP64
+// rounding is explicit, so a record made here and one made by the
+// rigid-body step's warp agree bit for bit.
+__device__ inline void geom_axis(const Domain &d, const BodyProps &p, int a, double Xa, double Va, double Wa,
+                                 double axa, BodyGeom &g) {
+    const int n = a == 0 ? d.nx : (a == 1 ? d.ny : d.nz);
+    const int per = a == 0 ? d.px : (a == 1 ? d.py : d.pz);
+    const double inv = a == 0 ? d.inx : (a == 1 ? d.iny : d.inz);
+    const int half = p.E + REMAP_MARGIN;
+    const double c = per ? __fma_rn(-(double)n, floor(__dmul_rn(Xa, inv)), Xa) : Xa;
+    const double fc = floor(c);
+    int o = (int)fc - half;
+    if (per) o = ((o % n) + n) % n;
+    g.origin[a] = o;
+    g.ci[a] = (int)fc;
+    g.cfd[a] = __dsub_rn(c, fc);
+    g.cf[a] = (float)g.cfd[a];
+    g.v[a] = (float)Va;
+    g.w[a] = (float)Wa;
+    g.ax[a] = (float)axa;
+    int lo = (int)floor(__dsub_rn(Xa, p.reach)), hi = (int)floor(__dadd_rn(Xa, p.reach));
+    int width = hi - lo + 1;
+    int elo = lo - STATIC_REACH, ewidth = width + 2 * STATIC_REACH;
+    if (per) {
+        lo %= n;
+        if (lo < 0) lo += n;
+        if (width > n) width = n;
+        elo %= n;
+        if (elo < 0) elo += n;
+        if (ewidth > n) ewidth = n;
     }
-    for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) {
-        const BodyState sk = sp.body_cur[k];
-        const BodyProps pk = dv.props[k];
-        const double reach = pk.r + 0.5 * pk.l;
-        {
-            const double inv[3] = {d.inx, d.iny, d.inz};
-            for (int a = 0; a < 3; ++a) {
-                const double c = per[a] ? sk.X[a] - n3[a] * floor(sk.X[a] * inv[a]) : sk.X[a];
-                const double fc = floor(c);
-                cwi[k][a] = (int)fc;
-                cwf[k][a] = (float)(c - fc);
-            }
-        }
-        const double w = sk.q[0], qx = sk.q[1], qy = sk.q[2], qz = sk.q[3];
-        ax[k][0] = (float)(1 - 2 * (qy * qy + qz * qz));
-        ax[k][1] = (float)(2 * (qx * qy + w * qz));
-        ax[k][2] = (float)(2 * (qx * qz - w * qy));
-        for (int a = 0; a < 3; ++a) {
-            int lo = (int)floor(sk.X[a] - reach), hi = (int)floor(sk.X[a] + reach);
-            int width = hi - lo + 1;
-            int elo = lo - STATIC_REACH, ewidth = width + 2 * STATIC_REACH;
-            if (per[a]) {
-                lo %= n3[a];
-                if (lo < 0) lo += n3[a];
-                if (width > n3[a]) width = n3[a];
-                elo %= n3[a];
-                if (elo < 0) elo += n3[a];
-                if (ewidth > n3[a]) ewidth = n3[a];
-            }
-            box[k][a] = lo;
-            box[k][3 + a] = width;
-            ebox[k][a] = elo;
-            ebox[k][3 + a] = ewidth;
+    g.box[a] = lo;
+    g.box[3 + a] = width;
+    g.ebox[a] = elo;
+    g.ebox[3 + a] = ewidth;
+}
+
+__device__ inline void geom_scalars(const BodyProps &p, BodyGeom &g) {
+    g.r2 = p.r2f;
+    g.h = p.hf;
+    g.margin = p.marginf;
+    g.shape = p.shape;
+    g.side = 2 * (p.E + REMAP_MARGIN) + 1;
+}
+
+// a body may not cross a wall: its extent along axis a (with the x axis'
+// component axa of a capsule) beyond the wall planes
+__device__ inline bool outside_walls(const Domain &d, const BodyProps &p, int a, double Xa, double axa) {
+    const int per = a == 0 ? d.px : (a == 1 ? d.py : d.pz);
+    if (per) return false;
+    const int n = a == 0 ? d.nx : (a == 1 ? d.ny : d.nz);
+    const double ext = p.r + (p.shape == 1 ? 0.5 * p.l * fabs(axa) : 0.0);
+    return Xa - ext < -0.5 || Xa + ext > n - 0.5;
+}
+
+// the whole record of state s, one thread (prep_kernel's fallback)
+__device__ void make_geom(const Domain &d, const BodyProps &p, const BodyState &s, BodyGeom &g, int *status) {
+    const double w = s.q[0], qx = s.q[1], qy = s.q[2], qz = s.q[3];
+    const double axv[3] = {__dsub_rn(1.0, __dmul_rn(2.0, __fma_rn(qy, qy, __dmul_rn(qz, qz)))),
+                           __dmul_rn(2.0, __fma_rn(qx, qy, __dmul_rn(w, qz))),
+                           __dmul_rn(2.0, __fma_rn(qx, qz, -__dmul_rn(w, qy)))};
+    bool out = false;
+    for (int a = 0; a < 3; ++a) {
+        geom_axis(d, p, a, s.X[a], s.V[a], s.W[a], axv[a], g);
+        out = out || outside_walls(d, p, a, s.X[a], axv[a]);
+    }
+    geom_scalars(p, g);
+    if (out) atomicOr(status, ST_OUTSIDE);
+}
+
+__device__ inline bool same_state(const BodyState &a, const BodyState &b) {
+    const long long *x = reinterpret_cast<const long long *>(&a), *y = reinterpret_cast<const long long *>(&b);
+    bool eq = true;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) eq = eq && x[i] == y[i];
+    return eq;
+}
+
+// Drive terms (Eq. FB1-FB3) and spring forces (Eq. osci_i, osci_j) of step
+// n into scratch: they depend on state n only.  Thread `rank` of `count`
+// takes drive terms rank, rank + count, ... and springs likewise.
+__device__ void body_loads(const Device &dv, const StepPtrs &sp, int drive_rank, int spring_rank, int count) {
+    const double t = (double)*dv.t_dev;
+    for (int k = drive_rank; k < dv.nd; k += count) {
+        const DriveTerm dt = dv.drives[k];
+        double f = 0.0;
+        if (!(t < dt.t_on || t >= dt.t_off)) f = dt.amp * sin(dt.omega * t - dt.phase);
+        double R[3][3];                                 // the drive acts along R(q) axis
+        quat_to_matrix(sp.body_cur[dt.body].q, R);
+        for (int i = 0; i < 3; ++i)
+            dv.drive_f[3 * k + i] = f * (R[i][0] * dt.axis[0] + R[i][1] * dt.axis[1] + R[i][2] * dt.axis[2]);
+    }
+    for (int k = spring_rank; k < dv.ns; k += count) {
+        const Spring sp_ = dv.springs[k];
+        const BodyState si = sp.body_cur[sp_.i], sj = sp.body_cur[sp_.j];
+        const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
+        const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        const double inv_len = len > 0 ? 1.0 / len : 0.0;
+        for (int i = 0; i < 3; ++i)
+            dv.spring_f[3 * k + i] = -sp_.k * (len - sp_.rest) * (dd[i] * inv_len) - sp_.gamma * (si.V[i] - sj.V[i]);
+    }
+}
+
+// the drive and spring loads of step n, two warps on two SM sub-partitions
+// (an FP64 warp instruction occupies its sub-partition's FP64 pipe for the
+// same time however many lanes it carries)
+__global__ void __launch_bounds__(64) loads_kernel(const Device dv, const StepPtrs sp) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) body_loads(dv, sp, lane, dv.ns, 32);
+    else body_loads(dv, sp, dv.nd, lane, 32);
+}
+
+// does the cell span [b0, b0 + bw) (unwrapped) meet the span [e0, e0 + ew)
+// (e0 wrapped into [0, n) on a periodic axis, ew <= n) of an axis of n cells?
+__device__ inline bool spans_meet(int b0, int bw, int e0, int ew, int n, int periodic) {
+    if (!periodic) return b0 < e0 + ew && e0 < b0 + bw;
+    if (bw >= n || ew >= n) return true;
+    int o = (b0 - e0) % n;
+    if (o < 0) o += n;
+    return o < ew || o + bw > n;
+}
+
+// Per-step preparation, one block: the geometry records of states n and
+// n-1 (slots by body buffer: remade only when the slot's stamp differs from
+// the state, i.e. when no rigid-body step produced that state), each body's
+// remap candidates (the bodies, in order, whose grown box meets its remap
+// cube; a warp a body, ballots over the candidates), and the start of the
+// boundary kernel's list.
+constexpr int PREP_THREADS = 128;
+
+__global__ void __launch_bounds__(PREP_THREADS) prep_kernel(const Device dv, const StepPtrs sp) {
+    const Domain d = dv.dom;
+    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    BodyGeom *cur = dv.geom + sp.parity * dv.nb, *prev = dv.geom + (sp.parity ^ 1) * dv.nb;
+    BodyState *scur = dv.gstamp + sp.parity * dv.nb, *sprev = dv.gstamp + (sp.parity ^ 1) * dv.nb;
+    if (threadIdx.x == 0) *dv.bcount = 0;           // the remap refills the boundary kernel's list
+    if (warp < 2) {
+        BodyGeom *g = warp == 0 ? cur : prev;
+        BodyState *st = warp == 0 ? scur : sprev;
+        const BodyState *state = warp == 0 ? sp.body_cur : sp.body_prev;
+        for (int k = lane; k < dv.nb; k += 32) {
+            const BodyState sb = state[k];
+            if (same_state(sb, st[k])) continue;
+            make_geom(d, dv.props[k], sb, g[k], dv.status);
+            st[k] = sb;
         }
     }
     __syncthreads();
-    const BodyProps pb = dv.props[b];
-    const BodyState sb = sp.body_cur[b];
-    const int half = pb.E + REMAP_MARGIN;
-    const int side = 2 * half + 1;
-    const int vol = side * side * side;
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l == 0) {
-        // a body may not cross a wall (its extent beyond the wall planes)
-        double R[3][3];
-        quat_to_matrix(sb.q, R);
-        for (int k = 0; k < 3; ++k) {
-            if (per[k]) continue;
-            const double ext = pb.r + (pb.shape == 1 ? 0.5 * pb.l * fabs(R[k][0]) : 0.0);
-            if (sb.X[k] - ext < -0.5 || sb.X[k] + ext > n3[k] - 0.5) atomicOr(dv.status, ST_OUTSIDE);
-        }
+    __shared__ int s_box[LBM_MAX_BODIES_DEV][8];        // ebox (6), then origin packed per axis below
+    __shared__ int s_org[LBM_MAX_BODIES_DEV][4];
+    for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) {
+        for (int i = 0; i < 6; ++i) s_box[k][i] = cur[k].ebox[i];
+        for (int i = 0; i < 3; ++i) s_org[k][i] = cur[k].origin[i];
+        s_org[k][3] = cur[k].side;
     }
-    if (l >= vol) return;
-    const int lx = l % side, ly = (l / side) % side, lz = l / (side * side);
-    int x = origin[0] + lx;
-    int y = origin[1] + ly;
-    int z = origin[2] + lz;
-    if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else if (x < 0 || x >= d.nx) return;
-    if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else if (y < 0 || y >= d.ny) return;
-    if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else if (z < 0 || z >= d.nz) return;
-    const long long c = ((long long)z * d.ny + y) * d.nx + x;
-    const int p3[3] = {x, y, z};
+    __syncthreads();
+    for (int b = warp; b < dv.nb; b += PREP_THREADS / 32) {
+        int cnt = 0;
+        for (int k0 = 0; k0 < dv.nb; k0 += 32) {
+            const int k = k0 + lane;
+            bool meets = k < dv.nb;
+            for (int a = 0; a < 3 && meets; ++a)
+                meets = spans_meet(s_org[b][a], s_org[b][3], s_box[k][a], s_box[k][3 + a], n3[a], per[a]);
+            const unsigned bal = __ballot_sync(0xffffffffu, meets);
+            if (meets) dv.cand[b * dv.nb + cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)k;
+            cnt += __popc(bal);
+        }
+        if (lane == 0) cur[b].ncand = cnt;
+    }
+}
 
-    int id = NO_BODY;
-    bool reached = false;           // within STATIC_REACH cells of some body's box
-    for (int k = 0; k < dv.nb; ++k) {
-        bool in = true;
-        for (int a = 0; a < 3 && in; ++a) {
-            int o = p3[a] - ebox[k][a];
-            if (per[a] && o < 0) o += n3[a];
-            in = o >= 0 && o < ebox[k][3 + a];
+// a coordinate of the cube, o + l with o in [0, n) and l < side, wrapped
+// into [0, n) on a periodic axis (one compare unless the cube exceeds the axis)
+__device__ inline int wrap_up(int v, int n) { return v < n ? v : (v - n < n ? v - n : v % n); }
+
+// Remap: block row blockIdx.y = body b; the threads cover the cube of side
+// 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) at state n, 32 x 8 threads a
+// block over x and (y, z) rows.  Every covered cell gets its epoch-n flags
+// from the geometry of all bodies and the epoch-(n-1) buffer; overlapping
+// cubes write identical values.  A cell tests only body b's candidates, in
+// body order (integer boxes, the FP32 screen, and the FP64 inside test only
+// within the screen's margin).  Fluid cells flagged F_NEAR or F_SOLID_PREV
+// are appended to the boundary kernel's list.
+constexpr int REMAP_TX = 32, REMAP_TY = 8, REMAP_THREADS = REMAP_TX * REMAP_TY;
+constexpr int REMAP_STAGED = 8;
+static_assert(sizeof(BodyGeom) % sizeof(int) == 0, "geometry records are copied as ints");
+
+__global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
+    const Domain d = dv.dom;
+    const int b = blockIdx.y;
+    const BodyGeom *__restrict__ geo = dv.geom + sp.parity * dv.nb;    // state n
+    // body b's candidates (prep_kernel's list), the first REMAP_STAGED of
+    // them with their records in shared memory
+    __shared__ BodyGeom cg[REMAP_STAGED];
+    __shared__ int cid[LBM_MAX_BODIES_DEV];
+    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
+    const int side = geo[b].side;
+    const int nyb = (side + REMAP_TY - 1) / REMAP_TY;
+    const int lz = blockIdx.x / nyb, ly0 = (blockIdx.x - lz * nyb) * REMAP_TY;
+    if (lz >= side) return;                   // the grid covers the largest body's cube
+    const int org[3] = {geo[b].origin[0], geo[b].origin[1], geo[b].origin[2]};
+    const int ncand = geo[b].ncand;
+    const int tid = threadIdx.y * REMAP_TX + threadIdx.x;
+    const int lane = tid & 31;
+    for (int i = tid; i < ncand; i += REMAP_THREADS) cid[i] = dv.cand[b * dv.nb + i];
+    {
+        constexpr int W = (int)(sizeof(BodyGeom) / sizeof(int));
+        const int staged = min(ncand, REMAP_STAGED);
+        for (int i = tid; i < staged * W; i += REMAP_THREADS) {
+            const int kb = dv.cand[b * dv.nb + i / W];
+            reinterpret_cast<int *>(cg)[i] = reinterpret_cast<const int *>(geo + kb)[i % W];
         }
-        if (!in) continue;
-        reached = true;
-        for (int a = 0; a < 3 && in; ++a) {
-            int o = p3[a] - box[k][a];
-            if (per[a] && o < 0) o += n3[a];
-            in = o >= 0 && o < box[k][3 + a];
-        }
-        if (!in) continue;
-        // FP32 screen; cells within its margin of the surface take the FP64 test
-        const BodyProps pk = dv.props[k];
-        const int screen = inside_screen(d, pk, cwi[k], cwf[k], ax[k], x, y, z);
-        if (screen == 0 || (screen < 0 && !cell_inside(d, pk, sp.body_cur[k], x, y, z))) continue;
-        if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
-        id = k;
     }
-    // farther than STATIC_REACH from every body's box: the cell holds its
-    // static flags in both epoch buffers already (nothing within reach was
-    // solid in the last three steps, at most 0.5 cells of motion per step)
-    if (!reached) return;
-    const uint8_t solid = id != NO_BODY ? F_SOLID : 0;
-    uint8_t flags = solid | wall_bit(d, x, y, z);
-    if (!init_mode) {
-        const uint8_t prev = sp.flags_prev[c] & F_SOLID;
-        if (prev) flags |= F_SOLID_PREV;
-        // does any pull source x - e_a hold an obstacle of step n-1?  (all
-        // 18 loads are independent; sources beyond a wall do not count)
-        uint8_t near = 0;
+    __syncthreads();
+
+    // x in chunks of 32 (cubes wider than a warp take several); every lane
+    // runs every chunk, so the ballots below see whole warps
+    for (int lx0 = 0; lx0 < side; lx0 += REMAP_TX) {
+        const int lx = lx0 + threadIdx.x, ly = ly0 + threadIdx.y;
+        bool live = lx < side && ly < side;
+        int x = org[0] + lx, y = org[1] + ly, z = org[2] + lz;
+        if (d.px) x = wrap_up(x, d.nx); else live = live && x >= 0 && x < d.nx;
+        if (d.py) y = wrap_up(y, d.ny); else live = live && y >= 0 && y < d.ny;
+        if (d.pz) z = wrap_up(z, d.nz); else live = live && z >= 0 && z < d.nz;
+        const long long c = ((long long)z * d.ny + y) * d.nx + x;
+        const int p3[3] = {x, y, z};
+
+        int id = NO_BODY;
+        bool reached = false;           // within STATIC_REACH cells of some body's box
+        for (int i = 0; i < ncand && live; ++i) {
+            const int kb = cid[i];
+            const BodyGeom *g = i < REMAP_STAGED ? cg + i : geo + kb;
+            bool in = true;
+            for (int a = 0; a < 3 && in; ++a) {
+                int o = p3[a] - g->ebox[a];
+                if (per[a] && o < 0) o += n3[a];
+                in = o >= 0 && o < g->ebox[3 + a];
+            }
+            if (!in) continue;
+            reached = true;
+            for (int a = 0; a < 3 && in; ++a) {
+                int o = p3[a] - g->box[a];
+                if (per[a] && o < 0) o += n3[a];
+                in = o >= 0 && o < g->box[3 + a];
+            }
+            if (!in) continue;
+            // FP32 screen; cells within its margin of the surface take the FP64 test
+            const int screen = inside_screen(d, g, x, y, z);
+            if (screen == 0 || (screen < 0 && !cell_inside(d, dv.props[kb], sp.body_cur[kb], x, y, z))) continue;
+            if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
+            id = kb;
+        }
+        // farther than STATIC_REACH from every body's box: the cell holds its
+        // static flags in both epoch buffers already (nothing within reach was
+        // solid in the last three steps, at most 0.5 cells of motion per step)
+        live = live && reached;
+        uint8_t flags = 0;
+        if (live) {
+            const uint8_t solid = id != NO_BODY ? F_SOLID : 0;
+            flags = solid | wall_bit(d, x, y, z);
+            if (!init_mode) {
+                const uint8_t prev = sp.flags_prev[c] & F_SOLID;
+                if (prev) flags |= F_SOLID_PREV;
+                // does any pull source x - e_a hold an obstacle of step n-1?  (all
+                // 18 loads are independent; sources beyond a wall do not count)
+                uint8_t near = 0;
+                const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+                if (x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
 #pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            const int sx = x - ex(a), sy = y - ey(a), sz = z - ez(a);
-            const bool in = !((!d.px && (sx < 0 || sx >= d.nx)) || (!d.py && (sy < 0 || sy >= d.ny)) ||
-                              (!d.pz && (sz < 0 || sz >= d.nz)));
-            const uint8_t v = sp.flags_prev[((long long)wrap_axis(sz, d.nz) * d.ny + wrap_axis(sy, d.ny)) * d.nx +
-                                            wrap_axis(sx, d.nx)];
-            near |= in ? v : 0;
+                    for (int a = 1; a < Q; ++a) near |= sp.flags_prev[c - ex(a) - ey(a) * sy - ez(a) * sz];
+                } else {
+#pragma unroll
+                    for (int a = 1; a < Q; ++a) {
+                        const int sx_ = x - ex(a), sy_ = y - ey(a), sz_ = z - ez(a);
+                        const bool in = !((!d.px && (sx_ < 0 || sx_ >= d.nx)) || (!d.py && (sy_ < 0 || sy_ >= d.ny)) ||
+                                          (!d.pz && (sz_ < 0 || sz_ >= d.nz)));
+                        const uint8_t v = sp.flags_prev[((long long)wrap_axis(sz_, d.nz) * d.ny + wrap_axis(sy_, d.ny)) * d.nx +
+                                                        wrap_axis(sx_, d.nx)];
+                        near |= in ? v : 0;
+                    }
+                }
+                if (near & F_SOLID) flags |= F_NEAR;
+                if ((solid != 0) != (prev != 0) || (solid && sp.bid_prev[c] != id)) dv.changed[sp.parity] = 1;
+            }
+            sp.flags_cur[c] = flags;
+            sp.bid_cur[c] = (uint8_t)id;
         }
-        if (near & F_SOLID) flags |= F_NEAR;
-        if ((solid != 0) != (prev != 0) || (solid && sp.bid_prev[c] != id)) dv.changed[sp.parity] = 1;
+        // the boundary kernel's cells, appended with one atomic per warp
+        const bool mine = live && !init_mode && !(flags & F_SOLID) && (flags & (F_NEAR | F_SOLID_PREV));
+        const unsigned mb = __ballot_sync(0xffffffffu, mine);
+        if (mb) {
+            const int leader = __ffs(mb) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(dv.bcount, __popc(mb));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (mine) dv.blist[base + __popc(mb & ((1u << lane) - 1u))] = (uint32_t)c;
+        }
     }
-    sp.flags_cur[c] = flags;
-    sp.bid_cur[c] = (uint8_t)id;
 }
 
 // Links: block (k, b) scans z-plane k of the cube of side 2 E_b + 3 around
@@ -310,6 +473,15 @@ __global__ void links_kernel(const Device dv, const StepPtrs sp) {
     if (threadIdx.x == 0) *count = base;
 }
 
+// a stored deviation in FP32 (exact for FP32, FP16 times its power-of-two
+// scale, BF16), without a trip through FP64
+template <typename T> __device__ inline float load_dev_f(const T *p, float inv_scale);
+template <> __device__ inline float load_dev_f<float>(const float *p, float) { return *p; }
+template <> __device__ inline float load_dev_f<__half>(const __half *p, float s) { return __half2float(*p) * s; }
+template <> __device__ inline float load_dev_f<__nv_bfloat16>(const __nv_bfloat16 *p, float) {
+    return __bfloat162float(*p);
+}
+
 template <typename T> __device__ inline double load_dev(const T *p, float inv_scale);
 template <> __device__ inline double load_dev<double>(const double *p, float) { return *p; }
 template <> __device__ inline double load_dev<float>(const float *p, float) { return (double)*p; }
@@ -336,136 +508,215 @@ __device__ inline double wrap_near(double d, int n, int periodic) {
     return d > h ? d - n : (d < -h ? d + n : d);
 }
 
-// Rigid-body step (Algorithm 1, Eq. totalFSwimmer) for all bodies, run by
-// one block of 256 threads.  Phase 1 (threads over drive terms and springs)
-// evaluates every drive term (Eq. FB1-FB3) and spring force (Eq. osci_i,
-// osci_j) into scratch; phase 2 (thread b) adds, in order, the momentum-
-// exchange partial sums, g times the volume, its drive terms in term order
-// and its springs in spring order, then advances by semi-implicit Euler
-// (dt = 1) in FP64.
-__device__ void integrate_block(const Device &dv, const StepPtrs &sp, int with_fluid) {
+// Rigid-body step (Algorithm 1, Eq. totalFSwimmer) of body b by one warp
+// (all 32 lanes call it).  An FP64 warp instruction costs the same however
+// many lanes it carries, so lanes hold components: six load components,
+// three axes, nine rotation-matrix entries, four quaternion components.
+// Per axis it adds, in order, the momentum-exchange sum, g times the
+// volume, the body's drive terms in term order and its springs in spring
+// order (body_loads' scratch), then advances by semi-implicit Euler
+// (dt = 1) in FP64.  It also writes the geometry record of the new state
+// into that state's slot, with its stamp, and checks the new state (walls,
+// finite, at most MAX_STEP per step).
+__device__ void integrate_body_warp(const Device &dv, const StepPtrs &sp, int b, int with_fluid) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const long long tstep = *dv.t_dev;
-    const double t = (double)tstep;
-    for (int k = threadIdx.x; k < dv.nd; k += blockDim.x) {
-        const DriveTerm dt = dv.drives[k];
-        double f = 0.0;
-        if (!(t < dt.t_on || t >= dt.t_off)) f = dt.amp * sin(dt.omega * t - dt.phase);
-        double R[3][3];                                 // the drive acts along R(q) axis
-        quat_to_matrix(sp.body_cur[dt.body].q, R);
-        for (int i = 0; i < 3; ++i)
-            dv.drive_f[3 * k + i] = f * (R[i][0] * dt.axis[0] + R[i][1] * dt.axis[1] + R[i][2] * dt.axis[2]);
-    }
-    for (int k = threadIdx.x; k < dv.ns; k += blockDim.x) {
-        const Spring sp_ = dv.springs[k];
-        const BodyState si = sp.body_cur[sp_.i], sj = sp.body_cur[sp_.j];
-        const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
-        const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-        const double inv_len = len > 0 ? 1.0 / len : 0.0;
-        for (int i = 0; i < 3; ++i)
-            dv.spring_f[3 * k + i] = -sp_.k * (len - sp_.rest) * (dd[i] * inv_len) - sp_.gamma * (si.V[i] - sj.V[i]);
-    }
-    __syncthreads();
-    const int b = threadIdx.x;
-    if (b < dv.nb) {
-        const BodyProps pb = dv.props[b];
-        const BodyState s = sp.body_cur[b];
-        double R[3][3];
-        quat_to_matrix(s.q, R);
-        double F[3], Tq[3];
-        for (int i = 0; i < 6; ++i) {
-            double v = 0.0;
-            if (with_fluid)
-                for (int k = 0; k < FORCE_BLOCKS; ++k) v += dv.fpart[((long long)b * FORCE_BLOCKS + k) * 6 + i];
-            const double prev = dv.fh[b * 6 + i];
-            dv.fh[b * 6 + i] = v;
-            if (dv.avg_force && tstep > 0) v = 0.5 * (v + prev);
-            if (i < 3) F[i] = v + dv.g[i] * pb.volume; else Tq[i - 3] = v;
+    const BodyProps *pb = dv.props + b;
+    const double *st = reinterpret_cast<const double *>(sp.body_cur + b);       // X q V W
+    const int ax = lane < 3 ? lane : 0;
+
+    // hydrodynamic load of step n, lane i < 6 component i
+    double hyd = 0.0;
+    if (with_fluid && dv.precision == 0) {
+        if (lane < 6)
+            for (int k = 0; k < FORCE_BLOCKS; ++k) hyd += __ldcg(dv.fpart + ((long long)b * FORCE_BLOCKS + k) * 6 + lane);
+    } else if (with_fluid) {
+        // F = S1 / 36 + Fv, T = (S2 - c x S1) / 36 + Tv - c x Fv with c the
+        // centre's position within its cell (the force kernel's terms)
+        double fv = 0.0;
+        int si = 0;
+        if (lane < 6) {
+            fv = (double)__ldcg(dv.fx + b * 6 + lane) * (1.0 / (double)(1LL << FIX_BITS));
+            si = __ldcg(dv.fi + b * 6 + lane);
+            dv.fx[b * 6 + lane] = 0;
+            dv.fi[b * 6 + lane] = 0;
         }
-        for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k)
-            for (int i = 0; i < 3; ++i) F[i] += dv.drive_f[3 * k + i];
-        for (int kk = pb.spring_first; kk < pb.spring_first + pb.spring_count; ++kk) {
+        const int i = lane % 3, j = (i + 1) % 3, k = (i + 2) % 3;
+        const double s1j = (double)__shfl_sync(FULL, si, j), s1k = (double)__shfl_sync(FULL, si, k);
+        const double fvj = __shfl_sync(FULL, fv, j), fvk = __shfl_sync(FULL, fv, k);
+        const double *c = dv.geom[sp.parity * dv.nb + b].cfd;
+        if (lane < 3) hyd = (double)si * (1.0 / 36.0) + fv;
+        else if (lane < 6)
+            hyd = ((double)si - (c[j] * s1k - c[k] * s1j)) * (1.0 / 36.0) + fv - (c[j] * fvk - c[k] * fvj);
+    }
+    double v = hyd;
+    if (lane < 6) {
+        const double prev = dv.fh[b * 6 + lane];
+        dv.fh[b * 6 + lane] = hyd;
+        if (dv.avg_force && tstep > 0) v = 0.5 * (hyd + prev);
+    }
+
+    // translation, lanes 0..2
+    double F = v + dv.g[ax] * pb->volume;
+    if (lane < 3) {
+        for (int k = pb->drive_first; k < pb->drive_first + pb->drive_count; ++k) F += dv.drive_f[3 * k + ax];
+        for (int kk = pb->spring_first; kk < pb->spring_first + pb->spring_count; ++kk) {
             const int k = dv.spring_list[kk];
-            const bool first = dv.springs[k].i == b;
-            for (int i = 0; i < 3; ++i) F[i] += first ? dv.spring_f[3 * k + i] : -dv.spring_f[3 * k + i];
-        }
-        BodyState n = s;
-        for (int i = 0; i < 3; ++i) {
-            n.V[i] = s.V[i] + F[i] * pb.inv_m;
-            n.X[i] = s.X[i] + n.V[i];
-        }
-        // Omega += R diag(1/I) R^T T
-        double Tb[3], dW[3];
-        for (int i = 0; i < 3; ++i)
-            Tb[i] = (R[0][i] * Tq[0] + R[1][i] * Tq[1] + R[2][i] * Tq[2]) * pb.inv_inertia[i];
-        for (int i = 0; i < 3; ++i) dW[i] = R[i][0] * Tb[0] + R[i][1] * Tb[1] + R[i][2] * Tb[2];
-        for (int i = 0; i < 3; ++i) n.W[i] = s.W[i] + dW[i];
-        // q += 1/2 (0, Omega) (x) q, renormalised
-        const double w = s.q[0], v0 = s.q[1], v1 = s.q[2], v2 = s.q[3];
-        const double c0 = n.W[1] * v2 - n.W[2] * v1, c1 = n.W[2] * v0 - n.W[0] * v2,
-                     c2 = n.W[0] * v1 - n.W[1] * v0;
-        double q4[4] = {w - 0.5 * (n.W[0] * v0 + n.W[1] * v1 + n.W[2] * v2),
-                        v0 + 0.5 * (w * n.W[0] + c0), v1 + 0.5 * (w * n.W[1] + c1),
-                        v2 + 0.5 * (w * n.W[2] + c2)};
-        const double inv_nn = rsqrt(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
-        for (int i = 0; i < 4; ++i) n.q[i] = q4[i] * inv_nn;
-        bool finite = true;
-        for (int i = 0; i < 3; ++i)
-            finite = finite && isfinite(n.X[i]) && isfinite(n.V[i]) && isfinite(n.W[i]);
-        if (!finite) atomicOr(dv.status, ST_NAN);
-        else if (fabs(n.V[0]) > MAX_STEP || fabs(n.V[1]) > MAX_STEP || fabs(n.V[2]) > MAX_STEP)
-            atomicOr(dv.status, ST_UNSTABLE);
-        sp.body_next[b] = n;
-        if (dv.tape) {
-            const TapeCtl tc = *dv.tape;
-            const long long j = tstep - tc.t0;
-            if (tc.on && j >= 0 && j < tc.cap) {
-                const double *src = &n.X[0];
-                double *st = tc.state + ((j + 2) * dv.nb + b) * 13;
-                for (int i = 0; i < 13; ++i) st[i] = src[i];
-                for (int i = 0; i < 6; ++i) tc.force[(j * dv.nb + b) * 6 + i] = dv.fh[b * 6 + i];
-            }
-        }
-        if (dv.hist) {
-            double *h = dv.hist + ((tstep % dv.hist_cap) * dv.nb + b) * 13;
-            const double *src = &n.X[0];
-            for (int i = 0; i < 13; ++i) h[i] = src[i];
+            const double f = dv.spring_f[3 * k + ax];
+            F += dv.springs[k].i == b ? f : -f;
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        *dv.t_dev = tstep + 1;
-        dv.changed[sp.parity ^ 1] = 0;
+    const double Vn = st[7 + ax] + F * pb->inv_m;
+    const double Xn = st[ax] + Vn;
+
+    // R(q) of state n, entry (r, c) on lane 3 r + c < 9: 1 - 2 (a^2 + b^2)
+    // on the diagonal, 2 (p q +- w u) off it
+    const double qw = st[3], qv[3] = {st[4], st[5], st[6]};
+    double Rrc;
+    {
+        const int r = lane < 9 ? lane / 3 : 0, cc = lane < 9 ? lane % 3 : 0;
+        double A, Bq, Cq, D, base;
+        if (r == cc) {
+            A = -qv[(r + 1) % 3]; Bq = qv[(r + 1) % 3];
+            Cq = -qv[(r + 2) % 3]; D = qv[(r + 2) % 3];
+            base = 1.0;
+        } else {
+            const bool plus = (r == 1 && cc == 0) || (r == 0 && cc == 2) || (r == 2 && cc == 1);
+            A = qv[min(r, cc)]; Bq = qv[max(r, cc)];
+            Cq = plus ? qw : -qw; D = qv[3 - r - cc];
+            base = 0.0;
+        }
+        Rrc = base + 2.0 * (A * Bq + Cq * D);
     }
+    // Omega += R diag(1/I) R^T T, lanes 0..2
+    const double T0 = __shfl_sync(FULL, v, 3), T1 = __shfl_sync(FULL, v, 4), T2 = __shfl_sync(FULL, v, 5);
+    const double R0i = __shfl_sync(FULL, Rrc, ax), R1i = __shfl_sync(FULL, Rrc, 3 + ax),
+                 R2i = __shfl_sync(FULL, Rrc, 6 + ax);
+    const double Tb = (R0i * T0 + R1i * T1 + R2i * T2) * pb->inv_inertia[ax];
+    const double Tb0 = __shfl_sync(FULL, Tb, 0), Tb1 = __shfl_sync(FULL, Tb, 1), Tb2 = __shfl_sync(FULL, Tb, 2);
+    const double Ri0 = __shfl_sync(FULL, Rrc, 3 * ax), Ri1 = __shfl_sync(FULL, Rrc, 3 * ax + 1),
+                 Ri2 = __shfl_sync(FULL, Rrc, 3 * ax + 2);
+    const double Wn = st[10 + ax] + (Ri0 * Tb0 + Ri1 * Tb1 + Ri2 * Tb2);
+
+    // q += 1/2 (0, Omega) (x) q, renormalised; lane 0 the scalar part,
+    // lane 1 + i the vector component i
+    const double W0 = __shfl_sync(FULL, Wn, 0), W1 = __shfl_sync(FULL, Wn, 1), W2 = __shfl_sync(FULL, Wn, 2);
+    const double Wv[3] = {W0, W1, W2};
+    double q4;
+    {
+        const int i = lane >= 1 && lane <= 3 ? lane - 1 : 0, i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+        if (lane == 0) q4 = qw - 0.5 * (W0 * qv[0] + W1 * qv[1] + W2 * qv[2]);
+        else q4 = qv[i] + 0.5 * (qw * Wv[i] + (Wv[i1] * qv[i2] - Wv[i2] * qv[i1]));
+    }
+    double sq = lane < 4 ? q4 * q4 : 0.0;
+    sq += __shfl_xor_sync(FULL, sq, 1);
+    sq += __shfl_xor_sync(FULL, sq, 2);
+    const double qn = q4 * rsqrt(sq);
+
+    // checks of state n+1
+    const bool finite = lane >= 3 || (isfinite(Xn) && isfinite(Vn) && isfinite(Wn));
+    const bool all_finite = __all_sync(FULL, finite);
+    const bool fast = __any_sync(FULL, lane < 3 && fabs(Vn) > MAX_STEP);
+
+    // the new state, its tape and history entries
+    auto put = [&](double *o) {
+        if (lane < 3) {
+            o[lane] = Xn;
+            o[7 + lane] = Vn;
+            o[10 + lane] = Wn;
+        }
+        if (lane < 4) o[3 + lane] = qn;
+    };
+    put(reinterpret_cast<double *>(sp.body_next + b));
+    if (dv.tape) {
+        const TapeCtl tc = *dv.tape;
+        const long long j = tstep - tc.t0;
+        if (tc.on && j >= 0 && j < tc.cap) {
+            put(tc.state + ((j + 2) * dv.nb + b) * 13);
+            if (lane < 6) tc.force[(j * dv.nb + b) * 6 + lane] = hyd;
+        }
+    }
+    if (dv.hist) put(dv.hist + ((tstep % dv.hist_cap) * dv.nb + b) * 13);
+
+    // the geometry record of state n+1 (its slot is the body buffer it was
+    // written to), lanes 0..2 an axis each; the body x axis is column 0 of R(q_{n+1})
+    const int slot = sp.parity ^ 1;
+    const double nw = __shfl_sync(FULL, qn, 0), nq[3] = {__shfl_sync(FULL, qn, 1), __shfl_sync(FULL, qn, 2),
+                                                         __shfl_sync(FULL, qn, 3)};
+    const double axa = ax == 0 ? __dsub_rn(1.0, __dmul_rn(2.0, __fma_rn(nq[1], nq[1], __dmul_rn(nq[2], nq[2]))))
+                     : ax == 1 ? __dmul_rn(2.0, __fma_rn(nq[0], nq[1], __dmul_rn(nw, nq[2])))
+                               : __dmul_rn(2.0, __fma_rn(nq[0], nq[2], -__dmul_rn(nw, nq[1])));
+    BodyGeom *g = dv.geom + slot * dv.nb + b;
+    const bool out = lane < 3 && outside_walls(dv.dom, *pb, ax, Xn, axa);
+    if (lane < 3) geom_axis(dv.dom, *pb, ax, Xn, Vn, Wn, axa, *g);
+    if (lane == 0) geom_scalars(*pb, *g);
+    put(reinterpret_cast<double *>(dv.gstamp + slot * dv.nb + b));
+    const bool any_out = __any_sync(FULL, out);
+    if (lane == 0) {
+        if (!all_finite) atomicOr(dv.status, ST_NAN);
+        else if (fast) atomicOr(dv.status, ST_UNSTABLE);
+        if (any_out) atomicOr(dv.status, ST_OUTSIDE);
+    }
+}
+
+// after every body's step: the clock advances and the next epoch's change
+// flag starts clear
+__device__ inline void finish_step(const Device &dv, const StepPtrs &sp) {
+    *dv.t_dev = *dv.t_dev + 1;
+    dv.changed[sp.parity ^ 1] = 0;
+}
+
+// round(v 2^FIX_BITS) to the nearest integer, ties away from zero, from the
+// bits of v in integer operations (a 64-bit conversion would take the slow
+// FP64 pipe); |v| < 2^(62 - FIX_BITS) is the caller's to ensure
+__device__ inline long long to_fixed(float v) {
+    const unsigned u = __float_as_uint(v);
+    const int e = (int)((u >> 23) & 0xffu);
+    if (e == 0 || e == 0xff) return 0;
+    const long long m = (long long)((u & 0x7fffffu) | 0x800000u);     // v = m 2^(e - 150)
+    const int sh = e - 150 + FIX_BITS;
+    long long r;
+    if (sh >= 0) r = m << sh;
+    else if (sh > -25) r = (m + (1LL << (-sh - 1))) >> (-sh);
+    else r = 0;
+    return (u >> 31) ? -r : r;
 }
 
 // Momentum exchange (Eq. hydroF): blocks (k, b), k < FORCE_BLOCKS, split the
 // links of body b into contiguous chunks and sum
 //   F = sum e_a [2 f~_a(x_f) + 6 w_a rho(x_f) e_-a . u_w(x_f + e_a)],
 //   T = sum (x_f + e_a / 2 - X) x F_link
-// with f~ of step n (dst) and the body state of step n, in FP64; each block
-// reduces with warp shuffles in a fixed order and writes its partial sums.
-// The last block to finish then runs the rigid-body step for all bodies,
-// adding the partial sums in block order (deterministic).
+// with f~ of step n (dst) and the body state of step n.  The last block to
+// finish runs the rigid-body step for all bodies.
+//
+// FP64 storage: every term in FP64; each block reduces with warp shuffles
+// in a fixed order and writes its partial sums, which the rigid-body step
+// adds in block order (deterministic).
+//
+// 32/16-bit storage: f~_a = w_a + delta_a splits each link term into a
+// constant part 2 w_a e_a and a small variable part v e_a with
+// v = 2 delta_a + 6 w_a rho e_-a . u_w.  With the fluid cell at integer
+// offset i from the centre's cell and c the centre's position within it
+// (x_f - X = i - c), the sums are
+//   F = S1 / 36 + Fv,  T = (S2 - c x S1) / 36 + Tv - c x Fv,
+//   S1 = sum 72 w_a e_a,  S2 = sum i x 72 w_a e_a   (exact integers),
+//   Fv = sum v e_a,  Tv = sum v (i x e_a)           (FP32 terms, each rounded
+// to 2^-FIX_BITS and added as 64-bit integers),
+// since e_a x e_a = 0.  The large, cancelling constant part never meets a
+// rounding, the variable part is ~1e-3 of a term, and integer sums make
+// the result independent of the order of the blocks' atomic additions.
 template <typename T>
 __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, const StepPtrs sp) {
     const Domain d = dv.dom;
     const int b = blockIdx.y, kb = blockIdx.x;
     const BodyProps pb = dv.props[b];
-    const BodyState sb = sp.body_cur[b];
     const int side = 2 * (pb.E + 1) + 1;
     const int *counts = dv.seg_count + (long long)b * dv.link_side;
     const Link *links = dv.links + (long long)b * dv.link_side * dv.seg_cap;
     const T *pop = static_cast<const T *>(sp.dst);
     const long long C = d.C;
     const float s = dv.f16_inv_scale;
-    // body centre wrapped into the domain (once per block)
-    const double xw[3] = {d.px ? sb.X[0] - d.nx * floor(sb.X[0] * d.inx) : sb.X[0],
-                          d.py ? sb.X[1] - d.ny * floor(sb.X[1] * d.iny) : sb.X[1],
-                          d.pz ? sb.X[2] - d.nz * floor(sb.X[2] * d.inz) : sb.X[2]};
-    const int ci[3] = {(int)floor(xw[0]), (int)floor(xw[1]), (int)floor(xw[2])};
-    const double cfr[3] = {xw[0] - ci[0], xw[1] - ci[1], xw[2] - ci[2]};
-    const float vf[3] = {(float)sb.V[0], (float)sb.V[1], (float)sb.V[2]};
-    const float wf[3] = {(float)sb.W[0], (float)sb.W[1], (float)sb.W[2]};
 
     // exclusive prefix of the segment counts: thread t holds segments
     // [t per, (t+1) per), per <= 4 (side <= MAX_SEGMENTS), block scan
@@ -504,98 +755,180 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
     const int total = prefix[side];
     const int chunk = (total + FORCE_BLOCKS - 1) / FORCE_BLOCKS;
     const int j0 = kb * chunk, j1 = min(total, j0 + chunk);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int j = j0 + threadIdx.x; j < j1; j += FORCE_THREADS) {
-        int lo = 0, hi = side - 1;       // segment k with prefix[k] <= j < prefix[k+1]
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (prefix[mid] <= j) lo = mid; else hi = mid - 1;
-        }
-        const Link lk = links[(long long)lo * dv.seg_cap + (j - prefix[lo])];
-        const long long c = lk.cell;
-        const int a = (int)lk.dir;
-        // cells are 32-bit indices (C < 2^31): 32-bit division
-        const unsigned cu = lk.cell, nxu = (unsigned)d.nx, nyu = (unsigned)d.ny;
-        const int x = (int)(cu % nxu), y = (int)((cu / nxu) % nyu), z = (int)(cu / (nxu * nyu));
-        double rho = 1.0;
-        if constexpr (sizeof(T) == 8) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    if constexpr (sizeof(T) == 8) {
+        const BodyState sb = sp.body_cur[b];
+        // body centre wrapped into the domain (once per block)
+        const double xw[3] = {d.px ? sb.X[0] - d.nx * floor(sb.X[0] * d.inx) : sb.X[0],
+                              d.py ? sb.X[1] - d.ny * floor(sb.X[1] * d.iny) : sb.X[1],
+                              d.pz ? sb.X[2] - d.nz * floor(sb.X[2] * d.inz) : sb.X[2]};
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int j = j0 + threadIdx.x; j < j1; j += FORCE_THREADS) {
+            int lo = 0, hi = side - 1;       // segment k with prefix[k] <= j < prefix[k+1]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (prefix[mid] <= j) lo = mid; else hi = mid - 1;
+            }
+            const Link lk = links[(long long)lo * dv.seg_cap + (j - prefix[lo])];
+            const long long c = lk.cell;
+            const int a = (int)lk.dir;
+            // cells are 32-bit indices (C < 2^31): 32-bit division
+            const unsigned cu = lk.cell, nxu = (unsigned)d.nx, nyu = (unsigned)d.ny;
+            const int x = (int)(cu % nxu), y = (int)((cu / nxu) % nyu), z = (int)(cu / (nxu * nyu));
+            double rho = 1.0;
             for (int q = 0; q < Q; ++q) rho += load_dev<T>(pop + q * C + c, s);
-        } else {
-            float drho = 0.0f;          // FP32 sum of the stored deviations
-            for (int q = 0; q < Q; ++q) drho += (float)load_dev<T>(pop + q * C + c, s);
-            rho += (double)drho;
-        }
-        // the link terms in FP64: the force is a small difference of ~1e3
-        // terms of size ~0.1 (2 f~_a), which FP32 terms would not keep
-        const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
-        double o0, o1, o2, mag;
-        if constexpr (sizeof(T) == 8) {
+            const double g_a = wgt(a) + load_dev<T>(pop + a * C + c, s);
             // offsets of the fluid cell, of the link end and of the link midpoint
-            o0 = wrap_near(x - xw[0], d.nx, d.px);
-            o1 = wrap_near(y - xw[1], d.ny, d.py);
-            o2 = wrap_near(z - xw[2], d.nz, d.pz);
+            const double o0 = wrap_near(x - xw[0], d.nx, d.px);
+            const double o1 = wrap_near(y - xw[1], d.ny, d.py);
+            const double o2 = wrap_near(z - xw[2], d.nz, d.pz);
             const double e0 = o0 + ex(a), e1 = o1 + ey(a), e2 = o2 + ez(a);
             const double u0 = sb.V[0] + (sb.W[1] * e2 - sb.W[2] * e1);
             const double u1 = sb.V[1] + (sb.W[2] * e0 - sb.W[0] * e2);
             const double u2 = sb.V[2] + (sb.W[0] * e1 - sb.W[1] * e0);
             const double eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);   // e_-a . u_w
-            mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
-        } else {
-            // offsets from the centre's cell (integer minimum image) and its
-            // FP64 fraction; the moving-wall term (~1e-3 of the link) in FP32
-            o0 = (double)near_cell_k(x - ci[0], d.nx, d.px) - cfr[0];
-            o1 = (double)near_cell_k(y - ci[1], d.ny, d.py) - cfr[1];
-            o2 = (double)near_cell_k(z - ci[2], d.nz, d.pz) - cfr[2];
-            const float e0 = (float)o0 + ex(a), e1 = (float)o1 + ey(a), e2 = (float)o2 + ez(a);
+            const double mag = 2.0 * g_a + 6.0 * wgt(a) * rho * eu;
+            const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
+            const double m0 = o0 + 0.5 * ex(a), m1 = o1 + 0.5 * ey(a), m2 = o2 + 0.5 * ez(a);
+            acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];
+            acc[3] += m1 * fl[2] - m2 * fl[1];
+            acc[4] += m2 * fl[0] - m0 * fl[2];
+            acc[5] += m0 * fl[1] - m1 * fl[0];
+        }
+        __shared__ double part[FORCE_THREADS / 32][6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double v = acc[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) part[warp][i] = v;
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                double v = lane < FORCE_THREADS / 32 ? part[lane][i] : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) dv.fpart[((long long)b * FORCE_BLOCKS + kb) * 6 + i] = v;
+            }
+        }
+    } else {
+        const BodyGeom *g = dv.geom + sp.parity * dv.nb + b;       // state n
+        const int ci[3] = {g->ci[0], g->ci[1], g->ci[2]};
+        const float cf[3] = {g->cf[0], g->cf[1], g->cf[2]};
+        const float vf[3] = {g->v[0], g->v[1], g->v[2]}, wf[3] = {g->w[0], g->w[1], g->w[2]};
+        long long accx[6] = {0, 0, 0, 0, 0, 0};
+        int acci[6] = {0, 0, 0, 0, 0, 0};
+        int bad = 0;
+        for (int j = j0 + threadIdx.x; j < j1; j += FORCE_THREADS) {
+            int lo = 0, hi = side - 1;       // segment k with prefix[k] <= j < prefix[k+1]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (prefix[mid] <= j) lo = mid; else hi = mid - 1;
+            }
+            const Link lk = links[(long long)lo * dv.seg_cap + (j - prefix[lo])];
+            const long long c = lk.cell;
+            const int a = (int)lk.dir;
+            const unsigned cu = lk.cell, nxu = (unsigned)d.nx, nyu = (unsigned)d.ny;
+            const int x = (int)(cu % nxu), y = (int)((cu / nxu) % nyu), z = (int)(cu / (nxu * nyu));
+            float drho = 0.0f;          // FP32 sum of the stored deviations
+            for (int q = 0; q < Q; ++q) drho += load_dev_f<T>(pop + q * C + c, s);
+            const float rho = 1.0f + drho;
+            const float da = load_dev_f<T>(pop + a * C + c, s);
+            const int i0 = near_cell_k(x - ci[0], d.nx, d.px);
+            const int i1 = near_cell_k(y - ci[1], d.ny, d.py);
+            const int i2 = near_cell_k(z - ci[2], d.nz, d.pz);
+            // u_w at the link end x_f + e_a
+            const float e0 = ((float)i0 - cf[0]) + ex(a), e1 = ((float)i1 - cf[1]) + ey(a),
+                        e2 = ((float)i2 - cf[2]) + ez(a);
             const float u0 = vf[0] + (wf[1] * e2 - wf[2] * e1);
             const float u1 = vf[1] + (wf[2] * e0 - wf[0] * e2);
             const float u2 = vf[2] + (wf[0] * e1 - wf[1] * e0);
             const float eu = -(ex(a) * u0 + ey(a) * u1 + ez(a) * u2);
-            mag = 2.0 * g_a + (double)((float)(6.0 * wgt(a)) * (float)rho * eu);
+            const float w6 = a < 7 ? 1.0f / 3.0f : 1.0f / 6.0f;    // 6 w_a (a > 0)
+            const float v = 2.0f * da + w6 * rho * eu;
+            // |delta| >= 2 is no fluid state; the bound keeps every sum in range
+            if (!(fabsf(v) < 4.0f)) bad |= v != v ? ST_NAN : ST_UNSTABLE;
+            const long long vx = to_fixed(v);
+            accx[0] += ex(a) * vx;
+            accx[1] += ey(a) * vx;
+            accx[2] += ez(a) * vx;
+            const int c0 = i1 * ez(a) - i2 * ey(a), c1 = i2 * ex(a) - i0 * ez(a), c2 = i0 * ey(a) - i1 * ex(a);
+            accx[3] += to_fixed((float)c0 * v);
+            accx[4] += to_fixed((float)c1 * v);
+            accx[5] += to_fixed((float)c2 * v);
+            const int K = a < 7 ? 4 : 2;          // 72 w_a
+            acci[0] += K * ex(a);
+            acci[1] += K * ey(a);
+            acci[2] += K * ez(a);
+            acci[3] += K * c0;
+            acci[4] += K * c1;
+            acci[5] += K * c2;
         }
-        const double fl[3] = {ex(a) * mag, ey(a) * mag, ez(a) * mag};
-        const double m0 = o0 + 0.5 * ex(a), m1 = o1 + 0.5 * ey(a), m2 = o2 + 0.5 * ez(a);
-        acc[0] += fl[0]; acc[1] += fl[1]; acc[2] += fl[2];
-        acc[3] += m1 * fl[2] - m2 * fl[1];
-        acc[4] += m2 * fl[0] - m0 * fl[2];
-        acc[5] += m0 * fl[1] - m1 * fl[0];
-    }
-    __shared__ double part[FORCE_THREADS / 32][6];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        double v = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) part[warp][i] = v;
-    }
-    __syncthreads();
-    if (warp == 0) {
+        if (bad) atomicOr(dv.status, bad);
+        __shared__ long long px_[FORCE_THREADS / 32][6];
+        __shared__ int pi_[FORCE_THREADS / 32][6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            double v = lane < FORCE_THREADS / 32 ? part[lane][i] : 0.0;
+            long long v = accx[i];
+            int w = acci[i];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) dv.fpart[((long long)b * FORCE_BLOCKS + kb) * 6 + i] = v;
+            for (int o = 16; o > 0; o >>= 1) {
+                v += __shfl_down_sync(0xffffffffu, v, o);
+                w += __shfl_down_sync(0xffffffffu, w, o);
+            }
+            if (lane == 0) {
+                px_[warp][i] = v;
+                pi_[warp][i] = w;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int i = threadIdx.x;
+            long long v = 0;
+            int w = 0;
+            for (int k = 0; k < FORCE_THREADS / 32; ++k) {
+                v += px_[k][i];
+                w += pi_[k][i];
+            }
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(dv.fx + b * 6 + i), (unsigned long long)v);
+            if (w) atomicAdd(dv.fi + b * 6 + i, w);
+            __threadfence();            // before the block counts itself done
         }
     }
-    // the last block to finish integrates the bodies
-    __shared__ bool last;
+    // the last of body b's blocks integrates body b with its first warp
+    // (the drive and spring loads were evaluated beside the bulk kernel);
+    // the last body ends the step
+    __shared__ int last_of_body;
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned done = atomicAdd(dv.blocks_done, 1u);
-        last = done == gridDim.x * gridDim.y - 1;
+        last_of_body = atomicAdd(dv.body_done + b, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last) return;
+    if (!last_of_body || threadIdx.x >= 32) return;
     __threadfence();
-    integrate_block(dv, sp, 1);
-    if (threadIdx.x == 0) *dv.blocks_done = 0u;
+    integrate_body_warp(dv, sp, b, 1);
+    __syncwarp();
+    if (threadIdx.x != 0) return;
+    dv.body_done[b] = 0u;
+    __threadfence();
+    if (atomicAdd(dv.blocks_done, 1u) != gridDim.y - 1) return;
+    __threadfence();
+    *dv.blocks_done = 0u;
+    finish_step(dv, sp);
 }
 
-// the rigid-body step alone (bodies without fluid)
+// the rigid-body step alone (bodies without fluid), one block: the loads,
+// then a warp a body
 __global__ void __launch_bounds__(256) integrate_kernel(const Device dv, const StepPtrs sp, int with_fluid) {
-    integrate_block(dv, sp, with_fluid);
+    body_loads(dv, sp, threadIdx.x, threadIdx.x, blockDim.x);
+    __syncthreads();
+    for (int b = threadIdx.x >> 5; b < dv.nb; b += blockDim.x >> 5) integrate_body_warp(dv, sp, b, with_fluid);
+    __syncthreads();
+    if (threadIdx.x == 0) finish_step(dv, sp);
 }
 
 // ---- field export / import -----------------------------------------------
@@ -655,13 +988,15 @@ void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8
 }
 
 void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s) {
-    const long long side = dv.remap_side;
-    const unsigned bx = blocks_for(side * side * side, REMAP_THREADS);
-    remap_kernel<<<dim3(bx, dv.nb), REMAP_THREADS, 0, s>>>(dv, sp, init_mode);
+    prep_kernel<<<1, PREP_THREADS, 0, s>>>(dv, sp);
+    const int side = dv.remap_side;
+    const unsigned bx = (unsigned)(((side + REMAP_TY - 1) / REMAP_TY) * side);
+    remap_kernel<<<dim3(bx, dv.nb), dim3(REMAP_TX, REMAP_TY), 0, s>>>(dv, sp, init_mode);
 }
 
 void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     links_kernel<<<dim3(dv.link_side, dv.nb), 256, 0, s>>>(dv, sp);
+    loads_kernel<<<1, 64, 0, s>>>(dv, sp);
 }
 
 void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s) {

@@ -67,7 +67,9 @@ constexpr int LBM_MAX_BODIES_DEV = 254;
 struct BodyProps {
     int shape;          // 0 sphere, 1 capsule
     int E;              // ceil(r + l/2) + 1: half-width of the box that holds every solid cell
+    float r2f, hf, marginf;     // r^2, l / 2 and the FP32 inside test's margin 2e-2 max(r^2, 1), in FP32
     double r, l, m, volume;
+    double reach;       // r + l / 2
     double inertia[3];      // body-frame principal moments of inertia
     double inv_m, inv_inertia[3];
     int drive_first, drive_count;   // this body's drive terms, in term order
@@ -94,6 +96,31 @@ struct Link {
     uint32_t cell;
     uint32_t dir;
 };
+
+// One body state in the forms the cell kernels use: integers and FP32, so
+// that no per-cell path needs the (slow) FP64 pipe.  The rigid-body step
+// writes the record of the state it produces; prep_kernel checks each
+// slot's stamp against the state in use and remakes it when they differ.
+struct BodyGeom {
+    int origin[3];          // corner of the body's remap cube, floor(X) - (E + REMAP_MARGIN), wrapped into [0, n) on periodic axes
+    int ci[3];              // centre wrapped into the domain: its cell ...
+    float cf[3];            // ... and its position within that cell
+    float ax[3];            // body x axis (a capsule's axis)
+    float v[3], w[3];       // velocity and angular velocity
+    float r2, h, margin;    // r^2, l / 2 and the margin of the FP32 inside test
+    int shape;
+    int side;               // edge of the remap cube, 2 (E + REMAP_MARGIN) + 1
+    int ncand;              // state n: bodies whose grown box meets this body's remap cube (cand list)
+    int box[6];             // per axis: lower corner (wrapped) and width of [floor(X - reach), floor(X + reach)]
+    int ebox[6];            // the same grown by STATIC_REACH cells
+    double cfd[3];          // the position within the cell in FP64
+};
+
+// momentum-exchange sums of 32/16-bit storage: FP32 link terms rounded to
+// multiples of 2^-FIX_BITS and added as 64-bit integers (exact, so the sum
+// does not depend on the order in which blocks add their parts).  With
+// |term| < 2^9 (the force kernel's bound) a sum of 2^13 terms stays in range.
+constexpr int FIX_BITS = 40;
 
 struct Domain {
     int nx, ny, nz;
@@ -167,6 +194,8 @@ struct Device {
     int minb;               // its minimum resident blocks per SM (0: the default variant)
     int nb, ns, nd;
     double tau, omega, g[3];
+    float omega_f, guo_f, g_f[3];   // omega, 1 - omega / 2 and g rounded to FP32 once (the FP32 collision's)
+    float om1_f, ow_f[3], gw_f[3];  // 1 - omega; omega w and (1 - omega / 2) w per weight class (rest, axis, diagonal)
     int forced;
     int avg_force;          // the rigid-body step uses the mean load of steps n and n-1
     float f16_scale, f16_inv_scale;
@@ -175,10 +204,19 @@ struct Device {
     const DriveTerm *drives;
     const int *spring_list; // per-body spring indices (BodyProps::spring_first/count)
     double *fh;             // [nb][6] force, torque of the last step
-    double *fpart;          // [nb][FORCE_BLOCKS][6] per-block partial sums of the force kernel
+    double *fpart;          // [nb][FORCE_BLOCKS][6] per-block partial sums of the force kernel (FP64 storage)
+    long long *fx;          // [nb][6] 32/16-bit storage: fixed-point sums of the variable link terms
+    int *fi;                // [nb][6] 32/16-bit storage: integer sums of the constant link terms
+    BodyGeom *geom;         // [2][nb]: slot p holds the geometry of the state in body buffer p (parity)
+    BodyState *gstamp;      // [2][nb]: the state each slot was made from (prep_kernel remakes on mismatch)
+    long long blist_cap;
+    uint8_t *cand;          // [nb][nb]: body b's remap candidates in body order (BodyGeom::ncand of them)
+    uint32_t *blist;        // cells the remap found fluid with F_NEAR or F_SOLID_PREV (the boundary kernel's)
+    int *bcount;            // entries in blist (a cell in two bodies' cubes may appear twice)
     double *drive_f;        // [nd][3] drive forces of the current step (integrator scratch)
     double *spring_f;       // [ns][3] spring forces on body i of each spring (integrator scratch)
-    unsigned *blocks_done;  // force blocks finished in the current step
+    unsigned *blocks_done;  // bodies whose rigid-body step finished in the current step
+    unsigned *body_done;    // [nb] force blocks of each body finished in the current step
     Link *links;            // [nb][link_side][seg_cap]
     int *seg_count;         // [nb][link_side]
     int link_side, seg_cap, remap_side;

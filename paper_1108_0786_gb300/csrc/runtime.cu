@@ -142,8 +142,10 @@ lbm::StepPtrs step_ptrs(lbm_t *h, int p) {
 
 // the kernels of one step of parity p, in Algorithm 2's order; `ev`
 // (optional) brackets each kernel slot with a pair of events.  With `fork`
-// the boundary-cell kernel runs on a second stream concurrently with the
-// bulk kernel (they write disjoint cells) and joins before the force sums.
+// the boundary-cell kernel, then the link lists and the drive and spring
+// loads, run on a second stream concurrently with the bulk kernel (they
+// touch no data the bulk kernel reads or writes) and join before the force
+// sums.
 void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bool *ran = nullptr,
                   bool fork = false) {
     const lbm::StepPtrs sp = step_ptrs(h, p);
@@ -161,11 +163,12 @@ void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bo
         cudaEventRecord(h->fork_ev, s);
         cudaStreamWaitEvent(h->side, h->fork_ev, 0);
         lbm::launch_boundary_fix(h->dv, sp, h->side);
+        if (bodies) lbm::launch_links(h->dv, sp, h->side);
         cudaEventRecord(h->join_ev, h->side);
     }
     if (fl) run(LBM_KERNEL_STREAM_COLLIDE, s, [&] { lbm::launch_stream_collide(h->dv, sp, s); });
     if (boundary && !forked) run(LBM_KERNEL_BOUNDARY, s, [&] { lbm::launch_boundary_fix(h->dv, sp, s); });
-    if (bodies && fl) run(LBM_KERNEL_LINKS, s, [&] { lbm::launch_links(h->dv, sp, s); });
+    if (bodies && fl && !forked) run(LBM_KERNEL_LINKS, s, [&] { lbm::launch_links(h->dv, sp, s); });
     if (forked) cudaStreamWaitEvent(s, h->join_ev, 0);
     if (bodies && fl) {
         // momentum exchange; its last block runs the rigid-body step
@@ -179,10 +182,10 @@ int kernels_per_step(const lbm_t *h) {
     const bool bodies = nb(h) > 0, fl = fluid(h);
     const bool walls = (h->bc & 7) != 7;
     int n = 0;
-    if (bodies && fl) n += 1;                               // remap
+    if (bodies && fl) n += 2;                               // body preparation, remap
     if (fl) n += 1;                                         // bulk stream-collide
     if (fl) n += (bodies ? 1 : 0) + (walls ? 1 : 0);        // boundary cells
-    if (bodies && fl) n += 2;                               // links, force + rigid-body step
+    if (bodies && fl) n += 3;                               // links, drive and spring loads, force + rigid-body step
     if (bodies && !fl) n += 1;                              // rigid-body step alone
     return n;
 }
@@ -227,6 +230,17 @@ int ensure_device(lbm_t *h) {
     dv.tau = h->tau;
     dv.omega = 1.0 / h->tau;
     for (int i = 0; i < 3; ++i) dv.g[i] = h->g[i];
+    dv.omega_f = (float)dv.omega;
+    dv.guo_f = (float)(1.0 - 0.5 * dv.omega);
+    for (int i = 0; i < 3; ++i) dv.g_f[i] = (float)dv.g[i];
+    dv.om1_f = (float)(1.0 - dv.omega);
+    {
+        const double wc[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+        for (int i = 0; i < 3; ++i) {
+            dv.ow_f[i] = (float)(dv.omega * wc[i]);
+            dv.gw_f[i] = (float)((1.0 - 0.5 * dv.omega) * wc[i]);
+        }
+    }
     dv.forced = (h->g[0] != 0.0 || h->g[1] != 0.0 || h->g[2] != 0.0) ? 1 : 0;
     dv.avg_force = (h->options & LBM_OPT_AVERAGE_FORCE) ? 1 : 0;
     dv.f16_scale = h->precision == LBM_PREC_F16 ? 1024.0f : 1.0f;
@@ -277,12 +291,29 @@ int ensure_device(lbm_t *h) {
     if ((rc = alloc_into(h, &drives, sizeof(DriveTerm) * std::max<size_t>(h->drives.size(), 1)))) return rc;
     if ((rc = alloc_into(h, &dv.fh, sizeof(double) * 6 * std::max(B, 1)))) return rc;
     if ((rc = alloc_into(h, &dv.fpart, sizeof(double) * 6 * lbm::FORCE_BLOCKS * std::max(B, 1)))) return rc;
+    if ((rc = alloc_into(h, &dv.fx, sizeof(long long) * 6 * std::max(B, 1)))) return rc;
+    if ((rc = alloc_into(h, &dv.fi, sizeof(int) * 6 * std::max(B, 1)))) return rc;
+    if ((rc = alloc_into(h, &dv.geom, sizeof(lbm::BodyGeom) * 2 * std::max(B, 1)))) return rc;
+    if ((rc = alloc_into(h, &dv.gstamp, sizeof(BodyState) * 2 * std::max(B, 1)))) return rc;
+    {
+        // every cube cell is listed at most once per body cube, and a cell
+        // lies in few cubes: the smaller of the two bounds below (the
+        // remap checks the capacity and reports an overflow)
+        const long long rs = dv.remap_side;
+        const long long cubes = (long long)B * rs * rs * rs, two_c = 2 * C + 1024;
+        const size_t cap = B > 0 && fluid(h) ? (size_t)std::min(cubes, two_c) : 1;
+        dv.blist_cap = (long long)cap;
+        if ((rc = alloc_into(h, &dv.blist, sizeof(uint32_t) * cap))) return rc;
+        if ((rc = alloc_into(h, &dv.cand, (size_t)std::max(B, 1) * std::max(B, 1)))) return rc;
+        if ((rc = alloc_into(h, &dv.bcount, sizeof(int) * 4))) return rc;
+    }
     int *slist;
     if ((rc = alloc_into(h, &slist, sizeof(int) * std::max<size_t>(spring_list.size(), 1)))) return rc;
     dv.spring_list = slist;
     if ((rc = alloc_into(h, &dv.drive_f, sizeof(double) * 3 * std::max<size_t>(h->drives.size(), 1)))) return rc;
     if ((rc = alloc_into(h, &dv.spring_f, sizeof(double) * 3 * std::max<size_t>(h->springs.size(), 1)))) return rc;
     if ((rc = alloc_into(h, &dv.blocks_done, sizeof(unsigned) * 4))) return rc;
+    if ((rc = alloc_into(h, &dv.body_done, sizeof(unsigned) * std::max(B, 1)))) return rc;
     const size_t nlinks = (size_t)std::max(B, 1) * dv.link_side * dv.seg_cap;
     if ((rc = alloc_into(h, &dv.links, sizeof(lbm::Link) * (B > 0 && fluid(h) ? nlinks : 1)))) return rc;
     if ((rc = alloc_into(h, &dv.seg_count, sizeof(int) * std::max(B, 1) * dv.link_side))) return rc;
@@ -303,7 +334,15 @@ int ensure_device(lbm_t *h) {
     CK(cudaMemsetAsync(h->pop[1], 0, es * lbm::Q * C, s));
     CK(cudaMemsetAsync(dv.fh, 0, sizeof(double) * 6 * std::max(B, 1), s));
     CK(cudaMemsetAsync(dv.fpart, 0, sizeof(double) * 6 * lbm::FORCE_BLOCKS * std::max(B, 1), s));
+    CK(cudaMemsetAsync(dv.fx, 0, sizeof(long long) * 6 * std::max(B, 1), s));
+    CK(cudaMemsetAsync(dv.fi, 0, sizeof(int) * 6 * std::max(B, 1), s));
+    CK(cudaMemsetAsync(dv.geom, 0, sizeof(lbm::BodyGeom) * 2 * std::max(B, 1), s));
+    // stamps that match no state (q = 0 is no unit quaternion): the first
+    // step computes every geometry record
+    CK(cudaMemsetAsync(dv.gstamp, 0, sizeof(BodyState) * 2 * std::max(B, 1), s));
+    CK(cudaMemsetAsync(dv.bcount, 0, sizeof(int) * 4, s));
     CK(cudaMemsetAsync(dv.blocks_done, 0, sizeof(unsigned) * 4, s));
+    CK(cudaMemsetAsync(dv.body_done, 0, sizeof(unsigned) * std::max(B, 1), s));
     if (!spring_list.empty())
         CK(cudaMemcpyAsync(slist, spring_list.data(), sizeof(int) * spring_list.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dv.seg_count, 0, sizeof(int) * std::max(B, 1) * dv.link_side, s));
@@ -358,7 +397,7 @@ int check_status(lbm_t *h) {
     if (st & lbm::ST_OUTSIDE) return fail(h, LBM_E_OUTSIDE, "a body crosses a wall of the domain");
     if (st & lbm::ST_UNSTABLE)
         return fail(h, LBM_E_UNSTABLE, "a body moved more than %g lattice units in one step", LBM_MAX_BODY_STEP);
-    if (st & lbm::ST_LINKS) return fail(h, LBM_E_LINKS, "link list capacity exceeded");
+    if (st & lbm::ST_LINKS) return fail(h, LBM_E_LINKS, "link or boundary-cell list capacity exceeded");
     if (st & lbm::ST_TIMEOUT) return fail(h, LBM_E_TIMEOUT, "a bounded wait on a bulk copy ran out");
     return LBM_OK;
 }
@@ -469,6 +508,10 @@ int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass,
     BodyProps p{};
     p.shape = shape; p.r = radius; p.l = length; p.m = mass;
     p.E = (int)std::ceil(radius + 0.5 * length) + 1;
+    p.reach = radius + 0.5 * length;
+    p.r2f = (float)(radius * radius);
+    p.hf = (float)(0.5 * length);
+    p.marginf = 2e-2f * std::max(p.r2f, 1.0f);
     const double r = radius, l = length;
     double I[3];
     if (shape == LBM_SHAPE_SPHERE) {

@@ -140,11 +140,14 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     }
     const Cd rho = (Cd)1 + s;
     const Cd inv = (Cd)1 / rho;
-    const Cd gx = (Cd)dv.g[0], gy = (Cd)dv.g[1], gz = (Cd)dv.g[2];
+    // FP32 takes the parameters rounded once on the host (no FP64 conversion per cell)
+    const bool f32 = sizeof(Cd) == 4;
+    const Cd gx = f32 ? (Cd)dv.g_f[0] : (Cd)dv.g[0], gy = f32 ? (Cd)dv.g_f[1] : (Cd)dv.g[1],
+             gz = f32 ? (Cd)dv.g_f[2] : (Cd)dv.g[2];
     const Cd ux = (jx + (Cd)0.5 * gx) * inv, uy = (jy + (Cd)0.5 * gy) * inv, uz = (jz + (Cd)0.5 * gz) * inv;
     const Cd usq = ux * ux + uy * uy + uz * uz;
-    const Cd om = (Cd)dv.omega;
-    const Cd guo = (Cd)(1.0 - 0.5 * dv.omega);
+    const Cd om = f32 ? (Cd)dv.omega_f : (Cd)dv.omega;
+    const Cd guo = f32 ? (Cd)dv.guo_f : (Cd)(1.0 - 0.5 * dv.omega);
     const Cd ug = ux * gx + uy * gy + uz * gz;
     const Cd base = s - (Cd)1.5 * rho * usq;    // deviation of f_eq without the e.u terms, over w
     Cd m = 0, px = 0, py = 0, pz = 0;
@@ -210,6 +213,88 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     }
 }
 
+// LBGK (+ Guo) of one cell for 16-bit storage, the form with the fewest
+// instructions (these kernels are bound by instruction issue, not by HBM):
+// opposite directions (b, b + 1) are paired, the moments come from pair
+// sums and differences, and each relaxation is one FMA,
+//   f~_b = (1 - omega) f_b + (omega w_b) (a +- c) [+ (1 - omega/2) w_b (s +- t)],
+//   a = drho - 1.5 rho u.u + 4.5 rho (e.u)^2,  c = 3 rho e.u,
+//   s = 9 (e.u)(e.g) - 3 u.g,  t = 3 e.g,
+// the same expression as collide<> (other roundings).  SCALED: f holds
+// k delta (k = f16_scale, a power of two) on entry and exit, so the scale
+// enters only rho, u and the per-cell constants, never a population.
+template <bool SCALED>
+__device__ __forceinline__ void collide_lean(float (&f)[Q], const Device &dv) {
+    const float k = SCALED ? dv.f16_scale : 1.0f, ik = SCALED ? dv.f16_inv_scale : 1.0f;
+    float s = f[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float del[Q / 2];
+#pragma unroll
+    for (int p = 0; p < Q / 2; ++p) {
+        const int b = 2 * p + 1;
+        s += f[b] + f[b + 1];
+        del[p] = f[b] - f[b + 1];
+        if (ex(b)) jx += ex(b) > 0 ? del[p] : -del[p];
+        if (ey(b)) jy += ey(b) > 0 ? del[p] : -del[p];
+        if (ez(b)) jz += ez(b) > 0 ? del[p] : -del[p];
+    }
+    const float rho = fmaf(s, ik, 1.0f);
+    const float inv = ik / rho;
+    const float kh = 0.5f * k;
+    const float gx = dv.g_f[0], gy = dv.g_f[1], gz = dv.g_f[2];
+    const float ux = fmaf(kh, gx, jx) * inv, uy = fmaf(kh, gy, jy) * inv, uz = fmaf(kh, gz, jz) * inv;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float kr = k * rho;
+    const float base = fmaf(-1.5f * kr, usq, s);       // k (drho - 1.5 rho u.u)
+    const float A = 4.5f * kr, Cc = 3.0f * kr;
+    const float om1 = dv.om1_f;
+    const bool forced = dv.forced;
+    const float ug3 = forced ? -3.0f * k * (ux * gx + uy * gy + uz * gz) : 0.0f;
+    f[0] = fmaf(om1, f[0], dv.ow_f[0] * base + (forced ? dv.gw_f[0] * ug3 : 0.0f));
+#pragma unroll
+    for (int p = 0; p < Q / 2; ++p) {
+        const int b = 2 * p + 1;
+        const int wc = b < 7 ? 1 : 2;
+        const float eu = (float)ex(b) * ux + (float)ey(b) * uy + (float)ez(b) * uz;
+        const float a = fmaf(A, eu * eu, base);
+        const float c = Cc * eu;
+        const float ow = dv.ow_f[wc];
+        float r1 = ow * (a + c), r2 = ow * (a - c);
+        if (forced) {
+            const float eg = (float)ex(b) * gx + (float)ey(b) * gy + (float)ez(b) * gz;
+            const float sym = fmaf(9.0f * k * eu, eg, ug3), asym = 3.0f * k * eg;
+            const float gw = dv.gw_f[wc];
+            r1 = fmaf(gw, sym + asym, r1);
+            r2 = fmaf(gw, sym - asym, r2);
+        }
+        f[b] = fmaf(om1, f[b], r1);
+        f[b + 1] = fmaf(om1, f[b + 1], r2);
+    }
+}
+
+// 16-bit storage without a per-population scale: FP16 keeps k delta, so the
+// stored value itself is what collide_lean<true> works on
+template <typename T> __device__ __forceinline__ float raw_ld(T v);
+template <> __device__ __forceinline__ float raw_ld<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float raw_ld<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// two results to one 32-bit word of 16-bit storage (one packed conversion)
+template <typename T> __device__ __forceinline__ unsigned raw_pack(float lo, float hi);
+template <> __device__ __forceinline__ unsigned raw_pack<__half>(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    unsigned u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+template <> __device__ __forceinline__ unsigned raw_pack<__nv_bfloat16>(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    unsigned u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+template <typename T> __device__ __forceinline__ T raw_st(float v);
+template <> __device__ __forceinline__ __half raw_st<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 raw_st<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
 // MINB == 1 leaves the register budget to the compiler (an explicit minimum
 // of one block lets it spend far more registers than it needs)
 template <typename T, int V, int BX, int BY, int MINB>
@@ -236,6 +321,12 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
 
     uint8_t fl[V];
     load_vec<uint8_t, V>(sp.flags_cur + c0, fl);
+    // 16-bit storage: stored values as they are (collide_lean takes FP16's scale)
+    constexpr bool raw16 = sizeof(T) == 2;
+    auto ld = [&](T v) -> Cd {
+        if constexpr (raw16) return raw_ld<T>(v);
+        else return Codec<T>::ld(v, inv_scale);
+    };
 
     Cd f[Q][V];
 #pragma unroll
@@ -247,19 +338,19 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
         load_vec<T, V>(row + x0, A);
         if (ex(b) == 0) {
 #pragma unroll
-            for (int i = 0; i < V; ++i) f[b][i] = Codec<T>::ld(A[i], inv_scale);
+            for (int i = 0; i < V; ++i) f[b][i] = ld(A[i]);
         } else if (ex(b) > 0) {          // pull from x - 1
             T left = shfl(A[V - 1], 1, true);
             if (lane == 0 || x0 == 0) left = row[x0 == 0 ? d.nx - 1 : x0 - 1];
-            f[b][0] = Codec<T>::ld(left, inv_scale);
+            f[b][0] = ld(left);
 #pragma unroll
-            for (int i = 1; i < V; ++i) f[b][i] = Codec<T>::ld(A[i - 1], inv_scale);
+            for (int i = 1; i < V; ++i) f[b][i] = ld(A[i - 1]);
         } else {                          // pull from x + 1
             T right = shfl(A[0], 1, false);
             if (lane == 31 || x0 + V == d.nx) right = row[x0 + V == d.nx ? 0 : x0 + V];
 #pragma unroll
-            for (int i = 0; i < V - 1; ++i) f[b][i] = Codec<T>::ld(A[i + 1], inv_scale);
-            f[b][V - 1] = Codec<T>::ld(right, inv_scale);
+            for (int i = 0; i < V - 1; ++i) f[b][i] = ld(A[i + 1]);
+            f[b][V - 1] = ld(right);
         }
     }
 
@@ -268,7 +359,8 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
         Cd g[Q];
 #pragma unroll
         for (int b = 0; b < Q; ++b) g[b] = f[b][i];
-        collide<Cd, std::is_same<T, float>::value>(g, dv);
+        if constexpr (raw16) collide_lean<std::is_same<T, __half>::value>(g, dv);
+        else collide<Cd, std::is_same<T, float>::value>(g, dv);
         const bool solid = fl[i] & F_SOLID;
 #pragma unroll
         for (int b = 0; b < Q; ++b) f[b][i] = solid ? (Cd)0 : g[b];
@@ -282,10 +374,22 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
     if (all_mine) {
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
-            T out[V];
+            if constexpr (raw16 && V % 2 == 0) {
+                unsigned w[V / 2];
 #pragma unroll
-            for (int i = 0; i < V; ++i) out[i] = Codec<T>::st(f[b][i], scale);
-            store_vec<T, V>(dst + (long long)b * C + c0, out);
+                for (int i = 0; i < V / 2; ++i) w[i] = raw_pack<T>(f[b][2 * i], f[b][2 * i + 1]);
+                T out[V];
+                memcpy(&out, &w, sizeof(out));
+                store_vec<T, V>(dst + (long long)b * C + c0, out);
+            } else {
+                T out[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    if constexpr (raw16) out[i] = raw_st<T>(f[b][i]);
+                    else out[i] = Codec<T>::st(f[b][i], scale);
+                }
+                store_vec<T, V>(dst + (long long)b * C + c0, out);
+            }
         }
         return;
     }
@@ -293,7 +397,133 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
     for (int b = 0; b < Q; ++b)
 #pragma unroll
         for (int i = 0; i < V; ++i)
-            if (fl[i] == 0 || (fl[i] & F_SOLID)) dst[(long long)b * C + c0 + i] = Codec<T>::st(f[b][i], scale);
+            if (fl[i] == 0 || (fl[i] & F_SOLID)) {
+                if constexpr (raw16) dst[(long long)b * C + c0 + i] = raw_st<T>(f[b][i]);
+                else dst[(long long)b * C + c0 + i] = Codec<T>::st(f[b][i], scale);
+            }
+}
+
+// 16-bit values packed two to a 32-bit word (the lower address in the low
+// half): widening to FP32 and narrowing back (round to nearest even)
+template <typename T> __device__ __forceinline__ float half_lo(unsigned w);
+template <typename T> __device__ __forceinline__ float half_hi(unsigned w);
+template <typename T> __device__ __forceinline__ unsigned half_bits(float v);
+template <> __device__ __forceinline__ float half_lo<__half>(unsigned w) {
+    return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+}
+template <> __device__ __forceinline__ float half_hi<__half>(unsigned w) {
+    return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+}
+template <> __device__ __forceinline__ unsigned half_bits<__half>(float v) {
+    return __half_as_ushort(__float2half_rn(v));
+}
+template <> __device__ __forceinline__ float half_lo<__nv_bfloat16>(unsigned w) { return __uint_as_float(w << 16); }
+template <> __device__ __forceinline__ float half_hi<__nv_bfloat16>(unsigned w) {
+    return __uint_as_float(w & 0xffff0000u);
+}
+template <> __device__ __forceinline__ unsigned half_bits<__nv_bfloat16>(float v) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// The bulk kernel for 16-bit storage, V (even) cells per thread.  The
+// populations stay packed two to a word (the thread's cells 2j and 2j + 1
+// in word j) from load to store, half the registers of widened values, so
+// that more warps -- or more bytes per warp -- keep HBM requests in flight.
+// A shift along x is a byte permute of adjacent words (and of one word
+// shuffled from the neighbouring lane); a cell's 19 values are widened to
+// FP32 just before its collision (collide_lean, the row-staged kernel's
+// arithmetic) and narrowed back into their half-words after it.
+template <typename T, int V, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB)
+bulk16_kernel(const Device dv, const StepPtrs sp) {
+    static_assert(sizeof(T) == 2 && V % 2 == 0, "two 16-bit cells a word");
+    constexpr int W = V / 2;
+    using RawV = typename Raw<2 * V>::type;
+    const Domain d = dv.dom;
+    const int nxq = d.nx / V;
+    int xq = blockIdx.x * BX + threadIdx.x;
+    int y = blockIdx.y * BY + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool active = xq < nxq && y < d.ny;
+    xq = min(xq, nxq - 1);              // inactive lanes still join the shuffles
+    y = min(y, d.ny - 1);
+    const int lane = threadIdx.x & 31;
+    const int x0 = xq * V;
+    const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? d.nz - 1 : z - 1, zp = z == d.nz - 1 ? 0 : z + 1;
+    const long long C = d.C;
+    const long long c0 = ((long long)z * d.ny + y) * d.nx + x0;
+    const unsigned short *__restrict__ src = static_cast<const unsigned short *>(sp.src);
+    unsigned short *__restrict__ dst = static_cast<unsigned short *>(sp.dst);
+
+    uint8_t fl[V];
+    load_vec<uint8_t, V>(sp.flags_cur + c0, fl);
+
+    unsigned w[Q][W];
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+        const int ys = ey(b) > 0 ? ym : (ey(b) < 0 ? yp : y);
+        const int zs = ez(b) > 0 ? zm : (ez(b) < 0 ? zp : z);
+        const unsigned short *row = src + (long long)b * C + ((long long)zs * d.ny + ys) * d.nx;
+        unsigned R[W];
+        {
+            const RawV r = __ldg(reinterpret_cast<const RawV *>(row + x0));
+            memcpy(&R, &r, sizeof(R));
+        }
+        if (ex(b) == 0) {
+#pragma unroll
+            for (int j = 0; j < W; ++j) w[b][j] = R[j];
+        } else if (ex(b) > 0) {          // pull from x - 1: the left neighbour's last half-word first
+            unsigned lw = __shfl_up_sync(0xffffffffu, R[W - 1], 1);
+            if (lane == 0 || x0 == 0) lw = (unsigned)row[x0 == 0 ? d.nx - 1 : x0 - 1] << 16;
+            w[b][0] = __byte_perm(lw, R[0], 0x5432);
+#pragma unroll
+            for (int j = 1; j < W; ++j) w[b][j] = __byte_perm(R[j - 1], R[j], 0x5432);
+        } else {                          // pull from x + 1: the right neighbour's first half-word last
+            unsigned rw = __shfl_down_sync(0xffffffffu, R[0], 1);
+            if (lane == 31 || x0 + V == d.nx) rw = (unsigned)row[x0 + V == d.nx ? 0 : x0 + V];
+#pragma unroll
+            for (int j = 0; j < W - 1; ++j) w[b][j] = __byte_perm(R[j], R[j + 1], 0x5432);
+            w[b][W - 1] = __byte_perm(R[W - 1], rw, 0x5432);
+        }
+    }
+
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int j = i >> 1;
+        const bool hi = i & 1;
+        float g[Q];
+#pragma unroll
+        for (int b = 0; b < Q; ++b) g[b] = hi ? half_hi<T>(w[b][j]) : half_lo<T>(w[b][j]);
+        collide_lean<std::is_same<T, __half>::value>(g, dv);
+        const bool solid = fl[i] & F_SOLID;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            const unsigned h = solid ? 0u : half_bits<T>(g[b]);
+            w[b][j] = hi ? __byte_perm(w[b][j], h, 0x5410) : __byte_perm(h, w[b][j], 0x7610);
+        }
+    }
+    if (!active) return;
+    // fluid cells with a non-zero flag byte belong to the boundary kernel,
+    // which may run concurrently: leave them alone
+    bool all_mine = true;
+#pragma unroll
+    for (int i = 0; i < V; ++i) all_mine = all_mine && (fl[i] == 0 || (fl[i] & F_SOLID));
+    if (all_mine) {
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            RawV r;
+            memcpy(&r, &w[b], sizeof(r));
+            *reinterpret_cast<RawV *>(dst + (long long)b * C + c0) = r;
+        }
+        return;
+    }
+#pragma unroll
+    for (int b = 0; b < Q; ++b)
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+            if (fl[i] == 0 || (fl[i] & F_SOLID))
+                dst[(long long)b * C + c0 + i] = (unsigned short)((i & 1) ? w[b][i >> 1] >> 16 : w[b][i >> 1] & 0xffffu);
 }
 
 // Velocity of body b's surface at lattice point p in the compute type R:
@@ -319,23 +549,19 @@ __device__ inline void wall_velocity(const Domain &d, const BodyState &b, int px
 
 // a body for the moving-wall term: the centre wrapped into the domain and
 // split into its cell (int) and the offset within it (FP32), velocity and
-// angular velocity in FP32
+// angular velocity in FP32 (copied from the step's geometry record)
 struct WallBody {
     int ic[3];
     float frac[3], v[3], w[3];
 };
 
-__device__ inline WallBody wall_body(const Domain &d, const BodyState &b) {
+__device__ inline WallBody wall_body(const BodyGeom &g) {
     WallBody r;
-    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
-    const double inv[3] = {d.inx, d.iny, d.inz};
     for (int i = 0; i < 3; ++i) {
-        const double c = per[i] ? b.X[i] - n3[i] * floor(b.X[i] * inv[i]) : b.X[i];
-        const double fc = floor(c);
-        r.ic[i] = (int)fc;
-        r.frac[i] = (float)(c - fc);
-        r.v[i] = (float)b.V[i];
-        r.w[i] = (float)b.W[i];
+        r.ic[i] = g.ci[i];
+        r.frac[i] = g.cf[i];
+        r.v[i] = g.v[i];
+        r.w[i] = g.w[i];
     }
     return r;
 }
@@ -359,41 +585,36 @@ __device__ inline void wall_velocity_wrapped(const Domain &d, const WallBody &b,
 }
 
 // Cells with a non-zero flag byte: refill, bounce-back at walls and moving
-// obstacles, then LBGK.  mode 0: block row blockIdx.y = body b, the threads
-// cover the cube of side 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) (the
-// cube the remap wrote); mode 1: blockIdx.y = wall face (axis * 2 + side).
-// Every load a cell needs is issued before any of them is used, so a thread
-// waits for memory about twice instead of once per direction.
+// obstacles, then LBGK.  mode 0: the cells the remap listed (fluid with
+// F_NEAR or F_SOLID_PREV), one a thread, on a grid sized for the longest
+// possible list; mode 1: blockIdx.y = wall face (axis * 2 + side), the
+// face's cells.  A cell in
+// both sets, or listed twice, is computed more than once with the same
+// result.  Every load a cell needs is issued before any of them is used, so
+// a thread waits for memory about twice instead of once per direction.
 template <typename T>
 __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const StepPtrs sp, int mode) {
     using Cd = typename Codec<T>::C;
     const Domain d = dv.dom;
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
     // 32/16-bit storage: the bodies of step n-1 with their centres wrapped
-    // into the domain (one FP64 floor per body and block), so that a link's
-    // minimum-image offset is an FP64 difference and two compares
+    // into the domain, so that a link's minimum-image offset is an integer
+    // difference, two compares and the FP32 position within the cell
     __shared__ WallBody wb[sizeof(T) == 8 ? 1 : LBM_MAX_BODIES_DEV];
-    __shared__ int origin[3];               // mode 0: the cube corner (one FP64 floor per axis and block)
-    if constexpr (sizeof(T) != 8)
-        for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) wb[k] = wall_body(d, sp.body_prev[k]);
-    if (mode == 0 && threadIdx.x == 0) {
-        const BodyState sb = sp.body_cur[blockIdx.y];
-        const int half = dv.props[blockIdx.y].E + REMAP_MARGIN;
-        for (int a = 0; a < 3; ++a) origin[a] = (int)floor(sb.X[a]) - half;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int listed = mode == 0 ? *dv.bcount : 0;
+    if (mode == 0 && (int)(blockIdx.x * blockDim.x) >= listed) return;      // the whole block is past the list
+    if constexpr (sizeof(T) != 8) {
+        for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) wb[k] = wall_body(dv.geom[(sp.parity ^ 1) * dv.nb + k]);
+        __syncthreads();
     }
-    __syncthreads();
     int x, y, z;
     if (mode == 0) {
-        const int b = blockIdx.y;
-        const int half = dv.props[b].E + REMAP_MARGIN;
-        const int side = 2 * half + 1;
-        if (l >= side * side * side) return;
-        x = origin[0] + l % side;
-        y = origin[1] + (l / side) % side;
-        z = origin[2] + l / (side * side);
-        if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else if (x < 0 || x >= d.nx) return;
-        if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else if (y < 0 || y >= d.ny) return;
-        if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else if (z < 0 || z >= d.nz) return;
+        if (l >= listed) return;
+        const unsigned cl = dv.blist[l];          // C < 2^31: 32-bit division
+        const unsigned nxu = (unsigned)d.nx, nyu = (unsigned)d.ny;
+        x = (int)(cl % nxu);
+        y = (int)((cl / nxu) % nyu);
+        z = (int)(cl / (nxu * nyu));
     } else {
         const int axis = blockIdx.y >> 1, hi = blockIdx.y & 1;
         const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
@@ -427,27 +648,55 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
         }
 #pragma unroll
         for (int a = 1; a < Q; ++a) ok[a] = ok[a] && !(sp.flags_cur[nc[a]] & (F_SOLID | F_SOLID_PREV));
-        double sum = 0.0;
-        int cnt = 0;
-#pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            Cd drho = 0;
-#pragma unroll
-            for (int bb = 0; bb < Q; ++bb) drho += Codec<T>::ld(src[bb * C + nc[a]], s);
-            if (ok[a]) {
-                sum += 1.0 + (double)drho;
-                ++cnt;
-            }
-        }
-        const double rho = cnt ? sum / cnt : 1.0;
         const int k = sp.bid_prev[c];
-        double u[3] = {0.0, 0.0, 0.0};
-        if (k != NO_BODY) surface_velocity(d, sp.body_cur[k], x, y, z, u);
-        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        if constexpr (sizeof(T) == 8) {
+            double sum = 0.0;
+            int cnt = 0;
 #pragma unroll
-        for (int b = 0; b < Q; ++b) {
-            const double eu = ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2];
-            f[b] = (Cd)(wgt(b) * (rho - 1.0) + wgt(b) * rho * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+            for (int a = 1; a < Q; ++a) {
+                Cd drho = 0;
+#pragma unroll
+                for (int bb = 0; bb < Q; ++bb) drho += Codec<T>::ld(src[bb * C + nc[a]], s);
+                if (ok[a]) {
+                    sum += 1.0 + (double)drho;
+                    ++cnt;
+                }
+            }
+            const double rho = cnt ? sum / cnt : 1.0;
+            double u[3] = {0.0, 0.0, 0.0};
+            if (k != NO_BODY) surface_velocity(d, sp.body_cur[k], x, y, z, u);
+            const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+                const double eu = ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2];
+                f[b] = (Cd)(wgt(b) * (rho - 1.0) + wgt(b) * rho * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+            }
+        } else {
+            // FP32: the mean of the neighbours' density deviations (small
+            // numbers: no 1 + drho is ever rounded), u_w of state n
+            float dsum = 0.0f;
+            int cnt = 0;
+#pragma unroll
+            for (int a = 1; a < Q; ++a) {
+                float drho = 0.0f;
+#pragma unroll
+                for (int bb = 0; bb < Q; ++bb) drho += Codec<T>::ld(src[bb * C + nc[a]], s);
+                if (ok[a]) {
+                    dsum += drho;
+                    ++cnt;
+                }
+            }
+            const float drho = cnt ? dsum / (float)cnt : 0.0f;
+            const float rho = 1.0f + drho;
+            float u[3] = {0.0f, 0.0f, 0.0f};
+            if (k != NO_BODY) wall_velocity_wrapped(d, wall_body(dv.geom[sp.parity * dv.nb + k]), x, y, z, u);
+            const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+                const float w = (float)wgt(b);
+                const float eu = ex(b) * u[0] + ey(b) * u[1] + ez(b) * u[2];
+                f[b] = w * drho + w * rho * (3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+            }
         }
     } else {
         // bounce-back at walls (Eq. 4) and at obstacles of step n-1
@@ -619,11 +868,18 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
                 for (int b = 0; b < Q; ++b) {
                     int xs = x - ex(b);
                     xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-                    f[b] = Codec<T>::ld(rowb[b * nx + xs], inv_scale);
+                    if constexpr (sizeof(T) == 2) f[b] = raw_ld<T>(rowb[b * nx + xs]);
+                    else f[b] = Codec<T>::ld(rowb[b * nx + xs], inv_scale);
                 }
-                collide<Cd, std::is_same<T, float>::value>(f, dv);
+                if constexpr (sizeof(T) == 2) {
+                    collide_lean<std::is_same<T, __half>::value>(f, dv);
 #pragma unroll
-                for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = Codec<T>::st(f[b], scale);
+                    for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = raw_st<T>(f[b]);
+                } else {
+                    collide<Cd, std::is_same<T, float>::value>(f, dv);
+#pragma unroll
+                    for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = Codec<T>::st(f[b], scale);
+                }
             }
         }
         __syncthreads();                         // stage st is free again
@@ -684,6 +940,20 @@ void launch_bulk(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     bulk_kernel<T, V, BX, BY, MINB><<<grid, dim3(BX, BY), 0, s>>>(dv, sp);
 }
 
+template <typename T, int V, int BX, int BY, int MINB>
+void launch_bulk16(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    const int nxq = dv.dom.nx / V;
+    dim3 grid((nxq + BX - 1) / BX, (dv.dom.ny + BY - 1) / BY, dv.dom.nz);
+    bulk16_kernel<T, V, BX, BY, MINB><<<grid, dim3(BX, BY), 0, s>>>(dv, sp);
+}
+
+template <typename T, int V, int MINB>
+void launch_shape16(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    const int nxq = dv.dom.nx / V;
+    if (nxq >= 128) launch_bulk16<T, V, 128, 2, MINB>(dv, sp, s);
+    else launch_bulk16<T, V, 32, 8, MINB>(dv, sp, s);
+}
+
 // launch shapes: V cells per thread in blocks of 256 threads (BX a multiple
 // of 32 along x); MINB > 1 caps the registers so that MINB blocks fit an SM
 template <typename T, int V, int MINB>
@@ -709,15 +979,21 @@ const Variant kVariants[] = {
     {1, 2, 4, launch_shape<float, 2, 4>},
     {1, 1, 1, launch_shape<float, 1, 1>},
     {1, 4, 1, launch_shape<float, 4, 1>},
-    {2, 4, 1, launch_shape<__half, 4, 1>},
-    {2, 2, 1, launch_shape<__half, 2, 1>},
-    {2, 2, 3, launch_shape<__half, 2, 3>},
-    {2, 8, 1, launch_shape<__half, 8, 1>},
+    {2, 4, 1, launch_shape16<__half, 4, 1>},
+    {2, 4, 2, launch_shape16<__half, 4, 2>},
+    {2, 4, 3, launch_shape16<__half, 4, 3>},
+    {2, 8, 1, launch_shape16<__half, 8, 1>},
+    {2, 8, 2, launch_shape16<__half, 8, 2>},
+    {2, 2, 1, launch_shape16<__half, 2, 1>},
+    {2, 2, 4, launch_shape16<__half, 2, 4>},
     {2, 1, 1, launch_shape<__half, 1, 1>},
-    {3, 4, 1, launch_shape<__nv_bfloat16, 4, 1>},
-    {3, 2, 1, launch_shape<__nv_bfloat16, 2, 1>},
-    {3, 2, 3, launch_shape<__nv_bfloat16, 2, 3>},
-    {3, 8, 1, launch_shape<__nv_bfloat16, 8, 1>},
+    {3, 4, 1, launch_shape16<__nv_bfloat16, 4, 1>},
+    {3, 4, 2, launch_shape16<__nv_bfloat16, 4, 2>},
+    {3, 4, 3, launch_shape16<__nv_bfloat16, 4, 3>},
+    {3, 8, 1, launch_shape16<__nv_bfloat16, 8, 1>},
+    {3, 8, 2, launch_shape16<__nv_bfloat16, 8, 2>},
+    {3, 2, 1, launch_shape16<__nv_bfloat16, 2, 1>},
+    {3, 2, 4, launch_shape16<__nv_bfloat16, 2, 4>},
     {3, 1, 1, launch_shape<__nv_bfloat16, 1, 1>},
     {0, -1, 1, launch_tma<double, 2, 1>, tma_fits<double, 2, 1>},
     {1, -1, 1, launch_tma<float, 4, 1>, tma_fits<float, 4, 1>},
@@ -742,9 +1018,11 @@ const Variant *find_variant(int precision, int vec, int minb) {
 template <typename T>
 void launch_boundary(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     if (dv.nb > 0) {
+        // the list's length is on the device: blocks past it return at once
         const long long side = dv.remap_side;
-        const unsigned bx = (unsigned)((side * side * side + 255) / 256);
-        boundary_kernel<T><<<dim3(bx, dv.nb), 256, 0, s>>>(dv, sp, 0);
+        const long long most = (long long)dv.nb * side * side * side;
+        const unsigned bx = (unsigned)((most + 255) / 256);
+        boundary_kernel<T><<<bx, 256, 0, s>>>(dv, sp, 0);
     }
     if (!(dv.dom.px && dv.dom.py && dv.dom.pz)) {
         const long long nx = dv.dom.nx, ny = dv.dom.ny, nz = dv.dom.nz;

@@ -257,8 +257,8 @@ def test_kernel_timing_and_launch_accounting():
     lat = lbm.from_scenario(sc, precision="f32")
     lat.step(2)
     ms = lat.time_kernels(3)
-    assert lat.kernels_per_step == 5
-    assert ms["integrate"] == 0.0            # the force kernel's last block integrates
+    assert lat.kernels_per_step == 7
+    assert ms["integrate"] == 0.0            # the force kernel's last blocks integrate
     assert all(v > 0 for k, v in ms.items() if k != "integrate"), ms
     assert lat.steps_done == 5
 
@@ -279,8 +279,8 @@ def test_graph_steps_equal_eager_steps():
 @pytest.mark.parametrize("precision,shapes", [
     ("f64", ((1, 0), (2, 0), (-1, 1))),
     ("f32", ((1, 0), (2, 0), (2, 4), (4, 0), (-1, 1), (-1, 2))),
-    ("f16", ((1, 0), (2, 0), (2, 3), (4, 0), (8, 0), (-1, 2), (-1, 3), (-1, 4))),
-    ("bf16", ((1, 0), (2, 0), (2, 3), (4, 0), (8, 0), (-1, 2), (-1, 3), (-1, 4)))])
+    ("f16", ((1, 0), (2, 0), (2, 4), (4, 0), (4, 2), (4, 3), (8, 0), (8, 2), (-1, 2), (-1, 3), (-1, 4))),
+    ("bf16", ((1, 0), (2, 0), (2, 4), (4, 0), (4, 2), (4, 3), (8, 0), (8, 2), (-1, 2), (-1, 3), (-1, 4)))])
 def test_launch_shapes_are_bitwise_identical(precision, shapes):
     """The bulk kernel's launch shape changes only the memory access
     pattern and register budget (-1: rows staged in shared memory by bulk
