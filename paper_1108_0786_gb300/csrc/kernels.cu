@@ -34,11 +34,13 @@ __device__ inline bool cell_inside(const Domain &d, const BodyProps &p, const Bo
 
 // The inside test in FP32: the minimum-image offset as an integer difference
 // of cells (wrapped by compares) minus the centre's offset within its cell,
-// then the distance in FP32 from that small, nearly exact offset.  Returns 1
-// (inside) or 0 (outside) when the squared distance is farther than
-// 2e-2 max(r^2, 1) from r^2 -- orders of magnitude above its FP32 error --
-// and -1 otherwise (the FP64 test decides), so the map is the FP64 map bit
-// for bit.
+// then the distance in FP32 from that small, nearly exact offset.  Its
+// error in the squared distance stays below about 1e-5 max(r^2, 1) (offsets
+// exact to an FP32 ulp of the few-cell offset, an axis rounded once, a few
+// roundings of the sums), growing like 1.3e-7 l r for long thin capsules;
+// outside the margin max(1e-3 max(r^2, 1), 2e-6 l max(r, 1)) of r^2 it
+// returns 1 (inside) or 0 (outside), within it -1 and the FP64 test
+// decides: the map is the FP64 map bit for bit.
 __device__ inline int inside_screen(const Domain &d, const BodyGeom *__restrict__ g, int x, int y, int z) {
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz}, q3[3] = {x, y, z};
     float o[3];
@@ -201,12 +203,12 @@ __global__ void __launch_bounds__(64) loads_kernel(const Device dv, const StepPt
     else body_loads(dv, sp, dv.nd, lane, 32);
 }
 
-// does the cell span [b0, b0 + bw) (unwrapped) meet the span [e0, e0 + ew)
-// (e0 wrapped into [0, n) on a periodic axis, ew <= n) of an axis of n cells?
+// does the cell span [b0, b0 + bw) meet the span [e0, e0 + ew) on an axis of
+// n cells?  (On a periodic axis b0 and e0 are wrapped into [0, n).)
 __device__ inline bool spans_meet(int b0, int bw, int e0, int ew, int n, int periodic) {
     if (!periodic) return b0 < e0 + ew && e0 < b0 + bw;
     if (bw >= n || ew >= n) return true;
-    int o = (b0 - e0) % n;
+    int o = b0 - e0;                // the start of [b0, ..) seen from e0, in [0, n)
     if (o < 0) o += n;
     return o < ew || o + bw > n;
 }

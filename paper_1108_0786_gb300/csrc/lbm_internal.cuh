@@ -56,10 +56,16 @@ constexpr uint8_t NO_BODY = 0xFF;
 // device status word bits
 constexpr int ST_OVERLAP = 1, ST_OUTSIDE = 2, ST_NAN = 4, ST_UNSTABLE = 8, ST_LINKS = 16, ST_TIMEOUT = 32;
 
-// cells added around a body's extent in the remap region; with at most
-// MAX_STEP lattice units of motion per step the region covers every cell
-// whose flags can differ from the static value in either epoch buffer
-constexpr int REMAP_MARGIN = 4;
+// cells added around a body's extent in the remap region (the cube of
+// half-width E + REMAP_MARGIN around floor(X)).  The remap of step n
+// rewrites the buffer that holds epoch n-2, so the cube must hold every
+// cell solid in epochs n-3 .. n and the neighbours of those solid in n-3
+// and n-1.  A solid cell lies within reach = r + l/2 of its epoch's centre
+// on each axis, the centre moves at most MAX_STEP = 0.5 per step and axis,
+// so these cells lie within reach + 1.5 + 1 of X_n: at most
+// floor(X) + ceil(reach) + 3 = floor(X) + E + 2 above and less below.  One
+// cell more is kept as a spare.
+constexpr int REMAP_MARGIN = 3;
 constexpr double MAX_STEP = 0.5;
 constexpr int FORCE_BLOCKS = 8;     // blocks per body in the momentum-exchange sum
 constexpr int LBM_MAX_BODIES_DEV = 254;
@@ -67,7 +73,7 @@ constexpr int LBM_MAX_BODIES_DEV = 254;
 struct BodyProps {
     int shape;          // 0 sphere, 1 capsule
     int E;              // ceil(r + l/2) + 1: half-width of the box that holds every solid cell
-    float r2f, hf, marginf;     // r^2, l / 2 and the FP32 inside test's margin 2e-2 max(r^2, 1), in FP32
+    float r2f, hf, marginf;     // r^2, l / 2 and the FP32 inside test's margin, in FP32
     double r, l, m, volume;
     double reach;       // r + l / 2
     double inertia[3];      // body-frame principal moments of inertia

@@ -511,7 +511,9 @@ int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass,
     p.reach = radius + 0.5 * length;
     p.r2f = (float)(radius * radius);
     p.hf = (float)(0.5 * length);
-    p.marginf = 2e-2f * std::max(p.r2f, 1.0f);
+    // the FP32 inside test's margin: its error stays near 1e-5 max(r^2, 1)
+    // and grows like 1.3e-7 l r for long thin capsules
+    p.marginf = (float)std::max(1e-3 * std::max(radius * radius, 1.0), 2e-6 * length * std::max(radius, 1.0));
     const double r = radius, l = length;
     double I[3];
     if (shape == LBM_SHAPE_SPHERE) {
