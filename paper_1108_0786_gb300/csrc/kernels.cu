@@ -277,6 +277,8 @@ __device__ inline int wrap_up(int v, int n) { return v < n ? v : (v - n < n ? v 
 // are appended to the boundary kernel's list.
 constexpr int REMAP_TX = 32, REMAP_TY = 8, REMAP_THREADS = REMAP_TX * REMAP_TY;
 constexpr int REMAP_STAGED = 8;
+constexpr int REMAP_LAYERS = 1;         // cube layers a block (more layers serialise each block's latency chain)
+constexpr int REMAP_LIST_BUF = 2048;    // list entries a block gathers before the global append
 static_assert(sizeof(BodyGeom) % sizeof(int) == 0, "geometry records are copied as ints");
 
 __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
@@ -290,12 +292,17 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
     const int side = geo[b].side;
     const int nyb = (side + REMAP_TY - 1) / REMAP_TY;
-    const int lz = blockIdx.x / nyb, ly0 = (blockIdx.x - lz * nyb) * REMAP_TY;
-    if (lz >= side) return;                   // the grid covers the largest body's cube
+    const int lzb = (blockIdx.x / nyb) * REMAP_LAYERS, ly0 = (blockIdx.x % nyb) * REMAP_TY;
+    if (lzb >= side) return;                  // the grid covers the largest body's cube
+    // this block's share of the boundary kernel's list, gathered in shared
+    // memory and appended with one atomic at the end
+    __shared__ uint32_t lbuf[REMAP_LIST_BUF];
+    __shared__ int lcount, lbase;
     const int org[3] = {geo[b].origin[0], geo[b].origin[1], geo[b].origin[2]};
     const int ncand = geo[b].ncand;
     const int tid = threadIdx.y * REMAP_TX + threadIdx.x;
     const int lane = tid & 31;
+    if (tid == 0) lcount = 0;
     for (int i = tid; i < ncand; i += REMAP_THREADS) cid[i] = dv.cand[b * dv.nb + i];
     {
         constexpr int W = (int)(sizeof(BodyGeom) / sizeof(int));
@@ -307,88 +314,109 @@ __global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, c
     }
     __syncthreads();
 
-    // x in chunks of 32 (cubes wider than a warp take several); every lane
-    // runs every chunk, so the ballots below see whole warps
-    for (int lx0 = 0; lx0 < side; lx0 += REMAP_TX) {
-        const int lx = lx0 + threadIdx.x, ly = ly0 + threadIdx.y;
-        bool live = lx < side && ly < side;
-        int x = org[0] + lx, y = org[1] + ly, z = org[2] + lz;
-        if (d.px) x = wrap_up(x, d.nx); else live = live && x >= 0 && x < d.nx;
-        if (d.py) y = wrap_up(y, d.ny); else live = live && y >= 0 && y < d.ny;
-        if (d.pz) z = wrap_up(z, d.nz); else live = live && z >= 0 && z < d.nz;
-        const long long c = ((long long)z * d.ny + y) * d.nx + x;
-        const int p3[3] = {x, y, z};
+    // REMAP_LAYERS layers of the cube a block, x in chunks of 32 (cubes wider
+    // than a warp take several); every lane runs every chunk, so the ballots
+    // below see whole warps
+    const int lz_end = min(side, lzb + REMAP_LAYERS);
+    for (int lz = lzb; lz < lz_end; ++lz)
+        for (int lx0 = 0; lx0 < side; lx0 += REMAP_TX) {
+            const int lx = lx0 + threadIdx.x, ly = ly0 + threadIdx.y;
+            bool live = lx < side && ly < side;
+            int x = org[0] + lx, y = org[1] + ly, z = org[2] + lz;
+            if (d.px) x = wrap_up(x, d.nx); else live = live && x >= 0 && x < d.nx;
+            if (d.py) y = wrap_up(y, d.ny); else live = live && y >= 0 && y < d.ny;
+            if (d.pz) z = wrap_up(z, d.nz); else live = live && z >= 0 && z < d.nz;
+            const long long c = ((long long)z * d.ny + y) * d.nx + x;
+            const int p3[3] = {x, y, z};
 
-        int id = NO_BODY;
-        bool reached = false;           // within STATIC_REACH cells of some body's box
-        for (int i = 0; i < ncand && live; ++i) {
-            const int kb = cid[i];
-            const BodyGeom *g = i < REMAP_STAGED ? cg + i : geo + kb;
-            bool in = true;
-            for (int a = 0; a < 3 && in; ++a) {
-                int o = p3[a] - g->ebox[a];
-                if (per[a] && o < 0) o += n3[a];
-                in = o >= 0 && o < g->ebox[3 + a];
+            int id = NO_BODY;
+            bool reached = false;           // within STATIC_REACH cells of some body's box
+            for (int i = 0; i < ncand && live; ++i) {
+                const int kb = cid[i];
+                const BodyGeom *g = i < REMAP_STAGED ? cg + i : geo + kb;
+                bool in = true;
+                for (int a = 0; a < 3 && in; ++a) {
+                    int o = p3[a] - g->ebox[a];
+                    if (per[a] && o < 0) o += n3[a];
+                    in = o >= 0 && o < g->ebox[3 + a];
+                }
+                if (!in) continue;
+                reached = true;
+                for (int a = 0; a < 3 && in; ++a) {
+                    int o = p3[a] - g->box[a];
+                    if (per[a] && o < 0) o += n3[a];
+                    in = o >= 0 && o < g->box[3 + a];
+                }
+                if (!in) continue;
+                // FP32 screen; cells within its margin of the surface take the FP64 test
+                const int screen = inside_screen(d, g, x, y, z);
+                if (screen == 0 || (screen < 0 && !cell_inside(d, dv.props[kb], sp.body_cur[kb], x, y, z))) continue;
+                if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
+                id = kb;
             }
-            if (!in) continue;
-            reached = true;
-            for (int a = 0; a < 3 && in; ++a) {
-                int o = p3[a] - g->box[a];
-                if (per[a] && o < 0) o += n3[a];
-                in = o >= 0 && o < g->box[3 + a];
+            // farther than STATIC_REACH from every body's box: the cell holds its
+            // static flags in both epoch buffers already (nothing within reach was
+            // solid in the last three steps, at most 0.5 cells of motion per step)
+            live = live && reached;
+            uint8_t flags = 0;
+            if (live) {
+                const uint8_t solid = id != NO_BODY ? F_SOLID : 0;
+                flags = solid | wall_bit(d, x, y, z);
+                if (!init_mode) {
+                    const uint8_t prev = sp.flags_prev[c] & F_SOLID;
+                    if (prev) flags |= F_SOLID_PREV;
+                    // does any pull source x - e_a hold an obstacle of step n-1?  (all
+                    // 18 loads are independent; sources beyond a wall do not count)
+                    uint8_t near = 0;
+                    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+                    if (x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+#pragma unroll
+                        for (int a = 1; a < Q; ++a) near |= sp.flags_prev[c - ex(a) - ey(a) * sy - ez(a) * sz];
+                    } else {
+#pragma unroll
+                        for (int a = 1; a < Q; ++a) {
+                            const int sx_ = x - ex(a), sy_ = y - ey(a), sz_ = z - ez(a);
+                            const bool in = !((!d.px && (sx_ < 0 || sx_ >= d.nx)) || (!d.py && (sy_ < 0 || sy_ >= d.ny)) ||
+                                              (!d.pz && (sz_ < 0 || sz_ >= d.nz)));
+                            const uint8_t v = sp.flags_prev[((long long)wrap_axis(sz_, d.nz) * d.ny + wrap_axis(sy_, d.ny)) * d.nx +
+                                                            wrap_axis(sx_, d.nx)];
+                            near |= in ? v : 0;
+                        }
+                    }
+                    if (near & F_SOLID) flags |= F_NEAR;
+                    if ((solid != 0) != (prev != 0) || (solid && sp.bid_prev[c] != id)) dv.changed[sp.parity] = 1;
+                }
+                sp.flags_cur[c] = flags;
+                sp.bid_cur[c] = (uint8_t)id;
             }
-            if (!in) continue;
-            // FP32 screen; cells within its margin of the surface take the FP64 test
-            const int screen = inside_screen(d, g, x, y, z);
-            if (screen == 0 || (screen < 0 && !cell_inside(d, dv.props[kb], sp.body_cur[kb], x, y, z))) continue;
-            if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
-            id = kb;
-        }
-        // farther than STATIC_REACH from every body's box: the cell holds its
-        // static flags in both epoch buffers already (nothing within reach was
-        // solid in the last three steps, at most 0.5 cells of motion per step)
-        live = live && reached;
-        uint8_t flags = 0;
-        if (live) {
-            const uint8_t solid = id != NO_BODY ? F_SOLID : 0;
-            flags = solid | wall_bit(d, x, y, z);
-            if (!init_mode) {
-                const uint8_t prev = sp.flags_prev[c] & F_SOLID;
-                if (prev) flags |= F_SOLID_PREV;
-                // does any pull source x - e_a hold an obstacle of step n-1?  (all
-                // 18 loads are independent; sources beyond a wall do not count)
-                uint8_t near = 0;
-                const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-                if (x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
-#pragma unroll
-                    for (int a = 1; a < Q; ++a) near |= sp.flags_prev[c - ex(a) - ey(a) * sy - ez(a) * sz];
-                } else {
-#pragma unroll
-                    for (int a = 1; a < Q; ++a) {
-                        const int sx_ = x - ex(a), sy_ = y - ey(a), sz_ = z - ez(a);
-                        const bool in = !((!d.px && (sx_ < 0 || sx_ >= d.nx)) || (!d.py && (sy_ < 0 || sy_ >= d.ny)) ||
-                                          (!d.pz && (sz_ < 0 || sz_ >= d.nz)));
-                        const uint8_t v = sp.flags_prev[((long long)wrap_axis(sz_, d.nz) * d.ny + wrap_axis(sy_, d.ny)) * d.nx +
-                                                        wrap_axis(sx_, d.nx)];
-                        near |= in ? v : 0;
+            // the boundary kernel's cells: a shared-memory atomic per warp
+            // (past the buffer, a global one)
+            const bool mine = live && !init_mode && !(flags & F_SOLID) && (flags & (F_NEAR | F_SOLID_PREV));
+            const unsigned mb = __ballot_sync(0xffffffffu, mine);
+            if (mb) {
+                const int leader = __ffs(mb) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&lcount, __popc(mb));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                const int pos = base + __popc(mb & ((1u << lane) - 1u));
+                if (mine) {
+                    if (pos < REMAP_LIST_BUF) {
+                        lbuf[pos] = (uint32_t)c;
+                    } else {
+                        const int g = atomicAdd(dv.bcount, 1);
+                        if (g < dv.blist_cap) dv.blist[g] = (uint32_t)c;
+                        else atomicOr(dv.status, ST_LINKS);
                     }
                 }
-                if (near & F_SOLID) flags |= F_NEAR;
-                if ((solid != 0) != (prev != 0) || (solid && sp.bid_prev[c] != id)) dv.changed[sp.parity] = 1;
             }
-            sp.flags_cur[c] = flags;
-            sp.bid_cur[c] = (uint8_t)id;
         }
-        // the boundary kernel's cells, appended with one atomic per warp
-        const bool mine = live && !init_mode && !(flags & F_SOLID) && (flags & (F_NEAR | F_SOLID_PREV));
-        const unsigned mb = __ballot_sync(0xffffffffu, mine);
-        if (mb) {
-            const int leader = __ffs(mb) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(dv.bcount, __popc(mb));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (mine) dv.blist[base + __popc(mb & ((1u << lane) - 1u))] = (uint32_t)c;
-        }
+    __syncthreads();
+    if (tid == 0) lbase = lcount ? atomicAdd(dv.bcount, min(lcount, REMAP_LIST_BUF)) : 0;
+    __syncthreads();
+    const int nl = min(lcount, REMAP_LIST_BUF);
+    for (int i = tid; i < nl; i += REMAP_THREADS) {
+        if (lbase + i < dv.blist_cap) dv.blist[lbase + i] = lbuf[i];
+        else atomicOr(dv.status, ST_LINKS);
     }
 }
 
@@ -528,6 +556,19 @@ __device__ void integrate_body_warp(const Device &dv, const StepPtrs &sp, int b,
     const double *st = reinterpret_cast<const double *>(sp.body_cur + b);       // X q V W
     const int ax = lane < 3 ? lane : 0;
 
+    // external force on axis ax: g times the volume, then the body's drive
+    // terms in term order and its springs in spring order (loaded first, so
+    // that their chains of dependent loads overlap the ones below)
+    double Fext = dv.g[ax] * pb->volume;
+    if (lane < 3) {
+        for (int k = pb->drive_first; k < pb->drive_first + pb->drive_count; ++k) Fext += dv.drive_f[3 * k + ax];
+        for (int kk = pb->spring_first; kk < pb->spring_first + pb->spring_count; ++kk) {
+            const int k = dv.spring_list[kk];
+            const double f = dv.spring_f[3 * k + ax];
+            Fext += dv.springs[k].i == b ? f : -f;
+        }
+    }
+
     // hydrodynamic load of step n, lane i < 6 component i
     double hyd = 0.0;
     if (with_fluid && dv.precision == 0) {
@@ -560,15 +601,7 @@ __device__ void integrate_body_warp(const Device &dv, const StepPtrs &sp, int b,
     }
 
     // translation, lanes 0..2
-    double F = v + dv.g[ax] * pb->volume;
-    if (lane < 3) {
-        for (int k = pb->drive_first; k < pb->drive_first + pb->drive_count; ++k) F += dv.drive_f[3 * k + ax];
-        for (int kk = pb->spring_first; kk < pb->spring_first + pb->spring_count; ++kk) {
-            const int k = dv.spring_list[kk];
-            const double f = dv.spring_f[3 * k + ax];
-            F += dv.springs[k].i == b ? f : -f;
-        }
-    }
+    const double F = v + Fext;
     const double Vn = st[7 + ax] + F * pb->inv_m;
     const double Xn = st[ax] + Vn;
 
@@ -607,9 +640,15 @@ __device__ void integrate_body_warp(const Device &dv, const StepPtrs &sp, int b,
     const double Wv[3] = {W0, W1, W2};
     double q4;
     {
+        // lane 0: w - 1/2 (W . v); lane 1 + i: v_i + 1/2 (w W_i + (W x v)_i),
+        // one expression with the operands chosen per lane (no divergence)
         const int i = lane >= 1 && lane <= 3 ? lane - 1 : 0, i1 = (i + 1) % 3, i2 = (i + 2) % 3;
-        if (lane == 0) q4 = qw - 0.5 * (W0 * qv[0] + W1 * qv[1] + W2 * qv[2]);
-        else q4 = qv[i] + 0.5 * (qw * Wv[i] + (Wv[i1] * qv[i2] - Wv[i2] * qv[i1]));
+        const bool s0 = lane == 0;
+        const double base = s0 ? qw : qv[i];
+        const double p1 = s0 ? -W0 : qw, r1 = s0 ? qv[0] : Wv[i];
+        const double p2 = s0 ? -W1 : Wv[i1], r2 = s0 ? qv[1] : qv[i2];
+        const double p3 = s0 ? -W2 : -Wv[i2], r3 = s0 ? qv[2] : qv[i1];
+        q4 = base + 0.5 * (p1 * r1 + p2 * r2 + p3 * r3);
     }
     double sq = lane < 4 ? q4 * q4 : 0.0;
     sq += __shfl_xor_sync(FULL, sq, 1);
@@ -646,9 +685,14 @@ __device__ void integrate_body_warp(const Device &dv, const StepPtrs &sp, int b,
     const int slot = sp.parity ^ 1;
     const double nw = __shfl_sync(FULL, qn, 0), nq[3] = {__shfl_sync(FULL, qn, 1), __shfl_sync(FULL, qn, 2),
                                                          __shfl_sync(FULL, qn, 3)};
-    const double axa = ax == 0 ? __dsub_rn(1.0, __dmul_rn(2.0, __fma_rn(nq[1], nq[1], __dmul_rn(nq[2], nq[2]))))
-                     : ax == 1 ? __dmul_rn(2.0, __fma_rn(nq[0], nq[1], __dmul_rn(nw, nq[2])))
-                               : __dmul_rn(2.0, __fma_rn(nq[0], nq[2], -__dmul_rn(nw, nq[1])));
+    // column 0 of R: 1 - 2 (y^2 + z^2), 2 (x y + w z), 2 (x z - w y), one
+    // expression base + 2 (A B + C D) with the operands chosen per lane
+    double axa;
+    {
+        const double A = ax == 0 ? -nq[1] : nq[0], B = ax == 0 ? nq[1] : (ax == 1 ? nq[1] : nq[2]);
+        const double Cq = ax == 0 ? -nq[2] : (ax == 1 ? nw : -nw), D = ax == 0 ? nq[2] : (ax == 1 ? nq[2] : nq[1]);
+        axa = (ax == 0 ? 1.0 : 0.0) + 2.0 * (A * B + Cq * D);
+    }
     BodyGeom *g = dv.geom + slot * dv.nb + b;
     const bool out = lane < 3 && outside_walls(dv.dom, *pb, ax, Xn, axa);
     if (lane < 3) geom_axis(dv.dom, *pb, ax, Xn, Vn, Wn, axa, *g);
@@ -835,8 +879,18 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
             const int a = (int)lk.dir;
             const unsigned cu = lk.cell, nxu = (unsigned)d.nx, nyu = (unsigned)d.ny;
             const int x = (int)(cu % nxu), y = (int)((cu / nxu) % nyu), z = (int)(cu / (nxu * nyu));
-            float drho = 0.0f;          // FP32 sum of the stored deviations
-            for (int q = 0; q < Q; ++q) drho += load_dev_f<T>(pop + q * C + c, s);
+            // rho - 1 of the fluid cell: the boundary kernel's record when it
+            // collided the cell (nearly every link cell: bodies move far
+            // less than a cell a step), else the FP32 sum of the stored
+            // deviations (the bulk kernel's cells a body has just reached)
+            float drho;
+            const uint8_t fc = sp.flags_cur[c];
+            if (fc != 0 && !(fc & F_SOLID)) {
+                drho = __ldcg(dv.rho_near + c);
+            } else {
+                drho = 0.0f;
+                for (int q = 0; q < Q; ++q) drho += load_dev_f<T>(pop + q * C + c, s);
+            }
             const float rho = 1.0f + drho;
             const float da = load_dev_f<T>(pop + a * C + c, s);
             const int i0 = near_cell_k(x - ci[0], d.nx, d.px);
@@ -992,7 +1046,7 @@ void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8
 void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s) {
     prep_kernel<<<1, PREP_THREADS, 0, s>>>(dv, sp);
     const int side = dv.remap_side;
-    const unsigned bx = (unsigned)(((side + REMAP_TY - 1) / REMAP_TY) * side);
+    const unsigned bx = (unsigned)(((side + REMAP_TY - 1) / REMAP_TY) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS));
     remap_kernel<<<dim3(bx, dv.nb), dim3(REMAP_TX, REMAP_TY), 0, s>>>(dv, sp, init_mode);
 }
 

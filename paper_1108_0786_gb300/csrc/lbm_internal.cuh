@@ -217,6 +217,7 @@ struct Device {
     BodyState *gstamp;      // [2][nb]: the state each slot was made from (prep_kernel remakes on mismatch)
     long long blist_cap;
     uint8_t *cand;          // [nb][nb]: body b's remap candidates in body order (BodyGeom::ncand of them)
+    float *rho_near;        // [C] 32/16-bit storage: rho - 1 of each cell the boundary kernel collided this step
     uint32_t *blist;        // cells the remap found fluid with F_NEAR or F_SOLID_PREV (the boundary kernel's)
     int *bcount;            // entries in blist (a cell in two bodies' cubes may appear twice)
     double *drive_f;        // [nd][3] drive forces of the current step (integrator scratch)

@@ -305,6 +305,10 @@ int ensure_device(lbm_t *h) {
         dv.blist_cap = (long long)cap;
         if ((rc = alloc_into(h, &dv.blist, sizeof(uint32_t) * cap))) return rc;
         if ((rc = alloc_into(h, &dv.cand, (size_t)std::max(B, 1) * std::max(B, 1)))) return rc;
+        // the boundary cells' densities for the momentum exchange (32/16-bit
+        // storage; written and read only at cells the boundary kernel collides)
+        const bool need_rho = B > 0 && fluid(h) && h->precision != LBM_PREC_F64;
+        if ((rc = alloc_into(h, &dv.rho_near, sizeof(float) * (need_rho ? (size_t)C : 1)))) return rc;
         if ((rc = alloc_into(h, &dv.bcount, sizeof(int) * 4))) return rc;
     }
     int *slist;

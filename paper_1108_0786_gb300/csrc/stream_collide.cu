@@ -734,6 +734,13 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
             f[b] = v;
         }
     }
+    if constexpr (sizeof(T) != 8) {
+        // rho - 1 of the cell for the momentum exchange (the collision keeps it)
+        Cd drho = 0;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) drho += f[b];
+        dv.rho_near[c] = (float)drho;
+    }
     collide<Cd, std::is_same<T, float>::value>(f, dv);
     T *__restrict__ dst = static_cast<T *>(sp.dst);
 #pragma unroll
