@@ -277,20 +277,6 @@ template <typename T> __device__ __forceinline__ float raw_ld(T v);
 template <> __device__ __forceinline__ float raw_ld<__half>(__half v) { return __half2float(v); }
 template <> __device__ __forceinline__ float raw_ld<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// two results to one 32-bit word of 16-bit storage (one packed conversion)
-template <typename T> __device__ __forceinline__ unsigned raw_pack(float lo, float hi);
-template <> __device__ __forceinline__ unsigned raw_pack<__half>(float lo, float hi) {
-    const __half2 h = __floats2half2_rn(lo, hi);
-    unsigned u;
-    memcpy(&u, &h, 4);
-    return u;
-}
-template <> __device__ __forceinline__ unsigned raw_pack<__nv_bfloat16>(float lo, float hi) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    unsigned u;
-    memcpy(&u, &h, 4);
-    return u;
-}
 template <typename T> __device__ __forceinline__ T raw_st(float v);
 template <> __device__ __forceinline__ __half raw_st<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 raw_st<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
@@ -374,22 +360,13 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
     if (all_mine) {
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
-            if constexpr (raw16 && V % 2 == 0) {
-                unsigned w[V / 2];
+            T out[V];
 #pragma unroll
-                for (int i = 0; i < V / 2; ++i) w[i] = raw_pack<T>(f[b][2 * i], f[b][2 * i + 1]);
-                T out[V];
-                memcpy(&out, &w, sizeof(out));
-                store_vec<T, V>(dst + (long long)b * C + c0, out);
-            } else {
-                T out[V];
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    if constexpr (raw16) out[i] = raw_st<T>(f[b][i]);
-                    else out[i] = Codec<T>::st(f[b][i], scale);
-                }
-                store_vec<T, V>(dst + (long long)b * C + c0, out);
+            for (int i = 0; i < V; ++i) {
+                if constexpr (raw16) out[i] = raw_st<T>(f[b][i]);
+                else out[i] = Codec<T>::st(f[b][i], scale);
             }
+            store_vec<T, V>(dst + (long long)b * C + c0, out);
         }
         return;
     }
