@@ -98,10 +98,10 @@ extern "C" {
 #define LBM_MAX_BODY_STEP  0.5   /* largest displacement of a body per step */
 
 /* kernel slots reported by lbm_time_kernels */
-#define LBM_KERNEL_REMAP          0   /* map bodies to the lattice */
+#define LBM_KERNEL_REMAP          0   /* body geometry and remap candidates, then map bodies to the lattice */
 #define LBM_KERNEL_STREAM_COLLIDE 1   /* bulk pull + LBGK over all cells */
 #define LBM_KERNEL_BOUNDARY       2   /* refill / bounce-back cells near bodies and walls */
-#define LBM_KERNEL_LINKS          3   /* per-body link lists */
+#define LBM_KERNEL_LINKS          3   /* per-body link lists, then the step's drive and spring loads */
 #define LBM_KERNEL_FORCE          4   /* momentum exchange; with fluid it also runs the rigid-body step */
 #define LBM_KERNEL_INTEGRATE      5   /* drive, springs, rigid-body step when there is no fluid */
 #define LBM_NUM_KERNELS           6
@@ -226,9 +226,12 @@ int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots);
 /* Launch shape of the bulk stream-collide kernel: cells_per_thread
  * consecutive x cells per thread (1, 2, 4; 8 for 16-bit storage; nx must be
  * a multiple) and min_blocks_per_sm, a register cap that lets that many
- * 256-thread blocks share an SM (0 for each: the defaults).
+ * 256-thread blocks share an SM (0 for each: the defaults).  16-bit storage
+ * with an even cells_per_thread keeps the populations packed two to a
+ * 32-bit word between load and store.
  * cells_per_thread = -1 selects the row-staged kernel: persistent blocks
- * (min_blocks_per_sm of them per SM: 1 or 2) copy each x-row's 19 source rows
+ * (min_blocks_per_sm of them per SM: 1 or 2 for FP64 / FP32 storage, 2, 3
+ * or 4 for 16-bit storage) copy each x-row's 19 source rows
  * and flags into shared memory with bulk asynchronous copies (TMA) and
  * collide from there; it needs nx a multiple of 16 and the stages within the
  * shared memory of an SM (FP32: nx <= 1472 for 2 blocks per SM).  Only the

@@ -1,11 +1,17 @@
 // kernels.cu -- the per-body kernels of one coupled step and the field
 // export / import kernels:
-//   remap      map the bodies onto the lattice (Sec. 2.3), epoch flags
+//   prep       per-body geometry records (remade only for states set from
+//              outside), remap candidate lists
+//   remap      map the bodies onto the lattice (Sec. 2.3), epoch flags, the
+//              boundary kernel's cell list
 //   links      per-body list of fluid->solid links (ballot + block scan)
-//   force      momentum-exchange force and torque (Eq. hydroF), FP64,
-//              warp-shuffle reduction in a fixed order (deterministic)
-//   integrate  drive (Eq. FB1-FB3), springs (Eq. osci_i, osci_j) and the
-//              rigid-body time step (Algorithm 1), FP64, one thread a body
+//   loads      drive terms (Eq. FB1-FB3) and spring forces (Eq. osci_i,
+//              osci_j) of the step
+//   force      momentum-exchange force and torque (Eq. hydroF): FP64 with a
+//              fixed-order reduction for FP64 storage, exact integer and
+//              fixed-point sums for 32/16-bit storage (deterministic both);
+//              the last block of each body runs its rigid-body time step
+//              (Algorithm 1) in FP64 on one warp
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -733,8 +739,9 @@ __device__ inline long long to_fixed(float v) {
 // links of body b into contiguous chunks and sum
 //   F = sum e_a [2 f~_a(x_f) + 6 w_a rho(x_f) e_-a . u_w(x_f + e_a)],
 //   T = sum (x_f + e_a / 2 - X) x F_link
-// with f~ of step n (dst) and the body state of step n.  The last block to
-// finish runs the rigid-body step for all bodies.
+// with f~ of step n (dst) and the body state of step n.  The last of body
+// b's blocks to finish runs body b's rigid-body step on its first warp; the
+// last body to finish ends the step (clock, change flag).
 //
 // FP64 storage: every term in FP64; each block reduces with warp shuffles
 // in a fixed order and writes its partial sums, which the rigid-body step

@@ -171,7 +171,7 @@ void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bo
     if (bodies && fl && !forked) run(LBM_KERNEL_LINKS, s, [&] { lbm::launch_links(h->dv, sp, s); });
     if (forked) cudaStreamWaitEvent(s, h->join_ev, 0);
     if (bodies && fl) {
-        // momentum exchange; its last block runs the rigid-body step
+        // momentum exchange; the last block of each body runs its rigid-body step
         run(LBM_KERNEL_FORCE, s, [&] { lbm::launch_force(h->dv, sp, s); });
     } else if (bodies) {
         run(LBM_KERNEL_INTEGRATE, s, [&] { lbm::launch_integrate(h->dv, sp, 0, s); });
