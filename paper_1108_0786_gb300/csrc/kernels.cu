@@ -225,7 +225,7 @@ __device__ inline bool spans_meet(int b0, int bw, int e0, int ew, int n, int per
 // remap candidates (the bodies, in order, whose grown box meets its remap
 // cube; a warp a body, ballots over the candidates), and the start of the
 // boundary kernel's list.
-constexpr int PREP_THREADS = 128;
+constexpr int PREP_THREADS = 256;
 
 __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(const Device dv, const StepPtrs sp) {
     const Domain d = dv.dom;
@@ -287,7 +287,7 @@ constexpr int REMAP_LAYERS = 1;         // cube layers a block (more layers seri
 constexpr int REMAP_LIST_BUF = 2048;    // list entries a block gathers before the global append
 static_assert(sizeof(BodyGeom) % sizeof(int) == 0, "geometry records are copied as ints");
 
-__global__ void __launch_bounds__(REMAP_THREADS) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
+__global__ void __launch_bounds__(REMAP_THREADS, 5) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
     const Domain d = dv.dom;
     const int b = blockIdx.y;
     const BodyGeom *__restrict__ geo = dv.geom + sp.parity * dv.nb;    // state n
