@@ -135,6 +135,49 @@ def test_fp64_bodies_crossing_cells_remap_and_refill():
     assert len(flags_seen) == 12
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_body_states_set_mid_run(precision):
+    """States set from the host after stepping began (moved by a fraction of
+    a cell, turned, new velocities): the next step's geometry comes from
+    the new states, not from the records the last rigid-body step wrote.
+    The maps must stay identical to the oracle's; FP64 storage stays at the
+    parity bar, FP32 storage within its velocity and displacement bars."""
+    sc = wl.Scenario("mid-run states", 40, 32, 28, 1.0)
+    c = math.cos(0.4)
+    sc.bodies.append(wl.Body(wl.CAPSULE, 3.3, 6.0, 800.0, (13.4, 15.2, 13.7), (c, 0.0, 0.0, math.sin(0.4))))
+    sc.bodies.append(wl.Body(wl.SPHERE, 3.1, 0.0, 400.0, (28.6, 16.9, 14.4)))
+    sc.springs.append(wl.Spring(0, 1, 0.02, 15.0, 0.01))
+    sc.drives.append(wl.Drive(0, 2e-3, 1 / 40.0, 0.0))
+    sc.drives.append(wl.Drive(1, -2e-3, 1 / 40.0, 0.0))
+    gpu, ref = pair(sc, precision)
+    x0 = ref.bodies()[:, :3].copy()
+    gpu.step(20)
+    ref.step(20)
+    q = np.array([0.8, 0.3, -0.4, 0.33])
+    q /= np.linalg.norm(q)
+    for b, dx, v in ((0, (0.31, -0.27, 0.22), (3e-3, -2e-3, 1e-3)), (1, (-0.23, 0.18, -0.29), (-2e-3, 1e-3, 2e-3))):
+        st = ref.bodies()[b].copy()
+        st[0:3] += dx
+        if b == 0:
+            st[3:7] = q
+        st[7:10] = v
+        st[10:13] = (1e-3, -5e-4, 8e-4)
+        gpu.set_body_state(b, st)
+        ref.set_body_state(b, st)
+    for _ in range(3):
+        gpu.step(10)
+        ref.step(10)
+        assert np.array_equal(gpu.flags(), ref.flags())
+        if precision == "f64":
+            assert np.abs(gpu.pop() - ref.pop()).max() < POP_TOL
+            assert rel_traj_err(gpu.bodies(), ref.bodies()) < TRAJ_TOL
+        else:
+            ur = ref.u()
+            assert np.linalg.norm(gpu.u() - ur) <= 1e-5 * np.linalg.norm(ur)
+            disp = np.linalg.norm(ref.bodies()[:, :3] - x0, axis=1)
+            assert np.abs(gpu.bodies()[:, :3] - ref.bodies()[:, :3]).max() <= 1e-3 * disp.max()
+
+
 def test_fp64_single_step_edge_cases():
     """One step from a random state; a 1-cell-thick periodic slab and a
     domain narrower than a vector of cells."""
