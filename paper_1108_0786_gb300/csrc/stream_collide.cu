@@ -578,7 +578,8 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
     // difference, two compares and the FP32 position within the cell
     __shared__ WallBody wb[sizeof(T) == 8 ? 1 : LBM_MAX_BODIES_DEV];
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    const int listed = mode == 0 ? *dv.bcount : 0;
+    // the count may pass the capacity after an overflow (reported as an error): never read past it
+    const int listed = mode == 0 ? (int)min((long long)*dv.bcount, dv.blist_cap) : 0;
     if (mode == 0 && (int)(blockIdx.x * blockDim.x) >= listed) return;      // the whole block is past the list
     if constexpr (sizeof(T) != 8) {
         for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) wb[k] = wall_body(dv.geom[(sp.parity ^ 1) * dv.nb + k]);
