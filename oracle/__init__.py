@@ -51,9 +51,15 @@ def build(force: bool = False) -> str:
 
 def _load():
     global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+    if _lib is None:
+        _lib = load(build())
+    return _lib
+
+
+def load(path: str):
+    """Load a compiled copy of the oracle (this one, or a copy a test compiled
+    from an edited source) and declare its C signatures."""
+    lib = ctypes.CDLL(path)
     P = ctypes.c_void_p
     D = ctypes.c_double
     I = ctypes.c_int
@@ -82,7 +88,6 @@ def _load():
     lib.lbm_ref_flag_digest.restype = ctypes.c_ulonglong
     lib.lbm_ref_last_error.argtypes = [P]
     lib.lbm_ref_last_error.restype = ctypes.c_char_p
-    _lib = lib
     return lib
 
 
@@ -107,11 +112,11 @@ def equilibrium(rho, u):
     return out
 
 
-def from_scenario(sc, options=0):
+def from_scenario(sc, options=0, lib=None):
     """An Oracle holding the domain, bodies, springs and drive terms of a
     seeded scenario (any object with the fields of ``workloads.Scenario``)."""
     import math
-    o = Oracle(sc.nx, sc.ny, sc.nz, sc.tau, sc.bc, sc.g, options)
+    o = Oracle(sc.nx, sc.ny, sc.nz, sc.tau, sc.bc, sc.g, options, lib=lib)
     for b in sc.bodies:
         o.add_body(b.shape, b.radius, b.length, b.mass, b.pos, b.orient)
     for s in sc.springs:
@@ -139,8 +144,8 @@ def _dp(a: np.ndarray):
 class Oracle:
     """ctypes wrapper of one oracle lattice (lattice units, dx = dt = 1)."""
 
-    def __init__(self, nx, ny, nz, tau, bc=7, g=(0.0, 0.0, 0.0), options=0):
-        self._lib = _load()
+    def __init__(self, nx, ny, nz, tau, bc=7, g=(0.0, 0.0, 0.0), options=0, lib=None):
+        self._lib = lib if lib is not None else _load()
         self.shape = (nz, ny, nx)
         self.cells = nx * ny * nz
         h = ctypes.c_void_p()

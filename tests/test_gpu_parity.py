@@ -14,7 +14,6 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle_helpers import oracle_from_scenario
 from paper_1108_0786_gb300 import lbm, workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -33,7 +32,7 @@ def _cuda():
 
 
 def pair(sc, precision="f64", **kw):
-    return lbm.from_scenario(sc, precision=precision, **kw), oracle_from_scenario(sc)
+    return lbm.from_scenario(sc, precision=precision, **kw), oracle.from_scenario(sc)
 
 
 def rel_traj_err(a, b):
@@ -216,7 +215,7 @@ def channel_reference():
     """The oracle's channel-swimmer run (computed once per test session)."""
     if not _CHANNEL_REF:
         sc = wl.channel_swimmer()
-        ref = oracle_from_scenario(sc)
+        ref = oracle.from_scenario(sc)
         x0 = ref.bodies()[:, :3].copy()
         ref.step(sc.steps)
         _CHANNEL_REF.update(sc=sc, x0=x0, u=ref.u(), xb=ref.bodies()[:, :3].copy(), flags=ref.flags())

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle_helpers import momentum, oracle_from_scenario
+from oracle_helpers import momentum
 from paper_1108_0786_gb300 import workloads as wl
 
 E, W = oracle.lattice()
@@ -27,7 +27,7 @@ def swimmer():
 
 def test_fluid_plus_body_momentum_with_the_half_lagged_load():
     sc = swimmer()
-    o = oracle_from_scenario(sc, oracle.OPT_AVERAGE_FORCE)
+    o = oracle.from_scenario(sc, oracle.OPT_AVERAGE_FORCE)
     m = np.array([b.mass for b in sc.bodies])
     o.step(2)
     ref = None
@@ -49,7 +49,7 @@ def test_fluid_plus_body_momentum_with_the_half_lagged_load():
 
 def test_first_step_is_not_averaged_and_later_steps_differ():
     sc = swimmer()
-    plain, avg = oracle_from_scenario(sc), oracle_from_scenario(sc, oracle.OPT_AVERAGE_FORCE)
+    plain, avg = oracle.from_scenario(sc), oracle.from_scenario(sc, oracle.OPT_AVERAGE_FORCE)
     plain.step(1)
     avg.step(1)
     assert np.array_equal(plain.bodies(), avg.bodies())
@@ -59,6 +59,6 @@ def test_first_step_is_not_averaged_and_later_steps_differ():
 
 
 def test_reverse_mode_refuses_the_averaged_load():
-    o = oracle_from_scenario(swimmer(), oracle.OPT_AVERAGE_FORCE)
+    o = oracle.from_scenario(swimmer(), oracle.OPT_AVERAGE_FORCE)
     with pytest.raises(oracle.OracleError):
         o.adjoint(3, np.zeros((3, 13)))

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle_helpers import momentum, oracle_from_scenario
+from oracle_helpers import momentum
 from paper_1108_0786_gb300 import workloads as wl
 
 E, W = oracle.lattice()
@@ -116,7 +116,7 @@ def test_swimmer_conserves_fluid_plus_body_momentum():
     sc = wl.Scenario("swimmer", 32, 32, 32, 1.0)
     wl.add_swimmer(sc, (16.2, 16.0, 16.0), (1.0, 0.0, 0.0, 0.0), (wl.SPHERE,) * 3, 3.0, 0.0,
                    10.0, 0.01, 0.005, 5e-3, 50.0)
-    o = oracle_from_scenario(sc)
+    o = oracle.from_scenario(sc)
     m = np.array([b.mass for b in sc.bodies])
     v_prev = o.bodies()[:, 7:10]
     o.step(1)
