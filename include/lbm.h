@@ -139,7 +139,11 @@ int lbm_set_stream(lbm_t *h, void *stream);
  * capsule of cylinder `length` and cap `radius` along the body x axis, of
  * `mass`, centre pos[3] and orientation orient[4] (unit quaternion w,x,y,z,
  * normalised here; NULL for identity).  Inertia is that of a uniform solid.
- * Only before the first step.  Returns the body id (>= 0). */
+ * Only before the first step.  Returns the body id (>= 0).  With the fluid on,
+ * every periodic extent must be at least the side of the body's remap cube,
+ * 2 (ceil(radius + length/2) + 4) + 1 cells (the per-step scans around a body
+ * wrap on periodic axes and would otherwise visit cells twice); a shorter
+ * periodic axis is LBM_E_ARG. */
 int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass,
                  const double pos[3], const double orient[4]);
 
@@ -347,19 +351,25 @@ int lbm_bytes_per_cell(lbm_t *h);
  * Output (device pointer): out[nb][6] = F[3], T[3] per body, torque about
  * the body centre.  half_width bounds the links of every body: all its
  * solid cells lie within half_width - 1 cells of floor(X) on each axis.
+ * The scan covers the cube of side 2 half_width + 1 around floor(X), cut to
+ * one period on each periodic axis shorter than that side, so every cell and
+ * link is counted once.
  * Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default).
  *
  * Scratch: per-block partial sums live in one file-scope device array of
  * LBM_STATIC_SCRATCH_RECORDS records of 48 bytes (3 MiB), which every GPU
  * that loads the library holds until the process exits.  The first call on
- * a device looks up that array's device address, with the device current;
- * make that first call before any stream capture.  Every call shares the
+ * a device looks up that array's device address, with the device current,
+ * and looks it up again when the device's context has changed (after
+ * cudaDeviceReset); make that first call, and the first call after a reset,
+ * before any stream capture.  Every call shares the
  * array and leaves its last contents there; calls that overlap on the GPU
  * (for example on two streams) race and give wrong results.
  *
  * Errors: LBM_E_ARG for a null pointer, nb outside [1, LBM_MAX_BODIES], bad
  * sizes or bc, half_width outside [1, LBM_STATIC_SCRATCH_MAX_HALF_WIDTH], or
- * nb * ceil((2 half_width + 1)^3 / 256) > LBM_STATIC_SCRATCH_RECORDS;
+ * nb * ceil(sx sy sz / 256) > LBM_STATIC_SCRATCH_RECORDS, with s the scan's
+ * extent per axis (2 half_width + 1, or the axis length where it is cut);
  * LBM_E_CUDA for a CUDA error.  Nothing is allocated in any case. */
 #define LBM_STATIC_SCRATCH_RECORDS        65536
 #define LBM_STATIC_SCRATCH_MAX_HALF_WIDTH 64

@@ -512,6 +512,18 @@ int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass,
     BodyProps p{};
     p.shape = shape; p.r = radius; p.l = length; p.m = mass;
     p.E = (int)std::ceil(radius + 0.5 * length) + 1;
+    if (fluid(h)) {
+        // the remap and link scans wrap their cubes on periodic axes: a cube
+        // longer than the axis would visit cells twice and count their links
+        // twice
+        const int side = 2 * (p.E + lbm::REMAP_MARGIN) + 1;
+        const int n[3] = {h->nx, h->ny, h->nz};
+        for (int i = 0; i < 3; ++i)
+            if (((h->bc >> i) & 1) && n[i] < side)
+                return fail(h, LBM_E_ARG,
+                            "periodic extent %d along axis %d is shorter than the body's remap cube (side %d)", n[i],
+                            i, side);
+    }
     p.reach = radius + 0.5 * length;
     p.r2f = (float)(radius * radius);
     p.hf = (float)(0.5 * length);

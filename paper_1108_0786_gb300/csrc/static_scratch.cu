@@ -14,6 +14,8 @@
 // on two streams) race on the array and give wrong results.
 #include <mutex>
 
+#include <cuda.h>
+
 #include "../../include/lbm.h"
 #include "lbm_internal.cuh"
 
@@ -27,34 +29,79 @@ constexpr int NA_MAX_DEVICES = 64;
 static __device__ __align__(256) double g_force_partials[LBM_STATIC_SCRATCH_RECORDS * 6];
 
 std::mutex g_setup_mutex;
-double *g_partials_addr[NA_MAX_DEVICES] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id;  // context the address belongs to (0: none yet)
+    double *addr;
+};
+ScratchAddr g_partials_addr[NA_MAX_DEVICES] = {};
 
-// Device address of the array on the current device, resolved once per
-// device (host code cannot use the symbol itself as a device pointer).
+// Identifier of the current context, from the driver through the runtime's
+// entry-point lookup (no link against the driver library); 0 if the driver
+// does not offer it.
+unsigned long long current_context_id() {
+    typedef CUresult (*GetCurrent)(CUcontext *);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the array in the current context.  Host code cannot use
+// the symbol itself as a device pointer; the address is looked up once per
+// device with that device current, and again whenever the device's context
+// has changed (after cudaDeviceReset the module is loaded anew, possibly at
+// another address).  Without a context identifier (no context current yet,
+// or a driver without the query) it is looked up on every call.
 cudaError_t partials_address(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_addr[dev]) {
+    ScratchAddr &slot = g_partials_addr[dev];
+    if (id == 0 || slot.ctx_id != id || !slot.addr) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_force_partials);
         if (e != cudaSuccess) return e;
-        g_partials_addr[dev] = static_cast<double *>(p);
+        slot.addr = static_cast<double *>(p);
+        slot.ctx_id = id;
     }
-    *out = g_partials_addr[dev];
+    *out = slot.addr;
     return cudaSuccess;
 }
 
-// Block (k, b): cells k*256 .. of the cube of side 2 hw + 1 around
-// floor(X_b); every fluid cell adds the links (x_f, a) whose end x_f + e_a
-// is a cell of body b (Eq. hydroF, torque about the body centre at the link
-// midpoint), and the block writes its fixed-order sum to record
-// b * blocks + k.
+// Cells the scan covers along one axis: the cube's side, or the whole axis
+// when a periodic axis is shorter than the side (a wrapped cube would visit
+// its cells twice and add their links twice).
+inline int scan_extent(int side, int n, int periodic) { return periodic && n < side ? n : side; }
+
+// Block (k, b): cells k*256 .. of the box of extents (sx, sy, sz) that
+// starts at floor(X_b) - hw (the cube of side 2 hw + 1 around floor(X_b),
+// cut to one period on short periodic axes); every fluid cell adds the
+// links (x_f, a) whose end x_f + e_a is a cell of body b (Eq. hydroF,
+// torque about the body centre at the link midpoint), and the block writes
+// its fixed-order sum to record b * blocks + k.
 __global__ void __launch_bounds__(NA_THREADS)
 static_partials_kernel(const double *pop, const uint8_t *flags, const double *bodies, Domain d, int hw,
-                       int blocks, double *partials) {
+                       int sx, int sy, int sz, int blocks, double *partials) {
     const int b = blockIdx.y, k = blockIdx.x;
     BodyState sb;
     {
@@ -62,13 +109,12 @@ static_partials_kernel(const double *pop, const uint8_t *flags, const double *bo
         for (int i = 0; i < 3; ++i) { sb.X[i] = s[i]; sb.V[i] = s[7 + i]; sb.W[i] = s[10 + i]; }
         for (int i = 0; i < 4; ++i) sb.q[i] = s[3 + i];
     }
-    const int side = 2 * hw + 1;
     const long long l = (long long)k * NA_THREADS + threadIdx.x;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    if (l < (long long)side * side * side) {
-        int x = (int)floor(sb.X[0]) - hw + (int)(l % side);
-        int y = (int)floor(sb.X[1]) - hw + (int)((l / side) % side);
-        int z = (int)floor(sb.X[2]) - hw + (int)(l / ((long long)side * side));
+    if (l < (long long)sx * sy * sz) {
+        int x = (int)floor(sb.X[0]) - hw + (int)(l % sx);
+        int y = (int)floor(sb.X[1]) - hw + (int)((l / sx) % sy);
+        int z = (int)floor(sb.X[2]) - hw + (int)(l / ((long long)sx * sy));
         bool ok = true;
         if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else ok = ok && x >= 0 && x < d.nx;
         if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else ok = ok && y >= 0 && y < d.ny;
@@ -145,8 +191,10 @@ extern "C" int lbm_momentum_exchange_static(const double *pop, const unsigned ch
     const long long C = (long long)nx * ny * nz;
     if (C > (1LL << 31) - 1) return LBM_E_ARG;
     if (half_width < 1 || half_width > LBM_STATIC_SCRATCH_MAX_HALF_WIDTH) return LBM_E_ARG;
-    const long long side = 2LL * half_width + 1;
-    const int blocks = (int)((side * side * side + lbm::NA_THREADS - 1) / lbm::NA_THREADS);
+    const int side = 2 * half_width + 1;
+    const int sx = lbm::scan_extent(side, nx, bc & 1), sy = lbm::scan_extent(side, ny, bc & 2),
+              sz = lbm::scan_extent(side, nz, bc & 4);
+    const int blocks = (int)(((long long)sx * sy * sz + lbm::NA_THREADS - 1) / lbm::NA_THREADS);
     if ((long long)blocks * nb > LBM_STATIC_SCRATCH_RECORDS) return LBM_E_ARG;
     double *partials = nullptr;
     if (lbm::partials_address(&partials) != cudaSuccess) return LBM_E_CUDA;
@@ -154,7 +202,7 @@ extern "C" int lbm_momentum_exchange_static(const double *pop, const unsigned ch
                         1.0 / nx, 1.0 / ny, 1.0 / nz};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     lbm::static_partials_kernel<<<dim3(blocks, nb), lbm::NA_THREADS, 0, s>>>(pop, flags, bodies, d, half_width,
-                                                                            blocks, partials);
+                                                                            sx, sy, sz, blocks, partials);
     lbm::static_sum_kernel<<<(nb + 127) / 128, 128, 0, s>>>(partials, nb, blocks, out);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }

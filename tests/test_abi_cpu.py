@@ -44,8 +44,8 @@ def test_only_the_c_abi_is_exported(lib):
 
 def test_host_side_calls_without_a_device(lib):
     h = ctypes.c_void_p()
-    assert lib.lbm_create(8, 8, 8, 1.0, 7, ctypes.byref(h)) == 0
-    p = np.array([4.0, 4.0, 4.0])
+    assert lib.lbm_create(16, 16, 16, 1.0, 7, ctypes.byref(h)) == 0
+    p = np.array([8.0, 8.0, 8.0])
     dp = ctypes.POINTER(ctypes.c_double)
     assert lib.lbm_add_body(h, 0, 2.0, 0.0, 10.0, p.ctypes.data_as(dp), None) == 0
     assert lib.lbm_add_body(h, 1, 1.5, 3.0, 12.0, p.ctypes.data_as(dp), None) == 1
@@ -84,4 +84,22 @@ def test_bytes_per_cell_by_precision(lib):
         h = ctypes.c_void_p()
         assert lib.lbm_create_ex(16, 8, 8, 1.0, 7, prec, None, 0, ctypes.byref(h)) == 0
         assert lib.lbm_bytes_per_cell(h) == 2 * 19 * es + 1
+        lib.lbm_destroy(h)
+
+
+def test_bodies_wider_than_a_periodic_period_are_rejected(lib):
+    """A capsule of radius 1.5 and length 3 has a remap cube of side
+    2 (ceil(3) + 1 + 3) + 1 = 15: a periodic axis of 14 cells would make the
+    per-step scans visit cells twice, so the body is refused; walls on that
+    axis, or no fluid, lift the rule."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    p = np.array([7.0, 7.5, 7.5])
+    for dims, bc, options, want in (((14, 15, 15), 7, 0, lbm.E_ARG), ((15, 14, 15), 7, 0, lbm.E_ARG),
+                                    ((15, 15, 14), 7, 0, lbm.E_ARG), ((15, 15, 15), 7, 0, 0),
+                                    ((14, 15, 15), 6, 0, 0), ((14, 14, 14), 7, lbm.OPT_NO_FLUID, 0)):
+        h = ctypes.c_void_p()
+        assert lib.lbm_create_ex(*dims, 1.0, bc, lbm.PREC_F32, None, options, ctypes.byref(h)) == 0
+        assert lib.lbm_add_body(h, 1, 1.5, 3.0, 12.0, p.ctypes.data_as(dp), None) == want, (dims, bc, options)
+        if want:
+            assert b"remap cube" in lib.lbm_last_error(h)
         lib.lbm_destroy(h)

@@ -70,9 +70,9 @@ def test_fp64_three_sphere_swimmer_1000_steps():
 
 @pytest.mark.parametrize("nx,ny,nz,bc", [
     (37, 19, 23, wl.PERIODIC_X),              # odd x: one cell per thread; walls in y and z
-    (38, 21, 17, 2 | 4),                      # even x: two cells per thread; walls in x
+    (38, 21, 21, 2 | 4),                      # even x: two cells per thread; walls in x
     (40, 24, 20, 0),                          # walls on all six faces
-    (36, 20, 28, 7),                          # fully periodic
+    (36, 22, 28, 7),                          # fully periodic
 ])
 def test_fp64_ragged_boxes_walls_force_capsules(nx, ny, nz, bc):
     sc = wl.Scenario("ragged", nx, ny, nz, 0.8, bc=bc, g=(3e-6, -2e-6, 1e-6))
