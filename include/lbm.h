@@ -36,10 +36,12 @@
  *
  * Errors: every int-returning call returns LBM_OK (0) or a negative
  * LBM_E_* code and stores a message for lbm_last_error.  Errors found on
- * the device (overlapping bodies, a body crossing a wall, a non-finite body
- * state, a body faster than LBM_MAX_BODY_STEP per step) are latched in a
- * device status word and returned by the next synchronising call (lbm_sync,
- * lbm_get_*, lbm_save); the state after such an error is unspecified.
+ * the device (a bounded wait that ran out, a full link or cell list,
+ * overlapping bodies, a body crossing a wall, a non-finite body state or
+ * link term, a body faster than LBM_MAX_BODY_STEP per step) are latched in
+ * a device status word and returned by the next synchronising call
+ * (lbm_sync, lbm_get_*, lbm_save), in that order of precedence when several
+ * are latched; the state after such an error is unspecified.
  * Nothing is thrown across the ABI.  A handle is not thread safe.
  */
 #ifndef LBM_H
@@ -248,6 +250,26 @@ int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm);
  * which that step rewrites) and keep the fastest for the following steps.
  * Reports the choice through the optional outputs (synchronises). */
 int lbm_autotune(lbm_t *h, int trials, int *cells_per_thread, int *min_blocks_per_sm);
+
+/* Checks of the failure paths (failure detection; the paper has no
+ * counterpart).  They make the device latch an error from the host side,
+ * without faulting or hanging anything:
+ *   LBM_DEBUG_EXPIRE_WAITS, value 1: the first wait of every block of the
+ *     row-staged bulk kernel (lbm_tune with cells_per_thread = -1) is on a
+ *     barrier that no copy completes, bounded by about 2^16 SM cycles.  It
+ *     runs out as a real stall would: the block latches LBM_E_TIMEOUT, waits
+ *     (bounded) for its copies in flight and returns.  Value 0 (default):
+ *     the normal bound of about 1 s.
+ *   LBM_DEBUG_CELL_LIST_CAP, value k >= 1: the list of cells the boundary
+ *     kernel handles (fluid cells next to a body or uncovered) holds at most
+ *     k entries instead of its sized capacity; a step that finds more
+ *     latches LBM_E_LINKS, stores none past the capacity and handles only
+ *     those listed.  Value 0: the sized capacity.
+ * The steps after such an error are not valid.  Only before the first step
+ * (LBM_E_STATE after it); LBM_E_ARG for an unknown knob or value. */
+#define LBM_DEBUG_EXPIRE_WAITS  1
+#define LBM_DEBUG_CELL_LIST_CAP 2
+int lbm_debug_set(lbm_t *h, int knob, long long value);
 
 /* ---- reverse mode ---------------------------------------------------------
  *

@@ -80,6 +80,7 @@ def load(path: str):
     lib.lbm_ref_steps_done.argtypes = [P]
     lib.lbm_ref_steps_done.restype = ctypes.c_long
     lib.lbm_ref_num_threads.argtypes = []
+    lib.lbm_ref_set_num_threads.argtypes = [I]
     lib.lbm_ref_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), DP]
     lib.lbm_ref_equilibrium.argtypes = [D, DP, DP]
     lib.lbm_ref_body_props.argtypes = [P, I, DP]
@@ -94,6 +95,11 @@ def load(path: str):
 def num_threads() -> int:
     """OpenMP threads the oracle's parallel loops use."""
     return int(_load().lbm_ref_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """Use n OpenMP threads from now on; returns the count in use."""
+    return int(_load().lbm_ref_set_num_threads(int(n)))
 
 
 def lattice():

@@ -826,6 +826,17 @@ int lbm_ref_num_threads(void)
 #endif
 }
 
+/* threads of the parallel loops from now on (n >= 1); returns the count in use */
+int lbm_ref_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return lbm_ref_num_threads();
+}
+
 const char *lbm_ref_last_error(ref_lbm *h) { return h ? h->err : "null handle"; }
 
 /* ==========================================================================

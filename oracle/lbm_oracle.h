@@ -81,6 +81,7 @@ int  lbm_ref_lattice(int *e /* [19][3] */, double *w /* [19] */);
 int  lbm_ref_equilibrium(double rho, const double u[3], double *out /* [19] */);
 int  lbm_ref_body_props(ref_lbm *h, int b, double *out /* volume, I1, I2, I3 */);
 int  lbm_ref_num_threads(void);
+int  lbm_ref_set_num_threads(int n);
 /* Reverse mode: advances n steps (recording every one), then returns the
  * gradient of J = sum_b seed[b] . state_b(after the n steps) (seed: nb x 13)
  * with respect to the body states at the start (grad_state, nb x 13) and the

@@ -233,6 +233,7 @@ struct Device {
     double *hist;           // [hist_cap][nb][13] or null
     int hist_cap;
     TapeCtl *tape;          // recording switch of the reverse sweep, or null
+    int expire_waits;       // checks of the timeout path: the row-staged kernel's first wait cannot succeed
 };
 
 // pointers of one reverse step n of the cell part (adjoint.cu)

@@ -33,6 +33,8 @@ struct lbm_s {
     std::vector<DriveTerm> drives;
     int hist_cap = 0;
     int tune_vec = 0, tune_minb = 0;
+    int expire_waits = 0;               // lbm_debug_set knobs
+    long long list_cap_limit = 0;
     std::vector<int> drive_slot;        // creation index of each device drive term (grouped by body)
     // device
     bool ready = false, graphs_ready = false;
@@ -251,6 +253,7 @@ int ensure_device(lbm_t *h) {
     dv.hist_cap = h->hist_cap;
     dv.vec = h->tune_vec ? h->tune_vec : lbm::default_vector_width(dv);
     dv.minb = h->tune_minb;
+    dv.expire_waits = h->expire_waits;
 
     // per-body reciprocals and term lists (drive terms and springs keep
     // their creation order within a body)
@@ -302,7 +305,7 @@ int ensure_device(lbm_t *h) {
         const long long rs = dv.remap_side;
         const long long cubes = (long long)B * rs * rs * rs, two_c = 2 * C + 1024;
         const size_t cap = B > 0 && fluid(h) ? (size_t)std::min(cubes, two_c) : 1;
-        dv.blist_cap = (long long)cap;
+        dv.blist_cap = h->list_cap_limit > 0 ? std::min((long long)cap, h->list_cap_limit) : (long long)cap;
         if ((rc = alloc_into(h, &dv.blist, sizeof(uint32_t) * cap))) return rc;
         if ((rc = alloc_into(h, &dv.cand, (size_t)std::max(B, 1) * std::max(B, 1)))) return rc;
         // the boundary cells' densities for the momentum exchange (32/16-bit
@@ -396,13 +399,15 @@ int build_graphs(lbm_t *h) {
 int check_status(lbm_t *h) {
     int st = 0;
     CK(cudaMemcpy(&st, h->dv.status, sizeof st, cudaMemcpyDeviceToHost));
-    if (st & lbm::ST_NAN) return fail(h, LBM_E_NAN, "non-finite body state");
+    // a step cut short (a wait that ran out, a full list) comes first: the
+    // other bits may be its consequences
+    if (st & lbm::ST_TIMEOUT) return fail(h, LBM_E_TIMEOUT, "a bounded wait on a bulk copy ran out");
+    if (st & lbm::ST_LINKS) return fail(h, LBM_E_LINKS, "link or boundary-cell list capacity exceeded");
+    if (st & lbm::ST_NAN) return fail(h, LBM_E_NAN, "non-finite body state or link term");
     if (st & lbm::ST_OVERLAP) return fail(h, LBM_E_OVERLAP, "two bodies cover the same cell");
     if (st & lbm::ST_OUTSIDE) return fail(h, LBM_E_OUTSIDE, "a body crosses a wall of the domain");
     if (st & lbm::ST_UNSTABLE)
         return fail(h, LBM_E_UNSTABLE, "a body moved more than %g lattice units in one step", LBM_MAX_BODY_STEP);
-    if (st & lbm::ST_LINKS) return fail(h, LBM_E_LINKS, "link or boundary-cell list capacity exceeded");
-    if (st & lbm::ST_TIMEOUT) return fail(h, LBM_E_TIMEOUT, "a bounded wait on a bulk copy ran out");
     return LBM_OK;
 }
 
@@ -884,6 +889,21 @@ int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm) {
     }
     h->tune_vec = cells_per_thread;
     h->tune_minb = min_blocks_per_sm;
+    return LBM_OK;
+}
+
+int lbm_debug_set(lbm_t *h, int knob, long long value) {
+    if (!h) return LBM_E_ARG;
+    if (h->ready) return fail(h, LBM_E_STATE, "lbm_debug_set must come before the first step");
+    if (knob == LBM_DEBUG_EXPIRE_WAITS) {
+        if (value != 0 && value != 1) return fail(h, LBM_E_ARG, "LBM_DEBUG_EXPIRE_WAITS takes 0 or 1");
+        h->expire_waits = (int)value;
+    } else if (knob == LBM_DEBUG_CELL_LIST_CAP) {
+        if (value < 0) return fail(h, LBM_E_ARG, "LBM_DEBUG_CELL_LIST_CAP takes a capacity >= 1, or 0 for the default");
+        h->list_cap_limit = value;
+    } else {
+        return fail(h, LBM_E_ARG, "unknown debug knob %d", knob);
+    }
     return LBM_OK;
 }
 

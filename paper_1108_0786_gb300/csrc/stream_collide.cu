@@ -772,6 +772,7 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned b
 
 constexpr int TMA_THREADS = 256;
 constexpr long long TMA_WAIT_CYCLES = 1LL << 31;     // ~1 s of SM clock before a block gives up
+constexpr long long TMA_EXPIRE_CYCLES = 1LL << 16;   // the bound of the expired-wait check (~30 us)
 constexpr int TMA_HEADER = 128;                      // mbarriers, ahead of the stages
 
 __host__ __device__ constexpr size_t tma_stage_bytes(int nx, int elem) { return (size_t)Q * nx * elem + (size_t)nx; }
@@ -779,6 +780,7 @@ __host__ __device__ constexpr size_t tma_stage_bytes(int nx, int elem) { return 
 template <typename T, int NSTAGE, int MINB, int ROWS>
 __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Device dv, const StepPtrs sp) {
     using Cd = typename Codec<T>::C;
+    static_assert((NSTAGE + 1) * sizeof(uint64_t) <= TMA_HEADER, "the mbarriers fit the header");
     extern __shared__ __align__(128) unsigned char smem[];
     const Domain d = dv.dom;
     const int nx = d.nx;
@@ -798,7 +800,9 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
     const float inv_scale = dv.f16_inv_scale, scale = dv.f16_scale;
 
     if (threadIdx.x == 0) {
-        for (int st = 0; st < NSTAGE; ++st) mbar_init(&bar[st], 1);
+        // bar[NSTAGE] is never arrived at: with dv.expire_waits the first
+        // wait of every block is on it, so that its bounded wait runs out
+        for (int st = 0; st <= NSTAGE; ++st) mbar_init(&bar[st], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -830,7 +834,12 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
         const unsigned parity = (unsigned)((g / NSTAGE) & 1);
         const long long t0 = clock64();
         bool ready = false;
-        while (!(ready = mbar_try_wait(&bar[st], parity)) && clock64() - t0 < TMA_WAIT_CYCLES) {
+        if (dv.expire_waits && g == 0) {
+            while (!(ready = mbar_try_wait(&bar[NSTAGE], 0)) && clock64() - t0 < TMA_EXPIRE_CYCLES) {
+            }
+        } else {
+            while (!(ready = mbar_try_wait(&bar[st], parity)) && clock64() - t0 < TMA_WAIT_CYCLES) {
+            }
         }
         ok = __syncthreads_and(ready);
         if (!ok) break;

@@ -27,6 +27,7 @@ BC_PERIODIC_X, BC_PERIODIC_Y, BC_PERIODIC_Z = 1, 2, 4
 SHAPE_SPHERE, SHAPE_CAPSULE = 0, 1
 PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = 0, 1, 2, 3
 OPT_NO_FLUID = 1
+DEBUG_EXPIRE_WAITS, DEBUG_CELL_LIST_CAP = 1, 2
 OPT_AVERAGE_FORCE = 2
 FIELD_RHO, FIELD_U, FIELD_FLAGS, FIELD_POP = 0, 1, 2, 3
 DTYPE_F64, DTYPE_F32, DTYPE_U8 = 0, 1, 2
@@ -39,7 +40,8 @@ EXPORTED = (
     "lbm_set_body_state", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_steps_done",
     "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
-    "lbm_tune", "lbm_autotune", "lbm_kernels_per_step", "lbm_bytes_per_cell", "lbm_last_error",
+    "lbm_tune", "lbm_debug_set", "lbm_autotune", "lbm_kernels_per_step", "lbm_bytes_per_cell",
+    "lbm_last_error",
     "lbm_momentum_exchange_static", "lbm_adjoint_record", "lbm_adjoint_backward",
     "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_sync", "lbm_ensemble_destroy",
     "lbm_ensemble_last_error",
@@ -93,6 +95,7 @@ def load_library(path: Optional[str] = None):
         "lbm_load": ([P, ctypes.c_char_p], I),
         "lbm_time_kernels": ([P, I, DP, I], I),
         "lbm_tune": ([P, I, I], I),
+        "lbm_debug_set": ([P, I, ctypes.c_longlong], I),
         "lbm_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "lbm_kernels_per_step": ([P], I),
         "lbm_bytes_per_cell": ([P], I),
@@ -237,6 +240,11 @@ class Lattice:
     def tune(self, cells_per_thread, min_blocks_per_sm=0):
         """Launch shape of the bulk stream-collide kernel (0: default)."""
         return self._check(self._lib.lbm_tune(self._h, int(cells_per_thread), int(min_blocks_per_sm)))
+
+    def debug_set(self, knob, value):
+        """A check of a failure path (DEBUG_EXPIRE_WAITS, DEBUG_CELL_LIST_CAP);
+        before the first step."""
+        return self._check(self._lib.lbm_debug_set(self._h, int(knob), int(value)))
 
     def autotune(self, trials=5):
         """Time the compiled bulk-kernel shapes and keep the fastest;

@@ -103,3 +103,15 @@ def test_bodies_wider_than_a_periodic_period_are_rejected(lib):
         if want:
             assert b"remap cube" in lib.lbm_last_error(h)
         lib.lbm_destroy(h)
+
+
+def test_debug_knobs_take_only_their_values_before_the_first_step(lib):
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(16, 16, 16, 1.0, 7, ctypes.byref(h)) == 0
+    assert lib.lbm_debug_set(h, lbm.DEBUG_EXPIRE_WAITS, 1) == 0
+    assert lib.lbm_debug_set(h, lbm.DEBUG_EXPIRE_WAITS, 0) == 0
+    assert lib.lbm_debug_set(h, lbm.DEBUG_EXPIRE_WAITS, 2) == lbm.E_ARG
+    assert lib.lbm_debug_set(h, lbm.DEBUG_CELL_LIST_CAP, 8) == 0
+    assert lib.lbm_debug_set(h, lbm.DEBUG_CELL_LIST_CAP, -1) == lbm.E_ARG
+    assert lib.lbm_debug_set(h, 99, 0) == lbm.E_ARG
+    assert lib.lbm_destroy(h) == 0
