@@ -149,6 +149,16 @@ int lbm_set_stream(lbm_t *h, void *stream);
 int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass,
                  const double pos[3], const double orient[4]);
 
+/* Volume and body-frame principal moments of inertia of a uniform solid
+ * sphere or capsule (Sec. 2.2, 3.1-3.2; the values lbm_add_body uses), and
+ * their derivatives: out[4] = V, I1, I2, I3 (I1 about the capsule axis);
+ * d_mass[4] and d_length[4] (either may be NULL) the derivatives of the same
+ * four with respect to the mass and to the cylinder length (zero for a
+ * sphere).  For the chain rule of gradients with respect to mass and
+ * capsule length.  Host only, no handle; LBM_E_ARG for bad dimensions. */
+int lbm_body_properties(int shape, double radius, double length, double mass, double out[4],
+                        double d_mass[4], double d_length[4]);
+
 /* Damped harmonic spring between bodies i and j (Eq. spring_i, damp_i,
  * osci_i, osci_j): F_i = -k (|d| - rest) d/|d| - damping (V_i - V_j),
  * d = X_i - X_j, F_j = -F_i; rest is the centre-to-centre rest length.

@@ -17,31 +17,11 @@ from __future__ import annotations
 
 import copy
 import dataclasses
-import math
 
 import numpy as np
 import torch
 
 from . import lbm, workloads as wl
-
-
-def body_properties(shape, radius, length, mass):
-    """Principal moments of inertia (body frame) and volume of a uniform
-    solid sphere or capsule (a cylinder of length ``length`` plus two
-    hemispheres) -- the formulas the library applies in lbm_add_body --
-    as torch expressions, so that their derivatives follow."""
-    r, l, m = radius, length, mass
-    if shape == wl.SPHERE:
-        vol = 4.0 / 3.0 * math.pi * r ** 3 + 0.0 * l
-        i0 = 0.4 * m * r * r
-        return torch.stack([i0, i0, i0]), vol
-    vc = math.pi * r * r * l
-    vh = 2.0 / 3.0 * math.pi * r ** 3
-    vol = vc + 2.0 * vh
-    mc, mh = m * vc / vol, m * vh / vol
-    i0 = 0.5 * mc * r * r + 2.0 * (0.4 * mh * r * r)
-    i1 = mc * (r * r / 4.0 + l * l / 12.0) + 2.0 * mh * (0.4 * r * r + l * l / 4.0 + 3.0 * l * r / 8.0)
-    return torch.stack([i0, i1, i1]), vol
 
 
 def _scenario_with(sc, amp, phase, k, rest, damping, mass, length):
@@ -89,18 +69,16 @@ class _SwimmerRun(torch.autograd.Function):
 
 
 def _mass_length_chain(body, mass, length, gbody):
-    """dJ/dm and dJ/dl from dJ/d(m, I1, I2, I3, V) through the inertia and
-    volume formulas."""
-    with torch.enable_grad():
-        m = torch.tensor(mass, dtype=torch.float64, requires_grad=True)
-        l = torch.tensor(length if body.shape == wl.CAPSULE else 0.0, dtype=torch.float64,
-                         requires_grad=True)
-        inertia, vol = body_properties(body.shape, body.radius, l, m)
-        # J depends on (m, I, V): d/dm and d/dl through I(m, l) and V(l)
-        total = (float(gbody[0]) * m + (torch.from_numpy(gbody[1:4]) * inertia).sum() +
-                 float(gbody[4]) * vol)
-        dm, dl = torch.autograd.grad(total, (m, l), allow_unused=True)
-    return float(dm), (float(dl) if (dl is not None and body.shape == wl.CAPSULE) else 0.0)
+    """dJ/dm and dJ/dl from the reverse sweep's dJ/d(m, I1, I2, I3, V) and
+    the library's derivatives of (V, I1, I2, I3) with respect to mass and
+    length (lbm_body_properties)."""
+    l = length if body.shape == wl.CAPSULE else 0.0
+    _, d_m, d_l = lbm.body_properties(body.shape, body.radius, l, mass)
+    # gbody is ordered (m, I1, I2, I3, V), the derivatives (V, I1, I2, I3)
+    g = np.concatenate((gbody[4:5], gbody[1:4]))
+    dm = float(gbody[0] + g @ d_m)
+    dl = float(g @ d_l) if body.shape == wl.CAPSULE else 0.0
+    return dm, dl
 
 
 def swimmer_run(sc, steps, amp, phase, k, rest, damping, mass, length, state0, segment=64,

@@ -503,6 +503,59 @@ int lbm_set_stream(lbm_t *h, void *stream) {
     return LBM_OK;
 }
 
+namespace {
+// Volume and body-frame principal moments of inertia of a uniform solid
+// sphere, or capsule (cylinder of length l along the body x axis plus two
+// hemispherical caps), and their derivatives with respect to the mass and
+// the cylinder length: q = (V, I1, I2, I3).
+void body_properties(int shape, double r, double l, double m, double q[4], double dq_dm[4], double dq_dl[4]) {
+    if (shape == LBM_SHAPE_SPHERE) {
+        q[0] = 4.0 / 3.0 * M_PI * r * r * r;
+        dq_dm[0] = dq_dl[0] = 0.0;
+        for (int i = 1; i < 4; ++i) {
+            q[i] = 0.4 * m * r * r;
+            dq_dm[i] = 0.4 * r * r;
+            dq_dl[i] = 0.0;
+        }
+        return;
+    }
+    // I = m N / V with N the volume-weighted moment per unit density:
+    // cylinder (mass m vc / V) and two caps (m vh / V each), the caps'
+    // centroids 3r/8 beyond the cylinder's ends
+    const double vc = M_PI * r * r * l, vh = 2.0 / 3.0 * M_PI * r * r * r;
+    const double V = vc + 2.0 * vh, dV = M_PI * r * r;
+    const double N1 = vc * 0.5 * r * r + 2.0 * vh * 0.4 * r * r;
+    const double dN1 = dV * 0.5 * r * r;
+    const double N2 = vc * (r * r / 4.0 + l * l / 12.0) + 2.0 * vh * (0.4 * r * r + l * l / 4.0 + 3.0 * l * r / 8.0);
+    const double dN2 = dV * (r * r / 4.0 + l * l / 12.0) + vc * (l / 6.0) + 2.0 * vh * (l / 2.0 + 3.0 * r / 8.0);
+    q[0] = V;
+    dq_dm[0] = 0.0;
+    dq_dl[0] = dV;
+    const double N[2] = {N1, N2}, dN[2] = {dN1, dN2};
+    for (int i = 1; i < 4; ++i) {
+        const int k = i == 1 ? 0 : 1;
+        q[i] = m * N[k] / V;
+        dq_dm[i] = N[k] / V;
+        dq_dl[i] = m * (dN[k] * V - N[k] * dV) / (V * V);
+    }
+}
+}  // namespace
+
+int lbm_body_properties(int shape, double radius, double length, double mass, double out[4], double d_mass[4],
+                        double d_length[4]) {
+    if (!out || (shape != LBM_SHAPE_SPHERE && shape != LBM_SHAPE_CAPSULE) || !(radius > 0) || !(mass > 0) ||
+        !(length >= 0) || (shape == LBM_SHAPE_SPHERE && length != 0))
+        return LBM_E_ARG;
+    double q[4], dm[4], dl[4];
+    body_properties(shape, radius, length, mass, q, dm, dl);
+    for (int i = 0; i < 4; ++i) {
+        out[i] = q[i];
+        if (d_mass) d_mass[i] = dm[i];
+        if (d_length) d_length[i] = dl[i];
+    }
+    return LBM_OK;
+}
+
 int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass, const double pos[3],
                  const double orient[4]) {
     if (!h || !pos) return LBM_E_ARG;
@@ -535,20 +588,12 @@ int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass,
     // the FP32 inside test's margin: its error stays near 1e-5 max(r^2, 1)
     // and grows like 1.3e-7 l r for long thin capsules
     p.marginf = (float)std::max(1e-3 * std::max(radius * radius, 1.0), 2e-6 * length * std::max(radius, 1.0));
-    const double r = radius, l = length;
-    double I[3];
-    if (shape == LBM_SHAPE_SPHERE) {
-        p.volume = 4.0 / 3.0 * M_PI * r * r * r;
-        I[0] = I[1] = I[2] = 0.4 * mass * r * r;
-    } else {
-        // uniform solid capsule: cylinder of length l plus two hemispheres
-        const double vc = M_PI * r * r * l, vh = 2.0 / 3.0 * M_PI * r * r * r;
-        p.volume = vc + 2.0 * vh;
-        const double mc = mass * vc / p.volume, mh = mass * vh / p.volume;
-        I[0] = 0.5 * mc * r * r + 2.0 * (0.4 * mh * r * r);
-        I[1] = I[2] = mc * (r * r / 4.0 + l * l / 12.0) + 2.0 * mh * (0.4 * r * r + l * l / 4.0 + 3.0 * l * r / 8.0);
+    {
+        double q[4], dm[4], dl[4];
+        body_properties(shape, radius, length, mass, q, dm, dl);
+        p.volume = q[0];
+        for (int i = 0; i < 3; ++i) p.inertia[i] = q[1 + i];
     }
-    for (int i = 0; i < 3; ++i) p.inertia[i] = I[i];
     BodyState s{};
     for (int i = 0; i < 3; ++i) s.X[i] = pos[i];
     if (orient) {

@@ -277,9 +277,63 @@ template <typename T> __device__ __forceinline__ float raw_ld(T v);
 template <> __device__ __forceinline__ float raw_ld<__half>(__half v) { return __half2float(v); }
 template <> __device__ __forceinline__ float raw_ld<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename T> __device__ __forceinline__ T raw_st(float v);
-template <> __device__ __forceinline__ __half raw_st<__half>(float v) { return __float2half_rn(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 raw_st<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// ---- stochastic rounding of BF16 storage ------------------------------------
+// BF16 keeps 8 significant bits.  Rounded to nearest, a population whose
+// update is below half an ulp is rounded back to the same value every step:
+// slow terms are lost and the flow settles at a biased state (Guo's term in
+// the channel workload adds ~2e-8 a step to populations whose ulp is ~2e-7).
+// BF16 stores therefore round up with a probability equal to the fraction of
+// the ulp that is dropped: the rounding error has zero mean, and the slow
+// terms accumulate as they do in FP32.  The random bits come from a
+// counter-based hash of (cell, step), so a cell's rounding depends neither
+// on the launch shape nor on which kernel stores the cell: 8 bits for each
+// population, bytes of five 32-bit words per cell.
+struct Dither {
+    unsigned h[5];
+};
+
+// MurmurHash3's 32-bit finalizer (Appleby): a bijective integer mixer
+__device__ __forceinline__ unsigned fmix32(unsigned x) {
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ Dither bf16_dither(long long c, long long t) {
+    const unsigned key = (unsigned)c * 0x9E3779B1u ^ ((unsigned)t * 0x85EBCA77u + (unsigned)(t >> 32));
+    Dither d;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) d.h[k] = fmix32(key + (unsigned)k * 0x6A09E667u);
+    return d;
+}
+
+// the BF16 bits (low half of the result) of v rounded stochastically with
+// byte a % 4 of word a / 4 of d; adding 8 random bits and half a step of
+// them below the kept bits, then truncating, rounds the magnitude up with
+// the probability of the dropped fraction (to 2^-9 of an ulp)
+__device__ __forceinline__ unsigned bf16_sr_bits(float v, const Dither &d, int a) {
+    const unsigned r = __byte_perm(d.h[a >> 2], 0u, 0x4404u | ((unsigned)(a & 3) << 4));
+    return (__float_as_uint(v) + r + 0x80u) >> 16;
+}
+
+// a 16-bit population as stored: FP16 rounded to nearest, BF16 rounded
+// stochastically (the dither is used only for BF16)
+template <typename T> __device__ __forceinline__ T store16(float v, const Dither &d, int a);
+template <> __device__ __forceinline__ __half store16<__half>(float v, const Dither &, int) {
+    return __float2half_rn(v);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 store16<__nv_bfloat16>(float v, const Dither &d, int a) {
+    return __ushort_as_bfloat16((unsigned short)bf16_sr_bits(v, d, a));
+}
+
+template <typename T> __device__ __forceinline__ Dither dither_for(long long c, long long t) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) return bf16_dither(c, t);
+    else return Dither{};
+}
 
 // MINB == 1 leaves the register budget to the compiler (an explicit minimum
 // of one block lets it spend far more registers than it needs)
@@ -352,6 +406,13 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
         for (int b = 0; b < Q; ++b) f[b][i] = solid ? (Cd)0 : g[b];
     }
     if (!active) return;
+    // BF16 rounds stochastically (one cell per thread for 16-bit storage here)
+    static_assert(!raw16 || V == 1, "16-bit storage with several cells per thread uses bulk16_kernel");
+    const Dither dz = raw16 ? dither_for<T>(c0, *dv.t_dev) : Dither{};
+    auto st = [&](Cd v, int b) -> T {
+        if constexpr (raw16) return store16<T>(v, dz, b);
+        else return Codec<T>::st(v, scale);
+    };
     // fluid cells with a non-zero flag byte belong to the boundary kernel,
     // which may run concurrently: leave them alone
     bool all_mine = true;
@@ -362,10 +423,7 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
         for (int b = 0; b < Q; ++b) {
             T out[V];
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                if constexpr (raw16) out[i] = raw_st<T>(f[b][i]);
-                else out[i] = Codec<T>::st(f[b][i], scale);
-            }
+            for (int i = 0; i < V; ++i) out[i] = st(f[b][i], b);
             store_vec<T, V>(dst + (long long)b * C + c0, out);
         }
         return;
@@ -374,10 +432,7 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
     for (int b = 0; b < Q; ++b)
 #pragma unroll
         for (int i = 0; i < V; ++i)
-            if (fl[i] == 0 || (fl[i] & F_SOLID)) {
-                if constexpr (raw16) dst[(long long)b * C + c0 + i] = raw_st<T>(f[b][i]);
-                else dst[(long long)b * C + c0 + i] = Codec<T>::st(f[b][i], scale);
-            }
+            if (fl[i] == 0 || (fl[i] & F_SOLID)) dst[(long long)b * C + c0 + i] = st(f[b][i], b);
 }
 
 // 16-bit values packed two to a 32-bit word (the lower address in the low
@@ -400,6 +455,11 @@ template <> __device__ __forceinline__ float half_hi<__nv_bfloat16>(unsigned w) 
 }
 template <> __device__ __forceinline__ unsigned half_bits<__nv_bfloat16>(float v) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+// the stored bits of population a of a cell: FP16 to nearest, BF16 stochastically
+template <typename T> __device__ __forceinline__ unsigned store_bits(float v, const Dither &d, int a) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) return bf16_sr_bits(v, d, a);
+    else return half_bits<T>(v);
 }
 
 // The bulk kernel for 16-bit storage, V (even) cells per thread.  The
@@ -465,6 +525,7 @@ bulk16_kernel(const Device dv, const StepPtrs sp) {
         }
     }
 
+    const long long tstep = std::is_same<T, __nv_bfloat16>::value ? *dv.t_dev : 0;
 #pragma unroll
     for (int i = 0; i < V; ++i) {
         const int j = i >> 1;
@@ -474,9 +535,10 @@ bulk16_kernel(const Device dv, const StepPtrs sp) {
         for (int b = 0; b < Q; ++b) g[b] = hi ? half_hi<T>(w[b][j]) : half_lo<T>(w[b][j]);
         collide_lean<std::is_same<T, __half>::value>(g, dv);
         const bool solid = fl[i] & F_SOLID;
+        const Dither dz = dither_for<T>(c0 + i, tstep);
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
-            const unsigned h = solid ? 0u : half_bits<T>(g[b]);
+            const unsigned h = solid ? 0u : store_bits<T>(g[b], dz, b);
             w[b][j] = hi ? __byte_perm(w[b][j], h, 0x5410) : __byte_perm(h, w[b][j], 0x7610);
         }
     }
@@ -721,8 +783,14 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
     }
     collide<Cd, std::is_same<T, float>::value>(f, dv);
     T *__restrict__ dst = static_cast<T *>(sp.dst);
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        const Dither dz = bf16_dither(c, *dv.t_dev);
 #pragma unroll
-    for (int b = 0; b < Q; ++b) dst[(long long)b * C + c] = Codec<T>::st(f[b], dv.f16_scale);
+        for (int b = 0; b < Q; ++b) dst[(long long)b * C + c] = store16<T>(f[b], dz, b);
+    } else {
+#pragma unroll
+        for (int b = 0; b < Q; ++b) dst[(long long)b * C + c] = Codec<T>::st(f[b], dv.f16_scale);
+    }
 }
 
 // ---- TMA row-staged variant ---------------------------------------------------
@@ -798,6 +866,7 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
     T *__restrict__ dst = static_cast<T *>(sp.dst);
     const long long C = d.C;
     const float inv_scale = dv.f16_inv_scale, scale = dv.f16_scale;
+    const long long tstep = std::is_same<T, __nv_bfloat16>::value ? *dv.t_dev : 0;
 
     if (threadIdx.x == 0) {
         // bar[NSTAGE] is never arrived at: with dv.expire_waits the first
@@ -867,8 +936,9 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
                 }
                 if constexpr (sizeof(T) == 2) {
                     collide_lean<std::is_same<T, __half>::value>(f, dv);
+                    const Dither dz = dither_for<T>(c0 + x, tstep);
 #pragma unroll
-                    for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = raw_st<T>(f[b]);
+                    for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = store16<T>(f[b], dz, b);
                 } else {
                     collide<Cd, std::is_same<T, float>::value>(f, dv);
 #pragma unroll

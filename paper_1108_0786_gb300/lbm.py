@@ -36,7 +36,7 @@ PRECISIONS = {"f64": PREC_F64, "f32": PREC_F32, "f16": PREC_F16, "bf16": PREC_BF
 
 EXPORTED = (
     "lbm_create", "lbm_create_ex", "lbm_destroy", "lbm_set_allocator", "lbm_set_stream",
-    "lbm_add_body", "lbm_add_spring", "lbm_set_drive", "lbm_set_drive_window", "lbm_set_drive_axis",
+    "lbm_add_body", "lbm_body_properties", "lbm_add_spring", "lbm_set_drive", "lbm_set_drive_window", "lbm_set_drive_axis",
     "lbm_set_body_state", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_steps_done",
     "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
@@ -96,6 +96,7 @@ def load_library(path: Optional[str] = None):
         "lbm_time_kernels": ([P, I, DP, I], I),
         "lbm_tune": ([P, I, I], I),
         "lbm_debug_set": ([P, I, ctypes.c_longlong], I),
+        "lbm_body_properties": ([I, D, D, D, DP, DP, DP], I),
         "lbm_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "lbm_kernels_per_step": ([P], I),
         "lbm_bytes_per_cell": ([P], I),
@@ -122,6 +123,18 @@ class LbmError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"lbm error {code}: {msg}")
         self.code = code
+
+
+def body_properties(shape, radius, length, mass):
+    """(V, I1, I2, I3) of a uniform solid sphere or capsule as lbm_add_body
+    computes them, and their derivatives with respect to mass and length
+    (lbm_body_properties; runs on the host)."""
+    q, dm, dl = np.zeros(4), np.zeros(4), np.zeros(4)
+    rc = load_library().lbm_body_properties(int(shape), float(radius), float(length), float(mass), _dp(q),
+                                            _dp(dm), _dp(dl))
+    if rc != OK:
+        raise LbmError(rc, "bad body dimensions")
+    return q, dm, dl
 
 
 def _dp(a: np.ndarray):

@@ -356,13 +356,15 @@ def test_fp16_storage_channel_swimmer_against_fp64_oracle():
     assert rel_l2 < 5e-2, rel_l2
 
 
-def test_bf16_storage_channel_swimmer_accuracy():
-    """BF16 keeps 8 mantissa bits: its net displacement error on the channel
-    swimmer is about 1e-1, an order of magnitude above FP16's; the bound
-    here guards that figure."""
+def test_bf16_storage_channel_swimmer_against_fp64_oracle():
+    """BF16 deviation storage (8 significant bits, rounded stochastically)
+    with FP32 collision on the channel swimmer: net displacement within 1e-2
+    of the FP64 oracle over ten periods, the bar FP16 meets.  Rounded to
+    nearest, BF16 loses the channel's forcing (below half an ulp a step) and
+    misses this bar by about ten times."""
     rel_l2, disp_err, _, _ = channel_run("bf16")
-    assert disp_err < 0.3, disp_err
-    assert rel_l2 < 0.2, rel_l2
+    assert disp_err < 1e-2, disp_err
+    assert rel_l2 < 5e-2, rel_l2
 
 
 def test_averaged_load_option_matches_the_oracle():
