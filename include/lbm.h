@@ -199,6 +199,22 @@ int lbm_step(lbm_t *h, int n);
 /* Wait for all enqueued work and return any latched device error. */
 int lbm_sync(lbm_t *h);
 
+/* Time average of the velocity field (Sec. 6, Fig. 13: the flow around one
+ * and three swimmers averaged over five swimming cycles).
+ * lbm_average_begin starts the average, or restarts it from zero: from then
+ * on every step adds the velocity of the populations it wrote,
+ * u = (sum_a e_a f~_a - g/2) / rho (0 in obstacle cells, the LBM_FIELD_U
+ * value), to an FP64 sum of 3 doubles per cell on the device (allocated at
+ * the first call through the handle's allocator; one extra kernel a step).
+ * lbm_average_stop stops adding and keeps the sum.  lbm_average_get
+ * synchronises and writes the mean, FP64 [3][cells] in the field layout, to
+ * host memory `out` and the number of steps averaged to *steps (optional);
+ * LBM_E_STATE if no average was begun.  The moments are FP64 for FP64
+ * storage and FP32 for 32/16-bit storage. */
+int lbm_average_begin(lbm_t *h);
+int lbm_average_stop(lbm_t *h);
+int lbm_average_get(lbm_t *h, double *out, long long *steps);
+
 /* Number of completed (enqueued) steps. */
 long long lbm_steps_done(lbm_t *h);
 

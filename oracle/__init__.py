@@ -73,6 +73,8 @@ def load(path: str):
     lib.lbm_ref_set_drive_axis.argtypes = [P, I, DP]
     lib.lbm_ref_set_body_state.argtypes = [P, I, DP]
     lib.lbm_ref_step.argtypes = [P, I]
+    lib.lbm_ref_average_begin.argtypes = [P]
+    lib.lbm_ref_average_get.argtypes = [P, DP, ctypes.POINTER(ctypes.c_long)]
     lib.lbm_ref_get_bodies.argtypes = [P, DP]
     lib.lbm_ref_get_forces.argtypes = [P, DP]
     lib.lbm_ref_get_fields.argtypes = [P, I, P]
@@ -216,6 +218,16 @@ class Oracle:
 
     def step(self, n=1):
         return self._check(self._lib.lbm_ref_step(self._h, int(n)))
+
+    def average_begin(self):
+        return self._check(self._lib.lbm_ref_average_begin(self._h))
+
+    def average(self):
+        """(mean velocity [3, nz, ny, nx] since average_begin, steps averaged)."""
+        out = np.zeros((3,) + self.shape)
+        n = ctypes.c_long()
+        self._check(self._lib.lbm_ref_average_get(self._h, _dp(out), ctypes.byref(n)))
+        return out, int(n.value)
 
     @property
     def steps_done(self):

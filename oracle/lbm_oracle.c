@@ -123,6 +123,9 @@ struct ref_lbm {
     int started;
     unsigned long long flag_digest;   /* running digest of every step's obstacle map */
     struct tape *tape;                /* recording for the reverse sweep, or NULL */
+    double *avg_sum;                  /* running sum of the velocity [3][C], or NULL */
+    long avg_steps;                   /* steps added to it */
+    int avg_on;
     char err[256];
 };
 
@@ -216,6 +219,21 @@ static double feq(int a, double rho, const double u[3])
     return W[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
 }
 
+/* velocity of cell c from the post-collision populations G:
+ * u = (sum_a e_a f~_a - g/2) / rho, the velocity Guo's collision used;
+ * 0 in obstacle cells.  Returns rho (1 in obstacle cells). */
+static double cell_velocity(const ref_lbm *h, long c, int solid, double u[3])
+{
+    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < Q; ++a) {
+        double f = h->G[a * h->C + c];
+        rho += f;
+        m[0] += EX[a] * f; m[1] += EY[a] * f; m[2] += EZ[a] * f;
+    }
+    for (int i = 0; i < 3; ++i) u[i] = solid ? 0.0 : (m[i] - 0.5 * h->g[i]) / rho;
+    return solid ? 1.0 : rho;
+}
+
 /* ---- creation ------------------------------------------------------------ */
 
 int lbm_ref_create_ex(int nx, int ny, int nz, double tau, int bc,
@@ -258,7 +276,7 @@ int lbm_ref_destroy(ref_lbm *h)
 {
     if (!h) return REF_OK;
     free(h->F); free(h->G); free(h->bid_now); free(h->bid_prev);
-    free(h->spring); free(h->drive);
+    free(h->spring); free(h->drive); free(h->avg_sum);
     free(h);
     return REF_OK;
 }
@@ -716,6 +734,39 @@ static int one_step(ref_lbm *h)
     short *t = h->bid_prev; h->bid_prev = h->bid_now; h->bid_now = t;
     h->step++;
     if (tp) tp->n++;
+    if (h->avg_on) {                                 /* running velocity average (Sec. 6) */
+        for (long c = 0; c < h->C; ++c) {
+            double u[3];
+            cell_velocity(h, c, h->bid_prev[c] >= 0, u);
+            for (int i = 0; i < 3; ++i) h->avg_sum[i * h->C + c] += u[i];
+        }
+        h->avg_steps++;
+    }
+    return REF_OK;
+}
+
+/* Time average of the velocity field (Sec. 6, the flow fields averaged over
+ * five swimming cycles): from the next step on, each step adds the velocity
+ * of every cell after it (the REF_FIELD_U value) to a running sum. */
+int lbm_ref_average_begin(ref_lbm *h)
+{
+    if (!h) return REF_E_ARG;
+    if (!h->avg_sum) {
+        h->avg_sum = malloc(sizeof(double) * 3 * h->C);
+        if (!h->avg_sum) return fail(h, REF_E_OOM, "out of memory");
+    }
+    memset(h->avg_sum, 0, sizeof(double) * 3 * h->C);
+    h->avg_steps = 0;
+    h->avg_on = 1;
+    return REF_OK;
+}
+
+/* the mean velocity [3][C] over the steps since lbm_ref_average_begin */
+int lbm_ref_average_get(ref_lbm *h, double *out, long *steps)
+{
+    if (!h || !out || !h->avg_sum) return REF_E_ARG;
+    for (long k = 0; k < 3 * h->C; ++k) out[k] = h->avg_steps ? h->avg_sum[k] / h->avg_steps : 0.0;
+    if (steps) *steps = h->avg_steps;
     return REF_OK;
 }
 
@@ -772,17 +823,12 @@ int lbm_ref_get_fields(ref_lbm *h, int what, void *out)
     double *o = out;
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < C; ++c) {
-        double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
-        for (int a = 0; a < Q; ++a) {
-            double f = h->G[a * C + c];
-            rho += f;
-            m[0] += EX[a] * f; m[1] += EY[a] * f; m[2] += EZ[a] * f;
-        }
-        int solid = bid[c] >= 0;
+        double u[3];
+        double rho = cell_velocity(h, c, bid[c] >= 0, u);
         if (what == REF_FIELD_RHO) {
-            o[c] = solid ? 1.0 : rho;
+            o[c] = rho;
         } else {
-            for (int i = 0; i < 3; ++i) o[i * C + c] = solid ? 0.0 : (m[i] - 0.5 * h->g[i]) / rho;
+            for (int i = 0; i < 3; ++i) o[i * C + c] = u[i];
         }
     }
     return REF_OK;

@@ -72,6 +72,10 @@ int  lbm_ref_set_drive_window(ref_lbm *h, int term, double t_off);
 int  lbm_ref_set_drive_axis(ref_lbm *h, int term, const double axis[3]);
 int  lbm_ref_set_body_state(ref_lbm *h, int body, const double state[13]);
 int  lbm_ref_step(ref_lbm *h, int n);
+/* running time average of the velocity field from the next step on, and
+ * its mean [3][cells] with the number of steps averaged */
+int  lbm_ref_average_begin(ref_lbm *h);
+int  lbm_ref_average_get(ref_lbm *h, double *out, long *steps);
 int  lbm_ref_get_bodies(ref_lbm *h, double *out);
 int  lbm_ref_get_forces(ref_lbm *h, double *out);
 int  lbm_ref_get_fields(ref_lbm *h, int what, void *out);

@@ -1027,6 +1027,46 @@ __global__ void export_kernel(const Device dv, const T *pop, const uint8_t *flag
     }
 }
 
+// Running time average of the velocity (Sec. 6, the flow fields averaged
+// over swimming cycles): each step adds the velocity of the populations it
+// wrote, u = (sum e f~ - g/2) / rho (0 in obstacle cells, the value the U
+// field reports), to an FP64 sum per cell and component.  The moments are
+// FP64 for FP64 storage and FP32 otherwise (FP64 arithmetic is slow on this
+// part); the sum is FP64 so that long windows keep their digits.
+template <typename T>
+__global__ void __launch_bounds__(256) average_kernel(const Device dv, const StepPtrs sp) {
+    const long long C = dv.dom.C;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    double u[3] = {0.0, 0.0, 0.0};
+    if (!(sp.flags_cur[c] & F_SOLID)) {
+        const T *pop = static_cast<const T *>(sp.dst);
+        if constexpr (sizeof(T) == 8) {
+            double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
+            for (int a = 0; a < Q; ++a) {
+                const double v = pop[a * C + c];
+                drho += v;
+                j[0] += ex(a) * v; j[1] += ey(a) * v; j[2] += ez(a) * v;
+            }
+            for (int i = 0; i < 3; ++i) u[i] = (j[i] - 0.5 * dv.g[i]) / (1.0 + drho);
+        } else {
+            float drho = 0.0f, j[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const float v = load_dev_f<T>(pop + a * C + c, dv.f16_inv_scale);
+                drho += v;
+                if (ex(a)) j[0] += ex(a) > 0 ? v : -v;
+                if (ey(a)) j[1] += ey(a) > 0 ? v : -v;
+                if (ez(a)) j[2] += ez(a) > 0 ? v : -v;
+            }
+            const float inv = 1.0f / (1.0f + drho);
+            for (int i = 0; i < 3; ++i) u[i] = (double)((j[i] - 0.5f * dv.g_f[i]) * inv);
+        }
+    }
+    for (int i = 0; i < 3; ++i) dv.avg_u[i * C + c] += u[i];
+    if (c == 0) *dv.avg_n += 1;
+}
+
 template <typename T>
 __global__ void import_kernel(const Device dv, T *pop, const double *in) {
     const long long C = dv.dom.C;
@@ -1092,6 +1132,16 @@ void launch_export(const Device &dv, const void *pop, const uint8_t *flags, cons
                    int mask_solid, void *out, int dtype, cudaStream_t s) {
     if (dtype == 1) export_typed<float>(dv, pop, flags, bid, what, mask_solid, static_cast<float *>(out), s);
     else export_typed<double>(dv, pop, flags, bid, what, mask_solid, static_cast<double *>(out), s);
+}
+
+void launch_average(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    const unsigned bl = blocks_for(dv.dom.C, 256);
+    switch (dv.precision) {
+    case 0: average_kernel<double><<<bl, 256, 0, s>>>(dv, sp); break;
+    case 1: average_kernel<float><<<bl, 256, 0, s>>>(dv, sp); break;
+    case 2: average_kernel<__half><<<bl, 256, 0, s>>>(dv, sp); break;
+    default: average_kernel<__nv_bfloat16><<<bl, 256, 0, s>>>(dv, sp); break;
+    }
 }
 
 void launch_import_pop(const Device &dv, void *pop, const double *in, cudaStream_t s) {

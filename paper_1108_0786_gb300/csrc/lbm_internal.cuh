@@ -234,6 +234,8 @@ struct Device {
     int hist_cap;
     TapeCtl *tape;          // recording switch of the reverse sweep, or null
     int expire_waits;       // checks of the timeout path: the row-staged kernel's first wait cannot succeed
+    double *avg_u;          // [3][C] running sum of the velocity while an average is taken, or null
+    long long *avg_n;       // steps added to avg_u
 };
 
 // pointers of one reverse step n of the cell part (adjoint.cu)
@@ -285,6 +287,7 @@ void launch_integrate(const Device &dv, const StepPtrs &sp, int with_fluid, cuda
 void launch_export(const Device &dv, const void *pop, const uint8_t *flags, const uint8_t *bid,
                    int what, int mask_solid, void *out, int dtype, cudaStream_t s);
 void launch_import_pop(const Device &dv, void *pop, const double *in, cudaStream_t s);
+void launch_average(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 int adjoint_part_stride(const Device &dv);
 void launch_adj_integrate(const Device &dv, const AdjBody &ab, cudaStream_t s);
 void launch_adj_bulk(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s);

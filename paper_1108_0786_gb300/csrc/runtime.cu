@@ -35,6 +35,9 @@ struct lbm_s {
     int tune_vec = 0, tune_minb = 0;
     int expire_waits = 0;               // lbm_debug_set knobs
     long long list_cap_limit = 0;
+    double *avg_sum = nullptr;          // [3][C] running velocity sum (lbm_average_*)
+    long long *avg_count = nullptr;     // steps added to it (device)
+    unsigned graph_gen = 0;             // bumped whenever the step graphs are rebuilt with other kernels
     std::vector<int> drive_slot;        // creation index of each device drive term (grouped by body)
     // device
     bool ready = false, graphs_ready = false;
@@ -178,6 +181,18 @@ void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bo
     } else if (bodies) {
         run(LBM_KERNEL_INTEGRATE, s, [&] { lbm::launch_integrate(h->dv, sp, 0, s); });
     }
+    // the running velocity average reads the populations this step wrote
+    if (fl && h->dv.avg_u) lbm::launch_average(h->dv, sp, s);
+}
+
+// the step graphs bake in the kernels and their arguments: drop them so that
+// the next step rebuilds them
+void drop_graphs(lbm_t *h) {
+    for (int p = 0; p < 2; ++p)
+        if (h->single[p]) { cudaGraphExecDestroy(h->single[p]); h->single[p] = nullptr; }
+    if (h->chunk) { cudaGraphExecDestroy(h->chunk); h->chunk = nullptr; }
+    h->graphs_ready = false;
+    ++h->graph_gen;
 }
 
 int kernels_per_step(const lbm_t *h) {
@@ -189,6 +204,7 @@ int kernels_per_step(const lbm_t *h) {
     if (fl) n += (bodies ? 1 : 0) + (walls ? 1 : 0);        // boundary cells
     if (bodies && fl) n += 3;                               // links, drive and spring loads, force + rigid-body step
     if (bodies && !fl) n += 1;                              // rigid-body step alone
+    if (fl && h->dv.avg_u) n += 1;                          // running velocity average
     return n;
 }
 
@@ -719,6 +735,51 @@ int lbm_sync(lbm_t *h) {
     return sync_and_check(h);
 }
 
+int lbm_average_begin(lbm_t *h) {
+    if (!h) return LBM_E_ARG;
+    if (!fluid(h)) return fail(h, LBM_E_STATE, "no fluid to average");
+    int rc = ensure_device(h);
+    if (rc) return rc;
+    if ((rc = sync_and_check(h))) return rc;
+    if (!h->avg_sum) {
+        if ((rc = alloc_into(h, &h->avg_sum, sizeof(double) * 3 * (size_t)h->C))) return rc;
+        if ((rc = alloc_into(h, &h->avg_count, sizeof(long long)))) return rc;
+    }
+    CK(cudaMemsetAsync(h->avg_sum, 0, sizeof(double) * 3 * (size_t)h->C, h->stream));
+    CK(cudaMemsetAsync(h->avg_count, 0, sizeof(long long), h->stream));
+    if (!h->dv.avg_u) {
+        h->dv.avg_u = h->avg_sum;
+        h->dv.avg_n = h->avg_count;
+        drop_graphs(h);
+    }
+    return LBM_OK;
+}
+
+int lbm_average_stop(lbm_t *h) {
+    if (!h) return LBM_E_ARG;
+    if (h->dv.avg_u) {
+        h->dv.avg_u = nullptr;
+        h->dv.avg_n = nullptr;
+        drop_graphs(h);
+    }
+    return LBM_OK;
+}
+
+int lbm_average_get(lbm_t *h, double *out, long long *steps) {
+    if (!h || !out) return LBM_E_ARG;
+    if (!h->avg_sum) return fail(h, LBM_E_STATE, "no average was begun");
+    int rc = sync_and_check(h);
+    if (rc) return rc;
+    long long n = 0;
+    CK(cudaMemcpy(&n, h->avg_count, sizeof n, cudaMemcpyDeviceToHost));
+    const size_t count = 3 * (size_t)h->C;
+    CK(cudaMemcpy(out, h->avg_sum, sizeof(double) * count, cudaMemcpyDeviceToHost));
+    if (n > 0)
+        for (size_t i = 0; i < count; ++i) out[i] /= (double)n;
+    if (steps) *steps = n;
+    return LBM_OK;
+}
+
 long long lbm_steps_done(lbm_t *h) { return h ? h->steps : -1; }
 
 int lbm_get_bodies(lbm_t *h, double *out) {
@@ -985,11 +1046,7 @@ int lbm_autotune(lbm_t *h, int trials, int *best_cells, int *best_blocks) {
         cudaEventDestroy(e1);
         h->dv.vec = h->tune_vec = bv;
         h->dv.minb = h->tune_minb = bm;
-        // the step graphs bake in the launch shape: rebuild them
-        for (int p = 0; p < 2; ++p)
-            if (h->single[p]) { cudaGraphExecDestroy(h->single[p]); h->single[p] = nullptr; }
-        if (h->chunk) { cudaGraphExecDestroy(h->chunk); h->chunk = nullptr; }
-        h->graphs_ready = false;
+        drop_graphs(h);             // the step graphs bake in the launch shape
     }
     if (best_cells) *best_cells = h->dv.vec;
     if (best_blocks) *best_blocks = h->dv.minb;
@@ -1304,6 +1361,7 @@ struct lbm_ensemble_s {
     // one graph per set of members advanced together: CHUNK_STEPS steps of
     // each as parallel branches
     std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> graphs;
+    std::vector<unsigned> gens;             // the members' graph generations the cached graphs were built at
     std::string err;
 };
 
@@ -1412,6 +1470,15 @@ int lbm_ensemble_step(lbm_ensemble_t *e, const int *steps) {
             if ((rc = lbm_step(h, 1))) return ens_fail(e, rc, h->err.c_str());
             --left[i];
         }
+    }
+    // a member whose step graphs changed (an average begun or stopped, a new
+    // launch shape) invalidates the ensemble's graphs
+    std::vector<unsigned> gens(n);
+    for (int i = 0; i < n; ++i) gens[i] = e->members[i]->graph_gen;
+    if (gens != e->gens) {
+        for (auto &g : e->graphs) cudaGraphExecDestroy(g.second);
+        e->graphs.clear();
+        e->gens = gens;
     }
     for (;;) {
         std::vector<int> set;

@@ -217,13 +217,111 @@ def run(labels=None, precision="f32", period=PERIOD, steps=STEPS, domain=DOMAIN,
     return out
 
 
+# ---- the flow field around one and three swimmers (Sec. 6, Fig. 13) ---------
+
+FLOW_DOMAIN = (164, 164, 240)
+
+
+def flow_field_scenario(swimmers=1, domain=FLOW_DOMAIN, period=PERIOD):
+    """Design (a) swimmers in the Sec. 6 channel (walls in x and y, periodic
+    along the swimming axis z), drives on throughout.  Reading (the paper
+    does not place them): three swimmers lie side by side across the
+    channel, along x at a quarter of the width apart, centred in y and z."""
+    inf = float("inf")
+    one, _ = design("a", domain, period, steps=0, t_off=(inf, inf))
+    if swimmers == 1:
+        one.name = f"one design (a) swimmer, {domain[0]}x{domain[1]}x{domain[2]} channel"
+        return one
+    if swimmers != 3:
+        raise ValueError("the paper shows one and three swimmers")
+    import copy
+    import dataclasses
+    sc = copy.deepcopy(one)
+    sc.name = f"three design (a) swimmers, {domain[0]}x{domain[1]}x{domain[2]} channel"
+    sc.bodies, sc.springs, sc.drives = [], [], []
+    dx = domain[0] / 4.0
+    for k, off in enumerate((-dx, 0.0, dx)):
+        base = 3 * k
+        for b in one.bodies:
+            sc.bodies.append(dataclasses.replace(b, pos=(b.pos[0] + off, b.pos[1], b.pos[2])))
+        for sp in one.springs:
+            sc.springs.append(dataclasses.replace(sp, i=sp.i + base, j=sp.j + base))
+        for d in one.drives:
+            sc.drives.append(dataclasses.replace(d, body=d.body + base))
+    return sc
+
+
+def flow_field_study(swimmers=1, precision="f32", domain=FLOW_DOMAIN, period=PERIOD, cycles=5, warm_cycles=0):
+    """The velocity field averaged over `cycles` swimming cycles after
+    `warm_cycles` (the device-side running average, lbm_average_*): returns
+    (scenario, mean velocity [3, nz, ny, nx], steps averaged, body states at
+    the start and the end of the window)."""
+    from . import lbm
+    sc = flow_field_scenario(swimmers, domain, period)
+    lat = lbm.from_scenario(sc, precision=precision, options=lbm.OPT_AVERAGE_FORCE)
+    lat.step(warm_cycles * period)
+    start = lat.bodies()
+    lat.average_begin()
+    lat.step(cycles * period)
+    avg, n = lat.average()
+    end = lat.bodies()
+    lat.close()
+    return sc, avg, n, start, end
+
+
+def flow_field_summary(sc, avg, start, end, steps):
+    """Scalars of an averaged field: the mean and largest |u| over the
+    fluid, the mean axial velocity in the swimmers' mid-plane z, and each
+    swimmer's mean speed over the window."""
+    speed = np.sqrt((avg ** 2).sum(axis=0))
+    nz = avg.shape[1]
+    zc = int(round(np.mean([b.pos[2] for b in sc.bodies])))
+    swimmers = len(sc.bodies) // 3
+    v = [float((end[3 * k:3 * k + 3, 2] - start[3 * k:3 * k + 3, 2]).mean() / steps) for k in range(swimmers)]
+    return {"swimmers": swimmers, "steps": int(steps), "mean_speed": float(speed.mean()),
+            "max_speed": float(speed.max()), "midplane_mean_uz": float(avg[2, zc % nz].mean()),
+            "swimmer_speeds": v}
+
+
+def write_pgm(path, plane):
+    """An 8-bit greyscale image of a 2-D array scaled to its range."""
+    a = np.asarray(plane, dtype=np.float64)
+    lo, hi = float(a.min()), float(a.max())
+    img = np.zeros_like(a, dtype=np.uint8) if hi <= lo else ((a - lo) / (hi - lo) * 255.0).astype(np.uint8)
+    with open(path, "wb") as fh:
+        fh.write(b"P5\n%d %d\n255\n" % (img.shape[1], img.shape[0]))
+        fh.write(img[::-1].tobytes())
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--designs", default="".join(DESIGNS))
     ap.add_argument("--json", default=None, help="write the results as JSON to this file")
     ap.add_argument("--from-json", default=None, help="format results written earlier instead of running")
+    ap.add_argument("--flow-field", type=int, choices=(1, 3), default=None,
+                    help="the Sec. 6 flow field of 1 or 3 swimmers averaged over five cycles instead")
+    ap.add_argument("--out-prefix", default=None,
+                    help="with --flow-field: write <prefix>.npy (the mean velocity in the swimmers' x-z plane, "
+                         "[3, nz, nx]) and <prefix>.pgm (its magnitude)")
     args = ap.parse_args(argv)
+    if args.flow_field:
+        import time
+        t0 = time.perf_counter()
+        sc, avg, n, start, end = flow_field_study(args.flow_field, precision=args.precision)
+        res = flow_field_summary(sc, avg, start, end, n)
+        res["wall_s"] = round(time.perf_counter() - t0, 1)
+        res["cells"] = sc.cells
+        print(json.dumps(res, indent=1))
+        if args.out_prefix:
+            yc = int(round(sc.bodies[0].pos[1]))
+            plane = avg[:, :, yc, :]
+            np.save(args.out_prefix + ".npy", plane.astype(np.float32))
+            write_pgm(args.out_prefix + ".pgm", np.sqrt((plane ** 2).sum(axis=0)))
+        if args.json:
+            with open(args.json, "w") as fh:
+                json.dump(res, fh, indent=1)
+        return 0
     if args.from_json:
         with open(args.from_json) as fh:
             res = json.load(fh)

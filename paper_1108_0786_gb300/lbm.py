@@ -38,6 +38,7 @@ EXPORTED = (
     "lbm_create", "lbm_create_ex", "lbm_destroy", "lbm_set_allocator", "lbm_set_stream",
     "lbm_add_body", "lbm_body_properties", "lbm_add_spring", "lbm_set_drive", "lbm_set_drive_window", "lbm_set_drive_axis",
     "lbm_set_body_state", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_steps_done",
+    "lbm_average_begin", "lbm_average_stop", "lbm_average_get",
     "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
     "lbm_tune", "lbm_debug_set", "lbm_autotune", "lbm_kernels_per_step", "lbm_bytes_per_cell",
@@ -97,6 +98,9 @@ def load_library(path: Optional[str] = None):
         "lbm_tune": ([P, I, I], I),
         "lbm_debug_set": ([P, I, ctypes.c_longlong], I),
         "lbm_body_properties": ([I, D, D, D, DP, DP, DP], I),
+        "lbm_average_begin": ([P], I),
+        "lbm_average_stop": ([P], I),
+        "lbm_average_get": ([P, DP, ctypes.POINTER(ctypes.c_longlong)], I),
         "lbm_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "lbm_kernels_per_step": ([P], I),
         "lbm_bytes_per_cell": ([P], I),
@@ -253,6 +257,20 @@ class Lattice:
     def tune(self, cells_per_thread, min_blocks_per_sm=0):
         """Launch shape of the bulk stream-collide kernel (0: default)."""
         return self._check(self._lib.lbm_tune(self._h, int(cells_per_thread), int(min_blocks_per_sm)))
+
+    def average_begin(self):
+        """Start (or restart) the running time average of the velocity field."""
+        return self._check(self._lib.lbm_average_begin(self._h))
+
+    def average_stop(self):
+        return self._check(self._lib.lbm_average_stop(self._h))
+
+    def average(self):
+        """(mean velocity [3, nz, ny, nx], steps averaged)."""
+        out = np.zeros((3,) + self.shape)
+        n = ctypes.c_longlong()
+        self._check(self._lib.lbm_average_get(self._h, _dp(out), ctypes.byref(n)))
+        return out, int(n.value)
 
     def debug_set(self, knob, value):
         """A check of a failure path (DEBUG_EXPIRE_WAITS, DEBUG_CELL_LIST_CAP);
