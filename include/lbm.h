@@ -348,24 +348,43 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
  *
  * Many independent lattices (ensemble members, e.g. one swimmer design per
  * member on its own periodic box, of uneven sizes and step counts) stepped
- * together.  One CUDA graph holds, as parallel branches, CHUNK (16) steps of
- * every member of a set; one launch of it advances the whole set, and the
- * GPU's block scheduler spreads the members' kernels over the SMs.  Members
- * whose step budget runs out drop out of the set (a graph per set is built
- * on first use and kept).  There is no dependency between members: no
- * kernel waits on another.  The paper runs one simulation per design study
- * point; the ensemble is the throughput path for a set of such points.
+ * together.  One CUDA graph advances every member of a set by CHUNK (16)
+ * steps; members whose step budget runs out drop out of the set (a graph
+ * per set is built on first use and kept).
+ *   LBM_ENSEMBLE_BATCHED (default): each step is one launch of each per-step
+ *     kernel (body preparation, remap, boundary cells, links, loads, bulk
+ *     stream-collide, force) over all members of a storage precision: the
+ *     members' grids are flattened into one grid, and each block finds its
+ *     member's record in a device table.  ~8 launches a step for the whole
+ *     set, however many members.  Every member needs the fluid; the bulk
+ *     kernel runs in one shape for all members (lbm_ensemble_autotune), not
+ *     in the members' own.
+ *   LBM_ENSEMBLE_BRANCHES: the members' own step kernels as parallel graph
+ *     branches (7 launches a step per member).
+ * Both give the bits of the members stepped alone.  There is no dependency
+ * between members: no kernel waits on another.  The paper runs one
+ * simulation per design study point; the ensemble is the throughput path
+ * for a set of such points.
  *
  * lbm_ensemble_create: members (n handles, not owned) must share one stream
- * (lbm_set_stream); each keeps its own buffers, bodies, bulk-kernel shape
- * (lbm_tune / lbm_autotune before the first lbm_ensemble_step) and status
- * word.  lbm_ensemble_step advances member i by steps[i] steps (host array
- * of n counts, >= 0): whole chunks through the ensemble graphs, the rest
- * through the member's own step graphs.  Asynchronous, like lbm_step.
+ * (lbm_set_stream); each keeps its own buffers, bodies and status word.
+ * lbm_ensemble_step advances member i by steps[i] steps (host array of n
+ * counts, >= 0): whole chunks through the ensemble graphs, the rest through
+ * the member's own step graphs.  Asynchronous, like lbm_step.
  * lbm_ensemble_sync synchronises and returns the first member error.
- * lbm_ensemble_destroy releases the graphs, not the members. */
+ * lbm_ensemble_destroy releases the graphs and tables, not the members.
+ * lbm_ensemble_set_mode selects the mode (LBM_E_ARG for another value).
+ * lbm_ensemble_autotune times every batched bulk shape that fits all members
+ * of a precision (`trials` launches each, on the populations of the members'
+ * next step, which that step rewrites; the members must be at steps of the
+ * same parity, else LBM_E_STATE) and keeps the fastest; *cells_per_thread
+ * (optional) reports the choice for the first member's precision. */
 typedef struct lbm_ensemble_s lbm_ensemble_t;
+#define LBM_ENSEMBLE_BATCHED  0
+#define LBM_ENSEMBLE_BRANCHES 1
 int lbm_ensemble_create(lbm_t *const *members, int n, lbm_ensemble_t **out);
+int lbm_ensemble_set_mode(lbm_ensemble_t *e, int mode);
+int lbm_ensemble_autotune(lbm_ensemble_t *e, int trials, int *cells_per_thread);
 int lbm_ensemble_step(lbm_ensemble_t *e, const int *steps);
 int lbm_ensemble_sync(lbm_ensemble_t *e);
 int lbm_ensemble_destroy(lbm_ensemble_t *e);

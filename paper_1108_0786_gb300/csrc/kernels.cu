@@ -203,10 +203,17 @@ __device__ void body_loads(const Device &dv, const StepPtrs &sp, int drive_rank,
 // the drive and spring loads of step n, two warps on two SM sub-partitions
 // (an FP64 warp instruction occupies its sub-partition's FP64 pipe for the
 // same time however many lanes it carries)
-__global__ void __launch_bounds__(64) loads_kernel(const Device dv, const StepPtrs sp) {
+__device__ __forceinline__ void loads_body(const Device &dv, const StepPtrs &sp) {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 32) body_loads(dv, sp, lane, dv.ns, 32);
     else body_loads(dv, sp, dv.nd, lane, 32);
+}
+
+__global__ void __launch_bounds__(64) loads_kernel(const Device dv, const StepPtrs sp) { loads_body(dv, sp); }
+
+__global__ void __launch_bounds__(64) loads_batch(const Batch bt) {
+    LBM_BATCH_MEMBER(bt);
+    loads_body(sdv, ssp);
 }
 
 // does the cell span [b0, b0 + bw) meet the span [e0, e0 + ew) on an axis of
@@ -227,7 +234,7 @@ __device__ inline bool spans_meet(int b0, int bw, int e0, int ew, int n, int per
 // boundary kernel's list.
 constexpr int PREP_THREADS = 256;
 
-__global__ void __launch_bounds__(PREP_THREADS) prep_kernel(const Device dv, const StepPtrs sp) {
+__device__ __forceinline__ void prep_body(const Device &dv, const StepPtrs &sp) {
     const Domain d = dv.dom;
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -269,6 +276,13 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(const Device dv, con
     }
 }
 
+__global__ void __launch_bounds__(PREP_THREADS) prep_kernel(const Device dv, const StepPtrs sp) { prep_body(dv, sp); }
+
+__global__ void __launch_bounds__(PREP_THREADS) prep_batch(const Batch bt) {
+    LBM_BATCH_MEMBER(bt);
+    prep_body(sdv, ssp);
+}
+
 // a coordinate of the cube, o + l with o in [0, n) and l < side, wrapped
 // into [0, n) on a periodic axis (one compare unless the cube exceeds the axis)
 __device__ inline int wrap_up(int v, int n) { return v < n ? v : (v - n < n ? v - n : v % n); }
@@ -287,9 +301,9 @@ constexpr int REMAP_LAYERS = 1;         // cube layers a block (more layers seri
 constexpr int REMAP_LIST_BUF = 2048;    // list entries a block gathers before the global append
 static_assert(sizeof(BodyGeom) % sizeof(int) == 0, "geometry records are copied as ints");
 
-__global__ void __launch_bounds__(REMAP_THREADS, 5) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
+__device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp, const Blk &bk, int init_mode) {
     const Domain d = dv.dom;
-    const int b = blockIdx.y;
+    const int b = bk.y;
     const BodyGeom *__restrict__ geo = dv.geom + sp.parity * dv.nb;    // state n
     // body b's candidates (prep_kernel's list), the first REMAP_STAGED of
     // them with their records in shared memory
@@ -298,7 +312,7 @@ __global__ void __launch_bounds__(REMAP_THREADS, 5) remap_kernel(const Device dv
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
     const int side = geo[b].side;
     const int nyb = (side + REMAP_TY - 1) / REMAP_TY;
-    const int lzb = (blockIdx.x / nyb) * REMAP_LAYERS, ly0 = (blockIdx.x % nyb) * REMAP_TY;
+    const int lzb = (bk.x / nyb) * REMAP_LAYERS, ly0 = (bk.x % nyb) * REMAP_TY;
     if (lzb >= side) return;                  // the grid covers the largest body's cube
     // this block's share of the boundary kernel's list, gathered in shared
     // memory and appended with one atomic at the end
@@ -426,14 +440,23 @@ __global__ void __launch_bounds__(REMAP_THREADS, 5) remap_kernel(const Device dv
     }
 }
 
+__global__ void __launch_bounds__(REMAP_THREADS, 5) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
+    remap_body(dv, sp, launch_blk(), init_mode);
+}
+
+__global__ void __launch_bounds__(REMAP_THREADS, 5) remap_batch(const Batch bt) {
+    LBM_BATCH_MEMBER(bt);
+    remap_body(sdv, ssp, sbk, 0);
+}
+
 // Links: block (k, b) scans z-plane k of the cube of side 2 E_b + 3 around
 // floor(X_b) and stores the links (x_f, a) with x_f fluid and x_f + e_a a
 // cell of body b, in (y, x, a) order, into segment (b, k).  Runs only when
 // the remap changed a flag; otherwise the previous lists stand.
-__global__ void links_kernel(const Device dv, const StepPtrs sp) {
+__device__ __forceinline__ void links_body(const Device &dv, const StepPtrs &sp, const Blk &bk) {
     if (dv.changed[sp.parity] == 0) return;
     const Domain d = dv.dom;
-    const int b = blockIdx.y, k = blockIdx.x;
+    const int b = bk.y, k = bk.x;
     const BodyProps pb = dv.props[b];
     const int half = pb.E + 1;
     const int side = 2 * half + 1;
@@ -507,6 +530,13 @@ __global__ void links_kernel(const Device dv, const StepPtrs sp) {
         __syncthreads();
     }
     if (threadIdx.x == 0) *count = base;
+}
+
+__global__ void __launch_bounds__(256) links_kernel(const Device dv, const StepPtrs sp) { links_body(dv, sp, launch_blk()); }
+
+__global__ void __launch_bounds__(256) links_batch(const Batch bt) {
+    LBM_BATCH_MEMBER(bt);
+    links_body(sdv, ssp, sbk);
 }
 
 // a stored deviation in FP32 (exact for FP32, FP16 times its power-of-two
@@ -760,9 +790,9 @@ __device__ inline long long to_fixed(float v) {
 // rounding, the variable part is ~1e-3 of a term, and integer sums make
 // the result independent of the order of the blocks' atomic additions.
 template <typename T>
-__global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, const StepPtrs sp) {
+__device__ __forceinline__ void force_body(const Device &dv, const StepPtrs &sp, const Blk &bk) {
     const Domain d = dv.dom;
-    const int b = blockIdx.y, kb = blockIdx.x;
+    const int b = bk.y, kb = bk.x;
     const BodyProps pb = dv.props[b];
     const int side = 2 * (pb.E + 1) + 1;
     const int *counts = dv.seg_count + (long long)b * dv.link_side;
@@ -968,7 +998,7 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last_of_body = atomicAdd(dv.body_done + b, 1u) == gridDim.x - 1;
+        last_of_body = atomicAdd(dv.body_done + b, 1u) == (unsigned)bk.gx - 1;
     }
     __syncthreads();
     if (!last_of_body || threadIdx.x >= 32) return;
@@ -978,10 +1008,28 @@ __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, c
     if (threadIdx.x != 0) return;
     dv.body_done[b] = 0u;
     __threadfence();
-    if (atomicAdd(dv.blocks_done, 1u) != gridDim.y - 1) return;
+    if (atomicAdd(dv.blocks_done, 1u) != (unsigned)bk.gy - 1) return;
     __threadfence();
     *dv.blocks_done = 0u;
     finish_step(dv, sp);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, const StepPtrs sp) {
+    force_body<T>(dv, sp, launch_blk());
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FORCE_THREADS) force_batch(const Batch bt) {
+    LBM_BATCH_MEMBER(bt);
+    force_body<T>(sdv, ssp, sbk);
+}
+
+// the end of a step of a lattice without bodies: the step counter advances
+// (BF16 storage draws its rounding bits from it) and the next epoch's change
+// flag starts clear
+__global__ void tick_kernel(const Device dv, const StepPtrs sp) {
+    if (threadIdx.x == 0) finish_step(dv, sp);
 }
 
 // the rigid-body step alone (bodies without fluid), one block: the loads,
@@ -1114,6 +1162,44 @@ void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
 
 void launch_integrate(const Device &dv, const StepPtrs &sp, int with_fluid, cudaStream_t s) {
     integrate_kernel<<<1, 256, 0, s>>>(dv, sp, with_fluid);
+}
+
+void launch_tick(const Device &dv, const StepPtrs &sp, cudaStream_t s) { tick_kernel<<<1, 32, 0, s>>>(dv, sp); }
+
+// the grids of launch_remap, launch_links and launch_force for one lattice
+void batch_grid_small(const Device &dv, int k, int g[3]) {
+    g[0] = g[1] = g[2] = 0;
+    if (dv.nb == 0) return;
+    const int side = dv.remap_side;
+    switch (k) {
+    case BK_PREP: case BK_LOADS: g[0] = g[1] = g[2] = 1; break;
+    case BK_REMAP:
+        g[0] = ((side + REMAP_TY - 1) / REMAP_TY) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS);
+        g[1] = dv.nb; g[2] = 1;
+        break;
+    case BK_LINKS: g[0] = dv.link_side; g[1] = dv.nb; g[2] = 1; break;
+    case BK_FORCE: g[0] = FORCE_BLOCKS; g[1] = dv.nb; g[2] = 1; break;
+    default: break;
+    }
+}
+
+void launch_batch_small(int k, const Batch &bt, unsigned blocks, int precision, cudaStream_t s) {
+    if (blocks == 0) return;
+    switch (k) {
+    case BK_PREP: prep_batch<<<blocks, PREP_THREADS, 0, s>>>(bt); break;
+    case BK_REMAP: remap_batch<<<blocks, dim3(REMAP_TX, REMAP_TY), 0, s>>>(bt); break;
+    case BK_LINKS: links_batch<<<blocks, 256, 0, s>>>(bt); break;
+    case BK_LOADS: loads_batch<<<blocks, 64, 0, s>>>(bt); break;
+    case BK_FORCE:
+        switch (precision) {
+        case 0: force_batch<double><<<blocks, FORCE_THREADS, 0, s>>>(bt); break;
+        case 1: force_batch<float><<<blocks, FORCE_THREADS, 0, s>>>(bt); break;
+        case 2: force_batch<__half><<<blocks, FORCE_THREADS, 0, s>>>(bt); break;
+        default: force_batch<__nv_bfloat16><<<blocks, FORCE_THREADS, 0, s>>>(bt); break;
+        }
+        break;
+    default: break;
+    }
 }
 
 template <typename O>

@@ -238,6 +238,76 @@ struct Device {
     long long *avg_n;       // steps added to avg_u
 };
 
+// ---- batched launches over the members of an ensemble ------------------------
+//
+// Each per-step kernel is a body run by a block at block coordinates within
+// one lattice's grid: the launch's own (a single lattice), or, in a batched
+// launch over several lattices (members), the block's place in its member's
+// grid.  A batched launch flattens the members' grids into one 1-D grid:
+// member m owns the blocks [first[m], first[m + 1]).  Its block looks up its
+// member, copies the member's record and step pointers into shared memory
+// and runs the same body, so one launch does the work of one launch per
+// member, with no wait between blocks.
+struct Blk {
+    int x, y, z;        // block index within the lattice's grid
+    int gx, gy, gz;     // that grid's dimensions
+};
+
+__device__ __forceinline__ Blk launch_blk() {
+    return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
+}
+
+struct Batch {
+    const Device *dv;       // [members] member records
+    const StepPtrs *sp;     // [2][members] step pointers by step parity
+    const int *first;       // [members + 1] first flattened block of each member (this kernel's grids)
+    const int *grid;        // [members][3] each member's grid (this kernel's)
+    int members;
+    int parity;             // step parity of this launch
+};
+
+// the member record, step pointers and block coordinates of this block of a
+// batched launch, in shared memory (every thread of the block calls this)
+__device__ inline void batch_member(const Batch &bt, Device &sdv, StepPtrs &ssp, Blk &sbk) {
+    __shared__ int s_m;
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+        const int blk = (int)blockIdx.x;
+        int lo = 0, hi = bt.members - 1;        // the member m with first[m] <= blk < first[m + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bt.first[mid] <= blk) lo = mid; else hi = mid - 1;
+        }
+        const int m = lo;
+        s_m = m;
+        const int l = blk - bt.first[m];
+        const int gx = bt.grid[3 * m], gy = bt.grid[3 * m + 1], gz = bt.grid[3 * m + 2];
+        sbk = Blk{l % gx, (l / gx) % gy, l / (gx * gy), gx, gy, gz};
+    }
+    __syncthreads();
+    const int m = s_m;
+    const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    static_assert(sizeof(Device) % 4 == 0 && sizeof(StepPtrs) % 4 == 0, "records are copied as words");
+    const int *src = reinterpret_cast<const int *>(bt.dv + m);
+    int *dst = reinterpret_cast<int *>(&sdv);
+    for (int i = tid; i < (int)(sizeof(Device) / 4); i += nt) dst[i] = __ldg(src + i);
+    const int *ssrc = reinterpret_cast<const int *>(bt.sp + bt.parity * bt.members + m);
+    int *sdst = reinterpret_cast<int *>(&ssp);
+    for (int i = tid; i < (int)(sizeof(StepPtrs) / 4); i += nt) sdst[i] = __ldg(ssrc + i);
+    __syncthreads();
+}
+
+// the per-step kernels a batched step launches, in step order
+enum BatchKernel { BK_PREP, BK_REMAP, BK_BOUNDARY, BK_WALLS, BK_LINKS, BK_LOADS, BK_BULK, BK_FORCE, BK_COUNT };
+
+// the start of a batched kernel: sdv, ssp and sbk are this block's member
+// record, step pointers and block coordinates
+#define LBM_BATCH_MEMBER(bt)          \
+    __shared__ Device sdv;            \
+    __shared__ StepPtrs ssp;          \
+    __shared__ Blk sbk;               \
+    batch_member((bt), sdv, ssp, sbk)
+
 // pointers of one reverse step n of the cell part (adjoint.cu)
 struct AdjPtrs {
     const void *G;                  // post-collision populations of step n (storage type)
@@ -284,10 +354,22 @@ void prepare_bulk_variants();           // host: shared-memory opt-in of the sta
 void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_integrate(const Device &dv, const StepPtrs &sp, int with_fluid, cudaStream_t s);
+void launch_tick(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_export(const Device &dv, const void *pop, const uint8_t *flags, const uint8_t *bid,
                    int what, int mask_solid, void *out, int dtype, cudaStream_t s);
 void launch_import_pop(const Device &dv, void *pop, const double *in, cudaStream_t s);
 void launch_average(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+
+// batched launches (ensembles): the grid g[3] of kernel k of lattice dv (all
+// zero when it does not run), and one launch of k over `blocks` flattened
+// blocks of the members of bt (all of storage `precision`); for BK_BULK,
+// `variant` indexes the batched bulk shapes (batch_bulk_shape)
+void batch_grid_small(const Device &dv, int k, int g[3]);                     // kernels.cu
+void launch_batch_small(int k, const Batch &bt, unsigned blocks, int precision, cudaStream_t s);
+void batch_grid_cells(const Device &dv, int k, int variant, int g[3]);        // stream_collide.cu
+void launch_batch_cells(int k, int variant, const Batch &bt, unsigned blocks, int precision, cudaStream_t s);
+// batched bulk shape i of a precision: its cells per thread, or 0 past the list
+int batch_bulk_shape(int precision, int i);
 int adjoint_part_stride(const Device &dv);
 void launch_adj_integrate(const Device &dv, const AdjBody &ab, cudaStream_t s);
 void launch_adj_bulk(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s);

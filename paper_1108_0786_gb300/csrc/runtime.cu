@@ -8,6 +8,7 @@
 #include <vector>
 #include <cmath>
 #include <algorithm>
+#include <climits>
 
 #include "../../include/lbm.h"
 #include "lbm_internal.cuh"
@@ -180,6 +181,8 @@ void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bo
         run(LBM_KERNEL_FORCE, s, [&] { lbm::launch_force(h->dv, sp, s); });
     } else if (bodies) {
         run(LBM_KERNEL_INTEGRATE, s, [&] { lbm::launch_integrate(h->dv, sp, 0, s); });
+    } else if (fl) {
+        lbm::launch_tick(h->dv, sp, s);             // the step counter of a lattice without bodies
     }
     // the running velocity average reads the populations this step wrote
     if (fl && h->dv.avg_u) lbm::launch_average(h->dv, sp, s);
@@ -204,6 +207,7 @@ int kernels_per_step(const lbm_t *h) {
     if (fl) n += (bodies ? 1 : 0) + (walls ? 1 : 0);        // boundary cells
     if (bodies && fl) n += 3;                               // links, drive and spring loads, force + rigid-body step
     if (bodies && !fl) n += 1;                              // rigid-body step alone
+    if (!bodies && fl) n += 1;                              // step counter
     if (fl && h->dv.avg_u) n += 1;                          // running velocity average
     return n;
 }
@@ -1352,15 +1356,34 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
 
 // ---- ensembles ---------------------------------------------------------------
 
+// one storage precision's members of a batched set: the device tables of
+// its batched launches (member records, step pointers by parity, and per
+// kernel the members' flattened block ranges and grids)
+struct EnsGroup {
+    int precision = 1;
+    std::vector<int> members;               // ensemble indices
+    void *mem = nullptr;                    // the tables, one allocation (first member's allocator)
+    lbm::Batch bt[lbm::BK_COUNT];           // parity 0 (parity 1 differs only in .parity)
+    unsigned blocks[lbm::BK_COUNT] = {};
+};
+
+struct EnsGraph {
+    std::vector<int> set;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<EnsGroup> groups;           // batched mode only
+};
+
 struct lbm_ensemble_s {
     std::vector<lbm_t *> members;
     cudaStream_t stream = nullptr;          // the members' common stream
     cudaStream_t cap = nullptr;             // capture origin
-    cudaEvent_t fork = nullptr;
+    cudaStream_t side = nullptr;            // batched mode: boundary cells, links and loads beside the bulk kernel
+    cudaEvent_t fork = nullptr, bjoin = nullptr;
     std::vector<cudaEvent_t> join;          // one per member
-    // one graph per set of members advanced together: CHUNK_STEPS steps of
-    // each as parallel branches
-    std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> graphs;
+    int mode = LBM_ENSEMBLE_BATCHED;
+    int variant[4] = {-1, -1, -1, -1};      // batched bulk shape per precision (-1: the default)
+    // one graph per set of members advanced together (CHUNK_STEPS steps)
+    std::vector<EnsGraph> graphs;
     std::vector<unsigned> gens;             // the members' graph generations the cached graphs were built at
     std::string err;
 };
@@ -1372,41 +1395,206 @@ int ens_fail(lbm_ensemble_t *e, int code, const char *msg) {
     return code;
 }
 
-void ens_release(lbm_ensemble_t *e) {
-    for (auto &g : e->graphs) cudaGraphExecDestroy(g.second);
+void ens_drop_graphs(lbm_ensemble_t *e) {
+    if (!e->graphs.empty() && e->stream) cudaStreamSynchronize(e->stream);
+    for (auto &g : e->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (auto &grp : g.groups) dfree(e->members[grp.members[0]], grp.mem);
+    }
     e->graphs.clear();
+}
+
+void ens_release(lbm_ensemble_t *e) {
+    ens_drop_graphs(e);
     for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
     e->join.clear();
     if (e->fork) cudaEventDestroy(e->fork);
+    if (e->bjoin) cudaEventDestroy(e->bjoin);
     if (e->cap) cudaStreamDestroy(e->cap);
-    e->fork = nullptr;
-    e->cap = nullptr;
+    if (e->side) cudaStreamDestroy(e->side);
+    e->fork = e->bjoin = nullptr;
+    e->cap = e->side = nullptr;
+}
+
+// can the members of `set` run as batched launches?  (every member has fluid;
+// members without bodies skip the body kernels)
+bool ens_batchable(const lbm_ensemble_t *e, const std::vector<int> &set) {
+    for (int i : set)
+        if (!fluid(e->members[i])) return false;
+    return true;
+}
+
+int ens_variant(const lbm_ensemble_t *e, int precision, const std::vector<int> &members) {
+    int v = e->variant[precision];
+    auto fits = [&](int var) {
+        const int vec = lbm::batch_bulk_shape(precision, var);
+        if (vec == 0) return false;
+        for (int i : members)
+            if (e->members[i]->nx % vec) return false;
+        return true;
+    };
+    if (v >= 0 && fits(v)) return v;
+    for (int var : {1, 0})                  // two cells a thread where every nx allows it, else one
+        if (fits(var)) return var;
+    return 0;
+}
+
+// the device tables of one precision group of a batched set
+int ens_group_tables(lbm_ensemble_t *e, EnsGroup &g) {
+    const int M = (int)g.members.size();
+    lbm_t *h0 = e->members[g.members[0]];
+    const int variant = ens_variant(e, g.precision, g.members);
+    std::vector<lbm::Device> dvs(M);
+    std::vector<lbm::StepPtrs> sps(2 * M);
+    for (int j = 0; j < M; ++j) {
+        lbm_t *h = e->members[g.members[j]];
+        dvs[j] = h->dv;
+        sps[j] = step_ptrs(h, 0);
+        sps[M + j] = step_ptrs(h, 1);
+    }
+    std::vector<int> tab;                   // per kernel: first[M + 1], grid[3 M]
+    std::vector<size_t> off(lbm::BK_COUNT);
+    for (int k = 0; k < lbm::BK_COUNT; ++k) {
+        off[k] = tab.size();
+        tab.resize(tab.size() + (M + 1) + 3 * M);
+        int *first = tab.data() + off[k], *grid = first + M + 1;
+        long long total = 0;
+        for (int j = 0; j < M; ++j) {
+            int gd[3];
+            if (k == lbm::BK_BOUNDARY || k == lbm::BK_WALLS || k == lbm::BK_BULK)
+                lbm::batch_grid_cells(dvs[j], k, variant, gd);
+            else
+                lbm::batch_grid_small(dvs[j], k, gd);
+            first[j] = (int)total;
+            for (int i = 0; i < 3; ++i) grid[3 * j + i] = gd[i];
+            total += (long long)gd[0] * gd[1] * gd[2];
+        }
+        first[M] = (int)total;
+        if (total > INT_MAX) return ens_fail(e, LBM_E_ARG, "a batched launch exceeds 2^31 blocks");
+        g.blocks[k] = (unsigned)total;
+    }
+    const size_t b_dv = sizeof(lbm::Device) * M, b_sp = sizeof(lbm::StepPtrs) * 2 * M;
+    const size_t o_sp = (b_dv + 255) / 256 * 256, o_tab = o_sp + (b_sp + 255) / 256 * 256;
+    const size_t bytes = o_tab + sizeof(int) * tab.size();
+    g.mem = dalloc(h0, bytes);
+    if (!g.mem) return ens_fail(e, LBM_E_OOM, "device allocation of the ensemble's tables failed");
+    char *base = static_cast<char *>(g.mem);
+    cudaError_t err = cudaMemcpy(base, dvs.data(), b_dv, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(base + o_sp, sps.data(), b_sp, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(base + o_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
+    const int *dtab = reinterpret_cast<const int *>(base + o_tab);
+    for (int k = 0; k < lbm::BK_COUNT; ++k) {
+        lbm::Batch &b = g.bt[k];
+        b.dv = reinterpret_cast<const lbm::Device *>(base);
+        b.sp = reinterpret_cast<const lbm::StepPtrs *>(base + o_sp);
+        b.first = dtab + off[k];
+        b.grid = dtab + off[k] + M + 1;
+        b.members = M;
+        b.parity = 0;
+    }
+    e->variant[g.precision] = variant;
+    return LBM_OK;
+}
+
+// one batched step of every group: the kernels of enqueue_step, each as one
+// launch over the members of a group
+void ens_enqueue_batched(lbm_ensemble_t *e, std::vector<EnsGroup> &groups, int p) {
+    auto small = [&](int k, cudaStream_t st) {
+        for (auto &g : groups) {
+            lbm::Batch b = g.bt[k];
+            b.parity = p;
+            lbm::launch_batch_small(k, b, g.blocks[k], g.precision, st);
+        }
+    };
+    auto cells = [&](int k, cudaStream_t st) {
+        for (auto &g : groups) {
+            lbm::Batch b = g.bt[k];
+            b.parity = p;
+            lbm::launch_batch_cells(k, e->variant[g.precision], b, g.blocks[k], g.precision, st);
+        }
+    };
+    small(lbm::BK_PREP, e->cap);
+    small(lbm::BK_REMAP, e->cap);
+    cudaEventRecord(e->fork, e->cap);
+    cudaStreamWaitEvent(e->side, e->fork, 0);
+    cells(lbm::BK_BOUNDARY, e->side);
+    cells(lbm::BK_WALLS, e->side);
+    small(lbm::BK_LINKS, e->side);
+    small(lbm::BK_LOADS, e->side);
+    cudaEventRecord(e->bjoin, e->side);
+    cells(lbm::BK_BULK, e->cap);
+    cudaStreamWaitEvent(e->cap, e->bjoin, 0);
+    small(lbm::BK_FORCE, e->cap);
+    for (auto &g : groups)
+        for (int i : g.members) {
+            lbm_t *h = e->members[i];
+            const lbm::StepPtrs sp = step_ptrs(h, p);
+            if (nb(h) == 0) lbm::launch_tick(h->dv, sp, e->cap);
+            if (h->dv.avg_u) lbm::launch_average(h->dv, sp, e->cap);
+        }
 }
 
 // the graph advancing the members `set` by CHUNK_STEPS steps each (built on
-// first use): fork from the capture origin to every member's capture
-// stream, its chunk of steps, join back
+// first use).  Batched mode: per step, one launch of each per-step kernel
+// over all members of a storage precision.  Branch mode (and sets that
+// cannot be batched): fork from the capture origin to every member's
+// capture stream, its chunk of steps, join back.
 int ens_graph(lbm_ensemble_t *e, const std::vector<int> &set, cudaGraphExec_t *out) {
     for (auto &g : e->graphs)
-        if (g.first == set) { *out = g.second; return LBM_OK; }
+        if (g.set == set) { *out = g.exec; return LBM_OK; }
+    EnsGraph eg;
+    eg.set = set;
+    const bool batched = e->mode == LBM_ENSEMBLE_BATCHED && ens_batchable(e, set);
+    if (batched) {
+        for (int i : set) {
+            const int prec = e->members[i]->precision;
+            EnsGroup *g = nullptr;
+            for (auto &x : eg.groups)
+                if (x.precision == prec) g = &x;
+            if (!g) {
+                eg.groups.emplace_back();
+                g = &eg.groups.back();
+                g->precision = prec;
+            }
+            g->members.push_back(i);
+        }
+        for (auto &g : eg.groups) {
+            const int rc = ens_group_tables(e, g);
+            if (rc) {
+                for (auto &x : eg.groups)
+                    if (x.mem) dfree(e->members[x.members[0]], x.mem);
+                return rc;
+            }
+        }
+    }
     cudaGraph_t g = nullptr;
     cudaError_t err = cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal);
-    if (err != cudaSuccess) return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
-    cudaEventRecord(e->fork, e->cap);
-    for (int i : set) {
-        lbm_t *h = e->members[i];
-        cudaStreamWaitEvent(h->cap, e->fork, 0);
-        for (int k = 0; k < CHUNK_STEPS; ++k) enqueue_step(h, k & 1, h->cap, nullptr, nullptr, true);
-        cudaEventRecord(e->join[i], h->cap);
-        cudaStreamWaitEvent(e->cap, e->join[i], 0);
+    if (err == cudaSuccess) {
+        if (batched) {
+            for (int k = 0; k < CHUNK_STEPS; ++k) ens_enqueue_batched(e, eg.groups, k & 1);
+        } else {
+            cudaEventRecord(e->fork, e->cap);
+            for (int i : set) {
+                lbm_t *h = e->members[i];
+                cudaStreamWaitEvent(h->cap, e->fork, 0);
+                for (int k = 0; k < CHUNK_STEPS; ++k) enqueue_step(h, k & 1, h->cap, nullptr, nullptr, true);
+                cudaEventRecord(e->join[i], h->cap);
+                cudaStreamWaitEvent(e->cap, e->join[i], 0);
+            }
+        }
+        err = cudaStreamEndCapture(e->cap, &g);
     }
-    err = cudaStreamEndCapture(e->cap, &g);
-    if (err != cudaSuccess) return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
     cudaGraphExec_t x = nullptr;
-    err = cudaGraphInstantiate(&x, g, 0);
-    cudaGraphDestroy(g);
-    if (err != cudaSuccess) return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
-    e->graphs.emplace_back(set, x);
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&x, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (err != cudaSuccess) {
+        for (auto &grp : eg.groups)
+            if (grp.mem) dfree(e->members[grp.members[0]], grp.mem);
+        return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
+    }
+    eg.exec = x;
+    e->graphs.push_back(std::move(eg));
     *out = x;
     return LBM_OK;
 }
@@ -1431,7 +1619,9 @@ int lbm_ensemble_create(lbm_t *const *members, int n, lbm_ensemble_t **out) {
     e->members.assign(members, members + n);
     e->stream = members[0]->stream;
     cudaError_t err = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->bjoin, cudaEventDisableTiming);
     for (int i = 0; i < n && err == cudaSuccess; ++i) {
         cudaEvent_t ev = nullptr;
         err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -1476,8 +1666,7 @@ int lbm_ensemble_step(lbm_ensemble_t *e, const int *steps) {
     std::vector<unsigned> gens(n);
     for (int i = 0; i < n; ++i) gens[i] = e->members[i]->graph_gen;
     if (gens != e->gens) {
-        for (auto &g : e->graphs) cudaGraphExecDestroy(g.second);
-        e->graphs.clear();
+        ens_drop_graphs(e);
         e->gens = gens;
     }
     for (;;) {
@@ -1519,6 +1708,74 @@ int lbm_ensemble_sync(lbm_ensemble_t *e) {
 }
 
 const char *lbm_ensemble_last_error(lbm_ensemble_t *e) { return e ? e->err.c_str() : "null handle"; }
+
+int lbm_ensemble_set_mode(lbm_ensemble_t *e, int mode) {
+    if (!e || (mode != LBM_ENSEMBLE_BATCHED && mode != LBM_ENSEMBLE_BRANCHES)) return LBM_E_ARG;
+    if (mode != e->mode) {
+        ens_drop_graphs(e);
+        e->mode = mode;
+    }
+    return LBM_OK;
+}
+
+int lbm_ensemble_autotune(lbm_ensemble_t *e, int trials, int *cells_per_thread) {
+    if (!e || trials < 1) return LBM_E_ARG;
+    const int n = (int)e->members.size();
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) {
+        all[i] = i;
+        lbm_t *h = e->members[i];
+        int rc = ensure_device(h);
+        if (rc == LBM_OK) rc = sync_and_check(h);
+        if (rc) return ens_fail(e, rc, h->err.c_str());
+        if ((h->steps & 1) != (e->members[0]->steps & 1))
+            return ens_fail(e, LBM_E_STATE, "members must be at steps of the same parity to time the bulk shapes");
+    }
+    if (!ens_batchable(e, all)) return ens_fail(e, LBM_E_STATE, "a member without fluid cannot be batched");
+    const int p = (int)(e->members[0]->steps & 1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return ens_fail(e, LBM_E_CUDA, "event creation failed");
+    int rc = LBM_OK;
+    for (int prec = 0; prec < 4 && rc == LBM_OK; ++prec) {
+        EnsGroup g;
+        g.precision = prec;
+        for (int i = 0; i < n; ++i)
+            if (e->members[i]->precision == prec) g.members.push_back(i);
+        if (g.members.empty()) continue;
+        float best = 1e30f;
+        int best_v = -1;
+        for (int v = 0; lbm::batch_bulk_shape(prec, v) > 0 && rc == LBM_OK; ++v) {
+            bool fits = true;
+            for (int i : g.members) fits = fits && e->members[i]->nx % lbm::batch_bulk_shape(prec, v) == 0;
+            if (!fits) continue;
+            e->variant[prec] = v;
+            if ((rc = ens_group_tables(e, g))) break;
+            // the populations of every member's next step, which that step rewrites in full
+            lbm::Batch b = g.bt[lbm::BK_BULK];
+            b.parity = p;
+            lbm::launch_batch_cells(lbm::BK_BULK, v, b, g.blocks[lbm::BK_BULK], prec, e->stream);
+            cudaEventRecord(e0, e->stream);
+            for (int t = 0; t < trials; ++t)
+                lbm::launch_batch_cells(lbm::BK_BULK, v, b, g.blocks[lbm::BK_BULK], prec, e->stream);
+            cudaEventRecord(e1, e->stream);
+            cudaError_t err = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            dfree(e->members[g.members[0]], g.mem);
+            g.mem = nullptr;
+            if (err != cudaSuccess) { rc = ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err)); break; }
+            if (ms < best) { best = ms; best_v = v; }
+        }
+        e->variant[prec] = best_v;
+        if (cells_per_thread && prec == e->members[0]->precision && best_v >= 0)
+            *cells_per_thread = lbm::batch_bulk_shape(prec, best_v);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ens_drop_graphs(e);             // the graphs bake in the bulk shape
+    return rc;
+}
 
 int lbm_kernels_per_step(lbm_t *h) { return h ? kernels_per_step(h) : LBM_E_ARG; }
 

@@ -335,17 +335,14 @@ template <typename T> __device__ __forceinline__ Dither dither_for(long long c, 
     else return Dither{};
 }
 
-// MINB == 1 leaves the register budget to the compiler (an explicit minimum
-// of one block lets it spend far more registers than it needs)
-template <typename T, int V, int BX, int BY, int MINB>
-__global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB)
-bulk_kernel(const Device dv, const StepPtrs sp) {
+template <typename T, int V, int BX, int BY>
+__device__ __forceinline__ void bulk_body(const Device &dv, const StepPtrs &sp, const Blk &bk) {
     using Cd = typename Codec<T>::C;
     const Domain d = dv.dom;
     const int nxq = d.nx / V;
-    int xq = blockIdx.x * BX + threadIdx.x;
-    int y = blockIdx.y * BY + threadIdx.y;
-    const int z = blockIdx.z;
+    int xq = bk.x * BX + threadIdx.x;
+    int y = bk.y * BY + threadIdx.y;
+    const int z = bk.z;
     const bool active = xq < nxq && y < d.ny;
     xq = min(xq, nxq - 1);              // inactive lanes still join the shuffles
     y = min(y, d.ny - 1);
@@ -435,6 +432,20 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
             if (fl[i] == 0 || (fl[i] & F_SOLID)) dst[(long long)b * C + c0 + i] = st(f[b][i], b);
 }
 
+// MINB == 1 leaves the register budget to the compiler (an explicit minimum
+// of one block lets it spend far more registers than it needs)
+template <typename T, int V, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB)
+bulk_kernel(const Device dv, const StepPtrs sp) {
+    bulk_body<T, V, BX, BY>(dv, sp, launch_blk());
+}
+
+template <typename T, int V, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk_batch(const Batch bt) {
+    LBM_BATCH_MEMBER(bt);
+    bulk_body<T, V, BX, BY>(sdv, ssp, sbk);
+}
+
 // 16-bit values packed two to a 32-bit word (the lower address in the low
 // half): widening to FP32 and narrowing back (round to nearest even)
 template <typename T> __device__ __forceinline__ float half_lo(unsigned w);
@@ -453,9 +464,6 @@ template <> __device__ __forceinline__ float half_lo<__nv_bfloat16>(unsigned w) 
 template <> __device__ __forceinline__ float half_hi<__nv_bfloat16>(unsigned w) {
     return __uint_as_float(w & 0xffff0000u);
 }
-template <> __device__ __forceinline__ unsigned half_bits<__nv_bfloat16>(float v) {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
-}
 // the stored bits of population a of a cell: FP16 to nearest, BF16 stochastically
 template <typename T> __device__ __forceinline__ unsigned store_bits(float v, const Dither &d, int a) {
     if constexpr (std::is_same<T, __nv_bfloat16>::value) return bf16_sr_bits(v, d, a);
@@ -470,17 +478,16 @@ template <typename T> __device__ __forceinline__ unsigned store_bits(float v, co
 // shuffled from the neighbouring lane); a cell's 19 values are widened to
 // FP32 just before its collision (collide_lean, the row-staged kernel's
 // arithmetic) and narrowed back into their half-words after it.
-template <typename T, int V, int BX, int BY, int MINB>
-__global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB)
-bulk16_kernel(const Device dv, const StepPtrs sp) {
+template <typename T, int V, int BX, int BY>
+__device__ __forceinline__ void bulk16_body(const Device &dv, const StepPtrs &sp, const Blk &bk) {
     static_assert(sizeof(T) == 2 && V % 2 == 0, "two 16-bit cells a word");
     constexpr int W = V / 2;
     using RawV = typename Raw<2 * V>::type;
     const Domain d = dv.dom;
     const int nxq = d.nx / V;
-    int xq = blockIdx.x * BX + threadIdx.x;
-    int y = blockIdx.y * BY + threadIdx.y;
-    const int z = blockIdx.z;
+    int xq = bk.x * BX + threadIdx.x;
+    int y = bk.y * BY + threadIdx.y;
+    const int z = bk.z;
     const bool active = xq < nxq && y < d.ny;
     xq = min(xq, nxq - 1);              // inactive lanes still join the shuffles
     y = min(y, d.ny - 1);
@@ -565,6 +572,18 @@ bulk16_kernel(const Device dv, const StepPtrs sp) {
                 dst[(long long)b * C + c0 + i] = (unsigned short)((i & 1) ? w[b][i >> 1] >> 16 : w[b][i >> 1] & 0xffffu);
 }
 
+template <typename T, int V, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB)
+bulk16_kernel(const Device dv, const StepPtrs sp) {
+    bulk16_body<T, V, BX, BY>(dv, sp, launch_blk());
+}
+
+template <typename T, int V, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk16_batch(const Batch bt) {
+    LBM_BATCH_MEMBER(bt);
+    bulk16_body<T, V, BX, BY>(sdv, ssp, sbk);
+}
+
 // Velocity of body b's surface at lattice point p in the compute type R:
 // FP64 throughout for FP64 storage; otherwise the minimum-image offset in
 // FP64 and V + W x offset in R (the moving-wall term is ~1e-4 and its R
@@ -626,23 +645,23 @@ __device__ inline void wall_velocity_wrapped(const Domain &d, const WallBody &b,
 // Cells with a non-zero flag byte: refill, bounce-back at walls and moving
 // obstacles, then LBGK.  mode 0: the cells the remap listed (fluid with
 // F_NEAR or F_SOLID_PREV), one a thread, on a grid sized for the longest
-// possible list; mode 1: blockIdx.y = wall face (axis * 2 + side), the
+// possible list; mode 1: block row y = wall face (axis * 2 + side), the
 // face's cells.  A cell in
 // both sets, or listed twice, is computed more than once with the same
 // result.  Every load a cell needs is issued before any of them is used, so
 // a thread waits for memory about twice instead of once per direction.
 template <typename T>
-__global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const StepPtrs sp, int mode) {
+__device__ __forceinline__ void boundary_body(const Device &dv, const StepPtrs &sp, const Blk &bk, int mode) {
     using Cd = typename Codec<T>::C;
     const Domain d = dv.dom;
     // 32/16-bit storage: the bodies of step n-1 with their centres wrapped
     // into the domain, so that a link's minimum-image offset is an integer
     // difference, two compares and the FP32 position within the cell
     __shared__ WallBody wb[sizeof(T) == 8 ? 1 : LBM_MAX_BODIES_DEV];
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = bk.x * blockDim.x + threadIdx.x;
     // the count may pass the capacity after an overflow (reported as an error): never read past it
     const int listed = mode == 0 ? (int)min((long long)*dv.bcount, dv.blist_cap) : 0;
-    if (mode == 0 && (int)(blockIdx.x * blockDim.x) >= listed) return;      // the whole block is past the list
+    if (mode == 0 && (int)(bk.x * blockDim.x) >= listed) return;      // the whole block is past the list
     if constexpr (sizeof(T) != 8) {
         for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) wb[k] = wall_body(dv.geom[(sp.parity ^ 1) * dv.nb + k]);
         __syncthreads();
@@ -656,7 +675,7 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
         y = (int)((cl / nxu) % nyu);
         z = (int)(cl / (nxu * nyu));
     } else {
-        const int axis = blockIdx.y >> 1, hi = blockIdx.y & 1;
+        const int axis = bk.y >> 1, hi = bk.y & 1;
         const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
         if (per[axis]) return;
         const int ua = axis == 0 ? 1 : 0, va = axis == 2 ? 1 : 2;
@@ -791,6 +810,18 @@ __global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const St
 #pragma unroll
         for (int b = 0; b < Q; ++b) dst[(long long)b * C + c] = Codec<T>::st(f[b], dv.f16_scale);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) boundary_kernel(const Device dv, const StepPtrs sp, int mode) {
+    boundary_body<T>(dv, sp, launch_blk(), mode);
+}
+
+// a batched launch of one mode over the members
+template <typename T>
+__global__ void __launch_bounds__(256) boundary_batch(const Batch bt, int mode) {
+    LBM_BATCH_MEMBER(bt);
+    boundary_body<T>(sdv, ssp, sbk, mode);
 }
 
 // ---- TMA row-staged variant ---------------------------------------------------
@@ -1156,6 +1187,86 @@ void launch_boundary_fix(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     case 1: launch_boundary<float>(dv, sp, s); break;
     case 2: launch_boundary<__half>(dv, sp, s); break;
     default: launch_boundary<__nv_bfloat16>(dv, sp, s); break;
+    }
+}
+
+// ---- batched launches (ensembles) ------------------------------------------
+
+namespace {
+
+constexpr int BATCH_BX = 32, BATCH_BY = 8;      // ensembles' boxes are narrow: 32 x 8 threads a block
+
+template <typename T, int V>
+void bulk_batch_launch(const Batch &bt, unsigned blocks, cudaStream_t s) {
+    if constexpr (sizeof(T) == 2 && V % 2 == 0)
+        bulk16_batch<T, V, BATCH_BX, BATCH_BY, 1><<<blocks, dim3(BATCH_BX, BATCH_BY), 0, s>>>(bt);
+    else
+        bulk_batch<T, V, BATCH_BX, BATCH_BY, 1><<<blocks, dim3(BATCH_BX, BATCH_BY), 0, s>>>(bt);
+}
+
+struct BatchShape {
+    int precision, vec;
+    void (*fn)(const Batch &, unsigned, cudaStream_t);
+};
+
+const BatchShape kBatchShapes[] = {
+    {0, 1, bulk_batch_launch<double, 1>},  {0, 2, bulk_batch_launch<double, 2>},
+    {1, 1, bulk_batch_launch<float, 1>},   {1, 2, bulk_batch_launch<float, 2>},
+    {1, 4, bulk_batch_launch<float, 4>},
+    {2, 1, bulk_batch_launch<__half, 1>},  {2, 2, bulk_batch_launch<__half, 2>},
+    {2, 4, bulk_batch_launch<__half, 4>},
+    {3, 1, bulk_batch_launch<__nv_bfloat16, 1>}, {3, 2, bulk_batch_launch<__nv_bfloat16, 2>},
+    {3, 4, bulk_batch_launch<__nv_bfloat16, 4>},
+};
+
+const BatchShape *batch_shape(int precision, int i) {
+    for (const BatchShape &b : kBatchShapes)
+        if (b.precision == precision && i-- == 0) return &b;
+    return nullptr;
+}
+
+}  // namespace
+
+int batch_bulk_shape(int precision, int i) {
+    const BatchShape *b = batch_shape(precision, i);
+    return b ? b->vec : 0;
+}
+
+void batch_grid_cells(const Device &dv, int k, int variant, int g[3]) {
+    g[0] = g[1] = g[2] = 0;
+    const Domain &d = dv.dom;
+    if (k == BK_BOUNDARY && dv.nb > 0) {
+        const long long side = dv.remap_side;
+        g[0] = (int)((dv.nb * side * side * side + 255) / 256);
+        g[1] = g[2] = 1;
+    } else if (k == BK_WALLS && !(d.px && d.py && d.pz)) {
+        const long long nx = d.nx, ny = d.ny, nz = d.nz;
+        const long long area = std::max(ny * nz, std::max(nx * nz, nx * ny));
+        g[0] = (int)((area + 255) / 256);
+        g[1] = 6;
+        g[2] = 1;
+    } else if (k == BK_BULK) {
+        const BatchShape *b = batch_shape(dv.precision, variant);
+        if (!b || d.nx % b->vec) return;
+        g[0] = (d.nx / b->vec + BATCH_BX - 1) / BATCH_BX;
+        g[1] = (d.ny + BATCH_BY - 1) / BATCH_BY;
+        g[2] = d.nz;
+    }
+}
+
+void launch_batch_cells(int k, int variant, const Batch &bt, unsigned blocks, int precision, cudaStream_t s) {
+    if (blocks == 0) return;
+    if (k == BK_BULK) {
+        const BatchShape *b = batch_shape(precision, variant);
+        if (b) b->fn(bt, blocks, s);
+        return;
+    }
+    const int mode = k == BK_WALLS ? 1 : 0;
+    switch (precision) {
+    case 0: boundary_batch<double><<<blocks, 256, 0, s>>>(bt, mode); break;
+    case 1: boundary_batch<float><<<blocks, 256, 0, s>>>(bt, mode); break;
+    case 2: boundary_batch<__half><<<blocks, 256, 0, s>>>(bt, mode); break;
+    default: boundary_batch<__nv_bfloat16><<<blocks, 256, 0, s>>>(bt, mode); break;
     }
 }
 

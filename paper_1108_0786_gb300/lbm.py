@@ -28,6 +28,7 @@ SHAPE_SPHERE, SHAPE_CAPSULE = 0, 1
 PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = 0, 1, 2, 3
 OPT_NO_FLUID = 1
 DEBUG_EXPIRE_WAITS, DEBUG_CELL_LIST_CAP = 1, 2
+ENSEMBLE_BATCHED, ENSEMBLE_BRANCHES = 0, 1
 OPT_AVERAGE_FORCE = 2
 FIELD_RHO, FIELD_U, FIELD_FLAGS, FIELD_POP = 0, 1, 2, 3
 DTYPE_F64, DTYPE_F32, DTYPE_U8 = 0, 1, 2
@@ -44,8 +45,8 @@ EXPORTED = (
     "lbm_tune", "lbm_debug_set", "lbm_autotune", "lbm_kernels_per_step", "lbm_bytes_per_cell",
     "lbm_last_error",
     "lbm_momentum_exchange_static", "lbm_adjoint_record", "lbm_adjoint_backward",
-    "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_sync", "lbm_ensemble_destroy",
-    "lbm_ensemble_last_error",
+    "lbm_ensemble_create", "lbm_ensemble_set_mode", "lbm_ensemble_autotune", "lbm_ensemble_step",
+    "lbm_ensemble_sync", "lbm_ensemble_destroy", "lbm_ensemble_last_error",
 )
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -110,6 +111,8 @@ def load_library(path: Optional[str] = None):
         "lbm_adjoint_backward": ([P, DP, DP, DP, DP, DP, DP, DP], I),
         "lbm_ensemble_create": ([ctypes.POINTER(P), I, PP], I),
         "lbm_ensemble_step": ([P, ctypes.POINTER(I)], I),
+        "lbm_ensemble_set_mode": ([P, I], I),
+        "lbm_ensemble_autotune": ([P, I, ctypes.POINTER(I)], I),
         "lbm_ensemble_sync": ([P], I),
         "lbm_ensemble_destroy": ([P], I),
         "lbm_ensemble_last_error": ([P], ctypes.c_char_p),
@@ -414,8 +417,9 @@ def from_scenario(sc, precision="f32", torch_memory=True, options=0, history=0):
 class Ensemble:
     """Independent lattices stepped together (``lbm_ensemble_*``): one CUDA
     graph launch advances every member that still has whole 16-step chunks
-    left.  Members must share a stream (lattices created with torch_memory
-    use torch's current stream)."""
+    left; by default each step is one batched launch of each per-step kernel
+    over all members.  Members must share a stream (lattices created with
+    torch_memory use torch's current stream)."""
 
     def __init__(self, lattices):
         self._lib = load_library()
@@ -442,6 +446,17 @@ class Ensemble:
 
     def sync(self):
         return self._check(self._lib.lbm_ensemble_sync(self._h))
+
+    def set_mode(self, mode):
+        """ENSEMBLE_BATCHED (default) or ENSEMBLE_BRANCHES."""
+        return self._check(self._lib.lbm_ensemble_set_mode(self._h, int(mode)))
+
+    def autotune(self, trials=3):
+        """Time the batched bulk shapes and keep the fastest; returns its
+        cells per thread."""
+        v = ctypes.c_int(0)
+        self._check(self._lib.lbm_ensemble_autotune(self._h, int(trials), ctypes.byref(v)))
+        return v.value
 
     def close(self):
         if getattr(self, "_h", None):

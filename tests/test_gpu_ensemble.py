@@ -30,8 +30,9 @@ def members(count, edge_max=64):
     return [sc for sc in wl.ensemble_members() if sc.nx <= edge_max][:count]
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
-def test_ensemble_equals_members_stepped_alone(gpu, precision):
+@pytest.mark.parametrize("precision,mode", [("f64", lbm.ENSEMBLE_BATCHED), ("f32", lbm.ENSEMBLE_BATCHED),
+                                            ("f32", lbm.ENSEMBLE_BRANCHES)])
+def test_ensemble_equals_members_stepped_alone(gpu, precision, mode):
     scs = members(5)
     steps = [48, 16, 33, 0, 70]
     alone = []
@@ -42,6 +43,7 @@ def test_ensemble_equals_members_stepped_alone(gpu, precision):
         lat.close()
     lats = [lbm.from_scenario(sc, precision=precision) for sc in scs]
     ens = lbm.Ensemble(lats)
+    ens.set_mode(mode)
     ens.step(steps)
     ens.sync()
     for lat, (b, p, n) in zip(lats, alone):
@@ -99,6 +101,67 @@ def test_member_error_surfaces_at_sync(gpu):
     with pytest.raises(lbm.LbmError) as e:
         ens.sync()
     assert e.value.code == lbm.E_OVERLAP
+    ens.close()
+    for lat in lats:
+        lat.close()
+
+
+def mixed_members():
+    """Members the batched launches must tell apart: storage precisions
+    (one group each), walls, a box without bodies, odd and even extents."""
+    out = []
+    a = members(2)
+    out.append((a[0], "f32"))
+    out.append((a[1], "f64"))
+    ch = wl.Scenario("walled channel", 40, 36, 44, 0.8, bc=wl.PERIODIC_Z, g=(0.0, 0.0, 2e-6))
+    wl.add_swimmer(ch, (19.6, 17.8, 21.3), (0.7071, 0.0, -0.7071, 0.0), (wl.SPHERE, wl.CAPSULE, wl.SPHERE),
+                   3.0, 4.0, 12.0, 0.02, 0.01, 2e-3, 64.0, density=2.0)
+    out.append((ch, "f32"))
+    fluid = wl.Scenario("no bodies", 33, 20, 24, 0.9, bc=wl.PERIODIC_X | wl.PERIODIC_Z, g=(1e-5, 0.0, 0.0))
+    out.append((fluid, "bf16"))
+    out.append((a[0], "bf16"))
+    out.append((a[1], "f16"))
+    return out
+
+
+def test_batched_ensemble_of_mixed_members_equals_them_stepped_alone(gpu):
+    mix = mixed_members()
+    steps = [64, 48, 37, 80, 33, 50]
+    alone = []
+    for (sc, prec), n in zip(mix, steps):
+        lat = lbm.from_scenario(sc, precision=prec)
+        lat.step(n)
+        alone.append((lat.bodies(), lat.pop()))
+        lat.close()
+    lats = [lbm.from_scenario(sc, precision=prec) for sc, prec in mix]
+    ens = lbm.Ensemble(lats)
+    ens.step(steps)
+    ens.sync()
+    for lat, (b, p) in zip(lats, alone):
+        assert np.array_equal(lat.bodies(), b)
+        assert np.array_equal(lat.pop(), p)
+    ens.close()
+    for lat in lats:
+        lat.close()
+
+
+def test_ensemble_autotune_keeps_the_bits(gpu):
+    scs = members(4)
+    alone = []
+    for sc in scs:
+        lat = lbm.from_scenario(sc, precision="f32")
+        lat.step(64)
+        alone.append(lat.pop())
+        lat.close()
+    lats = [lbm.from_scenario(sc, precision="f32") for sc in scs]
+    ens = lbm.Ensemble(lats)
+    ens.step(16)
+    vec = ens.autotune(2)
+    assert vec in (1, 2, 4)
+    ens.step(48)
+    ens.sync()
+    for lat, p in zip(lats, alone):
+        assert np.array_equal(lat.pop(), p)
     ens.close()
     for lat in lats:
         lat.close()
