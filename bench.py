@@ -54,6 +54,8 @@ def parse_args():
                     help="time only the oracle CPU baseline (no GPU) and print it as one JSON line")
     ap.add_argument("--cpu-full", action="store_true",
                     help="with --cpu-only: every config at its full step count")
+    ap.add_argument("--overlap", action="store_true",
+                    help="overlapped steps (the bulk kernel's far tiles beside the force and remap)")
     ap.add_argument("--shape", default="auto",
                     help="bulk-kernel shape 'cells_per_thread,min_blocks_per_sm', or 'auto' for the autotuner")
     return ap.parse_args()
@@ -347,7 +349,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     sc = workload(args, rank)
-    lat = lbm.from_scenario(sc, precision=args.precision)
+    lat = lbm.from_scenario(sc, precision=args.precision,
+                            options=lbm.OPT_OVERLAP if args.overlap else 0)
     if args.shape != "auto":
         shape = tuple(int(v) for v in args.shape.split(","))
         lat.tune(*shape)               # a fixed bulk-kernel shape must be set before the first step

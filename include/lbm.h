@@ -86,6 +86,9 @@ extern "C" {
 #define LBM_OPT_AVERAGE_FORCE 2   /* rigid-body step with the mean hydrodynamic load of steps n and n-1
                                      (not in the paper: a stabiliser of the explicit coupling for
                                      light bodies; lbm_get_forces still reports step n's load) */
+#define LBM_OPT_OVERLAP   4       /* overlapped steps (the same bits): the bulk kernel of step n leaves
+                                     the tiles near a body to a near-cell kernel after the remap and
+                                     runs beside the force and remap of the neighbouring steps */
 
 #define LBM_FIELD_RHO   0     /* density, cells */
 #define LBM_FIELD_U     1     /* velocity, [3][cells] */

@@ -1032,6 +1032,67 @@ __global__ void tick_kernel(const Device dv, const StepPtrs sp) {
     if (threadIdx.x == 0) finish_step(dv, sp);
 }
 
+// The near tiles of the step of parity q (one block): the marks of that
+// parity's previous list are cleared, then every TILE_X-cell tile of an
+// x-row that meets the remap cube of a body in `states` grown by one cell is
+// marked and listed once.  The cube is the remap's: half-width
+// E + REMAP_MARGIN around floor(X).  Also stores the step's index.
+__global__ void __launch_bounds__(512) near_tiles_kernel(const Device dv, const BodyState *states, int q,
+                                                         int step_offset) {
+    const Domain d = dv.dom;
+    unsigned *mask = dv.near_mask[q];
+    int *list = dv.near_list[q];
+    const int old = min(dv.near_count[q], dv.near_cap);
+    for (int i = threadIdx.x; i < old; i += blockDim.x) mask[list[i]] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dv.near_count[q] = 0;
+        dv.tstep[q] = *dv.t_dev + step_offset;
+    }
+    __syncthreads();
+    const int ntx = (d.nx + TILE_X - 1) / TILE_X;
+    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
+    for (int b = 0; b < dv.nb; ++b) {
+        const int half = dv.props[b].E + REMAP_MARGIN + 1;
+        const int side = 2 * half + 1;
+        int o[3];
+        for (int a = 0; a < 3; ++a) o[a] = (int)floor(states[b].X[a]) - half;
+        for (int r = threadIdx.x; r < side * side; r += blockDim.x) {
+            int y = o[1] + r % side, z = o[2] + r / side;
+            if (per[1]) y = ((y % n3[1]) + n3[1]) % n3[1]; else if (y < 0 || y >= n3[1]) continue;
+            if (per[2]) z = ((z % n3[2]) + n3[2]) % n3[2]; else if (z < 0 || z >= n3[2]) continue;
+            // the row's x range as up to two unwrapped pieces [lo, hi]
+            int lo[2], hi[2], pieces = 1;
+            if (!per[0]) {
+                lo[0] = max(o[0], 0);
+                hi[0] = min(o[0] + side - 1, n3[0] - 1);
+            } else if (side >= n3[0]) {
+                lo[0] = 0;
+                hi[0] = n3[0] - 1;
+            } else {
+                const int x0 = ((o[0] % n3[0]) + n3[0]) % n3[0];
+                lo[0] = x0;
+                hi[0] = min(x0 + side - 1, n3[0] - 1);
+                if (x0 + side - 1 >= n3[0]) {
+                    lo[1] = 0;
+                    hi[1] = x0 + side - 1 - n3[0];
+                    pieces = 2;
+                }
+            }
+            const long long rowt = ((long long)z * n3[1] + y) * ntx;
+            for (int k = 0; k < pieces; ++k)
+                for (int cx = lo[k] / TILE_X; lo[k] <= hi[k] && cx <= hi[k] / TILE_X; ++cx) {
+                    const int t = (int)(rowt + cx);
+                    if (atomicExch(mask + t, 1u) == 0u) {
+                        const int i = atomicAdd(dv.near_count + q, 1);
+                        if (i < dv.near_cap) list[i] = t;
+                        else atomicOr(dv.status, ST_LINKS);
+                    }
+                }
+        }
+    }
+}
+
 // the rigid-body step alone (bodies without fluid), one block: the loads,
 // then a warp a body
 __global__ void __launch_bounds__(256) integrate_kernel(const Device dv, const StepPtrs sp, int with_fluid) {
@@ -1165,6 +1226,20 @@ void launch_integrate(const Device &dv, const StepPtrs &sp, int with_fluid, cuda
 }
 
 void launch_tick(const Device &dv, const StepPtrs &sp, cudaStream_t s) { tick_kernel<<<1, 32, 0, s>>>(dv, sp); }
+
+void launch_near_tiles(const Device &dv, const BodyState *states, int q, int step_offset, cudaStream_t s) {
+    near_tiles_kernel<<<1, 512, 0, s>>>(dv, states, q, step_offset);
+}
+
+long long near_tile_count(const Device &dv) {
+    return (long long)((dv.dom.nx + TILE_X - 1) / TILE_X) * dv.dom.ny * dv.dom.nz;
+}
+
+int near_tile_cap(const Device &dv, int emax) {
+    const long long side = 2LL * (emax + REMAP_MARGIN + 1) + 1;
+    const long long per_body = side * side * ((side + TILE_X - 1) / TILE_X + 1);
+    return (int)std::min<long long>((long long)dv.nb * per_body, near_tile_count(dv));
+}
 
 // the grids of launch_remap, launch_links and launch_force for one lattice
 void batch_grid_small(const Device &dv, int k, int g[3]) {

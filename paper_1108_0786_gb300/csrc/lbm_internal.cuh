@@ -190,8 +190,26 @@ struct StepPtrs {
     const BodyState *body_prev;             // state n-1
     const BodyState *body_cur;              // state n
     BodyState *body_next;                   // state n+1
+    // overlapped steps: the tiles of step n near a body, which the bulk
+    // kernel leaves to the near kernel (null: the bulk kernel does every cell)
+    const unsigned *far_skip;
+    const long long *tstep;                 // step index n (the BF16 rounding bits' counter)
     int parity;
 };
+
+// Overlapped steps.  The bulk kernel of step n needs only the populations of
+// step n-1 where no body is near: outside the remap cubes flags are static
+// in every epoch.  The tiles of TILE_X cells of an x-row that meet the remap
+// cube of any body at state n-1 grown by one cell (which holds the cube at
+// state n: a body moves at most half a cell a step) are near tiles; the bulk
+// kernel skips them and the near kernel does them after the remap.  So the
+// far part of step n's bulk runs beside the force and rigid-body step of
+// step n-1 and the remap of step n.  An option (LBM_OPT_OVERLAP), not the
+// default: the bulk kernel needs nearly every SM's memory parallelism to
+// hold HBM at its peak, so short kernels that share the SMs with it slow it
+// by about as much as their own time (measured on the 33.5 M-cell capsule
+// swarm: 0.889 ms a step overlapped against 0.872 ms serial).
+constexpr int TILE_X = 64;
 
 struct Device {
     Domain dom;
@@ -236,6 +254,14 @@ struct Device {
     int expire_waits;       // checks of the timeout path: the row-staged kernel's first wait cannot succeed
     double *avg_u;          // [3][C] running sum of the velocity while an average is taken, or null
     long long *avg_n;       // steps added to avg_u
+    // overlapped steps, by step parity: near-tile marks [tiles] (non-zero:
+    // near), near-tile lists [near_cap] and their lengths [2], the step index
+    int overlap;
+    unsigned *near_mask[2];
+    int *near_list[2];
+    int *near_count;
+    int near_cap;
+    long long *tstep;       // [2]
 };
 
 // ---- batched launches over the members of an ensemble ------------------------
@@ -262,9 +288,14 @@ struct Batch {
     const StepPtrs *sp;     // [2][members] step pointers by step parity
     const int *first;       // [members + 1] first flattened block of each member (this kernel's grids)
     const int *grid;        // [members][3] each member's grid (this kernel's)
+    const unsigned short *member;   // [blocks] the member of each flattened block
     int members;
     int parity;             // step parity of this launch
 };
+
+// blocks of a batched bulk launch walk this many z-planes of their member
+// (fewer, longer blocks: each block's look-up of its member is paid once)
+constexpr int BATCH_Z = 4;
 
 // the member record, step pointers and block coordinates of this block of a
 // batched launch, in shared memory (every thread of the block calls this)
@@ -272,12 +303,7 @@ __device__ inline void batch_member(const Batch &bt, Device &sdv, StepPtrs &ssp,
     __shared__ int s_m;
     if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
         const int blk = (int)blockIdx.x;
-        int lo = 0, hi = bt.members - 1;        // the member m with first[m] <= blk < first[m + 1]
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bt.first[mid] <= blk) lo = mid; else hi = mid - 1;
-        }
-        const int m = lo;
+        const int m = bt.member[blk];       // first[m] <= blk < first[m + 1]
         s_m = m;
         const int l = blk - bt.first[m];
         const int gx = bt.grid[3 * m], gy = bt.grid[3 * m + 1], gz = bt.grid[3 * m + 2];
@@ -355,6 +381,13 @@ void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_integrate(const Device &dv, const StepPtrs &sp, int with_fluid, cudaStream_t s);
 void launch_tick(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+// the near tiles of the step of parity q from the body states `states`
+// (their remap cubes grown by one cell), and that step's index,
+// t_dev + step_offset
+void launch_near_tiles(const Device &dv, const BodyState *states, int q, int step_offset, cudaStream_t s);
+void launch_near_bulk(const Device &dv, const StepPtrs &sp, cudaStream_t s);
+long long near_tile_count(const Device &dv);     // tiles of the lattice (host)
+int near_tile_cap(const Device &dv, int emax);   // most near tiles a step can have (host)
 void launch_export(const Device &dv, const void *pop, const uint8_t *flags, const uint8_t *bid,
                    int what, int mask_solid, void *out, int dtype, cudaStream_t s);
 void launch_import_pop(const Device &dv, void *pop, const double *in, cudaStream_t s);

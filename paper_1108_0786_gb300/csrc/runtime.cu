@@ -45,6 +45,11 @@ struct lbm_s {
     int device = 0;
     cudaStream_t stream = nullptr, cap = nullptr, side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // overlapped steps: the far bulk kernels' stream, and by step parity the
+    // events "far bulk of step n done" and "near cells of step n done"
+    cudaStream_t far = nullptr;
+    cudaEvent_t far_ev[2] = {nullptr, nullptr}, near_ev[2] = {nullptr, nullptr};
+    bool tiles_stale = false;           // the host set a body state: redo the next step's near tiles
     lbm_alloc_fn afn = nullptr;
     lbm_free_fn ffn = nullptr;
     void *actx = nullptr;
@@ -130,9 +135,14 @@ int alloc_into(lbm_t *h, T **out, size_t bytes) {
 bool fluid(const lbm_t *h) { return !(h->options & LBM_OPT_NO_FLUID); }
 int nb(const lbm_t *h) { return (int)h->props.size(); }
 
-lbm::StepPtrs step_ptrs(lbm_t *h, int p) {
+// the step pointers of parity p; `overlap`: the bulk kernel leaves the near
+// tiles to the near kernel and the step index comes from the near-tile kernel
+lbm::StepPtrs step_ptrs(lbm_t *h, int p, bool overlap = false) {
     const int q = p ^ 1;
     lbm::StepPtrs sp{};
+    overlap = overlap && h->dv.overlap;
+    sp.far_skip = overlap ? h->dv.near_mask[p] : nullptr;
+    sp.tstep = overlap ? h->dv.tstep + p : h->dv.t_dev;
     sp.src = h->pop[q];
     sp.dst = h->pop[p];
     sp.flags_prev = h->flags[q];
@@ -152,6 +162,8 @@ lbm::StepPtrs step_ptrs(lbm_t *h, int p) {
 // loads, run on a second stream concurrently with the bulk kernel (they
 // touch no data the bulk kernel reads or writes) and join before the force
 // sums.
+void enqueue_overlapped(lbm_t *h, int p, cudaStream_t s, bool first);
+
 void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bool *ran = nullptr,
                   bool fork = false) {
     const lbm::StepPtrs sp = step_ptrs(h, p);
@@ -188,6 +200,42 @@ void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bo
     if (fl && h->dv.avg_u) lbm::launch_average(h->dv, sp, s);
 }
 
+// One overlapped step n of parity p (lattices with bodies and fluid).  Two
+// streams: the chain s (remap, links, loads, boundary and near cells, the
+// next step's near tiles, force + rigid-body step) and the far stream (the
+// bulk kernel outside the near tiles).  far(n) waits for the near cells of
+// step n-1 (its sources; the chain of step n-1 also made step n's near
+// tiles); the near and boundary cells of step n wait for far(n-1), which
+// reads the buffer they write.  So far(n) runs beside force(n-1), remap(n)
+// and everything else of step n.  `first`: the first step of a capture
+// (its predecessors completed before the graph started).
+void enqueue_overlapped(lbm_t *h, int p, cudaStream_t s, bool first) {
+    const lbm::StepPtrs sp = step_ptrs(h, p, true);
+    const int q = p ^ 1;
+    // far stream: wait for step n-1's near cells, then the far bulk kernel
+    if (first) {
+        cudaEventRecord(h->fork_ev, s);
+        cudaStreamWaitEvent(h->far, h->fork_ev, 0);
+    } else {
+        cudaStreamWaitEvent(h->far, h->near_ev[q], 0);
+    }
+    lbm::launch_stream_collide(h->dv, sp, h->far);
+    cudaEventRecord(h->far_ev[p], h->far);
+    // the chain
+    lbm::launch_remap(h->dv, sp, 0, s);
+    lbm::launch_links(h->dv, sp, s);
+    if (!first) cudaStreamWaitEvent(s, h->far_ev[q], 0);
+    lbm::launch_boundary_fix(h->dv, sp, s);
+    lbm::launch_near_bulk(h->dv, sp, s);
+    lbm::launch_near_tiles(h->dv, sp.body_cur, q, 1, s);        // step n+1's, from state n
+    cudaEventRecord(h->near_ev[p], s);
+    lbm::launch_force(h->dv, sp, s);
+    if (h->dv.avg_u) {
+        cudaStreamWaitEvent(s, h->far_ev[p], 0);
+        lbm::launch_average(h->dv, sp, s);
+    }
+}
+
 // the step graphs bake in the kernels and their arguments: drop them so that
 // the next step rebuilds them
 void drop_graphs(lbm_t *h) {
@@ -196,6 +244,10 @@ void drop_graphs(lbm_t *h) {
     if (h->chunk) { cudaGraphExecDestroy(h->chunk); h->chunk = nullptr; }
     h->graphs_ready = false;
     ++h->graph_gen;
+}
+
+bool overlapped(const lbm_t *h) {
+    return fluid(h) && nb(h) > 0 && (h->options & LBM_OPT_OVERLAP);
 }
 
 int kernels_per_step(const lbm_t *h) {
@@ -209,6 +261,7 @@ int kernels_per_step(const lbm_t *h) {
     if (bodies && !fl) n += 1;                              // rigid-body step alone
     if (!bodies && fl) n += 1;                              // step counter
     if (fl && h->dv.avg_u) n += 1;                          // running velocity average
+    if (overlapped(h)) n += 2;                              // near cells, next step's near tiles
     return n;
 }
 
@@ -220,7 +273,23 @@ int init_flags(lbm_t *h) {
         sp.body_cur = h->bodies[0];
         lbm::launch_remap(h->dv, sp, 1, h->stream);
     }
+    // the first step's near tiles
+    if (h->dv.overlap) lbm::launch_near_tiles(h->dv, h->bodies[0], 0, 0, h->stream);
+    h->tiles_stale = false;
     CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+// the next step's near tiles from the current body states, after the host
+// set a state or steps ran without the overlapped graphs
+int refresh_tiles(lbm_t *h) {
+    if (!h->tiles_stale) return LBM_OK;
+    if (h->dv.overlap) {
+        const int p = (int)(h->steps & 1);
+        lbm::launch_near_tiles(h->dv, h->bodies[p], p, 0, h->stream);
+        CK(cudaGetLastError());
+    }
+    h->tiles_stale = false;
     return LBM_OK;
 }
 
@@ -347,6 +416,15 @@ int ensure_device(lbm_t *h) {
     if ((rc = alloc_into(h, &dv.status, sizeof(int) * 4))) return rc;
     dv.changed = dv.status + 2;
     if ((rc = alloc_into(h, &dv.t_dev, sizeof(long long)))) return rc;
+    if ((rc = alloc_into(h, &dv.tstep, sizeof(long long) * 2))) return rc;
+    dv.overlap = overlapped(h) ? 1 : 0;
+    dv.near_cap = dv.overlap ? lbm::near_tile_cap(dv, emax) : 0;
+    for (int i = 0; i < 2; ++i) {
+        const size_t tiles = dv.overlap ? (size_t)lbm::near_tile_count(dv) : 1;
+        if ((rc = alloc_into(h, &dv.near_mask[i], sizeof(unsigned) * tiles))) return rc;
+        if ((rc = alloc_into(h, &dv.near_list[i], sizeof(int) * std::max(dv.near_cap, 1)))) return rc;
+    }
+    if ((rc = alloc_into(h, &dv.near_count, sizeof(int) * 2))) return rc;
     dv.hist = nullptr;
     if (h->hist_cap > 0 && (rc = alloc_into(h, &dv.hist, sizeof(double) * 13 * h->hist_cap * std::max(B, 1))))
         return rc;
@@ -377,6 +455,11 @@ int ensure_device(lbm_t *h) {
     CK(cudaMemcpyAsync(dv.status, st, sizeof st, cudaMemcpyHostToDevice, s));
     const long long t0 = 0;
     CK(cudaMemcpyAsync(dv.t_dev, &t0, sizeof t0, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dv.tstep, 0, sizeof(long long) * 2, s));
+    CK(cudaMemsetAsync(dv.near_count, 0, sizeof(int) * 2, s));
+    for (int i = 0; i < 2; ++i)
+        CK(cudaMemsetAsync(dv.near_mask[i], 0,
+                           sizeof(unsigned) * (dv.overlap ? (size_t)lbm::near_tile_count(dv) : 1), s));
     CK(cudaMemsetAsync(h->tape.ctl, 0, sizeof(lbm::TapeCtl), s));
     if (B) CK(cudaMemcpyAsync(props, props_h.data(), sizeof(BodyProps) * B, cudaMemcpyHostToDevice, s));
     if (!h->springs.empty())
@@ -394,23 +477,44 @@ int ensure_device(lbm_t *h) {
 
 int build_graphs(lbm_t *h) {
     if (h->graphs_ready) return LBM_OK;
-    if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    // overlapped steps: the chain (captured on cap) takes precedence over the
+    // far bulk kernel, so that its short kernels start as soon as SMs free
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    if (!h->cap) CK(cudaStreamCreateWithPriority(&h->cap, cudaStreamNonBlocking, greatest));
     if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
     if (!h->join_ev) CK(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+    const bool ov = h->dv.overlap != 0;
+    if (ov) {
+        if (!h->far) CK(cudaStreamCreateWithPriority(&h->far, cudaStreamNonBlocking, least));
+        for (int i = 0; i < 2; ++i) {
+            if (!h->far_ev[i]) CK(cudaEventCreateWithFlags(&h->far_ev[i], cudaEventDisableTiming));
+            if (!h->near_ev[i]) CK(cudaEventCreateWithFlags(&h->near_ev[i], cudaEventDisableTiming));
+        }
+    }
+    // steps p0, p0 + 1, ... of a graph; the far stream joins back at the end
+    auto steps = [&](int p0, int n) {
+        for (int i = 0; i < n; ++i) {
+            const int p = (p0 + i) & 1;
+            if (ov) enqueue_overlapped(h, p, h->cap, i == 0);
+            else enqueue_step(h, p, h->cap, nullptr, nullptr, true);
+        }
+        if (ov) cudaStreamWaitEvent(h->cap, h->far_ev[(p0 + n - 1) & 1], 0);
+    };
     for (int p = 0; p < 2; ++p) {
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-        enqueue_step(h, p, h->cap, nullptr, nullptr, true);
+        steps(p, 1);
         CK(cudaStreamEndCapture(h->cap, &g));
-        CK(cudaGraphInstantiate(&h->single[p], g, 0));
+        CK(cudaGraphInstantiate(&h->single[p], g, cudaGraphInstantiateFlagUseNodePriority));
         cudaGraphDestroy(g);
     }
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < CHUNK_STEPS; ++i) enqueue_step(h, i & 1, h->cap, nullptr, nullptr, true);
+    steps(0, CHUNK_STEPS);
     CK(cudaStreamEndCapture(h->cap, &g));
-    CK(cudaGraphInstantiate(&h->chunk, g, 0));
+    CK(cudaGraphInstantiate(&h->chunk, g, cudaGraphInstantiateFlagUseNodePriority));
     cudaGraphDestroy(g);
     h->graphs_ready = true;
     return LBM_OK;
@@ -447,6 +551,11 @@ void release_device(lbm_t *h) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->join_ev) cudaEventDestroy(h->join_ev);
+    if (h->far) cudaStreamDestroy(h->far);
+    for (int i = 0; i < 2; ++i) {
+        if (h->far_ev[i]) cudaEventDestroy(h->far_ev[i]);
+        if (h->near_ev[i]) cudaEventDestroy(h->near_ev[i]);
+    }
     for (void *p : h->tape.allocs) dfree(h, p);
     h->tape.allocs.clear();
     for (void *p : h->allocs) dfree(h, p);
@@ -484,7 +593,7 @@ int lbm_create_ex(int nx, int ny, int nz, double tau, int bc, int precision, con
     if (!out) return LBM_E_ARG;
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5) || bc < 0 || bc > 7 || precision < 0 || precision > 3 ||
-        (options & ~(LBM_OPT_NO_FLUID | LBM_OPT_AVERAGE_FORCE)))
+        (options & ~(LBM_OPT_NO_FLUID | LBM_OPT_AVERAGE_FORCE | LBM_OPT_OVERLAP)))
         return LBM_E_ARG;
     const long long C = (long long)nx * ny * nz;
     if (C > (1LL << 31) - 1) return LBM_E_ARG;   // link cells are 32-bit indices
@@ -691,6 +800,7 @@ int lbm_set_body_state(lbm_t *h, int b, const double state[13]) {
             return fail(h, LBM_E_STATE, "after the first step a body may move by less than %g per axis",
                         LBM_MAX_BODY_STEP);
     CK(cudaMemcpy(cur, &s, sizeof s, cudaMemcpyHostToDevice));
+    h->tiles_stale = true;
     return LBM_OK;
 }
 
@@ -719,6 +829,7 @@ int lbm_step(lbm_t *h, int n) {
     int rc = ensure_device(h);
     if (rc) return rc;
     if ((rc = build_graphs(h))) return rc;
+    if (n > 0 && (rc = refresh_tiles(h))) return rc;
     while (n > 0) {
         const int p = (int)(h->steps & 1);
         if (p == 0 && n >= CHUNK_STEPS) {
@@ -954,9 +1065,11 @@ int lbm_load(lbm_t *h, const char *path) {
     get(h->dv.t_dev, sizeof(long long));
     std::fclose(f);
     if (!ok) return fail(h, LBM_E_ARG, "reading %s failed", path);
-    // the next step rebuilds its link lists from the restored flags
+    // the next step rebuilds its link lists from the restored flags, and
+    // its near tiles from the restored states
     const int st[4] = {0, 0, 1, 1};
     CK(cudaMemcpy(h->dv.status, st, sizeof st, cudaMemcpyHostToDevice));
+    h->tiles_stale = true;
     return LBM_OK;
 }
 
@@ -972,6 +1085,7 @@ int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots) {
         bool ran[LBM_NUM_KERNELS] = {false, false, false, false, false, false};
         enqueue_step(h, (int)(h->steps & 1), h->stream, ev, ran);
         h->steps += 1;
+        h->tiles_stale = true;              // steps without the overlapped graphs
         CK(cudaStreamSynchronize(h->stream));
         for (int k = 0; k < LBM_NUM_KERNELS; ++k) {
             if (!ran[k]) continue;
@@ -1235,6 +1349,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
                 sp.body_prev = S(m + j - 1);
                 sp.body_cur = S(m + j);
                 sp.body_next = scratch;
+                sp.tstep = dr.t_dev;
                 sp.parity = j & 1;
                 if (j == L) {
                     // the flags of the epoch after the run: the last reverse
@@ -1452,8 +1567,11 @@ int ens_group_tables(lbm_ensemble_t *e, EnsGroup &g) {
         sps[j] = step_ptrs(h, 0);
         sps[M + j] = step_ptrs(h, 1);
     }
+    if (M > 65535) return ens_fail(e, LBM_E_ARG, "more than 65535 members of one precision");
     std::vector<int> tab;                   // per kernel: first[M + 1], grid[3 M]
     std::vector<size_t> off(lbm::BK_COUNT);
+    std::vector<unsigned short> owner;      // per kernel, per flattened block: its member
+    std::vector<size_t> own_off(lbm::BK_COUNT);
     for (int k = 0; k < lbm::BK_COUNT; ++k) {
         off[k] = tab.size();
         tab.resize(tab.size() + (M + 1) + 3 * M);
@@ -1472,16 +1590,21 @@ int ens_group_tables(lbm_ensemble_t *e, EnsGroup &g) {
         first[M] = (int)total;
         if (total > INT_MAX) return ens_fail(e, LBM_E_ARG, "a batched launch exceeds 2^31 blocks");
         g.blocks[k] = (unsigned)total;
+        own_off[k] = owner.size();
+        for (int j = 0; j < M; ++j) owner.insert(owner.end(), (size_t)(first[j + 1] - first[j]), (unsigned short)j);
     }
     const size_t b_dv = sizeof(lbm::Device) * M, b_sp = sizeof(lbm::StepPtrs) * 2 * M;
     const size_t o_sp = (b_dv + 255) / 256 * 256, o_tab = o_sp + (b_sp + 255) / 256 * 256;
-    const size_t bytes = o_tab + sizeof(int) * tab.size();
+    const size_t o_own = o_tab + (sizeof(int) * tab.size() + 255) / 256 * 256;
+    const size_t bytes = o_own + sizeof(unsigned short) * std::max<size_t>(owner.size(), 1);
     g.mem = dalloc(h0, bytes);
     if (!g.mem) return ens_fail(e, LBM_E_OOM, "device allocation of the ensemble's tables failed");
     char *base = static_cast<char *>(g.mem);
     cudaError_t err = cudaMemcpy(base, dvs.data(), b_dv, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(base + o_sp, sps.data(), b_sp, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(base + o_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && !owner.empty())
+        err = cudaMemcpy(base + o_own, owner.data(), sizeof(unsigned short) * owner.size(), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return ens_fail(e, LBM_E_CUDA, cudaGetErrorString(err));
     const int *dtab = reinterpret_cast<const int *>(base + o_tab);
     for (int k = 0; k < lbm::BK_COUNT; ++k) {
@@ -1490,6 +1613,7 @@ int ens_group_tables(lbm_ensemble_t *e, EnsGroup &g) {
         b.sp = reinterpret_cast<const lbm::StepPtrs *>(base + o_sp);
         b.first = dtab + off[k];
         b.grid = dtab + off[k] + M + 1;
+        b.member = reinterpret_cast<const unsigned short *>(base + o_own) + own_off[k];
         b.members = M;
         b.parity = 0;
     }
@@ -1687,6 +1811,7 @@ int lbm_ensemble_step(lbm_ensemble_t *e, const int *steps) {
         }
         for (int i : set) {
             e->members[i]->steps += chunks * CHUNK_STEPS;
+            e->members[i]->tiles_stale = true;      // the ensemble's steps are not overlapped
             left[i] -= chunks * CHUNK_STEPS;
         }
     }

@@ -330,8 +330,9 @@ template <> __device__ __forceinline__ __nv_bfloat16 store16<__nv_bfloat16>(floa
     return __ushort_as_bfloat16((unsigned short)bf16_sr_bits(v, d, a));
 }
 
-template <typename T> __device__ __forceinline__ Dither dither_for(long long c, long long t) {
-    if constexpr (std::is_same<T, __nv_bfloat16>::value) return bf16_dither(c, t);
+// the dither of cell c in the step whose index *t holds (read only for BF16)
+template <typename T> __device__ __forceinline__ Dither dither_for(long long c, const long long *t) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) return bf16_dither(c, *t);
     else return Dither{};
 }
 
@@ -402,10 +403,14 @@ __device__ __forceinline__ void bulk_body(const Device &dv, const StepPtrs &sp, 
 #pragma unroll
         for (int b = 0; b < Q; ++b) f[b][i] = solid ? (Cd)0 : g[b];
     }
-    if (!active) return;
+    // overlapped steps: a tile near a body is the near kernel's
+    const bool far = !sp.far_skip || sp.far_skip[((long long)z * d.ny + y) * ((d.nx + TILE_X - 1) / TILE_X) +
+                                                 x0 / TILE_X] == 0u;
+    if (!active || !far) return;
     // BF16 rounds stochastically (one cell per thread for 16-bit storage here)
     static_assert(!raw16 || V == 1, "16-bit storage with several cells per thread uses bulk16_kernel");
-    const Dither dz = raw16 ? dither_for<T>(c0, *dv.t_dev) : Dither{};
+    static_assert(TILE_X % V == 0, "a thread's cells lie in one tile");
+    const Dither dz = raw16 ? dither_for<T>(c0, sp.tstep) : Dither{};
     auto st = [&](Cd v, int b) -> T {
         if constexpr (raw16) return store16<T>(v, dz, b);
         else return Codec<T>::st(v, scale);
@@ -443,7 +448,11 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
-    bulk_body<T, V, BX, BY>(sdv, ssp, sbk);
+    for (int k = 0; k < BATCH_Z; ++k) {
+        const int z = sbk.z * BATCH_Z + k;
+        if (z >= sdv.dom.nz) break;
+        bulk_body<T, V, BX, BY>(sdv, ssp, Blk{sbk.x, sbk.y, z, sbk.gx, sbk.gy, sdv.dom.nz});
+    }
 }
 
 // 16-bit values packed two to a 32-bit word (the lower address in the low
@@ -532,7 +541,6 @@ __device__ __forceinline__ void bulk16_body(const Device &dv, const StepPtrs &sp
         }
     }
 
-    const long long tstep = std::is_same<T, __nv_bfloat16>::value ? *dv.t_dev : 0;
 #pragma unroll
     for (int i = 0; i < V; ++i) {
         const int j = i >> 1;
@@ -542,14 +550,18 @@ __device__ __forceinline__ void bulk16_body(const Device &dv, const StepPtrs &sp
         for (int b = 0; b < Q; ++b) g[b] = hi ? half_hi<T>(w[b][j]) : half_lo<T>(w[b][j]);
         collide_lean<std::is_same<T, __half>::value>(g, dv);
         const bool solid = fl[i] & F_SOLID;
-        const Dither dz = dither_for<T>(c0 + i, tstep);
+        const Dither dz = dither_for<T>(c0 + i, sp.tstep);
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
             const unsigned h = solid ? 0u : store_bits<T>(g[b], dz, b);
             w[b][j] = hi ? __byte_perm(w[b][j], h, 0x5410) : __byte_perm(h, w[b][j], 0x7610);
         }
     }
-    if (!active) return;
+    // overlapped steps: a tile near a body is the near kernel's
+    static_assert(TILE_X % V == 0, "a thread's cells lie in one tile");
+    const bool far = !sp.far_skip || sp.far_skip[((long long)z * d.ny + y) * ((d.nx + TILE_X - 1) / TILE_X) +
+                                                 x0 / TILE_X] == 0u;
+    if (!active || !far) return;
     // fluid cells with a non-zero flag byte belong to the boundary kernel,
     // which may run concurrently: leave them alone
     bool all_mine = true;
@@ -581,7 +593,11 @@ bulk16_kernel(const Device dv, const StepPtrs sp) {
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk16_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
-    bulk16_body<T, V, BX, BY>(sdv, ssp, sbk);
+    for (int k = 0; k < BATCH_Z; ++k) {
+        const int z = sbk.z * BATCH_Z + k;
+        if (z >= sdv.dom.nz) break;
+        bulk16_body<T, V, BX, BY>(sdv, ssp, Blk{sbk.x, sbk.y, z, sbk.gx, sbk.gy, sdv.dom.nz});
+    }
 }
 
 // Velocity of body b's surface at lattice point p in the compute type R:
@@ -803,7 +819,7 @@ __device__ __forceinline__ void boundary_body(const Device &dv, const StepPtrs &
     collide<Cd, std::is_same<T, float>::value>(f, dv);
     T *__restrict__ dst = static_cast<T *>(sp.dst);
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-        const Dither dz = bf16_dither(c, *dv.t_dev);
+        const Dither dz = bf16_dither(c, *sp.tstep);
 #pragma unroll
         for (int b = 0; b < Q; ++b) dst[(long long)b * C + c] = store16<T>(f[b], dz, b);
     } else {
@@ -897,7 +913,7 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
     T *__restrict__ dst = static_cast<T *>(sp.dst);
     const long long C = d.C;
     const float inv_scale = dv.f16_inv_scale, scale = dv.f16_scale;
-    const long long tstep = std::is_same<T, __nv_bfloat16>::value ? *dv.t_dev : 0;
+    const int ntx = (nx + TILE_X - 1) / TILE_X;
 
     if (threadIdx.x == 0) {
         // bar[NSTAGE] is never arrived at: with dv.expire_waits the first
@@ -948,10 +964,12 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
             const unsigned char *buf = stages + (size_t)st * stage_bytes + (size_t)rr * row_stage;
             const T *rowb = reinterpret_cast<const T *>(buf);
             const uint8_t *fl = buf + flag_off;
-            const long long c0 = (first + (g * ROWS + rr) * gridDim.x) * nx;
+            const long long r = first + (g * ROWS + rr) * gridDim.x;
+            const long long c0 = r * nx;
             for (int x = threadIdx.x; x < nx; x += TMA_THREADS) {
                 const uint8_t f8 = fl[x];
                 if (f8 != 0 && !(f8 & F_SOLID)) continue;      // the boundary kernel's cell
+                if (sp.far_skip && sp.far_skip[r * ntx + x / TILE_X]) continue;    // the near kernel's
                 if (f8 & F_SOLID) {
 #pragma unroll
                     for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = Codec<T>::st((Cd)0, scale);
@@ -967,7 +985,7 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Devic
                 }
                 if constexpr (sizeof(T) == 2) {
                     collide_lean<std::is_same<T, __half>::value>(f, dv);
-                    const Dither dz = dither_for<T>(c0 + x, tstep);
+                    const Dither dz = dither_for<T>(c0 + x, sp.tstep);
 #pragma unroll
                     for (int b = 0; b < Q; ++b) dst[(long long)b * C + c0 + x] = store16<T>(f[b], dz, b);
                 } else {
@@ -1190,6 +1208,37 @@ void launch_boundary_fix(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     }
 }
 
+// ---- overlapped steps: the near tiles -----------------------------------------
+
+namespace {
+
+// one listed near tile of the step a block (TILE_X threads, one cell each):
+// the bulk kernel's arithmetic on the cells whose flag byte is zero or solid
+// (the same bits as any launch shape of it)
+template <typename T>
+__global__ void __launch_bounds__(TILE_X) near_bulk_kernel(const Device dv, const StepPtrs sp) {
+    if ((int)blockIdx.x >= dv.near_count[sp.parity]) return;
+    const int t = dv.near_list[sp.parity][blockIdx.x];
+    const int ntx = (dv.dom.nx + TILE_X - 1) / TILE_X;
+    const int row = t / ntx;
+    const Blk bk{t % ntx, row % dv.dom.ny, row / dv.dom.ny, ntx, dv.dom.ny, dv.dom.nz};
+    StepPtrs own = sp;
+    own.far_skip = nullptr;
+    bulk_body<T, 1, TILE_X, 1>(dv, own, bk);
+}
+
+}  // namespace
+
+void launch_near_bulk(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+    const unsigned blocks = (unsigned)dv.near_cap;
+    switch (dv.precision) {
+    case 0: near_bulk_kernel<double><<<blocks, TILE_X, 0, s>>>(dv, sp); break;
+    case 1: near_bulk_kernel<float><<<blocks, TILE_X, 0, s>>>(dv, sp); break;
+    case 2: near_bulk_kernel<__half><<<blocks, TILE_X, 0, s>>>(dv, sp); break;
+    default: near_bulk_kernel<__nv_bfloat16><<<blocks, TILE_X, 0, s>>>(dv, sp); break;
+    }
+}
+
 // ---- batched launches (ensembles) ------------------------------------------
 
 namespace {
@@ -1250,7 +1299,7 @@ void batch_grid_cells(const Device &dv, int k, int variant, int g[3]) {
         if (!b || d.nx % b->vec) return;
         g[0] = (d.nx / b->vec + BATCH_BX - 1) / BATCH_BX;
         g[1] = (d.ny + BATCH_BY - 1) / BATCH_BY;
-        g[2] = d.nz;
+        g[2] = (d.nz + BATCH_Z - 1) / BATCH_Z;
     }
 }
 

@@ -27,6 +27,7 @@ BC_PERIODIC_X, BC_PERIODIC_Y, BC_PERIODIC_Z = 1, 2, 4
 SHAPE_SPHERE, SHAPE_CAPSULE = 0, 1
 PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = 0, 1, 2, 3
 OPT_NO_FLUID = 1
+OPT_OVERLAP = 4
 DEBUG_EXPIRE_WAITS, DEBUG_CELL_LIST_CAP = 1, 2
 ENSEMBLE_BATCHED, ENSEMBLE_BRANCHES = 0, 1
 OPT_AVERAGE_FORCE = 2

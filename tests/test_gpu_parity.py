@@ -299,7 +299,11 @@ def test_kernel_timing_and_launch_accounting():
     lat = lbm.from_scenario(sc, precision="f32")
     lat.step(2)
     ms = lat.time_kernels(3)
+    # body preparation, remap, bulk, boundary cells, links, loads, force +
+    # rigid-body step; overlapped steps add the near cells and the next
+    # step's near tiles
     assert lat.kernels_per_step == 7
+    assert lbm.from_scenario(sc, precision="f32", options=lbm.OPT_OVERLAP).kernels_per_step == 9
     assert ms["integrate"] == 0.0            # the force kernel's last blocks integrate
     assert all(v > 0 for k, v in ms.items() if k != "integrate"), ms
     assert lat.steps_done == 5
@@ -380,3 +384,36 @@ def test_averaged_load_option_matches_the_oracle():
     assert np.abs(lat.pop() - o.pop()).max() <= 1e-12
     np.testing.assert_allclose(lat.forces(), o.forces(), rtol=1e-9, atol=1e-13)
     lat.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16"])
+def test_overlapped_steps_equal_serial_steps(precision):
+    """Overlapped steps (the bulk kernel's far tiles beside the force and
+    remap of the neighbouring steps, the near tiles after the remap) give
+    the bits of serial steps: bodies crossing cell centres, walls, a body
+    state set mid-run (the next step's near tiles are redone), kernel timing
+    (steps outside the graphs) and odd step counts between graph chunks."""
+    sc = wl.Scenario("overlap", 64, 40, 36, 0.8, bc=wl.PERIODIC_X | wl.PERIODIC_Z, g=(2e-6, 0.0, 0.0))
+    c = math.cos(0.3)
+    sc.bodies.append(wl.Body(wl.SPHERE, 4.3, 0.0, 1e9, (12.2, 19.7, 12.9)))
+    sc.bodies.append(wl.Body(wl.CAPSULE, 3.1, 6.0, 1e9, (45.4, 18.3, 20.2), (c, 0.0, math.sin(0.3), 0.0)))
+    sc.bodies.append(wl.Body(wl.SPHERE, 3.0, 0.0, 400.0, (62.0, 20.5, 33.5)))    # across two periodic faces
+    runs = []
+    for options in (0, lbm.OPT_OVERLAP):
+        lat = lbm.from_scenario(sc, precision=precision, options=options)
+        for b, v in ((0, (0.11, 0.04, -0.03)), (1, (-0.07, -0.05, 0.06)), (2, (0.03, 0.0, 0.02))):
+            st = lat.bodies()[b].copy()
+            st[7:10] = v
+            lat.set_body_state(b, st)
+        lat.step(37)
+        st = lat.bodies()[1].copy()
+        st[0] += 0.3
+        st[10:13] = (0.01, -0.02, 0.015)
+        lat.set_body_state(1, st)
+        lat.step(16)
+        lat.time_kernels(2)
+        lat.step(33)
+        runs.append((lat.pop(), lat.bodies(), lat.flags(), lat.forces()))
+        lat.close()
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
