@@ -810,11 +810,15 @@ __device__ __forceinline__ void boundary_body(const Device &dv, const StepPtrs &
         }
     }
     if constexpr (sizeof(T) != 8) {
-        // rho - 1 of the cell for the momentum exchange (the collision keeps it)
-        Cd drho = 0;
+        // rho - 1 of the cell for the momentum exchange (the collision keeps
+        // it); a lattice without bodies has no momentum exchange and no
+        // record (a wall-face cell is listed here all the same)
+        if (dv.nb > 0) {
+            Cd drho = 0;
 #pragma unroll
-        for (int b = 0; b < Q; ++b) drho += f[b];
-        dv.rho_near[c] = (float)drho;
+            for (int b = 0; b < Q; ++b) drho += f[b];
+            dv.rho_near[c] = (float)drho;
+        }
     }
     collide<Cd, std::is_same<T, float>::value>(f, dv);
     T *__restrict__ dst = static_cast<T *>(sp.dst);
