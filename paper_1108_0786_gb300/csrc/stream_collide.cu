@@ -448,11 +448,7 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
-    for (int k = 0; k < BATCH_Z; ++k) {
-        const int z = sbk.z * BATCH_Z + k;
-        if (z >= sdv.dom.nz) break;
-        bulk_body<T, V, BX, BY>(sdv, ssp, Blk{sbk.x, sbk.y, z, sbk.gx, sbk.gy, sdv.dom.nz});
-    }
+    bulk_body<T, V, BX, BY>(sdv, ssp, sbk);
 }
 
 // 16-bit values packed two to a 32-bit word (the lower address in the low
@@ -593,11 +589,7 @@ bulk16_kernel(const Device dv, const StepPtrs sp) {
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk16_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
-    for (int k = 0; k < BATCH_Z; ++k) {
-        const int z = sbk.z * BATCH_Z + k;
-        if (z >= sdv.dom.nz) break;
-        bulk16_body<T, V, BX, BY>(sdv, ssp, Blk{sbk.x, sbk.y, z, sbk.gx, sbk.gy, sdv.dom.nz});
-    }
+    bulk16_body<T, V, BX, BY>(sdv, ssp, sbk);
 }
 
 // Velocity of body b's surface at lattice point p in the compute type R:
@@ -1303,7 +1295,7 @@ void batch_grid_cells(const Device &dv, int k, int variant, int g[3]) {
         if (!b || d.nx % b->vec) return;
         g[0] = (d.nx / b->vec + BATCH_BX - 1) / BATCH_BX;
         g[1] = (d.ny + BATCH_BY - 1) / BATCH_BY;
-        g[2] = (d.nz + BATCH_Z - 1) / BATCH_Z;
+        g[2] = d.nz;
     }
 }
 
