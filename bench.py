@@ -284,10 +284,40 @@ def variant_runs(sc, steps):
                      "stream_collide_gbs": round(lat.bytes_per_cell * sc.cells / (ms_k / 1e3) / 1e9, 1),
                      "bytes_per_cell": lat.bytes_per_cell,
                      "u_rel_l2_vs_f64": u_err, "net_displacement_rel_err_vs_f64": disp_err,
+                     "net_displacement_abs_err_lu": float(np.linalg.norm(net - ref_net, axis=1).max())
+                     if prec != "f64" else 0.0,
                      "error_after_steps": steps,
                      "error_reference": "FP64 storage on the GPU (oracle-pinned)"}
         lat.close()
+    res["largest_net_displacement_lu"] = float(np.linalg.norm(ref_net, axis=1).max())
+    res["channel_swimmer"] = channel_errors()
     return res
+
+
+def channel_errors():
+    """Each storage precision's error on the channel swimmer (128 x 64 x 64,
+    walls in y and z, body-force-driven duct flow, spheres of radius 6, ten
+    drive periods), the workload of the displacement bars, against the FP64
+    GPU path: the relative L2 error of the velocity field and the relative
+    error of the swimmer's net displacement."""
+    import numpy as np
+    from paper_1108_0786_gb300 import lbm, workloads as wl
+    sc = wl.channel_swimmer()
+    ref = lbm.from_scenario(sc, precision="f64")
+    x0 = ref.bodies()[:, :3].copy()
+    ref.step(sc.steps)
+    ref_u = ref.u()
+    ref_net = (ref.bodies()[:, :3] - x0).mean(axis=0)
+    ref.close()
+    out = {"steps": sc.steps, "net_displacement_lu": float(np.linalg.norm(ref_net))}
+    for prec in ("f32", "f16", "bf16"):
+        lat = lbm.from_scenario(sc, precision=prec)
+        lat.step(sc.steps)
+        net = (lat.bodies()[:, :3] - x0).mean(axis=0)
+        out[prec] = {"u_rel_l2": float(np.linalg.norm(lat.u() - ref_u) / np.linalg.norm(ref_u)),
+                     "net_displacement_rel_err": float(np.linalg.norm(net - ref_net) / np.linalg.norm(ref_net))}
+        lat.close()
+    return out
 
 
 # the oracle's timed samples: (config, steps at all threads, steps at 1 thread,

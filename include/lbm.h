@@ -103,7 +103,7 @@ extern "C" {
 #define LBM_MAX_BODY_STEP  0.5   /* largest displacement of a body per step */
 
 /* kernel slots reported by lbm_time_kernels */
-#define LBM_KERNEL_REMAP          0   /* map bodies to the lattice (after body geometry and candidates) */
+#define LBM_KERNEL_REMAP          0   /* body geometry and remap candidates, then map bodies to the lattice */
 #define LBM_KERNEL_STREAM_COLLIDE 1   /* bulk pull + LBGK over all cells */
 #define LBM_KERNEL_BOUNDARY       2   /* refill / bounce-back cells near bodies and walls */
 #define LBM_KERNEL_LINKS          3   /* per-body link lists, then the step's drive and spring loads */
@@ -394,12 +394,9 @@ int lbm_ensemble_destroy(lbm_ensemble_t *e);
 const char *lbm_ensemble_last_error(lbm_ensemble_t *e);
 
 /* Kernel launches one step makes (for launch accounting): with bodies and
- * fluid, remap, bulk stream-collide, boundary cells (one more launch with
- * walls), link lists, drive and spring loads, and the momentum exchange with
- * the rigid-body step, whose last block also prepares the next step's bodies
- * (a body-preparation kernel runs once more only after a state set from the
- * host); overlapped steps (LBM_OPT_OVERLAP) add the near cells and the next
- * step's near tiles. */
+ * fluid, body preparation, remap, bulk stream-collide, boundary cells (one
+ * more launch with walls), link lists, drive and spring loads, and the
+ * momentum exchange with the rigid-body step. */
 int lbm_kernels_per_step(lbm_t *h);
 
 /* Algorithmic bytes per cell the stream-collide kernel moves:

@@ -18,6 +18,10 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
 HEADER = os.path.join(ROOT, "include", "lbm.h")
 SOURCES = ["stream_collide.cu", "kernels.cu", "runtime.cu", "static_scratch.cu", "adjoint.cu"]
+# the cell kernels are compiled without implicit multiply-add contraction: a
+# cell's arithmetic then rounds the same in every kernel that runs it (launch
+# shapes, batched ensembles, the boundary kernel); the wanted FMAs are explicit
+NO_CONTRACT = {"stream_collide.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
@@ -49,7 +53,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc, *ARCH, *FLAGS, *extra_flags, "-c", s, "-o", o]
+            fmad = ["-fmad=false"] if src in NO_CONTRACT else []
+            cmd = [nvcc, *ARCH, *FLAGS, *fmad, *extra_flags, "-c", s, "-o", o]
             jobs.append(cmd)
     def run(cmd):
         if verbose:

@@ -234,41 +234,9 @@ __device__ inline bool spans_meet(int b0, int bw, int e0, int ew, int n, int per
 // boundary kernel's list.
 constexpr int PREP_THREADS = 256;
 
-// Each body's remap candidates for the state whose geometry records are in
-// slot `slot`: the bodies, in order, whose grown box meets its remap cube (a
-// warp a body, ballots over the candidates).  All threads of one block; the
-// records are read past L1 (the step's last block reads records that other
-// blocks of the same kernel wrote).
-__device__ void make_candidates(const Device &dv, int slot) {
-    const Domain d = dv.dom;
-    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    BodyGeom *cur = dv.geom + slot * dv.nb;
-    __shared__ int s_box[LBM_MAX_BODIES_DEV][8];        // ebox (6), then origin packed per axis below
-    __shared__ int s_org[LBM_MAX_BODIES_DEV][4];
-    for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) {
-        for (int i = 0; i < 6; ++i) s_box[k][i] = __ldcg(cur[k].ebox + i);
-        for (int i = 0; i < 3; ++i) s_org[k][i] = __ldcg(cur[k].origin + i);
-        s_org[k][3] = __ldcg(&cur[k].side);
-    }
-    __syncthreads();
-    for (int b = warp; b < dv.nb; b += blockDim.x / 32) {
-        int cnt = 0;
-        for (int k0 = 0; k0 < dv.nb; k0 += 32) {
-            const int k = k0 + lane;
-            bool meets = k < dv.nb;
-            for (int a = 0; a < 3 && meets; ++a)
-                meets = spans_meet(s_org[b][a], s_org[b][3], s_box[k][a], s_box[k][3 + a], n3[a], per[a]);
-            const unsigned bal = __ballot_sync(0xffffffffu, meets);
-            if (meets) dv.cand[b * dv.nb + cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)k;
-            cnt += __popc(bal);
-        }
-        if (lane == 0) cur[b].ncand = cnt;
-    }
-}
-
 __device__ __forceinline__ void prep_body(const Device &dv, const StepPtrs &sp) {
     const Domain d = dv.dom;
+    const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BodyGeom *cur = dv.geom + sp.parity * dv.nb, *prev = dv.geom + (sp.parity ^ 1) * dv.nb;
     BodyState *scur = dv.gstamp + sp.parity * dv.nb, *sprev = dv.gstamp + (sp.parity ^ 1) * dv.nb;
@@ -285,7 +253,27 @@ __device__ __forceinline__ void prep_body(const Device &dv, const StepPtrs &sp) 
         }
     }
     __syncthreads();
-    make_candidates(dv, sp.parity);
+    __shared__ int s_box[LBM_MAX_BODIES_DEV][8];        // ebox (6), then origin packed per axis below
+    __shared__ int s_org[LBM_MAX_BODIES_DEV][4];
+    for (int k = threadIdx.x; k < dv.nb; k += blockDim.x) {
+        for (int i = 0; i < 6; ++i) s_box[k][i] = cur[k].ebox[i];
+        for (int i = 0; i < 3; ++i) s_org[k][i] = cur[k].origin[i];
+        s_org[k][3] = cur[k].side;
+    }
+    __syncthreads();
+    for (int b = warp; b < dv.nb; b += PREP_THREADS / 32) {
+        int cnt = 0;
+        for (int k0 = 0; k0 < dv.nb; k0 += 32) {
+            const int k = k0 + lane;
+            bool meets = k < dv.nb;
+            for (int a = 0; a < 3 && meets; ++a)
+                meets = spans_meet(s_org[b][a], s_org[b][3], s_box[k][a], s_box[k][3 + a], n3[a], per[a]);
+            const unsigned bal = __ballot_sync(0xffffffffu, meets);
+            if (meets) dv.cand[b * dv.nb + cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)k;
+            cnt += __popc(bal);
+        }
+        if (lane == 0) cur[b].ncand = cnt;
+    }
 }
 
 __global__ void __launch_bounds__(PREP_THREADS) prep_kernel(const Device dv, const StepPtrs sp) { prep_body(dv, sp); }
@@ -1005,39 +993,25 @@ __device__ __forceinline__ void force_body(const Device &dv, const StepPtrs &sp,
     }
     // the last of body b's blocks integrates body b with its first warp
     // (the drive and spring loads were evaluated beside the bulk kernel);
-    // the last body's block ends the step: from the geometry records the
-    // rigid-body warps wrote it makes the next step's remap candidates and
-    // empties the next step's boundary-cell list (the work of the body
-    // preparation kernel, which steps then launch only after the host set a
-    // state)
-    __shared__ int last_of_body, last_block;
+    // the last body ends the step
+    __shared__ int last_of_body;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         last_of_body = atomicAdd(dv.body_done + b, 1u) == (unsigned)bk.gx - 1;
-        last_block = 0;
     }
     __syncthreads();
-    if (!last_of_body) return;
+    if (!last_of_body || threadIdx.x >= 32) return;
     __threadfence();
-    if (threadIdx.x < 32) {
-        integrate_body_warp(dv, sp, b, 1);
-        __syncwarp();
-        if (threadIdx.x == 0) {
-            dv.body_done[b] = 0u;
-            __threadfence();
-            last_block = atomicAdd(dv.blocks_done, 1u) == (unsigned)bk.gy - 1;
-        }
-    }
-    __syncthreads();
-    if (!last_block) return;
+    integrate_body_warp(dv, sp, b, 1);
+    __syncwarp();
+    if (threadIdx.x != 0) return;
+    dv.body_done[b] = 0u;
     __threadfence();
-    make_candidates(dv, sp.parity ^ 1);
-    if (threadIdx.x == 0) {
-        *dv.blocks_done = 0u;
-        *dv.bcount = 0;
-        finish_step(dv, sp);
-    }
+    if (atomicAdd(dv.blocks_done, 1u) != (unsigned)bk.gy - 1) return;
+    __threadfence();
+    *dv.blocks_done = 0u;
+    finish_step(dv, sp);
 }
 
 template <typename T>
@@ -1225,12 +1199,8 @@ void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8
     init_flags_kernel<<<blocks_for(dv.dom.C, 256), 256, 0, s>>>(dv.dom, flags0, flags1, bid0, bid1);
 }
 
-void launch_prep(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
+void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s) {
     prep_kernel<<<1, PREP_THREADS, 0, s>>>(dv, sp);
-}
-
-void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s, bool with_prep) {
-    if (with_prep) prep_kernel<<<1, PREP_THREADS, 0, s>>>(dv, sp);
     const int side = dv.remap_side;
     const unsigned bx = (unsigned)(((side + REMAP_TY - 1) / REMAP_TY) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS));
     remap_kernel<<<dim3(bx, dv.nb), dim3(REMAP_TX, REMAP_TY), 0, s>>>(dv, sp, init_mode);

@@ -365,11 +365,7 @@ struct AdjBody {
 // ---- launch wrappers (kernels.cu / stream_collide.cu / adjoint.cu) ---------
 void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8_t *bid0,
                        uint8_t *bid1, cudaStream_t s);
-// with_prep: the body-preparation kernel first (geometry records of host-set
-// states, remap candidates, an empty cell list); a step's force kernel leaves
-// the next step prepared, so steps launch it only after the host set a state
-void launch_prep(const Device &dv, const StepPtrs &sp, cudaStream_t s);
-void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s, bool with_prep = true);
+void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s);
 void launch_stream_collide(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_boundary_fix(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 bool needs_boundary_fix(const Device &dv);

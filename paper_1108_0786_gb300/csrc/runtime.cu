@@ -50,7 +50,6 @@ struct lbm_s {
     cudaStream_t far = nullptr;
     cudaEvent_t far_ev[2] = {nullptr, nullptr}, near_ev[2] = {nullptr, nullptr};
     bool tiles_stale = false;           // the host set a body state: redo the next step's near tiles
-    bool need_prep = true;              // the host set a body state: prepare the next step's bodies
     lbm_alloc_fn afn = nullptr;
     lbm_free_fn ffn = nullptr;
     void *actx = nullptr;
@@ -165,10 +164,8 @@ lbm::StepPtrs step_ptrs(lbm_t *h, int p, bool overlap = false) {
 // sums.
 void enqueue_overlapped(lbm_t *h, int p, cudaStream_t s, bool first);
 
-// with_prep: launch the body-preparation kernel (eager and ensemble steps);
-// the step graphs leave it to lbm_step after a host-set state
 void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bool *ran = nullptr,
-                  bool fork = false, bool with_prep = true) {
+                  bool fork = false) {
     const lbm::StepPtrs sp = step_ptrs(h, p);
     const bool bodies = nb(h) > 0, fl = fluid(h);
     auto run = [&](int slot, cudaStream_t st, auto &&fn) {
@@ -177,7 +174,7 @@ void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bo
         if (ev) cudaEventRecord(ev[2 * slot + 1], st);
         if (ran) ran[slot] = true;
     };
-    if (bodies && fl) run(LBM_KERNEL_REMAP, s, [&] { lbm::launch_remap(h->dv, sp, 0, s, with_prep); });
+    if (bodies && fl) run(LBM_KERNEL_REMAP, s, [&] { lbm::launch_remap(h->dv, sp, 0, s); });
     const bool boundary = fl && lbm::needs_boundary_fix(h->dv);
     const bool forked = boundary && fork;
     if (forked) {
@@ -225,7 +222,7 @@ void enqueue_overlapped(lbm_t *h, int p, cudaStream_t s, bool first) {
     lbm::launch_stream_collide(h->dv, sp, h->far);
     cudaEventRecord(h->far_ev[p], h->far);
     // the chain
-    lbm::launch_remap(h->dv, sp, 0, s, false);
+    lbm::launch_remap(h->dv, sp, 0, s);
     lbm::launch_links(h->dv, sp, s);
     if (!first) cudaStreamWaitEvent(s, h->far_ev[q], 0);
     lbm::launch_boundary_fix(h->dv, sp, s);
@@ -257,7 +254,7 @@ int kernels_per_step(const lbm_t *h) {
     const bool bodies = nb(h) > 0, fl = fluid(h);
     const bool walls = (h->bc & 7) != 7;
     int n = 0;
-    if (bodies && fl) n += 1;                               // remap (body preparation: only after a host-set state)
+    if (bodies && fl) n += 2;                               // body preparation, remap
     if (fl) n += 1;                                         // bulk stream-collide
     if (fl) n += (bodies ? 1 : 0) + (walls ? 1 : 0);        // boundary cells
     if (bodies && fl) n += 3;                               // links, drive and spring loads, force + rigid-body step
@@ -276,10 +273,9 @@ int init_flags(lbm_t *h) {
         sp.body_cur = h->bodies[0];
         lbm::launch_remap(h->dv, sp, 1, h->stream);
     }
-    // the first step's near tiles; its bodies are prepared at the first step
+    // the first step's near tiles
     if (h->dv.overlap) lbm::launch_near_tiles(h->dv, h->bodies[0], 0, 0, h->stream);
     h->tiles_stale = false;
-    h->need_prep = true;
     CK(cudaGetLastError());
     return LBM_OK;
 }
@@ -502,7 +498,7 @@ int build_graphs(lbm_t *h) {
         for (int i = 0; i < n; ++i) {
             const int p = (p0 + i) & 1;
             if (ov) enqueue_overlapped(h, p, h->cap, i == 0);
-            else enqueue_step(h, p, h->cap, nullptr, nullptr, true, false);
+            else enqueue_step(h, p, h->cap, nullptr, nullptr, true);
         }
         if (ov) cudaStreamWaitEvent(h->cap, h->far_ev[(p0 + n - 1) & 1], 0);
     };
@@ -805,7 +801,6 @@ int lbm_set_body_state(lbm_t *h, int b, const double state[13]) {
                         LBM_MAX_BODY_STEP);
     CK(cudaMemcpy(cur, &s, sizeof s, cudaMemcpyHostToDevice));
     h->tiles_stale = true;
-    h->need_prep = true;
     return LBM_OK;
 }
 
@@ -835,11 +830,6 @@ int lbm_step(lbm_t *h, int n) {
     if (rc) return rc;
     if ((rc = build_graphs(h))) return rc;
     if (n > 0 && (rc = refresh_tiles(h))) return rc;
-    if (n > 0 && h->need_prep) {
-        if (nb(h) > 0 && fluid(h)) lbm::launch_prep(h->dv, step_ptrs(h, (int)(h->steps & 1)), h->stream);
-        CK(cudaGetLastError());
-        h->need_prep = false;
-    }
     while (n > 0) {
         const int p = (int)(h->steps & 1);
         if (p == 0 && n >= CHUNK_STEPS) {
@@ -1080,7 +1070,6 @@ int lbm_load(lbm_t *h, const char *path) {
     const int st[4] = {0, 0, 1, 1};
     CK(cudaMemcpy(h->dv.status, st, sizeof st, cudaMemcpyHostToDevice));
     h->tiles_stale = true;
-    h->need_prep = true;
     return LBM_OK;
 }
 
@@ -1257,9 +1246,6 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         ~Guard() {
             cudaStreamSynchronize(h->stream);
             free_list(h, list);
-            // the recomputation rewrote geometry records and candidates:
-            // the next step prepares its bodies again
-            h->need_prep = true;
         }
     } guard{h, bk};
     // recompute and adjoint buffers

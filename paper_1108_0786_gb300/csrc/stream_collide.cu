@@ -128,6 +128,26 @@ __device__ __forceinline__ T shfl(T v, int delta, bool up) {
 // arithmetic; otherwise one direction at a time.  Both forms compute the
 // same expression (FP32 takes the paired one; the 16-bit kernels schedule
 // the per-direction one better).
+// explicit fused multiply-adds: this file is compiled without implicit
+// contraction (-fmad=false), so every kernel that runs a cell's arithmetic --
+// any launch shape, the batched ensemble kernels, the boundary kernel --
+// rounds it identically, and the FMAs the collision wants are spelled out
+__device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// e_b . (x, y, z) over the non-zero components of e_b only, in x, y, z
+// order (a zero component would still cost a multiply and an add: 0 * z is
+// not 0 for every z)
+template <typename R>
+__device__ __forceinline__ R edot(int b, R x, R y, R z) {
+    R r = 0;
+    bool any = false;
+    if (ex(b)) { r = ex(b) > 0 ? x : -x; any = true; }
+    if (ey(b)) { const R t = ey(b) > 0 ? y : -y; r = any ? r + t : t; any = true; }
+    if (ez(b)) { const R t = ez(b) > 0 ? z : -z; r = any ? r + t : t; }
+    return r;
+}
+
 template <typename Cd, bool CLOSE, bool PAIRED = CLOSE>
 __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     Cd s = 0, jx = 0, jy = 0, jz = 0;
@@ -144,26 +164,25 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
     const bool f32 = sizeof(Cd) == 4;
     const Cd gx = f32 ? (Cd)dv.g_f[0] : (Cd)dv.g[0], gy = f32 ? (Cd)dv.g_f[1] : (Cd)dv.g[1],
              gz = f32 ? (Cd)dv.g_f[2] : (Cd)dv.g[2];
-    const Cd ux = (jx + (Cd)0.5 * gx) * inv, uy = (jy + (Cd)0.5 * gy) * inv, uz = (jz + (Cd)0.5 * gz) * inv;
-    const Cd usq = ux * ux + uy * uy + uz * uz;
+    const Cd ux = mad((Cd)0.5, gx, jx) * inv, uy = mad((Cd)0.5, gy, jy) * inv, uz = mad((Cd)0.5, gz, jz) * inv;
+    const Cd usq = mad(ux, ux, mad(uy, uy, uz * uz));
     const Cd om = f32 ? (Cd)dv.omega_f : (Cd)dv.omega;
     const Cd guo = f32 ? (Cd)dv.guo_f : (Cd)(1.0 - 0.5 * dv.omega);
-    const Cd ug = ux * gx + uy * gy + uz * gz;
-    const Cd base = s - (Cd)1.5 * rho * usq;    // deviation of f_eq without the e.u terms, over w
+    const Cd ug = mad(ux, gx, mad(uy, gy, uz * gz));
+    const Cd base = mad((Cd)(-1.5) * rho, usq, s);     // deviation of f_eq without the e.u terms, over w
     Cd m = 0, px = 0, py = 0, pz = 0;
     // one relaxation: the increment of direction b towards deq (+ Guo's term
     // gt), kept for the conservation closure or applied directly
     auto relax = [&](int b, Cd deq, Cd gt) {
         if constexpr (CLOSE) {
-            Cd d = om * (deq - f[b]);
-            if (dv.forced) d += gt;
+            const Cd d = dv.forced ? mad(om, deq - f[b], gt) : om * (deq - f[b]);
             m += d;
             if (ex(b)) px += ex(b) > 0 ? d : -d;
             if (ey(b)) py += ey(b) > 0 ? d : -d;
             if (ez(b)) pz += ez(b) > 0 ? d : -d;
             f[b] += d;
         } else {
-            Cd o = f[b] - om * (f[b] - deq);
+            Cd o = mad(-om, f[b] - deq, f[b]);
             if (dv.forced) o += gt;
             f[b] = o;
         }
@@ -173,12 +192,12 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
             const Cd w = (Cd)wgt(b);
-            const Cd eu = (Cd)ex(b) * ux + (Cd)ey(b) * uy + (Cd)ez(b) * uz;
-            const Cd deq = w * (s + rho * ((Cd)3 * eu + (Cd)4.5 * eu * eu - (Cd)1.5 * usq));
+            const Cd eu = edot(b, ux, uy, uz);
+            const Cd deq = w * mad(rho, mad((Cd)4.5 * eu, eu, mad((Cd)3, eu, (Cd)(-1.5) * usq)), s);
             Cd gt = 0;
             if (dv.forced) {
-                const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
-                gt = guo * w * ((Cd)3 * (eg - ug) + (Cd)9 * eu * eg);
+                const Cd eg = edot(b, gx, gy, gz);
+                gt = guo * w * mad((Cd)9 * eu, eg, (Cd)3 * (eg - ug));
             }
             relax(b, deq, gt);
         }
@@ -190,13 +209,13 @@ __device__ __forceinline__ void collide(Cd (&f)[Q], const Device &dv) {
 #pragma unroll
     for (int b = 1; b < Q; b += 2) {
         const Cd w = (Cd)wgt(b);
-        const Cd eu = (Cd)ex(b) * ux + (Cd)ey(b) * uy + (Cd)ez(b) * uz;
-        const Cd a = base + (Cd)4.5 * rho * eu * eu;
+        const Cd eu = edot(b, ux, uy, uz);
+        const Cd a = mad((Cd)4.5 * rho * eu, eu, base);
         const Cd c = (Cd)3 * rho * eu;
         Cd g1 = 0, g2 = 0;
         if (dv.forced) {
-            const Cd eg = (Cd)ex(b) * gx + (Cd)ey(b) * gy + (Cd)ez(b) * gz;
-            const Cd sym = (Cd)9 * eu * eg - (Cd)3 * ug, asym = (Cd)3 * eg;
+            const Cd eg = edot(b, gx, gy, gz);
+            const Cd sym = mad((Cd)9 * eu, eg, (Cd)(-3) * ug), asym = (Cd)3 * eg;
             g1 = guo * w * (sym + asym);
             g2 = guo * w * (sym - asym);
         }
@@ -242,25 +261,25 @@ __device__ __forceinline__ void collide_lean(float (&f)[Q], const Device &dv) {
     const float kh = 0.5f * k;
     const float gx = dv.g_f[0], gy = dv.g_f[1], gz = dv.g_f[2];
     const float ux = fmaf(kh, gx, jx) * inv, uy = fmaf(kh, gy, jy) * inv, uz = fmaf(kh, gz, jz) * inv;
-    const float usq = ux * ux + uy * uy + uz * uz;
+    const float usq = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
     const float kr = k * rho;
     const float base = fmaf(-1.5f * kr, usq, s);       // k (drho - 1.5 rho u.u)
     const float A = 4.5f * kr, Cc = 3.0f * kr;
     const float om1 = dv.om1_f;
     const bool forced = dv.forced;
-    const float ug3 = forced ? -3.0f * k * (ux * gx + uy * gy + uz * gz) : 0.0f;
-    f[0] = fmaf(om1, f[0], dv.ow_f[0] * base + (forced ? dv.gw_f[0] * ug3 : 0.0f));
+    const float ug3 = forced ? -3.0f * k * fmaf(ux, gx, fmaf(uy, gy, uz * gz)) : 0.0f;
+    f[0] = fmaf(om1, f[0], forced ? fmaf(dv.gw_f[0], ug3, dv.ow_f[0] * base) : dv.ow_f[0] * base);
 #pragma unroll
     for (int p = 0; p < Q / 2; ++p) {
         const int b = 2 * p + 1;
         const int wc = b < 7 ? 1 : 2;
-        const float eu = (float)ex(b) * ux + (float)ey(b) * uy + (float)ez(b) * uz;
+        const float eu = edot(b, ux, uy, uz);
         const float a = fmaf(A, eu * eu, base);
         const float c = Cc * eu;
         const float ow = dv.ow_f[wc];
         float r1 = ow * (a + c), r2 = ow * (a - c);
         if (forced) {
-            const float eg = (float)ex(b) * gx + (float)ey(b) * gy + (float)ez(b) * gz;
+            const float eg = edot(b, gx, gy, gz);
             const float sym = fmaf(9.0f * k * eu, eg, ug3), asym = 3.0f * k * eg;
             const float gw = dv.gw_f[wc];
             r1 = fmaf(gw, sym + asym, r1);
@@ -336,17 +355,31 @@ template <typename T> __device__ __forceinline__ Dither dither_for(long long c, 
     else return Dither{};
 }
 
-template <typename T, int V, int BX, int BY>
+template <typename T, int V, int BX, int BY, bool FLAT = false>
 __device__ __forceinline__ void bulk_body(const Device &dv, const StepPtrs &sp, const Blk &bk) {
     using Cd = typename Codec<T>::C;
     const Domain d = dv.dom;
     const int nxq = d.nx / V;
-    int xq = bk.x * BX + threadIdx.x;
-    int y = bk.y * BY + threadIdx.y;
+    int xq, y;
+    bool active;
+    if constexpr (FLAT) {
+        // the z-plane's V-cell groups in row order, BX * BY a block: a warp's
+        // lanes may cross a row end, where the x-neighbour fallbacks below
+        // (first and last cell of a row) take over from the shuffles
+        const int per_plane = nxq * d.ny;
+        int q = bk.x * (BX * BY) + threadIdx.y * BX + threadIdx.x;
+        active = q < per_plane;
+        q = min(q, per_plane - 1);
+        xq = q % nxq;
+        y = q / nxq;
+    } else {
+        xq = bk.x * BX + threadIdx.x;
+        y = bk.y * BY + threadIdx.y;
+        active = xq < nxq && y < d.ny;
+        xq = min(xq, nxq - 1);          // inactive lanes still join the shuffles
+        y = min(y, d.ny - 1);
+    }
     const int z = bk.z;
-    const bool active = xq < nxq && y < d.ny;
-    xq = min(xq, nxq - 1);              // inactive lanes still join the shuffles
-    y = min(y, d.ny - 1);
     const int lane = threadIdx.x & 31;
     const int x0 = xq * V;
     const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
@@ -448,7 +481,7 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
-    bulk_body<T, V, BX, BY>(sdv, ssp, sbk);
+    bulk_body<T, V, BX, BY, true>(sdv, ssp, sbk);
 }
 
 // 16-bit values packed two to a 32-bit word (the lower address in the low
@@ -483,19 +516,33 @@ template <typename T> __device__ __forceinline__ unsigned store_bits(float v, co
 // shuffled from the neighbouring lane); a cell's 19 values are widened to
 // FP32 just before its collision (collide_lean, the row-staged kernel's
 // arithmetic) and narrowed back into their half-words after it.
-template <typename T, int V, int BX, int BY>
+template <typename T, int V, int BX, int BY, bool FLAT = false>
 __device__ __forceinline__ void bulk16_body(const Device &dv, const StepPtrs &sp, const Blk &bk) {
     static_assert(sizeof(T) == 2 && V % 2 == 0, "two 16-bit cells a word");
     constexpr int W = V / 2;
     using RawV = typename Raw<2 * V>::type;
     const Domain d = dv.dom;
     const int nxq = d.nx / V;
-    int xq = bk.x * BX + threadIdx.x;
-    int y = bk.y * BY + threadIdx.y;
+    int xq, y;
+    bool active;
+    if constexpr (FLAT) {
+        // the z-plane's V-cell groups in row order, BX * BY a block: a warp's
+        // lanes may cross a row end, where the x-neighbour fallbacks below
+        // (first and last cell of a row) take over from the shuffles
+        const int per_plane = nxq * d.ny;
+        int q = bk.x * (BX * BY) + threadIdx.y * BX + threadIdx.x;
+        active = q < per_plane;
+        q = min(q, per_plane - 1);
+        xq = q % nxq;
+        y = q / nxq;
+    } else {
+        xq = bk.x * BX + threadIdx.x;
+        y = bk.y * BY + threadIdx.y;
+        active = xq < nxq && y < d.ny;
+        xq = min(xq, nxq - 1);          // inactive lanes still join the shuffles
+        y = min(y, d.ny - 1);
+    }
     const int z = bk.z;
-    const bool active = xq < nxq && y < d.ny;
-    xq = min(xq, nxq - 1);              // inactive lanes still join the shuffles
-    y = min(y, d.ny - 1);
     const int lane = threadIdx.x & 31;
     const int x0 = xq * V;
     const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
@@ -589,7 +636,7 @@ bulk16_kernel(const Device dv, const StepPtrs sp) {
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk16_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
-    bulk16_body<T, V, BX, BY>(sdv, ssp, sbk);
+    bulk16_body<T, V, BX, BY, true>(sdv, ssp, sbk);
 }
 
 // Velocity of body b's surface at lattice point p in the compute type R:
@@ -1239,7 +1286,7 @@ void launch_near_bulk(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
 
 namespace {
 
-constexpr int BATCH_BX = 32, BATCH_BY = 8;      // ensembles' boxes are narrow: 32 x 8 threads a block
+constexpr int BATCH_BX = 32, BATCH_BY = 8;      // 256 threads a block, a plane's cells in row order
 
 template <typename T, int V>
 void bulk_batch_launch(const Batch &bt, unsigned blocks, cudaStream_t s) {
@@ -1293,8 +1340,9 @@ void batch_grid_cells(const Device &dv, int k, int variant, int g[3]) {
     } else if (k == BK_BULK) {
         const BatchShape *b = batch_shape(dv.precision, variant);
         if (!b || d.nx % b->vec) return;
-        g[0] = (d.nx / b->vec + BATCH_BX - 1) / BATCH_BX;
-        g[1] = (d.ny + BATCH_BY - 1) / BATCH_BY;
+        // a z-plane's V-cell groups in row order (no lanes idle at row ends)
+        g[0] = (int)(((long long)(d.nx / b->vec) * d.ny + BATCH_BX * BATCH_BY - 1) / (BATCH_BX * BATCH_BY));
+        g[1] = 1;
         g[2] = d.nz;
     }
 }

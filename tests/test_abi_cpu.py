@@ -57,9 +57,8 @@ def test_host_side_calls_without_a_device(lib):
     out = np.zeros(26)
     assert lib.lbm_get_bodies(h, out.ctypes.data_as(dp)) == 0
     assert np.array_equal(out[:3], p) and out[3] == 1.0
-    # remap, bulk, boundary, links, drive and spring loads, force + integrate (whose last
-    # block prepares the next step's bodies)
-    assert lib.lbm_kernels_per_step(h) == 6
+    # body preparation, remap, bulk, boundary, links, drive and spring loads, force + integrate
+    assert lib.lbm_kernels_per_step(h) == 7
     assert lib.lbm_bytes_per_cell(h) == 2 * 19 * 4 + 1
     assert lib.lbm_destroy(h) == 0
 
