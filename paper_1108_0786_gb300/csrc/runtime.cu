@@ -479,13 +479,13 @@ int build_graphs(lbm_t *h) {
     if (h->graphs_ready) return LBM_OK;
     // overlapped steps: the chain (captured on cap) takes precedence over the
     // far bulk kernel, so that its short kernels start as soon as SMs free
+    const bool ov = h->dv.overlap != 0;
     int least = 0, greatest = 0;
     CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    if (!h->cap) CK(cudaStreamCreateWithPriority(&h->cap, cudaStreamNonBlocking, greatest));
+    if (!h->cap) CK(cudaStreamCreateWithPriority(&h->cap, cudaStreamNonBlocking, ov ? greatest : 0));
     if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
     if (!h->join_ev) CK(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
-    const bool ov = h->dv.overlap != 0;
     if (ov) {
         if (!h->far) CK(cudaStreamCreateWithPriority(&h->far, cudaStreamNonBlocking, least));
         for (int i = 0; i < 2; ++i) {
@@ -507,14 +507,14 @@ int build_graphs(lbm_t *h) {
         CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
         steps(p, 1);
         CK(cudaStreamEndCapture(h->cap, &g));
-        CK(cudaGraphInstantiate(&h->single[p], g, cudaGraphInstantiateFlagUseNodePriority));
+        CK(cudaGraphInstantiate(&h->single[p], g, ov ? cudaGraphInstantiateFlagUseNodePriority : 0));
         cudaGraphDestroy(g);
     }
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     steps(0, CHUNK_STEPS);
     CK(cudaStreamEndCapture(h->cap, &g));
-    CK(cudaGraphInstantiate(&h->chunk, g, cudaGraphInstantiateFlagUseNodePriority));
+    CK(cudaGraphInstantiate(&h->chunk, g, ov ? cudaGraphInstantiateFlagUseNodePriority : 0));
     cudaGraphDestroy(g);
     h->graphs_ready = true;
     return LBM_OK;
