@@ -281,8 +281,9 @@ int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm);
 int lbm_autotune(lbm_t *h, int trials, int *cells_per_thread, int *min_blocks_per_sm);
 
 /* Checks of the failure paths (failure detection; the paper has no
- * counterpart).  They make the device latch an error from the host side,
- * without faulting or hanging anything:
+ * counterpart) and of the reverse sweep's schedule.  The first two make the
+ * device latch an error from the host side, without faulting or hanging
+ * anything:
  *   LBM_DEBUG_EXPIRE_WAITS, value 1: the first wait of every block of the
  *     row-staged bulk kernel (lbm_tune with cells_per_thread = -1) is on a
  *     barrier that no copy completes, bounded by about 2^16 SM cycles.  It
@@ -294,10 +295,18 @@ int lbm_autotune(lbm_t *h, int trials, int *cells_per_thread, int *min_blocks_pe
  *     k entries instead of its sized capacity; a step that finds more
  *     latches LBM_E_LINKS, stores none past the capacity and handles only
  *     those listed.  Value 0: the sized capacity.
- * The steps after such an error are not valid.  Only before the first step
- * (LBM_E_STATE after it); LBM_E_ARG for an unknown knob or value. */
+ *   LBM_DEBUG_ADJOINT_SERIAL, value 1: lbm_adjoint_backward recomputes and
+ *     reverses its segments in turn with one set of recomputation slots.
+ *     Value 0 (default): where the device has room for a second set, the
+ *     recomputation of segment k - 1 runs on its own stream beside the
+ *     reverse steps of segment k.  Both give the same bits.  Any time; it
+ *     holds for the following calls of lbm_adjoint_backward.
+ * The steps after such an error are not valid.  The first two only before
+ * the first step (LBM_E_STATE after it); LBM_E_ARG for an unknown knob or
+ * value. */
 #define LBM_DEBUG_EXPIRE_WAITS  1
 #define LBM_DEBUG_CELL_LIST_CAP 2
+#define LBM_DEBUG_ADJOINT_SERIAL 3
 int lbm_debug_set(lbm_t *h, int knob, long long value);
 
 /* ---- reverse mode ---------------------------------------------------------

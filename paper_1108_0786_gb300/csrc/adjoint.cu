@@ -28,6 +28,9 @@ namespace lbm {
 namespace {
 
 constexpr int ADJ_THREADS = 256;
+// boundary blocks are small: the cube's few link cells carry nearly all of
+// the work, and small blocks spread them over more SMs
+constexpr int ADJ_BOUNDARY_THREADS = 64;
 
 // density and velocity of step n from the post-collision deviations:
 // rho = 1 + sum delta; the collision adds g to the momentum (Guo), so
@@ -86,14 +89,16 @@ __device__ inline void collide_adjoint(A (&a)[Q], A rho, const A (&u)[3], const 
 
 // adjoint of the body-surface velocity u_w(p) = V + W x (p - X) for the
 // scalar uh . u_w: acc[0..2] += d/dX, acc[3..5] += d/dV, acc[6..8] += d/dW
-__device__ inline void adj_surface(const BodyState &b, const double o[3], const double uh[3], double acc[9]) {
-    acc[0] += b.W[1] * uh[2] - b.W[2] * uh[1];
-    acc[1] += b.W[2] * uh[0] - b.W[0] * uh[2];
-    acc[2] += b.W[0] * uh[1] - b.W[1] * uh[0];
-    acc[3] += uh[0]; acc[4] += uh[1]; acc[5] += uh[2];
-    acc[6] += o[1] * uh[2] - o[2] * uh[1];
-    acc[7] += o[2] * uh[0] - o[0] * uh[2];
-    acc[8] += o[0] * uh[1] - o[1] * uh[0];
+// (terms formed in S, summed in Acc)
+template <typename S, typename Acc>
+__device__ inline void adj_surface(const S W[3], const S o[3], const S uh[3], Acc acc[9]) {
+    acc[0] += (Acc)(W[1] * uh[2] - W[2] * uh[1]);
+    acc[1] += (Acc)(W[2] * uh[0] - W[0] * uh[2]);
+    acc[2] += (Acc)(W[0] * uh[1] - W[1] * uh[0]);
+    acc[3] += (Acc)uh[0]; acc[4] += (Acc)uh[1]; acc[5] += (Acc)uh[2];
+    acc[6] += (Acc)(o[1] * uh[2] - o[2] * uh[1]);
+    acc[7] += (Acc)(o[2] * uh[0] - o[0] * uh[2]);
+    acc[8] += (Acc)(o[0] * uh[1] - o[1] * uh[0]);
 }
 
 // ---- bulk cells: pure gather + transposed collision -------------------------
@@ -129,11 +134,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_bulk_kernel(const Device dv, 
 // + 1 around floor(X_k^n); only this body's adjoint terms are summed, into
 // part[k][blockIdx.x].  mode 1: wall faces, no body sums.
 template <typename A, typename T, bool FIRST>
-__global__ void __launch_bounds__(ADJ_THREADS) adj_boundary_kernel(const Device dv, const AdjPtrs ap, int mode) {
+__global__ void __launch_bounds__(ADJ_BOUNDARY_THREADS) adj_boundary_kernel(const Device dv, const AdjPtrs ap, int mode) {
     const Domain d = dv.dom;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     const int kb = mode == 0 ? (int)blockIdx.y : -1;
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    A acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int x = 0, y = 0, z = 0;
     bool live = true;
     if (mode == 0) {
@@ -198,32 +203,37 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_boundary_kernel(const Device 
                 const uint8_t fz = ap.flags_cur[zc];
                 if (fz & F_SOLID) {
                     // link (x, b) of step n: moving bounce-back of step n+1 and
-                    // the momentum exchange of step n share u_w(x + e_b; S^n)
+                    // the momentum exchange of step n share u_w(x + e_b; S^n).
+                    // The offset from the body centre is taken in FP64, the
+                    // link's terms in the adjoint's precision.
                     const int k = ap.bid_cur[zc];
-                    const BodyState sk = ap.body[k];
-                    double o[3], uw[3];
-                    offset_from(d, sk, (double)zx, (double)zy, (double)zz, o);
-                    uw[0] = sk.V[0] + (sk.W[1] * o[2] - sk.W[2] * o[1]);
-                    uw[1] = sk.V[1] + (sk.W[2] * o[0] - sk.W[0] * o[2]);
-                    uw[2] = sk.V[2] + (sk.W[0] * o[1] - sk.W[1] * o[0]);
-                    const double ua = -(ex(b) * uw[0] + ey(b) * uw[1] + ez(b) * uw[2]);   // e_-b . u_w
-                    double mh = 0.0;
+                    const BodyState &sk = ap.body[k];
+                    double od[3];
+                    offset_from(d, sk, (double)zx, (double)zy, (double)zz, od);
+                    const A o[3] = {(A)od[0], (A)od[1], (A)od[2]};
+                    const A W[3] = {(A)sk.W[0], (A)sk.W[1], (A)sk.W[2]};
+                    A uw[3];
+                    uw[0] = (A)sk.V[0] + (W[1] * o[2] - W[2] * o[1]);
+                    uw[1] = (A)sk.V[1] + (W[2] * o[0] - W[0] * o[2]);
+                    uw[2] = (A)sk.V[2] + (W[0] * o[1] - W[1] * o[0]);
+                    const A ua = -((A)ex(b) * uw[0] + (A)ey(b) * uw[1] + (A)ez(b) * uw[2]);   // e_-b . u_w
+                    A mh = 0;
                     if constexpr (!FIRST) {
                         const double *fa = ap.fadj + 6 * k;
-                        double m[3];
-                        offset_from(d, sk, x + 0.5 * ex(b), y + 0.5 * ey(b), z + 0.5 * ez(b), m);
-                        // (mid - X) x e_b
-                        const double t0 = m[1] * ez(b) - m[2] * ey(b), t1 = m[2] * ex(b) - m[0] * ez(b),
-                                     t2 = m[0] * ey(b) - m[1] * ex(b);
-                        mh = ex(b) * fa[0] + ey(b) * fa[1] + ez(b) * fa[2] + t0 * fa[3] + t1 * fa[4] + t2 * fa[5];
+                        // (mid - X) x e_b, mid = x + e_b / 2 = (x + e_b) - e_b / 2
+                        const A m[3] = {o[0] - (A)(0.5 * ex(b)), o[1] - (A)(0.5 * ey(b)), o[2] - (A)(0.5 * ez(b))};
+                        const A t0 = m[1] * (A)ez(b) - m[2] * (A)ey(b), t1 = m[2] * (A)ex(b) - m[0] * (A)ez(b),
+                                t2 = m[0] * (A)ey(b) - m[1] * (A)ex(b);
+                        mh = (A)ex(b) * (A)fa[0] + (A)ey(b) * (A)fa[1] + (A)ez(b) * (A)fa[2] + t0 * (A)fa[3] +
+                             t1 * (A)fa[4] + t2 * (A)fa[5];
                     }
-                    const double wh = (double)own[opp(b)];
-                    a[b] = (A)(wh + 2.0 * mh);
-                    cr += (A)(6.0 * wgt(b) * ua * (wh + mh));
+                    const A wh = own[opp(b)];
+                    a[b] = wh + (A)2 * mh;
+                    cr += (A)(6.0 * wgt(b)) * ua * (wh + mh);
                     if (k == kb) {
-                        const double sc = 6.0 * wgt(b) * rho_d * (wh + mh);
-                        const double uh[3] = {-ex(b) * sc, -ey(b) * sc, -ez(b) * sc};
-                        adj_surface(sk, o, uh, acc);
+                        const A sc = (A)(6.0 * wgt(b)) * rho * (wh + mh);
+                        const A uh[3] = {-(A)ex(b) * sc, -(A)ey(b) * sc, -(A)ez(b) * sc};
+                        adj_surface<A, A>(W, o, uh, acc);
                     }
                     // z uncovered at n+1: x (fluid at n and n+1) fed its density
                     if (!(ap.flags_next[zc] & F_SOLID) && fluid_next) cr += rin[zc];
@@ -277,7 +287,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_boundary_kernel(const Device 
                             uh[2] += pa * (cc * ez(b) - 3.0 * rho_d * uw[2]);
                         }
                         if (cnt) rh_out = (A)(rh / cnt);
-                        if (k == kb) adj_surface(sk, o, uh, acc);
+                        if (k == kb) adj_surface<double, A>(sk.W, o, uh, acc);
                     }
                 }
                 static_cast<A *>(ap.rout)[c] = rh_out;
@@ -286,20 +296,20 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_boundary_kernel(const Device 
     }
     if (mode != 0) return;
     // fixed-order block sum of this body's adjoint terms
-    __shared__ double part[ADJ_THREADS / 32][9];
+    __shared__ double part[ADJ_BOUNDARY_THREADS / 32][9];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        double v = acc[i];
+        A v = acc[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) part[warp][i] = v;
+        if (lane == 0) part[warp][i] = (double)v;
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            double v = lane < ADJ_THREADS / 32 ? part[lane][i] : 0.0;
+            double v = lane < ADJ_BOUNDARY_THREADS / 32 ? part[lane][i] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if (lane == 0) ap.part[((long long)kb * ap.part_stride + blockIdx.x) * 9 + i] = v;
@@ -539,12 +549,13 @@ void launch_bulk_cells(const Device &dv, const AdjPtrs &ap, cudaStream_t s) {
 template <typename A, typename T, bool FIRST>
 void launch_boundary_cells(const Device &dv, const AdjPtrs &ap, cudaStream_t s) {
     if (dv.nb > 0)
-        adj_boundary_kernel<A, T, FIRST><<<dim3(ap.part_stride, dv.nb), ADJ_THREADS, 0, s>>>(dv, ap, 0);
+        adj_boundary_kernel<A, T, FIRST><<<dim3(ap.part_stride, dv.nb), ADJ_BOUNDARY_THREADS, 0, s>>>(dv, ap, 0);
     if (!(dv.dom.px && dv.dom.py && dv.dom.pz)) {
         const long long nx = dv.dom.nx, ny = dv.dom.ny, nz = dv.dom.nz;
         const long long area = std::max(ny * nz, std::max(nx * nz, nx * ny));
-        adj_boundary_kernel<A, T, FIRST><<<dim3((unsigned)((area + ADJ_THREADS - 1) / ADJ_THREADS), 6),
-                                           ADJ_THREADS, 0, s>>>(dv, ap, 1);
+        adj_boundary_kernel<A, T, FIRST>
+            <<<dim3((unsigned)((area + ADJ_BOUNDARY_THREADS - 1) / ADJ_BOUNDARY_THREADS), 6), ADJ_BOUNDARY_THREADS, 0,
+               s>>>(dv, ap, 1);
     }
 }
 
@@ -552,7 +563,7 @@ void launch_boundary_cells(const Device &dv, const AdjPtrs &ap, cudaStream_t s) 
 
 int adjoint_part_stride(const Device &dv) {
     const long long side = dv.remap_side;
-    return (int)((side * side * side + ADJ_THREADS - 1) / ADJ_THREADS);
+    return (int)((side * side * side + ADJ_BOUNDARY_THREADS - 1) / ADJ_BOUNDARY_THREADS);
 }
 
 void launch_adj_integrate(const Device &dv, const AdjBody &ab, cudaStream_t s) {

@@ -35,6 +35,7 @@ struct lbm_s {
     int hist_cap = 0;
     int tune_vec = 0, tune_minb = 0;
     int expire_waits = 0;               // lbm_debug_set knobs
+    int adjoint_sets = 0;
     long long list_cap_limit = 0;
     double *avg_sum = nullptr;          // [3][C] running velocity sum (lbm_average_*)
     long long *avg_count = nullptr;     // steps added to it (device)
@@ -1118,13 +1119,17 @@ int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm) {
 
 int lbm_debug_set(lbm_t *h, int knob, long long value) {
     if (!h) return LBM_E_ARG;
-    if (h->ready) return fail(h, LBM_E_STATE, "lbm_debug_set must come before the first step");
+    if (h->ready && knob != LBM_DEBUG_ADJOINT_SERIAL)
+        return fail(h, LBM_E_STATE, "lbm_debug_set must come before the first step");
     if (knob == LBM_DEBUG_EXPIRE_WAITS) {
         if (value != 0 && value != 1) return fail(h, LBM_E_ARG, "LBM_DEBUG_EXPIRE_WAITS takes 0 or 1");
         h->expire_waits = (int)value;
     } else if (knob == LBM_DEBUG_CELL_LIST_CAP) {
         if (value < 0) return fail(h, LBM_E_ARG, "LBM_DEBUG_CELL_LIST_CAP takes a capacity >= 1, or 0 for the default");
         h->list_cap_limit = value;
+    } else if (knob == LBM_DEBUG_ADJOINT_SERIAL) {
+        if (value != 0 && value != 1) return fail(h, LBM_E_ARG, "LBM_DEBUG_ADJOINT_SERIAL takes 0 or 1");
+        h->adjoint_sets = value ? 1 : 0;
     } else {
         return fail(h, LBM_E_ARG, "unknown debug knob %d", knob);
     }
@@ -1240,19 +1245,31 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     const size_t pop_sz = es * lbm::Q * C;
     const int K = tp.seg;
     std::vector<void *> bk;         // this call's buffers
+    cudaStream_t rs = nullptr;      // the recomputation's stream
     struct Guard {
         lbm_t *h;
         std::vector<void *> &list;
+        cudaStream_t &rs;
         ~Guard() {
+            if (rs) {
+                cudaStreamSynchronize(rs);
+                cudaStreamDestroy(rs);
+            }
+            if (h->side) cudaStreamSynchronize(h->side);
             cudaStreamSynchronize(h->stream);
             free_list(h, list);
         }
-    } guard{h, bk};
-    // recompute and adjoint buffers
-    void *seg_pop = nullptr, *A[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
-    uint8_t *seg_flags = nullptr, *seg_bid = nullptr, *carry = nullptr;
-    double *sa[2], *fadj, *part, *grads, *r_fh, *drive_sc;
-    BodyState *scratch;
+    } guard{h, bk, rs};
+    // a slot set holds one segment's recomputed epochs: populations (slots
+    // 0..K), flags and body ids (slots 0..K+1)
+    struct SlotSet {
+        void *pop = nullptr;
+        uint8_t *flags = nullptr, *bid = nullptr;
+    } sets[2];
+    uint8_t *carry = nullptr;       // one set: the flags of epoch m + L kept from segment k + 1
+    void *A[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
+    double *sa[2], *fadj, *part, *grads, *r_fh = nullptr, *drive_sc, *r_drive_f = nullptr, *r_spring_f = nullptr;
+    BodyState *scratch = nullptr;
     lbm::Link *r_links = nullptr;
     int *r_seg = nullptr, *r_changed = nullptr;
     long long *r_t = nullptr;
@@ -1265,17 +1282,34 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     const size_t ngrad = 2 * (size_t)ND + 3 * (size_t)NS + 5 * (size_t)B;
     if ((rc = alloc_list(h, bk, &grads, sizeof(double) * ngrad))) return rc;
     if ((rc = alloc_list(h, bk, &drive_sc, sizeof(double) * 3 * std::max(ND, 1)))) return rc;
+    int nset = 0;
     if (fl) {
-        if ((rc = alloc_list(h, bk, &seg_pop, pop_sz * (K + 1)))) return rc;
-        if ((rc = alloc_list(h, bk, &seg_flags, (size_t)C * (K + 2)))) return rc;
-        if ((rc = alloc_list(h, bk, &seg_bid, (size_t)C * (K + 2)))) return rc;
-        if ((rc = alloc_list(h, bk, &carry, (size_t)C))) return rc;
+        // two sets let segment k - 1 be recomputed while segment k is
+        // reversed; the second is taken where the device has ample room
+        const size_t set_bytes = pop_sz * (K + 1) + 2 * (size_t)C * (K + 2);
+        nset = 1;
+        if (h->adjoint_sets != 1 && tp.nseg > 1) {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+                if (set_bytes <= total_b / 8 && free_b > 3 * set_bytes) nset = 2;
+            } else {
+                cudaGetLastError();
+            }
+        }
+        for (int i = 0; i < nset; ++i) {
+            if ((rc = alloc_list(h, bk, &sets[i].pop, pop_sz * (K + 1)))) return rc;
+            if ((rc = alloc_list(h, bk, &sets[i].flags, (size_t)C * (K + 2)))) return rc;
+            if ((rc = alloc_list(h, bk, &sets[i].bid, (size_t)C * (K + 2)))) return rc;
+        }
+        if (nset == 1 && (rc = alloc_list(h, bk, &carry, (size_t)C))) return rc;
         for (int i = 0; i < 2; ++i) {
             if ((rc = alloc_list(h, bk, &A[i], as * lbm::Q * C))) return rc;
             if ((rc = alloc_list(h, bk, &R[i], as * C))) return rc;
         }
         if ((rc = alloc_list(h, bk, &scratch, sizeof(BodyState) * B))) return rc;
         if ((rc = alloc_list(h, bk, &r_fh, sizeof(double) * 6 * B))) return rc;
+        if ((rc = alloc_list(h, bk, &r_drive_f, sizeof(double) * 3 * std::max(ND, 1)))) return rc;
+        if ((rc = alloc_list(h, bk, &r_spring_f, sizeof(double) * 3 * std::max(NS, 1)))) return rc;
         if ((rc = alloc_list(h, bk, &r_links, sizeof(lbm::Link) * (size_t)B * dv.link_side * dv.seg_cap))) return rc;
         if ((rc = alloc_list(h, bk, &r_seg, sizeof(int) * B * dv.link_side))) return rc;
         if ((rc = alloc_list(h, bk, &r_changed, sizeof(int) * 2))) return rc;
@@ -1284,17 +1318,28 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     cudaStream_t s = h->stream;
     if ((rc = build_graphs(h))) return rc;        // creates the side stream
     // the bulk part of each reverse step needs no body adjoint: it runs on
-    // the side stream, concurrently with the rigid-body and boundary parts
+    // the side stream, concurrently with the rigid-body and boundary parts;
+    // the recomputation runs on a stream of its own
     cudaStream_t side = h->side;
-    cudaEvent_t ev_main = nullptr, ev_side = nullptr;
+    if (fl) CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+    cudaEvent_t ev_main = nullptr, ev_side = nullptr, ev_rec = nullptr, ev_free_main = nullptr,
+                ev_free_side = nullptr;
     CK(cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_rec, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_free_main, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_free_side, cudaEventDisableTiming));
     struct Events {
-        cudaEvent_t &a, &b;
-        ~Events() { cudaEventDestroy(a); cudaEventDestroy(b); }
-    } events{ev_main, ev_side};
+        cudaEvent_t *e[5];
+        ~Events() {
+            for (cudaEvent_t *p : e)
+                if (*p) cudaEventDestroy(*p);
+        }
+    } events{{&ev_main, &ev_side, &ev_rec, &ev_free_main, &ev_free_side}};
     CK(cudaEventRecord(ev_main, s));
     CK(cudaEventRecord(ev_side, s));
+    CK(cudaEventRecord(ev_free_main, s));
+    CK(cudaEventRecord(ev_free_side, s));
     double *gd = grads, *gs = grads + 2 * ND, *gb = grads + 2 * ND + 3 * NS;
     CK(cudaMemsetAsync(grads, 0, sizeof(double) * ngrad, s));
     CK(cudaMemsetAsync(part, 0, sizeof(double) * 9 * B * (size_t)stride, s));
@@ -1302,7 +1347,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     int cur = 0;                    // sa[cur]: adjoint of state n + 1
     int ai = 0;                     // A[ai], R[ai]: adjoint entering reverse step n
     // the recomputation runs the forward kernels on its own link lists,
-    // change flags, clock and force output
+    // change flags, clock, drive and spring forces and force output
     lbm::Device dr = dv;
     dr.hist = nullptr;
     dr.tape = nullptr;
@@ -1312,59 +1357,88 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         dr.seg_count = r_seg;
         dr.changed = r_changed;
         dr.t_dev = r_t;
+        dr.drive_f = r_drive_f;
+        dr.spring_f = r_spring_f;
         CK(cudaMemsetAsync(A[0], 0, as * lbm::Q * C, s));
         CK(cudaMemsetAsync(R[0], 0, as * C, s));
         CK(cudaMemsetAsync(r_seg, 0, sizeof(int) * B * dv.link_side, s));
+        CK(cudaEventRecord(ev_rec, s));
+        CK(cudaStreamWaitEvent(rs, ev_rec, 0));
     }
     const BodyState *states = reinterpret_cast<const BodyState *>(tp.state);
     auto S = [&](long long t) { return states + (t - (tp.n0 - 1)) * B; };     // state t
-    auto slot_pop = [&](int j) { return static_cast<void *>(static_cast<char *>(seg_pop) + pop_sz * j); };
+    auto set_of = [&](int k) -> const SlotSet & { return sets[nset == 2 ? (k & 1) : 0]; };
+    auto slot_pop = [&](const SlotSet &st, int j) {
+        return static_cast<void *>(static_cast<char *>(st.pop) + pop_sz * j);
+    };
+    auto seg_len = [&](int k) { return std::min(K, tp.n - k * K); };
     const int ones[2] = {1, 1};
+    // recomputation of segment k into its slot set, on rs: epochs m - 1 ..
+    // m + L - 1 from the checkpoint (and m + L for the last segment)
+    auto recompute = [&](int k) -> int {
+        const long long m = tp.n0 + (long long)k * K;
+        const int L = seg_len(k);
+        const SlotSet &st = set_of(k);
+        if (nset == 1 && k < tp.nseg - 1)       // epoch m + L, recomputed with segment k + 1
+            CK(cudaMemcpyAsync(carry, st.flags + C, (size_t)C, cudaMemcpyDeviceToDevice, rs));
+        CK(cudaMemcpyAsync(st.pop, static_cast<char *>(tp.ckpt_pop) + pop_sz * k, pop_sz,
+                           cudaMemcpyDeviceToDevice, rs));
+        CK(cudaMemcpyAsync(st.flags, tp.ckpt_flags + C * k, (size_t)C, cudaMemcpyDeviceToDevice, rs));
+        CK(cudaMemcpyAsync(st.bid, tp.ckpt_bid + C * k, (size_t)C, cudaMemcpyDeviceToDevice, rs));
+        CK(cudaMemcpyAsync(r_t, &m, sizeof m, cudaMemcpyHostToDevice, rs));
+        CK(cudaMemcpyAsync(r_changed, ones, sizeof ones, cudaMemcpyHostToDevice, rs));
+        for (int j = 0; j <= L; ++j) {
+            // the remap rewrites only the cubes around the bodies: the slot
+            // starts from the epoch before it, as the forward's ping-pong
+            // buffers do
+            CK(cudaMemcpyAsync(st.flags + C * (j + 1), st.flags + C * j, (size_t)C, cudaMemcpyDeviceToDevice, rs));
+            CK(cudaMemcpyAsync(st.bid + C * (j + 1), st.bid + C * j, (size_t)C, cudaMemcpyDeviceToDevice, rs));
+            lbm::StepPtrs sp{};
+            sp.src = slot_pop(st, j);
+            sp.dst = slot_pop(st, j + 1);
+            sp.flags_prev = st.flags + C * j;
+            sp.bid_prev = st.bid + C * j;
+            sp.flags_cur = st.flags + C * (j + 1);
+            sp.bid_cur = st.bid + C * (j + 1);
+            sp.body_prev = S(m + j - 1);
+            sp.body_cur = S(m + j);
+            sp.body_next = scratch;
+            sp.tstep = dr.t_dev;
+            sp.parity = j & 1;
+            if (j == L) {
+                // the flags of the epoch after the run: the last reverse
+                // step needs them (its bounce-back and link cells)
+                if (k == tp.nseg - 1) lbm::launch_remap(dr, sp, 0, rs);
+                break;
+            }
+            lbm::launch_remap(dr, sp, 0, rs);
+            lbm::launch_stream_collide(dr, sp, rs);
+            if (lbm::needs_boundary_fix(dr)) lbm::launch_boundary_fix(dr, sp, rs);
+            lbm::launch_links(dr, sp, rs);
+            lbm::launch_force(dr, sp, rs);
+        }
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ev_rec, rs));
+        return LBM_OK;
+    };
+    // segment k's slots are rewritten by the recomputation of segment k - 2
+    // (two sets) or k - 1 (one set); it waits for the reverse steps that read
+    // them, ev_free_main / ev_free_side (the first reverse step of segment k
+    // - 1 reads slot 1 of segment k's set, the flags of epoch m + L, or with
+    // one set their copy in carry)
+    auto start_recompute = [&](int k) -> int {
+        CK(cudaStreamWaitEvent(rs, ev_free_main, 0));
+        CK(cudaStreamWaitEvent(rs, ev_free_side, 0));
+        return recompute(k);
+    };
+    if (fl && (rc = start_recompute(tp.nseg - 1))) return rc;
     for (int k = tp.nseg - 1; k >= 0; --k) {
         const long long m = tp.n0 + (long long)k * K;
-        const int L = std::min(K, tp.n - k * K);
+        const int L = seg_len(k);
+        const SlotSet &st = set_of(k);
         if (fl) {
-            CK(cudaStreamWaitEvent(s, ev_side, 0));     // the bulk adjoint read the slots
-            if (k < tp.nseg - 1)            // epoch m + L, recomputed with the later segment
-                CK(cudaMemcpyAsync(carry, seg_flags + C, (size_t)C, cudaMemcpyDeviceToDevice, s));
-            CK(cudaMemcpyAsync(seg_pop, static_cast<char *>(tp.ckpt_pop) + pop_sz * k, pop_sz,
-                               cudaMemcpyDeviceToDevice, s));
-            CK(cudaMemcpyAsync(seg_flags, tp.ckpt_flags + C * k, (size_t)C, cudaMemcpyDeviceToDevice, s));
-            CK(cudaMemcpyAsync(seg_bid, tp.ckpt_bid + C * k, (size_t)C, cudaMemcpyDeviceToDevice, s));
-            CK(cudaMemcpyAsync(r_t, &m, sizeof m, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(r_changed, ones, sizeof ones, cudaMemcpyHostToDevice, s));
-            for (int j = 0; j <= L; ++j) {
-                // the remap rewrites only the cubes around the bodies: the
-                // slot starts from the epoch before it, as the forward's
-                // ping-pong buffers do
-                CK(cudaMemcpyAsync(seg_flags + C * (j + 1), seg_flags + C * j, (size_t)C, cudaMemcpyDeviceToDevice, s));
-                CK(cudaMemcpyAsync(seg_bid + C * (j + 1), seg_bid + C * j, (size_t)C, cudaMemcpyDeviceToDevice, s));
-                lbm::StepPtrs sp{};
-                sp.src = slot_pop(j);
-                sp.dst = slot_pop(j + 1);
-                sp.flags_prev = seg_flags + C * j;
-                sp.bid_prev = seg_bid + C * j;
-                sp.flags_cur = seg_flags + C * (j + 1);
-                sp.bid_cur = seg_bid + C * (j + 1);
-                sp.body_prev = S(m + j - 1);
-                sp.body_cur = S(m + j);
-                sp.body_next = scratch;
-                sp.tstep = dr.t_dev;
-                sp.parity = j & 1;
-                if (j == L) {
-                    // the flags of the epoch after the run: the last reverse
-                    // step needs them (its bounce-back and link cells)
-                    if (k == tp.nseg - 1) lbm::launch_remap(dr, sp, 0, s);
-                    break;
-                }
-                lbm::launch_remap(dr, sp, 0, s);
-                lbm::launch_stream_collide(dr, sp, s);
-                if (lbm::needs_boundary_fix(dr)) lbm::launch_boundary_fix(dr, sp, s);
-                lbm::launch_links(dr, sp, s);
-                lbm::launch_force(dr, sp, s);
-            }
-            CK(cudaGetLastError());
-            CK(cudaEventRecord(ev_main, s));        // the segment's slots are ready
+            CK(cudaStreamWaitEvent(s, ev_rec, 0));      // the segment's slots are ready
+            CK(cudaEventRecord(ev_main, s));
         }
         for (int j = L - 1; j >= 0; --j) {
             const long long n = m + j;
@@ -1385,11 +1459,13 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
             lbm::launch_adj_integrate(dv, ab, s);
             if (fl) {
                 lbm::AdjPtrs ap{};
-                ap.G = slot_pop(j + 1);
-                ap.flags_cur = seg_flags + C * (j + 1);
-                ap.bid_cur = seg_bid + C * (j + 1);
-                ap.bid_prev = seg_bid + C * j;
-                ap.flags_next = (j + 1 < L || k == tp.nseg - 1) ? seg_flags + C * (j + 2) : carry;
+                ap.G = slot_pop(st, j + 1);
+                ap.flags_cur = st.flags + C * (j + 1);
+                ap.bid_cur = st.bid + C * (j + 1);
+                ap.bid_prev = st.bid + C * j;
+                ap.flags_next = (j + 1 < L || k == tp.nseg - 1) ? st.flags + C * (j + 2)
+                                : nset == 2                    ? set_of(k + 1).flags + C
+                                                               : carry;
                 ap.ain = A[ai];
                 ap.rin = R[ai];
                 ap.aout = A[ai ^ 1];
@@ -1404,9 +1480,21 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
                 CK(cudaEventRecord(ev_side, side));
                 lbm::launch_adj_boundary(dv, ap, false, s);
                 CK(cudaEventRecord(ev_main, s));
+                if (j == L - 1 && nset == 2) {
+                    // segment k + 1's set (read up to here) is free for the
+                    // recomputation of segment k - 1
+                    CK(cudaEventRecord(ev_free_main, s));
+                    CK(cudaEventRecord(ev_free_side, side));
+                    if (k > 0 && (rc = start_recompute(k - 1))) return rc;
+                }
                 ai ^= 1;
             }
             cur ^= 1;
+        }
+        if (fl && nset == 1) {
+            CK(cudaEventRecord(ev_free_main, s));
+            CK(cudaEventRecord(ev_free_side, side));
+            if (k > 0 && (rc = start_recompute(k - 1))) return rc;
         }
         CK(cudaGetLastError());
     }
@@ -1418,11 +1506,11 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         // the run and of the state n0 - 1 (its moving-wall velocities)
         CK(cudaMemsetAsync(fadj, 0, sizeof(double) * 6 * B, s));
         lbm::AdjPtrs ap{};
-        ap.G = slot_pop(0);
-        ap.flags_cur = seg_flags;
-        ap.bid_cur = seg_bid;
-        ap.bid_prev = seg_bid;
-        ap.flags_next = seg_flags + C;
+        ap.G = slot_pop(sets[0], 0);
+        ap.flags_cur = sets[0].flags;
+        ap.bid_cur = sets[0].bid;
+        ap.bid_prev = sets[0].bid;
+        ap.flags_next = sets[0].flags + C;
         ap.ain = A[ai];
         ap.rin = R[ai];
         ap.aout = A[ai ^ 1];

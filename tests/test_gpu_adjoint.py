@@ -89,6 +89,24 @@ def test_segment_length_does_not_change_the_gradients(gpu):
             assert np.array_equal(got[k], ref[k]), (seg, k)
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_overlapped_and_serial_recomputation_give_the_same_bits(gpu, precision):
+    """Two slot sets (segment k - 1 recomputed on its own stream beside the
+    reverse steps of segment k) and one (segments in turn) give the same
+    gradients bit for bit; so do a second call on the same recording."""
+    sc = scenario()
+    lat = set_motion(lbm.from_scenario(sc, precision=precision))
+    lat.adjoint_record(N_STEPS, 5)
+    runs = []
+    for serial in (0, 1, 0):
+        lat.debug_set(lbm.DEBUG_ADJOINT_SERIAL, serial)
+        runs.append(lat.adjoint_backward(SEED, want_pop=True))
+    lat.close()
+    for k in ("state", "prev", "drive", "spring", "body", "pop"):
+        assert np.array_equal(runs[0][k], runs[1][k]), k
+        assert np.array_equal(runs[0][k], runs[2][k]), k
+
+
 def test_run_starting_after_some_steps(gpu):
     """n0 > 0: the state before the first recorded step is its own input."""
     sc = scenario()
