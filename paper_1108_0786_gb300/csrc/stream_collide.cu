@@ -478,10 +478,20 @@ bulk_kernel(const Device dv, const StepPtrs sp) {
     bulk_body<T, V, BX, BY>(dv, sp, launch_blk());
 }
 
+// a batched bulk block takes BATCH_PZ consecutive z-planes of its member:
+// the member lookup at its start (a few dependent loads and barriers with
+// no population traffic in flight) is paid once for all of them
+constexpr int BATCH_PZ = 4;
+
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
-    bulk_body<T, V, BX, BY, true>(sdv, ssp, sbk);
+    const int z0 = sbk.z * BATCH_PZ, z1 = min(z0 + BATCH_PZ, sdv.dom.nz);
+    for (int z = z0; z < z1; ++z) {
+        Blk pb = sbk;
+        pb.z = z;
+        bulk_body<T, V, BX, BY, true>(sdv, ssp, pb);
+    }
 }
 
 // 16-bit values packed two to a 32-bit word (the lower address in the low
@@ -636,7 +646,12 @@ bulk16_kernel(const Device dv, const StepPtrs sp) {
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB) bulk16_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
-    bulk16_body<T, V, BX, BY, true>(sdv, ssp, sbk);
+    const int z0 = sbk.z * BATCH_PZ, z1 = min(z0 + BATCH_PZ, sdv.dom.nz);
+    for (int z = z0; z < z1; ++z) {
+        Blk pb = sbk;
+        pb.z = z;
+        bulk16_body<T, V, BX, BY, true>(sdv, ssp, pb);
+    }
 }
 
 // Velocity of body b's surface at lattice point p in the compute type R:
@@ -1288,12 +1303,12 @@ namespace {
 
 constexpr int BATCH_BX = 32, BATCH_BY = 8;      // 256 threads a block, a plane's cells in row order
 
-template <typename T, int V>
+template <typename T, int V, int MINB = 1>
 void bulk_batch_launch(const Batch &bt, unsigned blocks, cudaStream_t s) {
     if constexpr (sizeof(T) == 2 && V % 2 == 0)
-        bulk16_batch<T, V, BATCH_BX, BATCH_BY, 1><<<blocks, dim3(BATCH_BX, BATCH_BY), 0, s>>>(bt);
+        bulk16_batch<T, V, BATCH_BX, BATCH_BY, MINB><<<blocks, dim3(BATCH_BX, BATCH_BY), 0, s>>>(bt);
     else
-        bulk_batch<T, V, BATCH_BX, BATCH_BY, 1><<<blocks, dim3(BATCH_BX, BATCH_BY), 0, s>>>(bt);
+        bulk_batch<T, V, BATCH_BX, BATCH_BY, MINB><<<blocks, dim3(BATCH_BX, BATCH_BY), 0, s>>>(bt);
 }
 
 struct BatchShape {
@@ -1301,14 +1316,21 @@ struct BatchShape {
     void (*fn)(const Batch &, unsigned, cudaStream_t);
 };
 
+// per precision, index 0 and 1 are one and two cells a thread (the
+// untuned choice is 1, else 0), two cells with the registers capped for 3
+// resident blocks an SM in FP32 (the compiler's own choice leaves room for
+// two); the shapes after them cap the registers for 3 or 4 resident blocks
+// (those that spill little at the cap)
 const BatchShape kBatchShapes[] = {
     {0, 1, bulk_batch_launch<double, 1>},  {0, 2, bulk_batch_launch<double, 2>},
-    {1, 1, bulk_batch_launch<float, 1>},   {1, 2, bulk_batch_launch<float, 2>},
-    {1, 4, bulk_batch_launch<float, 4>},
+    {1, 1, bulk_batch_launch<float, 1>},   {1, 2, bulk_batch_launch<float, 2, 3>},
+    {1, 4, bulk_batch_launch<float, 4>},   {1, 2, bulk_batch_launch<float, 2, 4>},
     {2, 1, bulk_batch_launch<__half, 1>},  {2, 2, bulk_batch_launch<__half, 2>},
-    {2, 4, bulk_batch_launch<__half, 4>},
+    {2, 4, bulk_batch_launch<__half, 4>},  {2, 2, bulk_batch_launch<__half, 2, 4>},
+    {2, 4, bulk_batch_launch<__half, 4, 3>},
     {3, 1, bulk_batch_launch<__nv_bfloat16, 1>}, {3, 2, bulk_batch_launch<__nv_bfloat16, 2>},
-    {3, 4, bulk_batch_launch<__nv_bfloat16, 4>},
+    {3, 4, bulk_batch_launch<__nv_bfloat16, 4>}, {3, 2, bulk_batch_launch<__nv_bfloat16, 2, 4>},
+    {3, 4, bulk_batch_launch<__nv_bfloat16, 4, 3>},
 };
 
 const BatchShape *batch_shape(int precision, int i) {
@@ -1340,10 +1362,11 @@ void batch_grid_cells(const Device &dv, int k, int variant, int g[3]) {
     } else if (k == BK_BULK) {
         const BatchShape *b = batch_shape(dv.precision, variant);
         if (!b || d.nx % b->vec) return;
-        // a z-plane's V-cell groups in row order (no lanes idle at row ends)
+        // a z-plane's V-cell groups in row order (no lanes idle at row ends),
+        // BATCH_PZ planes a block
         g[0] = (int)(((long long)(d.nx / b->vec) * d.ny + BATCH_BX * BATCH_BY - 1) / (BATCH_BX * BATCH_BY));
         g[1] = 1;
-        g[2] = d.nz;
+        g[2] = (d.nz + BATCH_PZ - 1) / BATCH_PZ;
     }
 }
 
