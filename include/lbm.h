@@ -365,12 +365,17 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
  * per set is built on first use and kept).
  *   LBM_ENSEMBLE_BATCHED (default): each step is one launch of each per-step
  *     kernel (body preparation, remap, boundary cells, links, loads, bulk
- *     stream-collide, force) over all members of a storage precision: the
+ *     stream-collide, force) over the members of a storage precision: the
  *     members' grids are flattened into one grid, and each block finds its
- *     member's record in a device table.  ~8 launches a step for the whole
- *     set, however many members.  Every member needs the fluid; the bulk
- *     kernel runs in one shape for all members (lbm_ensemble_autotune), not
- *     in the members' own.
+ *     member's record in a device table.  A set of two or more members is
+ *     split into two halves of about equal cell counts, each its own chain
+ *     of launches; the second starts one remap behind the first, and the
+ *     latency-bound kernels run at a higher stream priority than the bulk
+ *     kernels, so one half's prep, remap and force run beside the other
+ *     half's bulk kernel.  ~16 launches a step for the whole set, however
+ *     many members.  Every member needs the fluid; the bulk kernel runs in
+ *     one shape for all members (lbm_ensemble_autotune), not in the
+ *     members' own.
  *   LBM_ENSEMBLE_BRANCHES: the members' own step kernels as parallel graph
  *     branches (7 launches a step per member).
  * Both give the bits of the members stepped alone.  There is no dependency

@@ -1564,11 +1564,14 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
 // kernel the members' flattened block ranges and grids)
 struct EnsGroup {
     int precision = 1;
+    int lane = 0;                           // batched mode: the chain of launches the group is in
     std::vector<int> members;               // ensemble indices
     void *mem = nullptr;                    // the tables, one allocation (first member's allocator)
     lbm::Batch bt[lbm::BK_COUNT];           // parity 0 (parity 1 differs only in .parity)
     unsigned blocks[lbm::BK_COUNT] = {};
 };
+
+constexpr int ENS_LANES = 2;             // chains of batched launches (see ens_lanes)
 
 struct EnsGraph {
     std::vector<int> set;
@@ -1582,6 +1585,11 @@ struct lbm_ensemble_s {
     cudaStream_t cap = nullptr;             // capture origin
     cudaStream_t side = nullptr;            // batched mode: boundary cells, links and loads beside the bulk kernel
     cudaEvent_t fork = nullptr, bjoin = nullptr;
+    // batched mode: the members split into ENS_LANES independent chains of
+    // launches, each with its own capture and side streams
+    cudaStream_t lcap[ENS_LANES] = {}, lside[ENS_LANES] = {}, lbulk[ENS_LANES] = {};
+    cudaEvent_t lfork[ENS_LANES] = {}, ljoin[ENS_LANES] = {}, ldone[ENS_LANES] = {}, lbdone[ENS_LANES] = {};
+    cudaEvent_t lstart = nullptr;
     std::vector<cudaEvent_t> join;          // one per member
     int mode = LBM_ENSEMBLE_BATCHED;
     int variant[4] = {-1, -1, -1, -1};      // batched bulk shape per precision (-1: the default)
@@ -1617,6 +1625,16 @@ void ens_release(lbm_ensemble_t *e) {
     if (e->side) cudaStreamDestroy(e->side);
     e->fork = e->bjoin = nullptr;
     e->cap = e->side = nullptr;
+    for (int l = 0; l < ENS_LANES; ++l) {
+        for (cudaStream_t *st : {&e->lcap[l], &e->lside[l], &e->lbulk[l]})
+            if (*st) cudaStreamDestroy(*st);
+        for (cudaEvent_t *ev : {&e->lfork[l], &e->ljoin[l], &e->ldone[l], &e->lbdone[l]})
+            if (*ev) cudaEventDestroy(*ev);
+        e->lcap[l] = e->lside[l] = e->lbulk[l] = nullptr;
+        e->lfork[l] = e->ljoin[l] = e->ldone[l] = e->lbdone[l] = nullptr;
+    }
+    if (e->lstart) cudaEventDestroy(e->lstart);
+    e->lstart = nullptr;
 }
 
 // can the members of `set` run as batched launches?  (every member has fluid;
@@ -1711,9 +1729,15 @@ int ens_group_tables(lbm_ensemble_t *e, EnsGroup &g) {
 
 // one batched step of every group: the kernels of enqueue_step, each as one
 // launch over the members of a group
-void ens_enqueue_batched(lbm_ensemble_t *e, std::vector<EnsGroup> &groups, int p) {
+// one batched step of the groups of `lane` on the lane's streams (the bulk
+// kernel on `bulk` if not null, else on `main`); `remapped` (if not null) is
+// recorded once the step's remap is enqueued
+void ens_enqueue_batched(lbm_ensemble_t *e, std::vector<EnsGroup> &groups, int lane, int p, cudaStream_t main,
+                         cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t remapped,
+                         cudaStream_t bulk = nullptr, cudaEvent_t bulk_done = nullptr) {
     auto small = [&](int k, cudaStream_t st) {
         for (auto &g : groups) {
+            if (g.lane != lane) continue;
             lbm::Batch b = g.bt[k];
             b.parity = p;
             lbm::launch_batch_small(k, b, g.blocks[k], g.precision, st);
@@ -1721,30 +1745,63 @@ void ens_enqueue_batched(lbm_ensemble_t *e, std::vector<EnsGroup> &groups, int p
     };
     auto cells = [&](int k, cudaStream_t st) {
         for (auto &g : groups) {
+            if (g.lane != lane) continue;
             lbm::Batch b = g.bt[k];
             b.parity = p;
             lbm::launch_batch_cells(k, e->variant[g.precision], b, g.blocks[k], g.precision, st);
         }
     };
-    small(lbm::BK_PREP, e->cap);
-    small(lbm::BK_REMAP, e->cap);
-    cudaEventRecord(e->fork, e->cap);
-    cudaStreamWaitEvent(e->side, e->fork, 0);
-    cells(lbm::BK_BOUNDARY, e->side);
-    cells(lbm::BK_WALLS, e->side);
-    small(lbm::BK_LINKS, e->side);
-    small(lbm::BK_LOADS, e->side);
-    cudaEventRecord(e->bjoin, e->side);
-    cells(lbm::BK_BULK, e->cap);
-    cudaStreamWaitEvent(e->cap, e->bjoin, 0);
-    small(lbm::BK_FORCE, e->cap);
-    for (auto &g : groups)
+    small(lbm::BK_PREP, main);
+    small(lbm::BK_REMAP, main);
+    if (remapped) cudaEventRecord(remapped, main);
+    cudaEventRecord(fork, main);
+    cudaStreamWaitEvent(side, fork, 0);
+    cells(lbm::BK_BOUNDARY, side);
+    cells(lbm::BK_WALLS, side);
+    small(lbm::BK_LINKS, side);
+    small(lbm::BK_LOADS, side);
+    cudaEventRecord(join, side);
+    if (bulk) {
+        cudaStreamWaitEvent(bulk, fork, 0);
+        cells(lbm::BK_BULK, bulk);
+        cudaEventRecord(bulk_done, bulk);
+        cudaStreamWaitEvent(main, bulk_done, 0);
+    } else {
+        cells(lbm::BK_BULK, main);
+    }
+    cudaStreamWaitEvent(main, join, 0);
+    small(lbm::BK_FORCE, main);
+    for (auto &g : groups) {
+        if (g.lane != lane) continue;
         for (int i : g.members) {
             lbm_t *h = e->members[i];
             const lbm::StepPtrs sp = step_ptrs(h, p);
-            if (nb(h) == 0) lbm::launch_tick(h->dv, sp, e->cap);
-            if (h->dv.avg_u) lbm::launch_average(h->dv, sp, e->cap);
+            if (nb(h) == 0) lbm::launch_tick(h->dv, sp, main);
+            if (h->dv.avg_u) lbm::launch_average(h->dv, sp, main);
         }
+    }
+}
+
+// Batched sets of two or more members run as ENS_LANES chains of launches
+// over halves of the members (balanced by cells).  The second chain starts
+// once the first has enqueued its first remap, so while one chain runs its
+// latency-bound kernels (prep, remap, force) the other runs its
+// bandwidth-bound bulk kernel; the offset persists from step to step.
+// Returns the lane of each member of `set` (indexed by ensemble index).
+std::vector<int> ens_lanes(const lbm_ensemble_t *e, const std::vector<int> &set) {
+    std::vector<int> lane(e->members.size(), 0);
+    if (set.size() < 2) return lane;
+    std::vector<int> order(set);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return e->members[a]->C > e->members[b]->C; });
+    long long load[ENS_LANES] = {};
+    for (int i : order) {
+        int l = 0;
+        for (int k = 1; k < ENS_LANES; ++k)
+            if (load[k] < load[l]) l = k;
+        lane[i] = l;
+        load[l] += e->members[i]->C;
+    }
+    return lane;
 }
 
 // the graph advancing the members `set` by CHUNK_STEPS steps each (built on
@@ -1758,16 +1815,20 @@ int ens_graph(lbm_ensemble_t *e, const std::vector<int> &set, cudaGraphExec_t *o
     EnsGraph eg;
     eg.set = set;
     const bool batched = e->mode == LBM_ENSEMBLE_BATCHED && ens_batchable(e, set);
+    int lanes = 1;
     if (batched) {
+        const std::vector<int> lane = ens_lanes(e, set);
         for (int i : set) {
             const int prec = e->members[i]->precision;
+            lanes = std::max(lanes, lane[i] + 1);
             EnsGroup *g = nullptr;
             for (auto &x : eg.groups)
-                if (x.precision == prec) g = &x;
+                if (x.precision == prec && x.lane == lane[i]) g = &x;
             if (!g) {
                 eg.groups.emplace_back();
                 g = &eg.groups.back();
                 g->precision = prec;
+                g->lane = lane[i];
             }
             g->members.push_back(i);
         }
@@ -1783,8 +1844,23 @@ int ens_graph(lbm_ensemble_t *e, const std::vector<int> &set, cudaGraphExec_t *o
     cudaGraph_t g = nullptr;
     cudaError_t err = cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal);
     if (err == cudaSuccess) {
-        if (batched) {
-            for (int k = 0; k < CHUNK_STEPS; ++k) ens_enqueue_batched(e, eg.groups, k & 1);
+        if (batched && lanes == 1) {
+            for (int k = 0; k < CHUNK_STEPS; ++k)
+                ens_enqueue_batched(e, eg.groups, 0, k & 1, e->cap, e->side, e->fork, e->bjoin, nullptr);
+        } else if (batched) {
+            cudaEventRecord(e->fork, e->cap);
+            for (int l = 0; l < lanes; ++l) cudaStreamWaitEvent(e->lcap[l], e->fork, 0);
+            for (int k = 0; k < CHUNK_STEPS; ++k)
+                for (int l = 0; l < lanes; ++l) {
+                    if (k == 0 && l > 0) cudaStreamWaitEvent(e->lcap[l], e->lstart, 0);
+                    ens_enqueue_batched(e, eg.groups, l, k & 1, e->lcap[l], e->lside[l], e->lfork[l], e->ljoin[l],
+                                        k == 0 && l + 1 < lanes ? e->lstart : nullptr, e->lbulk[l],
+                                        e->lbdone[l]);
+                }
+            for (int l = 0; l < lanes; ++l) {
+                cudaEventRecord(e->ldone[l], e->lcap[l]);
+                cudaStreamWaitEvent(e->cap, e->ldone[l], 0);
+            }
         } else {
             cudaEventRecord(e->fork, e->cap);
             for (int i : set) {
@@ -1798,7 +1874,8 @@ int ens_graph(lbm_ensemble_t *e, const std::vector<int> &set, cudaGraphExec_t *o
         err = cudaStreamEndCapture(e->cap, &g);
     }
     cudaGraphExec_t x = nullptr;
-    if (err == cudaSuccess) err = cudaGraphInstantiate(&x, g, 0);
+    if (err == cudaSuccess)
+        err = cudaGraphInstantiate(&x, g, batched && lanes > 1 ? cudaGraphInstantiateFlagUseNodePriority : 0);
     if (g) cudaGraphDestroy(g);
     if (err != cudaSuccess) {
         for (auto &grp : eg.groups)
@@ -1834,6 +1911,19 @@ int lbm_ensemble_create(lbm_t *const *members, int n, lbm_ensemble_t **out) {
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->bjoin, cudaEventDisableTiming);
+    // lanes: the latency-bound kernels' streams at the greatest priority,
+    // the bulk kernels' at the least, so that one lane's prep, remap and
+    // force blocks are dispatched ahead of the other lane's pending bulk blocks
+    int least = 0, greatest = 0;
+    if (err == cudaSuccess) err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    for (int l = 0; l < ENS_LANES && err == cudaSuccess; ++l) {
+        err = cudaStreamCreateWithPriority(&e->lcap[l], cudaStreamNonBlocking, greatest);
+        if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&e->lside[l], cudaStreamNonBlocking, greatest);
+        if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&e->lbulk[l], cudaStreamNonBlocking, least);
+        for (cudaEvent_t *ev : {&e->lfork[l], &e->ljoin[l], &e->ldone[l], &e->lbdone[l]})
+            if (err == cudaSuccess) err = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    }
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->lstart, cudaEventDisableTiming);
     for (int i = 0; i < n && err == cudaSuccess; ++i) {
         cudaEvent_t ev = nullptr;
         err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
