@@ -289,13 +289,17 @@ __device__ inline int wrap_up(int v, int n) { return v < n ? v : (v - n < n ? v 
 
 // Remap: block row blockIdx.y = body b; the threads cover the cube of side
 // 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) at state n, 32 x 8 threads a
-// block over x and (y, z) rows.  Every covered cell gets its epoch-n flags
-// from the geometry of all bodies and the epoch-(n-1) buffer; overlapping
-// cubes write identical values.  A cell tests only body b's candidates, in
-// body order (integer boxes, the FP32 screen, and the FP64 inside test only
-// within the screen's margin).  Fluid cells flagged F_NEAR or F_SOLID_PREV
-// are appended to the boundary kernel's list.
+// block over x and (y, z) rows, REMAP_R rows a thread (ly and ly + 8: their
+// flag loads are issued together, so a block's latency chain covers twice
+// the cells).  Every covered cell gets its epoch-n flags from the geometry
+// of all bodies and the epoch-(n-1) buffer; overlapping cubes write
+// identical values.  A cell tests only body b's candidates, in body order
+// (integer boxes, the FP32 screen, and the FP64 inside test only within the
+// screen's margin).  Fluid cells flagged F_NEAR or F_SOLID_PREV are appended
+// to the boundary kernel's list.
 constexpr int REMAP_TX = 32, REMAP_TY = 8, REMAP_THREADS = REMAP_TX * REMAP_TY;
+constexpr int REMAP_R = 2;
+constexpr int REMAP_ROWS = REMAP_TY * REMAP_R;  // cube rows a block covers in a layer
 constexpr int REMAP_STAGED = 8;
 constexpr int REMAP_LAYERS = 1;         // cube layers a block (more layers serialise each block's latency chain)
 constexpr int REMAP_LIST_BUF = 2048;    // list entries a block gathers before the global append
@@ -311,8 +315,8 @@ __device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp,
     __shared__ int cid[LBM_MAX_BODIES_DEV];
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
     const int side = geo[b].side;
-    const int nyb = (side + REMAP_TY - 1) / REMAP_TY;
-    const int lzb = (bk.x / nyb) * REMAP_LAYERS, ly0 = (bk.x % nyb) * REMAP_TY;
+    const int nyb = (side + REMAP_ROWS - 1) / REMAP_ROWS;
+    const int lzb = (bk.x / nyb) * REMAP_LAYERS, ly0 = (bk.x % nyb) * REMAP_ROWS;
     if (lzb >= side) return;                  // the grid covers the largest body's cube
     // this block's share of the boundary kernel's list, gathered in shared
     // memory and appended with one atomic at the end
@@ -335,97 +339,129 @@ __device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp,
     __syncthreads();
 
     // REMAP_LAYERS layers of the cube a block, x in chunks of 32 (cubes wider
-    // than a warp take several); every lane runs every chunk, so the ballots
-    // below see whole warps
+    // than a warp take several); every lane runs every chunk and row, so the
+    // ballots below see whole warps
     const int lz_end = min(side, lzb + REMAP_LAYERS);
     for (int lz = lzb; lz < lz_end; ++lz)
         for (int lx0 = 0; lx0 < side; lx0 += REMAP_TX) {
-            const int lx = lx0 + threadIdx.x, ly = ly0 + threadIdx.y;
-            bool live = lx < side && ly < side;
-            int x = org[0] + lx, y = org[1] + ly, z = org[2] + lz;
-            if (d.px) x = wrap_up(x, d.nx); else live = live && x >= 0 && x < d.nx;
-            if (d.py) y = wrap_up(y, d.ny); else live = live && y >= 0 && y < d.ny;
-            if (d.pz) z = wrap_up(z, d.nz); else live = live && z >= 0 && z < d.nz;
-            const long long c = ((long long)z * d.ny + y) * d.nx + x;
-            const int p3[3] = {x, y, z};
-
-            int id = NO_BODY;
-            bool reached = false;           // within STATIC_REACH cells of some body's box
-            for (int i = 0; i < ncand && live; ++i) {
-                const int kb = cid[i];
-                const BodyGeom *g = i < REMAP_STAGED ? cg + i : geo + kb;
-                bool in = true;
-                for (int a = 0; a < 3 && in; ++a) {
-                    int o = p3[a] - g->ebox[a];
-                    if (per[a] && o < 0) o += n3[a];
-                    in = o >= 0 && o < g->ebox[3 + a];
-                }
-                if (!in) continue;
-                reached = true;
-                for (int a = 0; a < 3 && in; ++a) {
-                    int o = p3[a] - g->box[a];
-                    if (per[a] && o < 0) o += n3[a];
-                    in = o >= 0 && o < g->box[3 + a];
-                }
-                if (!in) continue;
-                // FP32 screen; cells within its margin of the surface take the FP64 test
-                const int screen = inside_screen(d, g, x, y, z);
-                if (screen == 0 || (screen < 0 && !cell_inside(d, dv.props[kb], sp.body_cur[kb], x, y, z))) continue;
-                if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
-                id = kb;
-            }
-            // farther than STATIC_REACH from every body's box: the cell holds its
-            // static flags in both epoch buffers already (nothing within reach was
-            // solid in the last three steps, at most 0.5 cells of motion per step)
-            live = live && reached;
-            uint8_t flags = 0;
-            if (live) {
-                const uint8_t solid = id != NO_BODY ? F_SOLID : 0;
-                flags = solid | wall_bit(d, x, y, z);
-                if (!init_mode) {
-                    const uint8_t prev = sp.flags_prev[c] & F_SOLID;
-                    if (prev) flags |= F_SOLID_PREV;
-                    // does any pull source x - e_a hold an obstacle of step n-1?  (all
-                    // 18 loads are independent; sources beyond a wall do not count)
-                    uint8_t near = 0;
-                    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-                    if (x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+            const int lx = lx0 + threadIdx.x;
+            int xr[REMAP_R], yr[REMAP_R], zr[REMAP_R], idr[REMAP_R];
+            long long cr[REMAP_R];
+            bool liver[REMAP_R];
 #pragma unroll
-                        for (int a = 1; a < Q; ++a) near |= sp.flags_prev[c - ex(a) - ey(a) * sy - ez(a) * sz];
-                    } else {
-#pragma unroll
-                        for (int a = 1; a < Q; ++a) {
-                            const int sx_ = x - ex(a), sy_ = y - ey(a), sz_ = z - ez(a);
-                            const bool in = !((!d.px && (sx_ < 0 || sx_ >= d.nx)) || (!d.py && (sy_ < 0 || sy_ >= d.ny)) ||
-                                              (!d.pz && (sz_ < 0 || sz_ >= d.nz)));
-                            const uint8_t v = sp.flags_prev[((long long)wrap_axis(sz_, d.nz) * d.ny + wrap_axis(sy_, d.ny)) * d.nx +
-                                                            wrap_axis(sx_, d.nx)];
-                            near |= in ? v : 0;
-                        }
+            for (int r = 0; r < REMAP_R; ++r) {
+                const int ly = ly0 + threadIdx.y + r * REMAP_TY;
+                bool live = lx < side && ly < side;
+                int x = org[0] + lx, y = org[1] + ly, z = org[2] + lz;
+                if (d.px) x = wrap_up(x, d.nx); else live = live && x >= 0 && x < d.nx;
+                if (d.py) y = wrap_up(y, d.ny); else live = live && y >= 0 && y < d.ny;
+                if (d.pz) z = wrap_up(z, d.nz); else live = live && z >= 0 && z < d.nz;
+                const int p3[3] = {x, y, z};
+                int id = NO_BODY;
+                bool reached = false;           // within STATIC_REACH cells of some body's box
+                for (int i = 0; i < ncand && live; ++i) {
+                    const int kb = cid[i];
+                    const BodyGeom *g = i < REMAP_STAGED ? cg + i : geo + kb;
+                    bool in = true;
+                    for (int a = 0; a < 3 && in; ++a) {
+                        int o = p3[a] - g->ebox[a];
+                        if (per[a] && o < 0) o += n3[a];
+                        in = o >= 0 && o < g->ebox[3 + a];
                     }
-                    if (near & F_SOLID) flags |= F_NEAR;
-                    if ((solid != 0) != (prev != 0) || (solid && sp.bid_prev[c] != id)) dv.changed[sp.parity] = 1;
+                    if (!in) continue;
+                    reached = true;
+                    for (int a = 0; a < 3 && in; ++a) {
+                        int o = p3[a] - g->box[a];
+                        if (per[a] && o < 0) o += n3[a];
+                        in = o >= 0 && o < g->box[3 + a];
+                    }
+                    if (!in) continue;
+                    // FP32 screen; cells within its margin of the surface take the FP64 test
+                    const int screen = inside_screen(d, g, x, y, z);
+                    if (screen == 0 || (screen < 0 && !cell_inside(d, dv.props[kb], sp.body_cur[kb], x, y, z)))
+                        continue;
+                    if (id != NO_BODY) atomicOr(dv.status, ST_OVERLAP);
+                    id = kb;
                 }
-                sp.flags_cur[c] = flags;
-                sp.bid_cur[c] = (uint8_t)id;
+                // farther than STATIC_REACH from every body's box: the cell holds
+                // its static flags in both epoch buffers already (nothing within
+                // reach was solid in the last three steps, at most 0.5 cells of
+                // motion per step)
+                xr[r] = x;
+                yr[r] = y;
+                zr[r] = z;
+                idr[r] = id;
+                cr[r] = ((long long)z * d.ny + y) * d.nx + x;
+                liver[r] = live && reached;
             }
-            // the boundary kernel's cells: a shared-memory atomic per warp
-            // (past the buffer, a global one)
-            const bool mine = live && !init_mode && !(flags & F_SOLID) && (flags & (F_NEAR | F_SOLID_PREV));
-            const unsigned mb = __ballot_sync(0xffffffffu, mine);
-            if (mb) {
-                const int leader = __ffs(mb) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&lcount, __popc(mb));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                const int pos = base + __popc(mb & ((1u << lane) - 1u));
-                if (mine) {
-                    if (pos < REMAP_LIST_BUF) {
-                        lbuf[pos] = (uint32_t)c;
-                    } else {
-                        const int g = atomicAdd(dv.bcount, 1);
-                        if (g < dv.blist_cap) dv.blist[g] = (uint32_t)c;
-                        else atomicOr(dv.status, ST_LINKS);
+            // the epoch-(n-1) flags and body id of every row's cell and whether
+            // any pull source x - e_a held an obstacle of step n-1 (sources
+            // beyond a wall do not count): all loads before any use
+            uint8_t prevr[REMAP_R], nearr[REMAP_R], bidr[REMAP_R];
+#pragma unroll
+            for (int r = 0; r < REMAP_R; ++r) {
+                prevr[r] = 0;
+                nearr[r] = 0;
+                bidr[r] = NO_BODY;
+                if (!liver[r] || init_mode) continue;
+                const long long c = cr[r];
+                const int x = xr[r], y = yr[r], z = zr[r];
+                prevr[r] = sp.flags_prev[c];
+                bidr[r] = sp.bid_prev[c];
+                uint8_t near = 0;
+                const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+                if (x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+#pragma unroll
+                    for (int a = 1; a < Q; ++a) near |= sp.flags_prev[c - ex(a) - ey(a) * sy - ez(a) * sz];
+                } else {
+#pragma unroll
+                    for (int a = 1; a < Q; ++a) {
+                        const int sx_ = x - ex(a), sy_ = y - ey(a), sz_ = z - ez(a);
+                        const bool in = !((!d.px && (sx_ < 0 || sx_ >= d.nx)) || (!d.py && (sy_ < 0 || sy_ >= d.ny)) ||
+                                          (!d.pz && (sz_ < 0 || sz_ >= d.nz)));
+                        const uint8_t v = sp.flags_prev[((long long)wrap_axis(sz_, d.nz) * d.ny + wrap_axis(sy_, d.ny)) * d.nx +
+                                                        wrap_axis(sx_, d.nx)];
+                        near |= in ? v : 0;
+                    }
+                }
+                nearr[r] = near;
+            }
+#pragma unroll
+            for (int r = 0; r < REMAP_R; ++r) {
+                const bool live = liver[r];
+                const int id = idr[r];
+                const long long c = cr[r];
+                uint8_t flags = 0;
+                if (live) {
+                    const uint8_t solid = id != NO_BODY ? F_SOLID : 0;
+                    flags = solid | wall_bit(d, xr[r], yr[r], zr[r]);
+                    if (!init_mode) {
+                        const uint8_t prev = prevr[r] & F_SOLID;
+                        if (prev) flags |= F_SOLID_PREV;
+                        if (nearr[r] & F_SOLID) flags |= F_NEAR;
+                        if ((solid != 0) != (prev != 0) || (solid && bidr[r] != id)) dv.changed[sp.parity] = 1;
+                    }
+                    sp.flags_cur[c] = flags;
+                    sp.bid_cur[c] = (uint8_t)id;
+                }
+                // the boundary kernel's cells: a shared-memory atomic per warp
+                // (past the buffer, a global one)
+                const bool mine = live && !init_mode && !(flags & F_SOLID) && (flags & (F_NEAR | F_SOLID_PREV));
+                const unsigned mb = __ballot_sync(0xffffffffu, mine);
+                if (mb) {
+                    const int leader = __ffs(mb) - 1;
+                    int base = 0;
+                    if (lane == leader) base = atomicAdd(&lcount, __popc(mb));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    const int pos = base + __popc(mb & ((1u << lane) - 1u));
+                    if (mine) {
+                        if (pos < REMAP_LIST_BUF) {
+                            lbuf[pos] = (uint32_t)c;
+                        } else {
+                            const int g = atomicAdd(dv.bcount, 1);
+                            if (g < dv.blist_cap) dv.blist[g] = (uint32_t)c;
+                            else atomicOr(dv.status, ST_LINKS);
+                        }
                     }
                 }
             }
@@ -440,11 +476,11 @@ __device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp,
     }
 }
 
-__global__ void __launch_bounds__(REMAP_THREADS, 5) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
+__global__ void __launch_bounds__(REMAP_THREADS, 4) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
     remap_body(dv, sp, launch_blk(), init_mode);
 }
 
-__global__ void __launch_bounds__(REMAP_THREADS, 5) remap_batch(const Batch bt) {
+__global__ void __launch_bounds__(REMAP_THREADS, 4) remap_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
     remap_body(sdv, ssp, sbk, 0);
 }
@@ -1202,7 +1238,7 @@ void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8
 void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s) {
     prep_kernel<<<1, PREP_THREADS, 0, s>>>(dv, sp);
     const int side = dv.remap_side;
-    const unsigned bx = (unsigned)(((side + REMAP_TY - 1) / REMAP_TY) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS));
+    const unsigned bx = (unsigned)(((side + REMAP_ROWS - 1) / REMAP_ROWS) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS));
     remap_kernel<<<dim3(bx, dv.nb), dim3(REMAP_TX, REMAP_TY), 0, s>>>(dv, sp, init_mode);
 }
 
@@ -1249,7 +1285,7 @@ void batch_grid_small(const Device &dv, int k, int g[3]) {
     switch (k) {
     case BK_PREP: case BK_LOADS: g[0] = g[1] = g[2] = 1; break;
     case BK_REMAP:
-        g[0] = ((side + REMAP_TY - 1) / REMAP_TY) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS);
+        g[0] = ((side + REMAP_ROWS - 1) / REMAP_ROWS) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS);
         g[1] = dv.nb; g[2] = 1;
         break;
     case BK_LINKS: g[0] = dv.link_side; g[1] = dv.nb; g[2] = 1; break;
