@@ -224,6 +224,20 @@ long long lbm_steps_done(lbm_t *h);
 /* Body states after the last step, out[bodies][13] (synchronises). */
 int lbm_get_bodies(lbm_t *h, double *out);
 
+/* The same read without waiting: enqueues on the handle's stream a copy of
+ * the body states after the steps enqueued so far into host memory
+ * out[bodies][13] (page-locked memory lets the copy run asynchronously;
+ * `out` must stay valid until the read completes), and the status word
+ * beside it, and returns a ticket (>= 0; -1 before the first step, when the
+ * initial states are copied at once).  lbm_wait_ticket(h, ticket) waits for
+ * that read and returns the first error the status word held then (as
+ * lbm_sync).  Later steps may be enqueued before the wait: the read is
+ * ordered after the steps before it and before those after it, so a caller
+ * can keep the GPU stepping while reading each step's states one step late.
+ * LBM_E_ARG for a ticket never issued. */
+int lbm_get_bodies_async(lbm_t *h, double *out, long long *ticket);
+int lbm_wait_ticket(lbm_t *h, long long ticket);
+
 /* Hydrodynamic force and torque of the last step, out[bodies][6]: F[3],
  * T[3]; the torque is about the body centre (synchronises). */
 int lbm_get_forces(lbm_t *h, double *out);

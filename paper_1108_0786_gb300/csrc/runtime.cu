@@ -37,6 +37,12 @@ struct lbm_s {
     int expire_waits = 0;               // lbm_debug_set knobs
     int adjoint_sets = 0;
     long long list_cap_limit = 0;
+    // asynchronous reads (lbm_get_bodies_async): a ring of completion events
+    // and pinned status words, one per read ticket modulo READS
+    static constexpr int READS = 64;
+    cudaEvent_t rd_ev[READS] = {};
+    int *rd_status = nullptr;
+    long long rd_seq = 0;
     double *avg_sum = nullptr;          // [3][C] running velocity sum (lbm_average_*)
     long long *avg_count = nullptr;     // steps added to it (device)
     unsigned graph_gen = 0;             // bumped whenever the step graphs are rebuilt with other kernels
@@ -521,9 +527,7 @@ int build_graphs(lbm_t *h) {
     return LBM_OK;
 }
 
-int check_status(lbm_t *h) {
-    int st = 0;
-    CK(cudaMemcpy(&st, h->dv.status, sizeof st, cudaMemcpyDeviceToHost));
+int status_error(lbm_t *h, int st) {
     // a step cut short (a wait that ran out, a full list) comes first: the
     // other bits may be its consequences
     if (st & lbm::ST_TIMEOUT) return fail(h, LBM_E_TIMEOUT, "a bounded wait on a bulk copy ran out");
@@ -536,6 +540,12 @@ int check_status(lbm_t *h) {
     return LBM_OK;
 }
 
+int check_status(lbm_t *h) {
+    int st = 0;
+    CK(cudaMemcpy(&st, h->dv.status, sizeof st, cudaMemcpyDeviceToHost));
+    return status_error(h, st);
+}
+
 int sync_and_check(lbm_t *h) {
     if (!h->ready) return LBM_OK;
     CK(cudaStreamSynchronize(h->stream));
@@ -545,6 +555,13 @@ int sync_and_check(lbm_t *h) {
 
 void release_device(lbm_t *h) {
     if (h->ready) cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t &ev : h->rd_ev)
+        if (ev) {
+            cudaEventDestroy(ev);
+            ev = nullptr;
+        }
+    if (h->rd_status) cudaFreeHost(h->rd_status);
+    h->rd_status = nullptr;
     for (int p = 0; p < 2; ++p)
         if (h->single[p]) cudaGraphExecDestroy(h->single[p]);
     if (h->chunk) cudaGraphExecDestroy(h->chunk);
@@ -908,6 +925,37 @@ int lbm_get_bodies(lbm_t *h, double *out) {
     if (rc) return rc;
     if (nb(h)) CK(cudaMemcpy(out, h->bodies[h->steps & 1], sizeof(BodyState) * nb(h), cudaMemcpyDeviceToHost));
     return LBM_OK;
+}
+
+int lbm_get_bodies_async(lbm_t *h, double *out, long long *ticket) {
+    if (!h || !out || !ticket) return LBM_E_ARG;
+    *ticket = -1;
+    if (!h->ready) {
+        std::memcpy(out, h->init_state.data(), sizeof(BodyState) * nb(h));
+        return LBM_OK;
+    }
+    if (!h->rd_status) {
+        CK(cudaHostAlloc(reinterpret_cast<void **>(&h->rd_status), sizeof(int) * lbm_s::READS, cudaHostAllocDefault));
+        for (cudaEvent_t &ev : h->rd_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    const int slot = (int)(h->rd_seq % lbm_s::READS);
+    cudaStream_t s = h->stream;
+    if (nb(h))
+        CK(cudaMemcpyAsync(out, h->bodies[h->steps & 1], sizeof(BodyState) * nb(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->rd_status + slot, h->dv.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(h->rd_ev[slot], s));
+    *ticket = h->rd_seq++;
+    return LBM_OK;
+}
+
+int lbm_wait_ticket(lbm_t *h, long long ticket) {
+    if (!h || ticket >= h->rd_seq) return h ? fail(h, LBM_E_ARG, "no read with ticket %lld", ticket) : LBM_E_ARG;
+    if (ticket < 0) return LBM_OK;
+    // a slot re-recorded by a later read completes after this one
+    const int slot = (int)(ticket % lbm_s::READS);
+    CK(cudaEventSynchronize(h->rd_ev[slot]));
+    CK(cudaGetLastError());
+    return status_error(h, h->rd_status[slot]);
 }
 
 int lbm_get_forces(lbm_t *h, double *out) {

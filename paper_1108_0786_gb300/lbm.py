@@ -41,7 +41,8 @@ EXPORTED = (
     "lbm_add_body", "lbm_body_properties", "lbm_add_spring", "lbm_set_drive", "lbm_set_drive_window", "lbm_set_drive_axis",
     "lbm_set_body_state", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_steps_done",
     "lbm_average_begin", "lbm_average_stop", "lbm_average_get",
-    "lbm_get_bodies", "lbm_get_forces", "lbm_get_fields", "lbm_get_fields_device",
+    "lbm_get_bodies", "lbm_get_bodies_async", "lbm_wait_ticket", "lbm_get_forces", "lbm_get_fields",
+    "lbm_get_fields_device",
     "lbm_enable_history", "lbm_get_history", "lbm_save", "lbm_load", "lbm_time_kernels",
     "lbm_tune", "lbm_debug_set", "lbm_autotune", "lbm_kernels_per_step", "lbm_bytes_per_cell",
     "lbm_last_error",
@@ -89,6 +90,8 @@ def load_library(path: Optional[str] = None):
         "lbm_sync": ([P], I),
         "lbm_steps_done": ([P], ctypes.c_longlong),
         "lbm_get_bodies": ([P, DP], I),
+        "lbm_get_bodies_async": ([P, DP, ctypes.POINTER(ctypes.c_longlong)], I),
+        "lbm_wait_ticket": ([P, ctypes.c_longlong], I),
         "lbm_get_forces": ([P, DP], I),
         "lbm_get_fields": ([P, I, P, I], I),
         "lbm_get_fields_device": ([P, I, P, I], I),
@@ -308,6 +311,23 @@ class Lattice:
         out = np.zeros((self.nbodies, 13))
         self._check(self._lib.lbm_get_bodies(self._h, _dp(out)))
         return out
+
+    def bodies_async(self, out):
+        """Enqueue a read of the body states after the steps enqueued so far
+        into ``out`` (float64 [nbodies, 13], C-contiguous; page-locked memory,
+        e.g. a pinned torch tensor's ``.numpy()``, for an asynchronous copy;
+        it must stay alive until the read is waited for); returns a ticket
+        for ``wait``."""
+        if out.dtype != np.float64 or out.shape != (self.nbodies, 13) or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array of shape (nbodies, 13)")
+        t = ctypes.c_longlong(-1)
+        self._check(self._lib.lbm_get_bodies_async(self._h, _dp(out), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket):
+        """Wait for the read with this ticket; raises the first error the
+        device had latched by then."""
+        return self._check(self._lib.lbm_wait_ticket(self._h, int(ticket)))
 
     def forces(self):
         out = np.zeros((self.nbodies, 6))

@@ -57,6 +57,15 @@ def test_host_side_calls_without_a_device(lib):
     out = np.zeros(26)
     assert lib.lbm_get_bodies(h, out.ctypes.data_as(dp)) == 0
     assert np.array_equal(out[:3], p) and out[3] == 1.0
+    # before the first step an asynchronous read completes at once (ticket -1)
+    out2 = np.zeros(26)
+    t = ctypes.c_longlong(7)
+    lib.lbm_get_bodies_async.argtypes = [ctypes.c_void_p, dp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lbm_wait_ticket.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
+    assert lib.lbm_get_bodies_async(h, out2.ctypes.data_as(dp), ctypes.byref(t)) == 0
+    assert t.value == -1 and np.array_equal(out2, out)
+    assert lib.lbm_wait_ticket(h, -1) == 0
+    assert lib.lbm_wait_ticket(h, 0) == lbm.E_ARG          # never issued
     # body preparation, remap, bulk, boundary, links, drive and spring loads, force + integrate
     assert lib.lbm_kernels_per_step(h) == 7
     assert lib.lbm_bytes_per_cell(h) == 2 * 19 * 4 + 1

@@ -115,3 +115,24 @@ def test_expired_bulk_copy_wait_latches_e_timeout(precision, blocks):
     assert np.isfinite(lat.pop()).all()
     lat.close()
     context_still_usable()
+
+
+def test_error_surfaces_at_the_wait_of_an_asynchronous_read(cuda):
+    """A read enqueued after the failing step carries the status word with
+    it: lbm_wait_ticket reports the latched error."""
+    lat = swimmer(precision="f32")
+    lat.step(2)
+    buf = cuda.empty((lat.nbodies, 13), dtype=cuda.float64, pin_memory=True).numpy()
+    t = lat.bodies_async(buf)
+    lat.wait(t)                                        # no error yet
+    st = lat.bodies()[1].copy()
+    st[7:10] = (0.8, 0.0, 0.0)                         # above LBM_MAX_BODY_STEP = 0.5 per step
+    lat.set_body_state(1, st)
+    lat.step(1)
+    t = lat.bodies_async(buf)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.wait(t)
+    assert ei.value.code == lbm.E_UNSTABLE
+    lat.close()
+    context_still_usable()
+

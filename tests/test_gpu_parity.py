@@ -290,6 +290,36 @@ def test_checkpoint_round_trip_is_bitwise(tmp_path):
     assert np.array_equal(lat2.bodies(), a_bodies)
 
 
+def test_asynchronous_reads_match_synchronous_ones():
+    """lbm_get_bodies_async, waited for one step late while the next step
+    runs, returns each step's states as lbm_get_bodies does on a twin
+    handle; more reads than the ring of tickets holds."""
+    import torch
+    sc = wl.three_sphere_periodic()
+    a = lbm.from_scenario(sc, precision="f32")
+    b = lbm.from_scenario(sc, precision="f32")
+    bufs = [torch.empty((a.nbodies, 13), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    want = []
+    for k in range(70):
+        b.step(1)
+        want.append(b.bodies())
+    prev = None
+    for k in range(70):
+        a.step(1)
+        t = a.bodies_async(bufs[k & 1])
+        if prev is not None:
+            a.wait(prev)
+            assert np.array_equal(bufs[(k - 1) & 1], want[k - 1]), k
+        prev = t
+    a.wait(prev)
+    assert np.array_equal(bufs[1], want[69])
+    assert prev == 69
+    with pytest.raises(lbm.LbmError):
+        a.wait(70)
+    a.close()
+    b.close()
+
+
 def test_history_matches_per_step_states():
     sc = wl.three_sphere_periodic()
     lat = lbm.from_scenario(sc, precision="f32", history=64)
