@@ -391,7 +391,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
  *     one shape for all members (lbm_ensemble_autotune), not in the
  *     members' own.
  *   LBM_ENSEMBLE_BRANCHES: the members' own step kernels as parallel graph
- *     branches (7 launches a step per member).
+ *     branches (6 launches a step per member).
  * Both give the bits of the members stepped alone.  There is no dependency
  * between members: no kernel waits on another.  The paper runs one
  * simulation per design study point; the ensemble is the throughput path
@@ -422,9 +422,11 @@ int lbm_ensemble_destroy(lbm_ensemble_t *e);
 const char *lbm_ensemble_last_error(lbm_ensemble_t *e);
 
 /* Kernel launches one step makes (for launch accounting): with bodies and
- * fluid, body preparation, remap, bulk stream-collide, boundary cells (one
- * more launch with walls), link lists, drive and spring loads, and the
- * momentum exchange with the rigid-body step. */
+ * fluid, remap, bulk stream-collide, boundary cells (one more launch with
+ * walls), link lists, drive and spring loads, and the momentum exchange
+ * with the rigid-body step.  A body preparation kernel (geometry records of
+ * states the rigid-body step did not make) runs once before the first step
+ * after the host wrote a body state, and in every overlapped step. */
 int lbm_kernels_per_step(lbm_t *h);
 
 /* Algorithmic bytes per cell the stream-collide kernel moves:

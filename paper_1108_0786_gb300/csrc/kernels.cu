@@ -226,12 +226,14 @@ __device__ inline bool spans_meet(int b0, int bw, int e0, int ew, int n, int per
     return o < ew || o + bw > n;
 }
 
-// Per-step preparation, one block: the geometry records of states n and
-// n-1 (slots by body buffer: remade only when the slot's stamp differs from
-// the state, i.e. when no rigid-body step produced that state), each body's
-// remap candidates (the bodies, in order, whose grown box meets its remap
-// cube; a warp a body, ballots over the candidates), and the start of the
-// boundary kernel's list.
+// Body preparation, one block: the geometry records of states n and n-1
+// (slots by body buffer: remade only when the slot's stamp differs from the
+// state, i.e. when no rigid-body step produced that state), each body's
+// remap candidates for the batched remap (the bodies, in order, whose grown
+// box meets its remap cube; a warp a body, ballots over the candidates; a
+// single lattice's remap finds its own), and the start of the boundary
+// kernel's list.  A single lattice's steps whose states the rigid-body step
+// made (and whose list the previous step's last block emptied) skip it.
 constexpr int PREP_THREADS = 256;
 
 __device__ __forceinline__ void prep_body(const Device &dv, const StepPtrs &sp) {
@@ -283,6 +285,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batch(const Batch bt) {
     prep_body(sdv, ssp);
 }
 
+
 // a coordinate of the cube, o + l with o in [0, n) and l < side, wrapped
 // into [0, n) on a periodic axis (one compare unless the cube exceeds the axis)
 __device__ inline int wrap_up(int v, int n) { return v < n ? v : (v - n < n ? v - n : v % n); }
@@ -305,14 +308,16 @@ constexpr int REMAP_LAYERS = 1;         // cube layers a block (more layers seri
 constexpr int REMAP_LIST_BUF = 2048;    // list entries a block gathers before the global append
 static_assert(sizeof(BodyGeom) % sizeof(int) == 0, "geometry records are copied as ints");
 
+template <bool SELF_CAND>
 __device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp, const Blk &bk, int init_mode) {
     const Domain d = dv.dom;
     const int b = bk.y;
     const BodyGeom *__restrict__ geo = dv.geom + sp.parity * dv.nb;    // state n
-    // body b's candidates (prep_kernel's list), the first REMAP_STAGED of
-    // them with their records in shared memory
+    // body b's candidates, the first REMAP_STAGED of them with their
+    // records in shared memory
     __shared__ BodyGeom cg[REMAP_STAGED];
     __shared__ int cid[LBM_MAX_BODIES_DEV];
+    __shared__ int s_ncand;
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
     const int side = geo[b].side;
     const int nyb = (side + REMAP_ROWS - 1) / REMAP_ROWS;
@@ -323,18 +328,40 @@ __device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp,
     __shared__ uint32_t lbuf[REMAP_LIST_BUF];
     __shared__ int lcount, lbase;
     const int org[3] = {geo[b].origin[0], geo[b].origin[1], geo[b].origin[2]};
-    const int ncand = geo[b].ncand;
     const int tid = threadIdx.y * REMAP_TX + threadIdx.x;
     const int lane = tid & 31;
     if (tid == 0) lcount = 0;
-    for (int i = tid; i < ncand; i += REMAP_THREADS) cid[i] = dv.cand[b * dv.nb + i];
+    // the candidates: the bodies, in body order, whose grown box (the cells
+    // their flags of epochs n-3 .. n can reach) meets b's cube.  A single
+    // lattice's block finds them (the first warp, ballots over 32 bodies at
+    // a time); the batched remap takes the preparation kernel's list.  The
+    // first REMAP_STAGED records are staged in shared memory.
+    if constexpr (SELF_CAND) {
+        if (tid < 32) {
+            int cnt = 0;
+            for (int k0 = 0; k0 < dv.nb; k0 += 32) {
+                const int k = k0 + tid;
+                bool meets = k < dv.nb;
+                for (int a = 0; a < 3 && meets; ++a)
+                    meets = spans_meet(org[a], side, geo[k].ebox[a], geo[k].ebox[3 + a], n3[a], per[a]);
+                const unsigned bal = __ballot_sync(0xffffffffu, meets);
+                if (meets) cid[cnt + __popc(bal & ((1u << tid) - 1u))] = k;
+                cnt += __popc(bal);
+            }
+            if (tid == 0) s_ncand = cnt;
+        }
+    } else {
+        const int nc = geo[b].ncand;
+        for (int i = tid; i < nc; i += REMAP_THREADS) cid[i] = dv.cand[b * dv.nb + i];
+        if (tid == 0) s_ncand = nc;
+    }
+    __syncthreads();
+    const int ncand = s_ncand;
     {
         constexpr int W = (int)(sizeof(BodyGeom) / sizeof(int));
         const int staged = min(ncand, REMAP_STAGED);
-        for (int i = tid; i < staged * W; i += REMAP_THREADS) {
-            const int kb = dv.cand[b * dv.nb + i / W];
-            reinterpret_cast<int *>(cg)[i] = reinterpret_cast<const int *>(geo + kb)[i % W];
-        }
+        for (int i = tid; i < staged * W; i += REMAP_THREADS)
+            reinterpret_cast<int *>(cg)[i] = reinterpret_cast<const int *>(geo + cid[i / W])[i % W];
     }
     __syncthreads();
 
@@ -477,12 +504,12 @@ __device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp,
 }
 
 __global__ void __launch_bounds__(REMAP_THREADS, 4) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
-    remap_body(dv, sp, launch_blk(), init_mode);
+    remap_body<true>(dv, sp, launch_blk(), init_mode);
 }
 
 __global__ void __launch_bounds__(REMAP_THREADS, 4) remap_batch(const Batch bt) {
     LBM_BATCH_MEMBER(bt);
-    remap_body(sdv, ssp, sbk, 0);
+    remap_body<false>(sdv, ssp, sbk, 0);
 }
 
 // Links: block (k, b) scans z-plane k of the cube of side 2 E_b + 3 around
@@ -783,6 +810,7 @@ __device__ void integrate_body_warp(const Device &dv, const StepPtrs &sp, int b,
 __device__ inline void finish_step(const Device &dv, const StepPtrs &sp) {
     *dv.t_dev = *dv.t_dev + 1;
     dv.changed[sp.parity ^ 1] = 0;
+    if (dv.bcount) *dv.bcount = 0;          // the next remap refills the boundary kernel's list
 }
 
 // round(v 2^FIX_BITS) to the nearest integer, ties away from zero, from the
@@ -1235,8 +1263,12 @@ void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8
     init_flags_kernel<<<blocks_for(dv.dom.C, 256), 256, 0, s>>>(dv.dom, flags0, flags1, bid0, bid1);
 }
 
-void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s) {
+void launch_prep(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     prep_kernel<<<1, PREP_THREADS, 0, s>>>(dv, sp);
+}
+
+void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s, bool prep) {
+    if (prep) launch_prep(dv, sp, s);
     const int side = dv.remap_side;
     const unsigned bx = (unsigned)(((side + REMAP_ROWS - 1) / REMAP_ROWS) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS));
     remap_kernel<<<dim3(bx, dv.nb), dim3(REMAP_TX, REMAP_TY), 0, s>>>(dv, sp, init_mode);

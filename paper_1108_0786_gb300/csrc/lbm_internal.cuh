@@ -116,7 +116,7 @@ struct BodyGeom {
     float r2, h, margin;    // r^2, l / 2 and the margin of the FP32 inside test
     int shape;
     int side;               // edge of the remap cube, 2 (E + REMAP_MARGIN) + 1
-    int ncand;              // state n: bodies whose grown box meets this body's remap cube (cand list)
+    int ncand;              // state n: bodies whose grown box meets this body's remap cube (cand list; the batched remap's)
     int box[6];             // per axis: lower corner (wrapped) and width of [floor(X - reach), floor(X + reach)]
     int ebox[6];            // the same grown by STATIC_REACH cells
     double cfd[3];          // the position within the cell in FP64
@@ -365,7 +365,11 @@ struct AdjBody {
 // ---- launch wrappers (kernels.cu / stream_collide.cu / adjoint.cu) ---------
 void launch_init_flags(const Device &dv, uint8_t *flags0, uint8_t *flags1, uint8_t *bid0,
                        uint8_t *bid1, cudaStream_t s);
-void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s);
+// the remap of a step, after the body preparation (geometry records remade
+// where a state was set from outside, the boundary list emptied) unless
+// `prep` is false: steps whose states the rigid-body step made skip it
+void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s, bool prep = true);
+void launch_prep(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_stream_collide(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 void launch_boundary_fix(const Device &dv, const StepPtrs &sp, cudaStream_t s);
 bool needs_boundary_fix(const Device &dv);

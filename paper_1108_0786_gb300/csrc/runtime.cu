@@ -34,6 +34,9 @@ struct lbm_s {
     std::vector<DriveTerm> drives;
     int hist_cap = 0;
     int tune_vec = 0, tune_minb = 0;
+    // the next step needs the body preparation (geometry records of states
+    // the rigid-body step did not make; set when the host writes a state)
+    bool need_prep = true;
     int expire_waits = 0;               // lbm_debug_set knobs
     int adjoint_sets = 0;
     long long list_cap_limit = 0;
@@ -172,7 +175,7 @@ lbm::StepPtrs step_ptrs(lbm_t *h, int p, bool overlap = false) {
 void enqueue_overlapped(lbm_t *h, int p, cudaStream_t s, bool first);
 
 void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bool *ran = nullptr,
-                  bool fork = false) {
+                  bool fork = false, bool prep = true) {
     const lbm::StepPtrs sp = step_ptrs(h, p);
     const bool bodies = nb(h) > 0, fl = fluid(h);
     auto run = [&](int slot, cudaStream_t st, auto &&fn) {
@@ -181,7 +184,7 @@ void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bo
         if (ev) cudaEventRecord(ev[2 * slot + 1], st);
         if (ran) ran[slot] = true;
     };
-    if (bodies && fl) run(LBM_KERNEL_REMAP, s, [&] { lbm::launch_remap(h->dv, sp, 0, s); });
+    if (bodies && fl) run(LBM_KERNEL_REMAP, s, [&] { lbm::launch_remap(h->dv, sp, 0, s, prep); });
     const bool boundary = fl && lbm::needs_boundary_fix(h->dv);
     const bool forked = boundary && fork;
     if (forked) {
@@ -261,7 +264,7 @@ int kernels_per_step(const lbm_t *h) {
     const bool bodies = nb(h) > 0, fl = fluid(h);
     const bool walls = (h->bc & 7) != 7;
     int n = 0;
-    if (bodies && fl) n += 2;                               // body preparation, remap
+    if (bodies && fl) n += overlapped(h) ? 2 : 1;           // (body preparation,) remap
     if (fl) n += 1;                                         // bulk stream-collide
     if (fl) n += (bodies ? 1 : 0) + (walls ? 1 : 0);        // boundary cells
     if (bodies && fl) n += 3;                               // links, drive and spring loads, force + rigid-body step
@@ -301,6 +304,7 @@ int refresh_tiles(lbm_t *h) {
 }
 
 int upload_bodies(lbm_t *h) {
+    h->need_prep = true;
     const size_t bs = sizeof(BodyState) * nb(h);
     if (!bs) return LBM_OK;
     CK(cudaMemcpyAsync(h->bodies[0], h->init_state.data(), bs, cudaMemcpyHostToDevice, h->stream));
@@ -505,7 +509,7 @@ int build_graphs(lbm_t *h) {
         for (int i = 0; i < n; ++i) {
             const int p = (p0 + i) & 1;
             if (ov) enqueue_overlapped(h, p, h->cap, i == 0);
-            else enqueue_step(h, p, h->cap, nullptr, nullptr, true);
+            else enqueue_step(h, p, h->cap, nullptr, nullptr, true, false);
         }
         if (ov) cudaStreamWaitEvent(h->cap, h->far_ev[(p0 + n - 1) & 1], 0);
     };
@@ -819,6 +823,7 @@ int lbm_set_body_state(lbm_t *h, int b, const double state[13]) {
                         LBM_MAX_BODY_STEP);
     CK(cudaMemcpy(cur, &s, sizeof s, cudaMemcpyHostToDevice));
     h->tiles_stale = true;
+    h->need_prep = true;
     return LBM_OK;
 }
 
@@ -848,6 +853,14 @@ int lbm_step(lbm_t *h, int n) {
     if (rc) return rc;
     if ((rc = build_graphs(h))) return rc;
     if (n > 0 && (rc = refresh_tiles(h))) return rc;
+    if (n > 0 && h->need_prep && nb(h) > 0 && fluid(h) && !overlapped(h)) {
+        // the step graphs leave the body preparation out: it runs here after
+        // the host wrote a state (creation, lbm_set_body_state, lbm_load, a
+        // reverse sweep's recomputation)
+        lbm::launch_prep(h->dv, step_ptrs(h, (int)(h->steps & 1)), h->stream);
+        CK(cudaGetLastError());
+    }
+    if (n > 0) h->need_prep = false;
     while (n > 0) {
         const int p = (int)(h->steps & 1);
         if (p == 0 && n >= CHUNK_STEPS) {
@@ -1119,6 +1132,7 @@ int lbm_load(lbm_t *h, const char *path) {
     const int st[4] = {0, 0, 1, 1};
     CK(cudaMemcpy(h->dv.status, st, sizeof st, cudaMemcpyHostToDevice));
     h->tiles_stale = true;
+    h->need_prep = true;
     return LBM_OK;
 }
 
@@ -1286,6 +1300,9 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     if (!tp.recorded) return fail(h, LBM_E_STATE, "lbm_adjoint_backward needs a recording (lbm_adjoint_record)");
     int rc = sync_and_check(h);
     if (rc) return rc;
+    // the recomputation remakes the geometry records and the boundary list
+    // of the states it replays: the handle's next step prepares its own
+    h->need_prep = true;
     const int B = nb(h), ND = (int)h->drives.size(), NS = (int)h->springs.size();
     const long long C = h->C;
     const bool fl = fluid(h);
@@ -1799,6 +1816,7 @@ void ens_enqueue_batched(lbm_ensemble_t *e, std::vector<EnsGroup> &groups, int l
             lbm::launch_batch_cells(k, e->variant[g.precision], b, g.blocks[k], g.precision, st);
         }
     };
+    // the batched remap takes its candidates from the body preparation
     small(lbm::BK_PREP, main);
     small(lbm::BK_REMAP, main);
     if (remapped) cudaEventRecord(remapped, main);
@@ -1914,7 +1932,8 @@ int ens_graph(lbm_ensemble_t *e, const std::vector<int> &set, cudaGraphExec_t *o
             for (int i : set) {
                 lbm_t *h = e->members[i];
                 cudaStreamWaitEvent(h->cap, e->fork, 0);
-                for (int k = 0; k < CHUNK_STEPS; ++k) enqueue_step(h, k & 1, h->cap, nullptr, nullptr, true);
+                for (int k = 0; k < CHUNK_STEPS; ++k)
+                    enqueue_step(h, k & 1, h->cap, nullptr, nullptr, true, false);
                 cudaEventRecord(e->join[i], h->cap);
                 cudaStreamWaitEvent(e->cap, e->join[i], 0);
             }
@@ -2009,6 +2028,15 @@ int lbm_ensemble_step(lbm_ensemble_t *e, const int *steps) {
         if (left[i] > 0 && (h->steps & 1)) {
             if ((rc = lbm_step(h, 1))) return ens_fail(e, rc, h->err.c_str());
             --left[i];
+        }
+    }
+    // the ensemble's graphs leave the body preparation out: a member whose
+    // state the host wrote prepares here
+    for (int i = 0; i < n; ++i) {
+        lbm_t *h = e->members[i];
+        if (left[i] > 0 && h->need_prep && nb(h) > 0 && fluid(h) && !overlapped(h)) {
+            lbm::launch_prep(h->dv, step_ptrs(h, (int)(h->steps & 1)), h->stream);
+            h->need_prep = false;
         }
     }
     // a member whose step graphs changed (an average begun or stopped, a new

@@ -66,8 +66,8 @@ def test_host_side_calls_without_a_device(lib):
     assert t.value == -1 and np.array_equal(out2, out)
     assert lib.lbm_wait_ticket(h, -1) == 0
     assert lib.lbm_wait_ticket(h, 0) == lbm.E_ARG          # never issued
-    # body preparation, remap, bulk, boundary, links, drive and spring loads, force + integrate
-    assert lib.lbm_kernels_per_step(h) == 7
+    # remap, bulk, boundary, links, drive and spring loads, force + integrate
+    assert lib.lbm_kernels_per_step(h) == 6
     assert lib.lbm_bytes_per_cell(h) == 2 * 19 * 4 + 1
     assert lib.lbm_destroy(h) == 0
 
