@@ -1310,21 +1310,22 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     const size_t pop_sz = es * lbm::Q * C;
     const int K = tp.seg;
     std::vector<void *> bk;         // this call's buffers
-    cudaStream_t rs = nullptr;      // the recomputation's stream
+    cudaStream_t rs = nullptr, rss = nullptr;      // the recomputation's streams: main, side
     struct Guard {
         lbm_t *h;
         std::vector<void *> &list;
-        cudaStream_t &rs;
+        cudaStream_t &rs, &rss;
         ~Guard() {
-            if (rs) {
-                cudaStreamSynchronize(rs);
-                cudaStreamDestroy(rs);
-            }
+            for (cudaStream_t *st : {&rs, &rss})
+                if (*st) {
+                    cudaStreamSynchronize(*st);
+                    cudaStreamDestroy(*st);
+                }
             if (h->side) cudaStreamSynchronize(h->side);
             cudaStreamSynchronize(h->stream);
             free_list(h, list);
         }
-    } guard{h, bk, rs};
+    } guard{h, bk, rs, rss};
     // a slot set holds one segment's recomputed epochs: populations (slots
     // 0..K), flags and body ids (slots 0..K+1)
     struct SlotSet {
@@ -1386,21 +1387,26 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     // the side stream, concurrently with the rigid-body and boundary parts;
     // the recomputation runs on a stream of its own
     cudaStream_t side = h->side;
-    if (fl) CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+    if (fl) {
+        CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&rss, cudaStreamNonBlocking));
+    }
     cudaEvent_t ev_main = nullptr, ev_side = nullptr, ev_rec = nullptr, ev_free_main = nullptr,
-                ev_free_side = nullptr;
+                ev_free_side = nullptr, ev_rfork = nullptr, ev_rjoin = nullptr;
     CK(cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_rec, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_free_main, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_free_side, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_rfork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_rjoin, cudaEventDisableTiming));
     struct Events {
-        cudaEvent_t *e[5];
+        cudaEvent_t *e[7];
         ~Events() {
             for (cudaEvent_t *p : e)
                 if (*p) cudaEventDestroy(*p);
         }
-    } events{{&ev_main, &ev_side, &ev_rec, &ev_free_main, &ev_free_side}};
+    } events{{&ev_main, &ev_side, &ev_rec, &ev_free_main, &ev_free_side, &ev_rfork, &ev_rjoin}};
     CK(cudaEventRecord(ev_main, s));
     CK(cudaEventRecord(ev_side, s));
     CK(cudaEventRecord(ev_free_main, s));
@@ -1470,16 +1476,26 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
             sp.body_next = scratch;
             sp.tstep = dr.t_dev;
             sp.parity = j & 1;
+            // the body preparation only at the segment's first step: the
+            // later states' geometry records come from the recomputation's
+            // own rigid-body steps (the same bits as the tape's states)
+            const bool prep = j == 0;
             if (j == L) {
                 // the flags of the epoch after the run: the last reverse
                 // step needs them (its bounce-back and link cells)
-                if (k == tp.nseg - 1) lbm::launch_remap(dr, sp, 0, rs);
+                if (k == tp.nseg - 1) lbm::launch_remap(dr, sp, 0, rs, prep);
                 break;
             }
-            lbm::launch_remap(dr, sp, 0, rs);
+            lbm::launch_remap(dr, sp, 0, rs, prep);
+            // boundary cells, link lists and loads beside the bulk kernel,
+            // as in the forward step
+            CK(cudaEventRecord(ev_rfork, rs));
+            CK(cudaStreamWaitEvent(rss, ev_rfork, 0));
+            if (lbm::needs_boundary_fix(dr)) lbm::launch_boundary_fix(dr, sp, rss);
+            lbm::launch_links(dr, sp, rss);
+            CK(cudaEventRecord(ev_rjoin, rss));
             lbm::launch_stream_collide(dr, sp, rs);
-            if (lbm::needs_boundary_fix(dr)) lbm::launch_boundary_fix(dr, sp, rs);
-            lbm::launch_links(dr, sp, rs);
+            CK(cudaStreamWaitEvent(rs, ev_rjoin, 0));
             lbm::launch_force(dr, sp, rs);
         }
         CK(cudaGetLastError());
