@@ -318,14 +318,113 @@ __global__ void __launch_bounds__(ADJ_BOUNDARY_THREADS) adj_boundary_kernel(cons
 }
 
 // ---- rigid-body step, reversed ------------------------------------------------
-// One block.  Sh^{n+1} = sa_next + the cell sums of reverse step n+1
-// (part, in block order); then the reverse of Algorithm 1 at step t with the
-// state S^n and the hydrodynamic load fh^n of the tape:
+// Reverse of Algorithm 1 at step t with the state S^n and the hydrodynamic
+// load fh^n of the tape:
 //   V' = V + F / m, X' = X + V', W' = W + R diag(1/I) R^T T,
 //   q' = normalise(q + (0, W') q / 2),
-//   F = F_hydro + g vol + sum_d amp_d sin(omega_d t - phase_d) R e_x + springs.
-// Writes Sh^n (rigid-body part plus the lever-arm term Th x F_hydro of the
-// torque sum) to sa_cur, (Fh, Th) to fadj and adds dJ/dtheta.
+//   F = F_hydro + g vol + sum_d amp_d sin(omega_d t - phase_d) R a_d + springs.
+// The terms that depend only on S^n and fh^n (R, F, R^T T, W', q', the drive
+// sines, the spring geometry) are made for every step of a segment by
+// adj_terms_kernel, a thread per body, drive term or spring and step; the
+// serial kernel adj_integrate does the rest, linear in the adjoint.
+
+// state-only terms of steps t0 .. t0 + L - 1: thread (j, i) with i < nb a
+// body, then the drive terms, then the springs
+__global__ void __launch_bounds__(ADJ_THREADS)
+adj_terms_kernel(const Device dv, const BodyState *states, const double *fhs, long long t0, int L,
+                 AdjBodyTerms *tb, AdjDriveTerms *td, AdjSpringTerms *ts) {
+    const int per = dv.nb + dv.nd + dv.ns;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)L * per) return;
+    const int j = (int)(id / per), i = (int)(id % per);
+    const BodyState *S = states + (long long)j * dv.nb;
+    const double tt = (double)(t0 + j);
+    auto drive_value = [&](const DriveTerm &dt, double &sn_, double &cs) {
+        sn_ = 0.0;
+        cs = 0.0;
+        if (tt < dt.t_on || tt >= dt.t_off) return 0.0;
+        sincos(dt.omega * tt - dt.phase, &sn_, &cs);
+        return dt.amp * sn_;
+    };
+    if (i < dv.nb) {
+        const int b = i;
+        const BodyProps pb = dv.props[b];
+        const BodyState st = S[b];
+        const double *fh = fhs + ((long long)j * dv.nb + b) * 6;
+        double R[3][3];
+        quat_to_matrix(st.q, R);
+        // F: the hydrodynamic force, g times the volume, the body's drive
+        // terms in term order and its springs in spring order (the order
+        // of the forward's sums)
+        double F[3];
+        for (int a = 0; a < 3; ++a) F[a] = fh[a] + dv.g[a] * pb.volume;
+        for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k) {
+            const DriveTerm dt = dv.drives[k];
+            double sn_, cs;
+            const double f = drive_value(dt, sn_, cs);
+            for (int a = 0; a < 3; ++a)
+                F[a] += f * (R[a][0] * dt.axis[0] + R[a][1] * dt.axis[1] + R[a][2] * dt.axis[2]);
+        }
+        for (int kk = pb.spring_first; kk < pb.spring_first + pb.spring_count; ++kk) {
+            const int k = dv.spring_list[kk];
+            const Spring sp_ = dv.springs[k];
+            const BodyState si = S[sp_.i], sj = S[sp_.j];
+            const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
+            const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+            const double inv_len = len > 0 ? 1.0 / len : 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double f = -sp_.k * (len - sp_.rest) * (dd[a] * inv_len) - sp_.gamma * (si.V[a] - sj.V[a]);
+                F[a] += sp_.i == b ? f : -f;
+            }
+        }
+        const double *T = fh + 3;
+        double beta[3], W1[3];
+        for (int a = 0; a < 3; ++a) beta[a] = R[0][a] * T[0] + R[1][a] * T[1] + R[2][a] * T[2];
+        for (int a = 0; a < 3; ++a)
+            W1[a] = st.W[a] + (R[a][0] * beta[0] * pb.inv_inertia[0] + R[a][1] * beta[1] * pb.inv_inertia[1] +
+                               R[a][2] * beta[2] * pb.inv_inertia[2]);
+        const double w = st.q[0], v0 = st.q[1], v1 = st.q[2], v2 = st.q[3];
+        const double c0 = W1[1] * v2 - W1[2] * v1, c1 = W1[2] * v0 - W1[0] * v2, c2 = W1[0] * v1 - W1[1] * v0;
+        const double q4[4] = {w - 0.5 * (W1[0] * v0 + W1[1] * v1 + W1[2] * v2), v0 + 0.5 * (w * W1[0] + c0),
+                              v1 + 0.5 * (w * W1[1] + c1), v2 + 0.5 * (w * W1[2] + c2)};
+        const double inv_nn = rsqrt(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
+        AdjBodyTerms o;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) o.R[3 * r + c] = R[r][c];
+        for (int a = 0; a < 3; ++a) {
+            o.F[a] = F[a];
+            o.beta[a] = beta[a];
+            o.W1[a] = W1[a];
+        }
+        for (int a = 0; a < 4; ++a) o.q1[a] = q4[a] * inv_nn;
+        o.inv_nn = inv_nn;
+        tb[(long long)j * dv.nb + b] = o;
+    } else if (i < dv.nb + dv.nd) {
+        const int k = i - dv.nb;
+        const DriveTerm dt = dv.drives[k];
+        AdjDriveTerms o;
+        o.f = drive_value(dt, o.sn, o.cs);
+        double R[3][3];
+        quat_to_matrix(S[dt.body].q, R);
+        for (int a = 0; a < 3; ++a) o.aw[a] = R[a][0] * dt.axis[0] + R[a][1] * dt.axis[1] + R[a][2] * dt.axis[2];
+        td[(long long)j * dv.nd + k] = o;
+    } else {
+        const int k = i - dv.nb - dv.nd;
+        const Spring sp_ = dv.springs[k];
+        const BodyState si = S[sp_.i], sj = S[sp_.j];
+        const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
+        const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        AdjSpringTerms o;
+        o.len = len;
+        o.ratio = len > 0 ? (len - sp_.rest) / len : 0.0;
+        for (int a = 0; a < 3; ++a) {
+            o.dir[a] = len > 0 ? dd[a] / len : 0.0;
+            o.dv[a] = si.V[a] - sj.V[a];
+        }
+        ts[(long long)j * dv.ns + k] = o;
+    }
+}
+
 __device__ void adj_rot_matrix(const double q[4], const double Rh[3][3], double qh[4]) {
     const double w = q[0], x = q[1], y = q[2], z = q[3];
     qh[2] += -4 * y * Rh[0][0]; qh[3] += -4 * z * Rh[0][0];
@@ -339,10 +438,13 @@ __device__ void adj_rot_matrix(const double q[4], const double Rh[3][3], double 
     qh[1] += -4 * x * Rh[2][2]; qh[2] += -4 * y * Rh[2][2];
 }
 
+// One block.  Sh^{n+1} = sa_next + the cell sums of reverse step n+1
+// (part, in block order); then the reverse step with the state-only terms
+// of step n.  Writes Sh^n (rigid-body part plus the lever-arm term Th x
+// F_hydro of the torque sum) to sa_cur, (Fh, Th) to fadj and adds
+// dJ/dtheta.
 __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device dv, const AdjBody ab) {
     const int nb = dv.nb;
-    const long long t = ab.t;
-    const double tt = (double)t;
     const BodyState *S = ab.state;
     // 1. complete Sh^{n+1}: warp w adds body b's block sums, lanes over the
     //    blocks, then a fixed shuffle tree
@@ -364,63 +466,23 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
             for (int i = 0; i < 3; ++i) { sn[i] += acc[i]; sn[7 + i] += acc[3 + i]; sn[10 + i] += acc[6 + i]; }
         }
     }
-    // drive-term and spring forces of the forward step (the order of the
-    // forward's sums is kept below); each drive term's sine and cosine once
-    for (int k = threadIdx.x; k < dv.nd; k += blockDim.x) {
-        const DriveTerm dt = dv.drives[k];
-        double f = 0.0, sn_ = 0.0, cs = 0.0;
-        if (!(tt < dt.t_on || tt >= dt.t_off)) {
-            sincos(dt.omega * tt - dt.phase, &sn_, &cs);
-            f = dt.amp * sn_;
-        }
-        double R[3][3];
-        quat_to_matrix(S[dt.body].q, R);
-        for (int i = 0; i < 3; ++i)
-            dv.drive_f[3 * k + i] = f * (R[i][0] * dt.axis[0] + R[i][1] * dt.axis[1] + R[i][2] * dt.axis[2]);
-        ab.drive_sc[3 * k + 0] = f;
-        ab.drive_sc[3 * k + 1] = sn_;
-        ab.drive_sc[3 * k + 2] = cs;
-    }
-    for (int k = threadIdx.x; k < dv.ns; k += blockDim.x) {
-        const Spring sp_ = dv.springs[k];
-        const BodyState si = S[sp_.i], sj = S[sp_.j];
-        const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
-        const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-        const double inv_len = len > 0 ? 1.0 / len : 0.0;
-        for (int i = 0; i < 3; ++i)
-            dv.spring_f[3 * k + i] = -sp_.k * (len - sp_.rest) * (dd[i] * inv_len) - sp_.gamma * (si.V[i] - sj.V[i]);
-    }
     __syncthreads();
     // 2. per body: Euler step and rotation update, reversed
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         const BodyProps pb = dv.props[b];
         const BodyState s = S[b];
+        const AdjBodyTerms tm = ab.tb[b];
         const double *sn = ab.sa_next + 13 * b;
         const double *fh = ab.fh + 6 * b;
-        double R[3][3];
-        quat_to_matrix(s.q, R);
-        double F[3];
-        for (int i = 0; i < 3; ++i) F[i] = fh[i] + dv.g[i] * pb.volume;
-        for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k)
-            for (int i = 0; i < 3; ++i) F[i] += dv.drive_f[3 * k + i];
-        for (int kk = pb.spring_first; kk < pb.spring_first + pb.spring_count; ++kk) {
-            const int k = dv.spring_list[kk];
-            const bool first = dv.springs[k].i == b;
-            for (int i = 0; i < 3; ++i) F[i] += first ? dv.spring_f[3 * k + i] : -dv.spring_f[3 * k + i];
-        }
         const double *T = fh + 3;
-        double beta[3], W1[3];
-        for (int i = 0; i < 3; ++i) beta[i] = R[0][i] * T[0] + R[1][i] * T[1] + R[2][i] * T[2];
-        for (int i = 0; i < 3; ++i)
-            W1[i] = s.W[i] + (R[i][0] * beta[0] * pb.inv_inertia[0] + R[i][1] * beta[1] * pb.inv_inertia[1] +
-                              R[i][2] * beta[2] * pb.inv_inertia[2]);
+        double R[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) R[r][c] = tm.R[3 * r + c];
+        const double *beta = tm.beta, *W1 = tm.W1, *q1 = tm.q1;
         const double w = s.q[0], v0 = s.q[1], v1 = s.q[2], v2 = s.q[3];
-        const double c0 = W1[1] * v2 - W1[2] * v1, c1 = W1[2] * v0 - W1[0] * v2, c2 = W1[0] * v1 - W1[1] * v0;
-        double q4[4] = {w - 0.5 * (W1[0] * v0 + W1[1] * v1 + W1[2] * v2), v0 + 0.5 * (w * W1[0] + c0),
-                        v1 + 0.5 * (w * W1[1] + c1), v2 + 0.5 * (w * W1[2] + c2)};
-        const double inv_nn = rsqrt(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
-        double q1[4], dot = 0.0, qh4[4];
-        for (int i = 0; i < 4; ++i) { q1[i] = q4[i] * inv_nn; dot += q1[i] * sn[3 + i]; }
+        const double inv_nn = tm.inv_nn;
+        double dot = 0.0, qh4[4];
+        for (int i = 0; i < 4; ++i) dot += q1[i] * sn[3 + i];
         for (int i = 0; i < 4; ++i) qh4[i] = (sn[3 + i] - q1[i] * dot) * inv_nn;
         double out[13];
         const double qv[3] = {qh4[1], qh4[2], qh4[3]};
@@ -450,7 +512,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
             out[i] = sn[i];
             out[7 + i] = vh1;
             Fh[i] = vh1 * pb.inv_m;
-            F2 += vh1 * F[i];
+            F2 += vh1 * tm.F[i];
             gv += dv.g[i] * Fh[i];
         }
         ab.grad_body[5 * b] += -F2 * pb.inv_m * pb.inv_m;
@@ -459,10 +521,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
         out[0] += Th[1] * fh[2] - Th[2] * fh[1];
         out[1] += Th[2] * fh[0] - Th[0] * fh[2];
         out[2] += Th[0] * fh[1] - Th[1] * fh[0];
-        // drive terms of this body (their axis is the first column of R)
+        // drive terms of this body (F = f R a: dF_i / dR_ij = f a_j)
         for (int k = pb.drive_first; k < pb.drive_first + pb.drive_count; ++k) {
-            const double f = ab.drive_sc[3 * k];         // zero outside the drive window
-            const double *a = dv.drives[k].axis;         // F = f R a: dF_i / dR_ij = f a_j
+            const double f = ab.td[k].f;                 // zero outside the drive window
+            const double *a = dv.drives[k].axis;
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j) Rh[i][j] += f * Fh[i] * a[j];
         }
@@ -476,33 +538,28 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
     __syncthreads();
     // 3. drive-term and spring gradients (one thread per term), then the
     //    spring terms of each body's adjoint (thread b, its springs in order)
+    const double tt = (double)ab.t;
     for (int k = threadIdx.x; k < dv.nd; k += blockDim.x) {
         const DriveTerm dt = dv.drives[k];
         if (tt < dt.t_on || tt >= dt.t_off) continue;
-        const double sn_ = ab.drive_sc[3 * k + 1], cs = ab.drive_sc[3 * k + 2];
+        const AdjDriveTerms tdk = ab.td[k];
         const double *fa = ab.fadj + 6 * dt.body;
-        double R[3][3];
-        quat_to_matrix(S[dt.body].q, R);
-        double proj = 0.0;
-        for (int i = 0; i < 3; ++i)
-            proj += fa[i] * (R[i][0] * dt.axis[0] + R[i][1] * dt.axis[1] + R[i][2] * dt.axis[2]);
-        ab.grad_drive[2 * k] += sn_ * proj;
-        ab.grad_drive[2 * k + 1] += -dt.amp * cs * proj;
+        const double proj = fa[0] * tdk.aw[0] + fa[1] * tdk.aw[1] + fa[2] * tdk.aw[2];
+        ab.grad_drive[2 * k] += tdk.sn * proj;
+        ab.grad_drive[2 * k + 1] += -dt.amp * tdk.cs * proj;
     }
     for (int k = threadIdx.x; k < dv.ns; k += blockDim.x) {
         const Spring sp_ = dv.springs[k];
-        const BodyState si = S[sp_.i], sj = S[sp_.j];
-        const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
-        const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        const AdjSpringTerms tsk = ab.ts[k];
         double fh[3], dvv = 0.0, fd = 0.0;
         for (int i = 0; i < 3; ++i) {
             fh[i] = ab.fadj[6 * sp_.i + i] - ab.fadj[6 * sp_.j + i];
-            dvv += fh[i] * (si.V[i] - sj.V[i]);
+            dvv += fh[i] * tsk.dv[i];
         }
         ab.grad_spring[3 * k + 2] += -dvv;
-        if (len > 0) {
-            for (int i = 0; i < 3; ++i) fd += fh[i] * dd[i] / len;
-            ab.grad_spring[3 * k] += -(len - sp_.rest) * fd;
+        if (tsk.len > 0) {
+            for (int i = 0; i < 3; ++i) fd += fh[i] * tsk.dir[i];
+            ab.grad_spring[3 * k] += -(tsk.len - sp_.rest) * fd;
             ab.grad_spring[3 * k + 1] += sp_.k * fd;
         }
     }
@@ -512,18 +569,15 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_integrate_kernel(const Device
         for (int kk = pb.spring_first; kk < pb.spring_first + pb.spring_count; ++kk) {
             const int k = dv.spring_list[kk];
             const Spring sp_ = dv.springs[k];
-            const BodyState si = S[sp_.i], sj = S[sp_.j];
+            const AdjSpringTerms tsk = ab.ts[k];
             const double sign = sp_.i == b ? 1.0 : -1.0;
-            const double dd[3] = {si.X[0] - sj.X[0], si.X[1] - sj.X[1], si.X[2] - sj.X[2]};
-            const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
             double fh[3], fd = 0.0;
             for (int i = 0; i < 3; ++i) fh[i] = ab.fadj[6 * sp_.i + i] - ab.fadj[6 * sp_.j + i];
             for (int i = 0; i < 3; ++i) sc[7 + i] += -sign * sp_.gamma * fh[i];
-            if (!(len > 0)) continue;
-            double dir[3];
-            for (int i = 0; i < 3; ++i) { dir[i] = dd[i] / len; fd += fh[i] * dir[i]; }
+            if (!(tsk.len > 0)) continue;
+            for (int i = 0; i < 3; ++i) fd += fh[i] * tsk.dir[i];
             for (int i = 0; i < 3; ++i)
-                sc[i] += sign * (-sp_.k * (fd * dir[i] + (len - sp_.rest) / len * (fh[i] - fd * dir[i])));
+                sc[i] += sign * (-sp_.k * (fd * tsk.dir[i] + tsk.ratio * (fh[i] - fd * tsk.dir[i])));
         }
     }
 }
@@ -568,6 +622,14 @@ int adjoint_part_stride(const Device &dv) {
 
 void launch_adj_integrate(const Device &dv, const AdjBody &ab, cudaStream_t s) {
     adj_integrate_kernel<<<1, ADJ_THREADS, 0, s>>>(dv, ab);
+}
+
+void launch_adj_terms(const Device &dv, const BodyState *states, const double *fh, long long t0, int L,
+                      AdjBodyTerms *tb, AdjDriveTerms *td, AdjSpringTerms *ts, cudaStream_t s) {
+    const long long n = (long long)L * (dv.nb + dv.nd + dv.ns);
+    if (n > 0)
+        adj_terms_kernel<<<(unsigned)((n + ADJ_THREADS - 1) / ADJ_THREADS), ADJ_THREADS, 0, s>>>(dv, states, fh, t0, L,
+                                                                                                 tb, td, ts);
 }
 
 void launch_adj_bulk(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s) {

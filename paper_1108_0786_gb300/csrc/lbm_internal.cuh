@@ -349,16 +349,41 @@ struct AdjPtrs {
 };
 
 // pointers of the reversed rigid-body step n (adjoint.cu)
+// Terms of the reversed rigid-body step n that depend only on the state S^n
+// and the load of step n (adj_terms_kernel makes them for all steps of a
+// segment at once, so that the reverse sweep's serial chain holds only the
+// adjoint's own arithmetic).
+struct AdjBodyTerms {
+    double R[9];                    // R(q^n), row-major
+    double F[3];                    // total force of step n
+    double beta[3];                 // R^T T
+    double W1[3];                   // Omega after the update
+    double q1[4];                   // the renormalised quaternion
+    double inv_nn;                  // 1 / |q before renormalisation|
+};
+struct AdjDriveTerms {
+    double f, sn, cs;               // a sin(omega t - phase) (0 outside the window), its sine and cosine
+    double aw[3];                   // R(q^n) axis: the term's world direction
+};
+struct AdjSpringTerms {
+    double dir[3];                  // (X_i - X_j) / |X_i - X_j| (0 at zero length)
+    double len;                     // |X_i - X_j|
+    double ratio;                   // (len - rest) / len (0 at zero length)
+    double dv[3];                   // V_i - V_j
+};
+
 struct AdjBody {
     const BodyState *state;         // state n
     const double *fh;               // [nb][6] hydrodynamic force and torque of step n
+    const AdjBodyTerms *tb;         // [nb] state-only terms of step n
+    const AdjDriveTerms *td;        // [nd]
+    const AdjSpringTerms *ts;       // [ns]
     double *sa_next;                // [nb][13] adjoint of state n+1 (completed in place)
     double *sa_cur;                 // [nb][13] adjoint of state n (written)
     double *fadj;                   // [nb][6] adjoint of the hydrodynamic load (written)
     const double *part;             // cell sums of reverse step n+1
     int part_stride, part_count;
     double *grad_drive, *grad_spring, *grad_body;   // [nd][2], [ns][3], [nb][5] (added to)
-    double *drive_sc;               // [nd][3] scratch: drive value, sine, cosine of step n
     long long t;                    // step n
 };
 
@@ -406,6 +431,10 @@ void launch_batch_cells(int k, int variant, const Batch &bt, unsigned blocks, in
 int batch_bulk_shape(int precision, int i);
 int adjoint_part_stride(const Device &dv);
 void launch_adj_integrate(const Device &dv, const AdjBody &ab, cudaStream_t s);
+// the state-only terms of steps t0 .. t0 + L - 1 from the tape's states
+// (state t0 + j at states + j nb) and loads (fh + 6 j nb)
+void launch_adj_terms(const Device &dv, const BodyState *states, const double *fh, long long t0, int L,
+                      AdjBodyTerms *tb, AdjDriveTerms *td, AdjSpringTerms *ts, cudaStream_t s);
 void launch_adj_bulk(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s);
 void launch_adj_boundary(const Device &dv, const AdjPtrs &ap, bool first, cudaStream_t s);
 void launch_adj_reduce(const Device &dv, const double *part, int stride, int count, double *sa, cudaStream_t s);

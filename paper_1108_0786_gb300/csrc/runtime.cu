@@ -1334,7 +1334,14 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     } sets[2];
     uint8_t *carry = nullptr;       // one set: the flags of epoch m + L kept from segment k + 1
     void *A[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
-    double *sa[2], *fadj, *part, *grads, *r_fh = nullptr, *drive_sc, *r_drive_f = nullptr, *r_spring_f = nullptr;
+    double *sa[2], *fadj, *part, *grads, *r_fh = nullptr, *r_drive_f = nullptr, *r_spring_f = nullptr;
+    // the state-only terms of the reversed rigid-body steps of a segment,
+    // one set per slot set
+    struct TermSet {
+        lbm::AdjBodyTerms *tb = nullptr;
+        lbm::AdjDriveTerms *td = nullptr;
+        lbm::AdjSpringTerms *ts = nullptr;
+    } terms[2];
     BodyState *scratch = nullptr;
     lbm::Link *r_links = nullptr;
     int *r_seg = nullptr, *r_changed = nullptr;
@@ -1347,7 +1354,6 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     if ((rc = alloc_list(h, bk, &part, sizeof(double) * 9 * B * (size_t)stride))) return rc;
     const size_t ngrad = 2 * (size_t)ND + 3 * (size_t)NS + 5 * (size_t)B;
     if ((rc = alloc_list(h, bk, &grads, sizeof(double) * ngrad))) return rc;
-    if ((rc = alloc_list(h, bk, &drive_sc, sizeof(double) * 3 * std::max(ND, 1)))) return rc;
     int nset = 0;
     if (fl) {
         // two sets let segment k - 1 be recomputed while segment k is
@@ -1380,6 +1386,11 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         if ((rc = alloc_list(h, bk, &r_seg, sizeof(int) * B * dv.link_side))) return rc;
         if ((rc = alloc_list(h, bk, &r_changed, sizeof(int) * 2))) return rc;
         if ((rc = alloc_list(h, bk, &r_t, sizeof(long long)))) return rc;
+    }
+    for (int i = 0; i < std::max(nset, 1); ++i) {
+        if ((rc = alloc_list(h, bk, &terms[i].tb, sizeof(lbm::AdjBodyTerms) * K * std::max(B, 1)))) return rc;
+        if ((rc = alloc_list(h, bk, &terms[i].td, sizeof(lbm::AdjDriveTerms) * K * std::max(ND, 1)))) return rc;
+        if ((rc = alloc_list(h, bk, &terms[i].ts, sizeof(lbm::AdjSpringTerms) * K * std::max(NS, 1)))) return rc;
     }
     cudaStream_t s = h->stream;
     if ((rc = build_graphs(h))) return rc;        // creates the side stream
@@ -1439,6 +1450,14 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     const BodyState *states = reinterpret_cast<const BodyState *>(tp.state);
     auto S = [&](long long t) { return states + (t - (tp.n0 - 1)) * B; };     // state t
     auto set_of = [&](int k) -> const SlotSet & { return sets[nset == 2 ? (k & 1) : 0]; };
+    auto terms_of = [&](int k) -> const TermSet & { return terms[nset == 2 ? (k & 1) : 0]; };
+    // the state-only terms of segment k's steps, on stream st
+    auto make_terms = [&](int k, cudaStream_t st) {
+        const long long m = tp.n0 + (long long)k * K;
+        const TermSet &ts = terms_of(k);
+        lbm::launch_adj_terms(dv, S(m), tp.force + (m - tp.n0) * 6 * B, m, std::min(K, tp.n - k * K), ts.tb, ts.td,
+                              ts.ts, st);
+    };
     auto slot_pop = [&](const SlotSet &st, int j) {
         return static_cast<void *>(static_cast<char *>(st.pop) + pop_sz * j);
     };
@@ -1498,6 +1517,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
             CK(cudaStreamWaitEvent(rs, ev_rjoin, 0));
             lbm::launch_force(dr, sp, rs);
         }
+        make_terms(k, rs);
         CK(cudaGetLastError());
         CK(cudaEventRecord(ev_rec, rs));
         return LBM_OK;
@@ -1518,9 +1538,12 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         const int L = seg_len(k);
         const SlotSet &st = set_of(k);
         if (fl) {
-            CK(cudaStreamWaitEvent(s, ev_rec, 0));      // the segment's slots are ready
+            CK(cudaStreamWaitEvent(s, ev_rec, 0));      // the segment's slots and terms are ready
             CK(cudaEventRecord(ev_main, s));
+        } else {
+            make_terms(k, s);
         }
+        const TermSet &tset = terms_of(k);
         for (int j = L - 1; j >= 0; --j) {
             const long long n = m + j;
             lbm::AdjBody ab{};
@@ -1535,7 +1558,9 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
             ab.grad_drive = gd;
             ab.grad_spring = gs;
             ab.grad_body = gb;
-            ab.drive_sc = drive_sc;
+            ab.tb = tset.tb + (long long)j * B;
+            ab.td = tset.td + (long long)j * ND;
+            ab.ts = tset.ts + (long long)j * NS;
             ab.t = n;
             lbm::launch_adj_integrate(dv, ab, s);
             if (fl) {
