@@ -322,21 +322,35 @@ __device__ __forceinline__ unsigned fmix32(unsigned x) {
     return x;
 }
 
+// the five words of a cell and step: the finalizer of a key of (cell, step),
+// then four steps of a 32-bit linear congruential generator (the
+// multiplier and increment of Numerical Recipes' quick generator), each
+// output xor-shifted so that its low bytes carry the state's high bits
 __device__ __forceinline__ Dither bf16_dither(long long c, long long t) {
     const unsigned key = (unsigned)c * 0x9E3779B1u ^ ((unsigned)t * 0x85EBCA77u + (unsigned)(t >> 32));
     Dither d;
+    unsigned x = fmix32(key);
+    d.h[0] = x;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) d.h[k] = fmix32(key + (unsigned)k * 0x6A09E667u);
+    for (int k = 1; k < 5; ++k) {
+        x = x * 1664525u + 1013904223u;
+        d.h[k] = x ^ (x >> 15);
+    }
     return d;
 }
 
-// the BF16 bits (low half of the result) of v rounded stochastically with
-// byte a % 4 of word a / 4 of d; adding 8 random bits and half a step of
-// them below the kept bits, then truncating, rounds the magnitude up with
-// the probability of the dropped fraction (to 2^-9 of an ulp)
+// v rounded stochastically to BF16 with byte a % 4 of word a / 4 of d, its
+// bits in the upper half of the result: adding 8 random bits and half a
+// step of them below the kept bits, then truncating, rounds the magnitude
+// up with the probability of the dropped fraction (to 2^-9 of an ulp)
+__device__ __forceinline__ unsigned bf16_sr_word(float v, const Dither &d, int a) {
+    const unsigned r = __byte_perm(d.h[a >> 2], 0x80u, 0x5504u | ((unsigned)(a & 3) << 4));   // byte << 8 | 0x80
+    return __float_as_uint(v) + r;
+}
+
+// the same BF16 bits in the low half
 __device__ __forceinline__ unsigned bf16_sr_bits(float v, const Dither &d, int a) {
-    const unsigned r = __byte_perm(d.h[a >> 2], 0u, 0x4404u | ((unsigned)(a & 3) << 4));
-    return (__float_as_uint(v) + r + 0x80u) >> 16;
+    return bf16_sr_word(v, d, a) >> 16;
 }
 
 // a 16-bit population as stored: FP16 rounded to nearest, BF16 rounded
@@ -606,8 +620,14 @@ __device__ __forceinline__ void bulk16_body(const Device &dv, const StepPtrs &sp
         const Dither dz = dither_for<T>(c0 + i, sp.tstep);
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
-            const unsigned h = solid ? 0u : store_bits<T>(g[b], dz, b);
-            w[b][j] = hi ? __byte_perm(w[b][j], h, 0x5410) : __byte_perm(h, w[b][j], 0x7610);
+            if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+                // the rounded bits are the upper half of the sum: select them
+                const unsigned h = solid ? 0u : bf16_sr_word(g[b], dz, b);
+                w[b][j] = hi ? __byte_perm(w[b][j], h, 0x7610) : __byte_perm(h, w[b][j], 0x7632);
+            } else {
+                const unsigned h = solid ? 0u : store_bits<T>(g[b], dz, b);
+                w[b][j] = hi ? __byte_perm(w[b][j], h, 0x5410) : __byte_perm(h, w[b][j], 0x7610);
+            }
         }
     }
     // overlapped steps: a tile near a body is the near kernel's
