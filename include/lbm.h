@@ -231,8 +231,10 @@ int lbm_get_bodies(lbm_t *h, double *out);
  * beside it, and returns a ticket (>= 0; -1 before the first step, when the
  * initial states are copied at once).  lbm_wait_ticket(h, ticket) waits for
  * that read and returns the first error the status word held then (as
- * lbm_sync).  Later steps may be enqueued before the wait: the read is
- * ordered after the steps before it and before those after it, so a caller
+ * lbm_sync; the word is copied beside the next step, so it may also hold
+ * that step's errors).  The copy runs on a stream of its own after the
+ * steps enqueued before it and beside the step enqueued next; the step
+ * after that, which overwrites the buffer read, waits for it.  So a caller
  * can keep the GPU stepping while reading each step's states one step late.
  * LBM_E_ARG for a ticket never issued. */
 int lbm_get_bodies_async(lbm_t *h, double *out, long long *ticket);

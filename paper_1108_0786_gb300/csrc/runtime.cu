@@ -46,6 +46,11 @@ struct lbm_s {
     cudaEvent_t rd_ev[READS] = {};
     int *rd_status = nullptr;
     long long rd_seq = 0;
+    // the reads run on a stream of their own beside the following step; a
+    // step that overwrites a body buffer with a read pending waits for it
+    cudaStream_t rd_stream = nullptr;
+    cudaEvent_t rd_after = nullptr;
+    int rd_pending[2] = {-1, -1};           // ring slot of the last read of body buffer p, or -1
     double *avg_sum = nullptr;          // [3][C] running velocity sum (lbm_average_*)
     long long *avg_count = nullptr;     // steps added to it (device)
     unsigned graph_gen = 0;             // bumped whenever the step graphs are rebuilt with other kernels
@@ -553,12 +558,21 @@ int check_status(lbm_t *h) {
 int sync_and_check(lbm_t *h) {
     if (!h->ready) return LBM_OK;
     CK(cudaStreamSynchronize(h->stream));
+    if (h->rd_stream) CK(cudaStreamSynchronize(h->rd_stream));
     CK(cudaGetLastError());
     return check_status(h);
 }
 
 void release_device(lbm_t *h) {
     if (h->ready) cudaStreamSynchronize(h->stream);
+    if (h->rd_stream) {
+        cudaStreamSynchronize(h->rd_stream);
+        cudaStreamDestroy(h->rd_stream);
+        h->rd_stream = nullptr;
+    }
+    if (h->rd_after) cudaEventDestroy(h->rd_after);
+    h->rd_after = nullptr;
+    h->rd_pending[0] = h->rd_pending[1] = -1;
     for (cudaEvent_t &ev : h->rd_ev)
         if (ev) {
             cudaEventDestroy(ev);
@@ -847,6 +861,16 @@ int lbm_set_fields(lbm_t *h, int what, const void *in, int dtype) {
     return LBM_OK;
 }
 
+// before steps that write body buffer p: wait (on the handle's stream) for a
+// pending asynchronous read of it
+static int wait_read(lbm_t *h, int p) {
+    if (h->rd_pending[p] >= 0) {
+        CK(cudaStreamWaitEvent(h->stream, h->rd_ev[h->rd_pending[p]], 0));
+        h->rd_pending[p] = -1;
+    }
+    return LBM_OK;
+}
+
 int lbm_step(lbm_t *h, int n) {
     if (!h || n < 0) return LBM_E_ARG;
     int rc = ensure_device(h);
@@ -864,10 +888,12 @@ int lbm_step(lbm_t *h, int n) {
     while (n > 0) {
         const int p = (int)(h->steps & 1);
         if (p == 0 && n >= CHUNK_STEPS) {
+            if ((rc = wait_read(h, 0)) || (rc = wait_read(h, 1))) return rc;
             CK(cudaGraphLaunch(h->chunk, h->stream));
             h->steps += CHUNK_STEPS;
             n -= CHUNK_STEPS;
         } else {
+            if ((rc = wait_read(h, p ^ 1))) return rc;      // the step writes state n + 1 into buffer p ^ 1
             CK(cudaGraphLaunch(h->single[p], h->stream));
             h->steps += 1;
             n -= 1;
@@ -950,13 +976,21 @@ int lbm_get_bodies_async(lbm_t *h, double *out, long long *ticket) {
     if (!h->rd_status) {
         CK(cudaHostAlloc(reinterpret_cast<void **>(&h->rd_status), sizeof(int) * lbm_s::READS, cudaHostAllocDefault));
         for (cudaEvent_t &ev : h->rd_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaStreamCreateWithFlags(&h->rd_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->rd_after, cudaEventDisableTiming));
     }
     const int slot = (int)(h->rd_seq % lbm_s::READS);
-    cudaStream_t s = h->stream;
+    const int buf = (int)(h->steps & 1);
+    // after the steps enqueued so far, on the read stream: the next step
+    // reads this buffer and writes the other one, so it runs beside the copy
+    cudaStream_t s = h->rd_stream;
+    CK(cudaEventRecord(h->rd_after, h->stream));
+    CK(cudaStreamWaitEvent(s, h->rd_after, 0));
     if (nb(h))
-        CK(cudaMemcpyAsync(out, h->bodies[h->steps & 1], sizeof(BodyState) * nb(h), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(out, h->bodies[buf], sizeof(BodyState) * nb(h), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->rd_status + slot, h->dv.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(h->rd_ev[slot], s));
+    h->rd_pending[buf] = slot;
     *ticket = h->rd_seq++;
     return LBM_OK;
 }
@@ -2070,6 +2104,14 @@ int lbm_ensemble_step(lbm_ensemble_t *e, const int *steps) {
             if ((rc = lbm_step(h, 1))) return ens_fail(e, rc, h->err.c_str());
             --left[i];
         }
+    }
+    // the members' steps overwrite body buffers that asynchronous reads may
+    // still be copying
+    for (int i = 0; i < n; ++i) {
+        lbm_t *h = e->members[i];
+        int rc = wait_read(h, 0);
+        if (rc == LBM_OK) rc = wait_read(h, 1);
+        if (rc) return ens_fail(e, rc, h->err.c_str());
     }
     // the ensemble's graphs leave the body preparation out: a member whose
     // state the host wrote prepares here
