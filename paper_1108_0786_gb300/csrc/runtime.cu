@@ -1344,22 +1344,27 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     const size_t pop_sz = es * lbm::Q * C;
     const int K = tp.seg;
     std::vector<void *> bk;         // this call's buffers
-    cudaStream_t rs = nullptr, rss = nullptr;      // the recomputation's streams: main, side
+    // the recomputation's streams (main, side, graph capture) and graphs
+    cudaStream_t rs = nullptr, rss = nullptr, rcap = nullptr, rcaps = nullptr;
+    cudaGraphExec_t rgraph[2] = {nullptr, nullptr};
     struct Guard {
         lbm_t *h;
         std::vector<void *> &list;
-        cudaStream_t &rs, &rss;
+        cudaStream_t &rs, &rss, &rcap, &rcaps;
+        cudaGraphExec_t (&rgraph)[2];
         ~Guard() {
-            for (cudaStream_t *st : {&rs, &rss})
+            for (cudaStream_t *st : {&rs, &rss, &rcap, &rcaps})
                 if (*st) {
                     cudaStreamSynchronize(*st);
                     cudaStreamDestroy(*st);
                 }
+            for (cudaGraphExec_t &g : rgraph)
+                if (g) cudaGraphExecDestroy(g);
             if (h->side) cudaStreamSynchronize(h->side);
             cudaStreamSynchronize(h->stream);
             free_list(h, list);
         }
-    } guard{h, bk, rs, rss};
+    } guard{h, bk, rs, rss, rcap, rcaps, rgraph};
     // a slot set holds one segment's recomputed epochs: populations (slots
     // 0..K), flags and body ids (slots 0..K+1)
     struct SlotSet {
@@ -1367,6 +1372,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         uint8_t *flags = nullptr, *bid = nullptr;
     } sets[2];
     uint8_t *carry = nullptr;       // one set: the flags of epoch m + L kept from segment k + 1
+    BodyState *stage[2] = {nullptr, nullptr};   // a full segment's states, epochs m - 1 .. m + K - 1
     void *A[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
     double *sa[2], *fadj, *part, *grads, *r_fh = nullptr, *r_drive_f = nullptr, *r_spring_f = nullptr;
     // the state-only terms of the reversed rigid-body steps of a segment,
@@ -1403,6 +1409,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
             }
         }
         for (int i = 0; i < nset; ++i) {
+            if ((rc = alloc_list(h, bk, &stage[i], sizeof(BodyState) * B * (size_t)(K + 1)))) return rc;
             if ((rc = alloc_list(h, bk, &sets[i].pop, pop_sz * (K + 1)))) return rc;
             if ((rc = alloc_list(h, bk, &sets[i].flags, (size_t)C * (K + 2)))) return rc;
             if ((rc = alloc_list(h, bk, &sets[i].bid, (size_t)C * (K + 2)))) return rc;
@@ -1435,9 +1442,11 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     if (fl) {
         CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&rss, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&rcap, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&rcaps, cudaStreamNonBlocking));
     }
     cudaEvent_t ev_main = nullptr, ev_side = nullptr, ev_rec = nullptr, ev_free_main = nullptr,
-                ev_free_side = nullptr, ev_rfork = nullptr, ev_rjoin = nullptr;
+                ev_free_side = nullptr, ev_rfork = nullptr, ev_rjoin = nullptr, ev_cfork = nullptr, ev_cjoin = nullptr;
     CK(cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_rec, cudaEventDisableTiming));
@@ -1445,13 +1454,15 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     CK(cudaEventCreateWithFlags(&ev_free_side, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_rfork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_rjoin, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_cfork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_cjoin, cudaEventDisableTiming));
     struct Events {
-        cudaEvent_t *e[7];
+        cudaEvent_t *e[9];
         ~Events() {
             for (cudaEvent_t *p : e)
                 if (*p) cudaEventDestroy(*p);
         }
-    } events{{&ev_main, &ev_side, &ev_rec, &ev_free_main, &ev_free_side, &ev_rfork, &ev_rjoin}};
+    } events{{&ev_main, &ev_side, &ev_rec, &ev_free_main, &ev_free_side, &ev_rfork, &ev_rjoin, &ev_cfork, &ev_cjoin}};
     CK(cudaEventRecord(ev_main, s));
     CK(cudaEventRecord(ev_side, s));
     CK(cudaEventRecord(ev_free_main, s));
@@ -1499,10 +1510,76 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     const int ones[2] = {1, 1};
     // recomputation of segment k into its slot set, on rs: epochs m - 1 ..
     // m + L - 1 from the checkpoint (and m + L for the last segment)
+    // recomputation step j of a segment into slot set st, the states of
+    // epochs j - 1 and j at `prev` and `cur`, on stream `ms` with the side
+    // stream `ss`; `last`: only the remap (the flags of the epoch after the
+    // run, which the last reverse step needs)
+    auto recompute_step = [&](const SlotSet &st, int j, const BodyState *prev, const BodyState *cur, bool last,
+                              cudaStream_t ms, cudaStream_t ss, cudaEvent_t fork, cudaEvent_t join) -> int {
+        // the remap rewrites only the cubes around the bodies: the slot
+        // starts from the epoch before it, as the forward's ping-pong
+        // buffers do
+        CK(cudaMemcpyAsync(st.flags + C * (j + 1), st.flags + C * j, (size_t)C, cudaMemcpyDeviceToDevice, ms));
+        CK(cudaMemcpyAsync(st.bid + C * (j + 1), st.bid + C * j, (size_t)C, cudaMemcpyDeviceToDevice, ms));
+        lbm::StepPtrs sp{};
+        sp.src = slot_pop(st, j);
+        sp.dst = slot_pop(st, j + 1);
+        sp.flags_prev = st.flags + C * j;
+        sp.bid_prev = st.bid + C * j;
+        sp.flags_cur = st.flags + C * (j + 1);
+        sp.bid_cur = st.bid + C * (j + 1);
+        sp.body_prev = prev;
+        sp.body_cur = cur;
+        sp.body_next = scratch;
+        sp.tstep = dr.t_dev;
+        sp.parity = j & 1;
+        // the body preparation only at the segment's first step: the later
+        // states' geometry records come from the recomputation's own
+        // rigid-body steps (the same bits as the tape's states)
+        const bool prep = j == 0;
+        lbm::launch_remap(dr, sp, 0, ms, prep);
+        if (last) return LBM_OK;
+        // boundary cells, link lists and loads beside the bulk kernel, as in
+        // the forward step
+        CK(cudaEventRecord(fork, ms));
+        CK(cudaStreamWaitEvent(ss, fork, 0));
+        if (lbm::needs_boundary_fix(dr)) lbm::launch_boundary_fix(dr, sp, ss);
+        lbm::launch_links(dr, sp, ss);
+        CK(cudaEventRecord(join, ss));
+        lbm::launch_stream_collide(dr, sp, ms);
+        CK(cudaStreamWaitEvent(ms, join, 0));
+        lbm::launch_force(dr, sp, ms);
+        return LBM_OK;
+    };
+    // A full segment (K steps, not the last) is recomputed by a CUDA graph of
+    // its set: its states are staged (epochs m - 1 .. m + K - 1) into the
+    // set's staging buffer, so that one graph serves every full segment of
+    // the set.
+    auto full_graph = [&](int set) -> int {
+        if (rgraph[set]) return LBM_OK;
+        const SlotSet &st = sets[set];
+        CK(cudaStreamBeginCapture(rcap, cudaStreamCaptureModeThreadLocal));
+        int rc2 = LBM_OK;
+        for (int j = 0; j < K && rc2 == LBM_OK; ++j)
+            rc2 = recompute_step(st, j, stage[set] + (long long)j * B, stage[set] + (long long)(j + 1) * B, false, rcap,
+                                 rcaps, ev_cfork, ev_cjoin);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e1 = cudaStreamEndCapture(rcap, &g);
+        if (rc2) {
+            if (g) cudaGraphDestroy(g);
+            return rc2;
+        }
+        CK(e1);
+        const cudaError_t e2 = cudaGraphInstantiate(&rgraph[set], g, 0);
+        cudaGraphDestroy(g);
+        CK(e2);
+        return LBM_OK;
+    };
     auto recompute = [&](int k) -> int {
         const long long m = tp.n0 + (long long)k * K;
         const int L = seg_len(k);
         const SlotSet &st = set_of(k);
+        const int set = nset == 2 ? (k & 1) : 0;
         if (nset == 1 && k < tp.nseg - 1)       // epoch m + L, recomputed with segment k + 1
             CK(cudaMemcpyAsync(carry, st.flags + C, (size_t)C, cudaMemcpyDeviceToDevice, rs));
         CK(cudaMemcpyAsync(st.pop, static_cast<char *>(tp.ckpt_pop) + pop_sz * k, pop_sz,
@@ -1511,45 +1588,21 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         CK(cudaMemcpyAsync(st.bid, tp.ckpt_bid + C * k, (size_t)C, cudaMemcpyDeviceToDevice, rs));
         CK(cudaMemcpyAsync(r_t, &m, sizeof m, cudaMemcpyHostToDevice, rs));
         CK(cudaMemcpyAsync(r_changed, ones, sizeof ones, cudaMemcpyHostToDevice, rs));
-        for (int j = 0; j <= L; ++j) {
-            // the remap rewrites only the cubes around the bodies: the slot
-            // starts from the epoch before it, as the forward's ping-pong
-            // buffers do
-            CK(cudaMemcpyAsync(st.flags + C * (j + 1), st.flags + C * j, (size_t)C, cudaMemcpyDeviceToDevice, rs));
-            CK(cudaMemcpyAsync(st.bid + C * (j + 1), st.bid + C * j, (size_t)C, cudaMemcpyDeviceToDevice, rs));
-            lbm::StepPtrs sp{};
-            sp.src = slot_pop(st, j);
-            sp.dst = slot_pop(st, j + 1);
-            sp.flags_prev = st.flags + C * j;
-            sp.bid_prev = st.bid + C * j;
-            sp.flags_cur = st.flags + C * (j + 1);
-            sp.bid_cur = st.bid + C * (j + 1);
-            sp.body_prev = S(m + j - 1);
-            sp.body_cur = S(m + j);
-            sp.body_next = scratch;
-            sp.tstep = dr.t_dev;
-            sp.parity = j & 1;
-            // the body preparation only at the segment's first step: the
-            // later states' geometry records come from the recomputation's
-            // own rigid-body steps (the same bits as the tape's states)
-            const bool prep = j == 0;
-            if (j == L) {
-                // the flags of the epoch after the run: the last reverse
-                // step needs them (its bounce-back and link cells)
-                if (k == tp.nseg - 1) lbm::launch_remap(dr, sp, 0, rs, prep);
-                break;
+        if (L == K && k < tp.nseg - 1) {
+            int rc2;
+            if ((rc2 = full_graph(set))) return rc2;
+            CK(cudaMemcpyAsync(stage[set], S(m - 1), sizeof(BodyState) * B * (size_t)(K + 1),
+                               cudaMemcpyDeviceToDevice, rs));
+            CK(cudaGraphLaunch(rgraph[set], rs));
+        } else {
+            for (int j = 0; j < L; ++j) {
+                int rc2;
+                if ((rc2 = recompute_step(st, j, S(m + j - 1), S(m + j), false, rs, rss, ev_rfork, ev_rjoin))) return rc2;
             }
-            lbm::launch_remap(dr, sp, 0, rs, prep);
-            // boundary cells, link lists and loads beside the bulk kernel,
-            // as in the forward step
-            CK(cudaEventRecord(ev_rfork, rs));
-            CK(cudaStreamWaitEvent(rss, ev_rfork, 0));
-            if (lbm::needs_boundary_fix(dr)) lbm::launch_boundary_fix(dr, sp, rss);
-            lbm::launch_links(dr, sp, rss);
-            CK(cudaEventRecord(ev_rjoin, rss));
-            lbm::launch_stream_collide(dr, sp, rs);
-            CK(cudaStreamWaitEvent(rs, ev_rjoin, 0));
-            lbm::launch_force(dr, sp, rs);
+            if (k == tp.nseg - 1) {
+                int rc2;
+                if ((rc2 = recompute_step(st, L, S(m + L - 1), S(m + L), true, rs, rss, ev_rfork, ev_rjoin))) return rc2;
+            }
         }
         make_terms(k, rs);
         CK(cudaGetLastError());
