@@ -1,7 +1,8 @@
 // kernels.cu -- the per-body kernels of one coupled step and the field
 // export / import kernels:
 //   prep       per-body geometry records (remade only for states set from
-//              outside), remap candidate lists
+//              outside), remap candidate lists for the batched remap; a
+//              single lattice runs it only after the host wrote a state
 //   remap      map the bodies onto the lattice (Sec. 2.3), epoch flags, the
 //              boundary kernel's cell list
 //   links      per-body list of fluid->solid links (ballot + block scan)
