@@ -317,6 +317,237 @@ __global__ void __launch_bounds__(ADJ_BOUNDARY_THREADS) adj_boundary_kernel(cons
     }
 }
 
+// ---- boundary cells of the body cubes: a warp per cell -------------------------
+// Block (blk, kb) classifies the ADJ_BOUNDARY_THREADS cells blk * 64 ... of
+// body kb's cube as adj_boundary_kernel does (bulk cells: nothing; solid at
+// n: zero adjoint; the others the full rule) and lists the full-rule cells
+// in cube order.  Each warp then takes the listed cells w, w + 8, ... with
+// lane b the direction b: the pull, wall and link terms of the 18
+// directions in parallel, the cell's sums (the density terms, the
+// transposed collision's moments, the refill sums, body kb's terms) by
+// butterfly shuffles, so every lane holds the same sum and the order is
+// fixed.  The block adds its warps' body sums in warp order into
+// part[kb][blk] (the layout adj_integrate reads).
+constexpr int ADJ_CUBE_WARPS = 8;
+
+template <typename V> __device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename A, typename T, bool FIRST>
+__global__ void __launch_bounds__(32 * ADJ_CUBE_WARPS) adj_cube_kernel(const Device dv, const AdjPtrs ap) {
+    const Domain d = dv.dom;
+    const int kb = blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long C = d.C;
+    const int half = dv.props[kb].E + REMAP_MARGIN;
+    const int side = 2 * half + 1;
+    const BodyState &sb = ap.body[kb];
+    const int fx = (int)floor(sb.X[0]), fy = (int)floor(sb.X[1]), fz = (int)floor(sb.X[2]);
+    // cube cell l -> lattice cell (x, y, z); false outside the cube or the domain
+    auto cube_cell = [&](int l, int &x, int &y, int &z) {
+        if (l >= side * side * side) return false;
+        bool live = true;
+        x = fx - half + l % side;
+        y = fy - half + (l / side) % side;
+        z = fz - half + l / (side * side);
+        if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else live = live && x >= 0 && x < d.nx;
+        if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else live = live && y >= 0 && y < d.ny;
+        if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else live = live && z >= 0 && z < d.nz;
+        return live;
+    };
+    __shared__ int list[ADJ_BOUNDARY_THREADS];
+    __shared__ int wcount[ADJ_BOUNDARY_THREADS / 32];
+    __shared__ double wacc[ADJ_CUBE_WARPS][9];
+    A *__restrict__ aout = static_cast<A *>(ap.aout);
+    // 1. classify this block's cells (the first ADJ_BOUNDARY_THREADS threads)
+    bool listed = false;
+    const int l = blockIdx.x * ADJ_BOUNDARY_THREADS + tid;
+    if (tid < ADJ_BOUNDARY_THREADS) {
+        int x, y, z;
+        if (cube_cell(l, x, y, z)) {
+            const long long c = ((long long)z * d.ny + y) * d.nx + x;
+            const uint8_t fcur = ap.flags_cur[c], fnext = ap.flags_next[c];
+            if (fnext == 0 && !(fcur & F_SOLID_PREV)) {
+                // a bulk cell: adj_bulk's
+            } else if (fcur & F_SOLID) {            // obstacle at n: no adjoint
+#pragma unroll
+                for (int b = 0; b < Q; ++b) aout[(long long)b * C + c] = (A)0;
+                if constexpr (!FIRST) static_cast<A *>(ap.rout)[c] = (A)0;
+            } else {
+                listed = true;
+            }
+        }
+    }
+    unsigned lm = 0;                                 // the warp's listed lanes
+    if (warp < ADJ_BOUNDARY_THREADS / 32) {
+        lm = __ballot_sync(0xffffffffu, listed);
+        if (lane == 0) wcount[warp] = __popc(lm);
+    }
+    __syncthreads();
+    if (listed) {
+        int base = 0;
+        for (int w = 0; w < warp; ++w) base += wcount[w];
+        list[base + __popc(lm & ((1u << lane) - 1u))] = l;
+    }
+    int nlist = 0;
+    for (int w = 0; w < ADJ_BOUNDARY_THREADS / 32; ++w) nlist += wcount[w];
+    __syncthreads();
+    // 2. a warp per listed cell, lane b = direction b
+    const bool act = lane < Q;
+    const int b = act ? lane : 0;
+    const int bx = ex(b), by = ey(b), bz = ez(b), ob = opp(b);
+    const A wb = (A)wgt(b);
+    const A *__restrict__ ain = static_cast<const A *>(ap.ain);
+    const A *__restrict__ rin = static_cast<const A *>(ap.rin);
+    const T *__restrict__ G = static_cast<const T *>(ap.G);
+    A wsum[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};        // this warp's body-kb terms, cell by cell
+    for (int e = warp; e < nlist; e += ADJ_CUBE_WARPS) {
+        int x, y, z;
+        cube_cell(list[e], x, y, z);
+        const long long c = ((long long)z * d.ny + y) * d.nx + x;
+        const uint8_t fcur = ap.flags_cur[c], fnext = ap.flags_next[c];
+        const bool fluid_next = !(fnext & F_SOLID);
+        // density and velocity of step n from the post-collision populations
+        const A gv = act ? (A)G[(long long)b * C + c] : (A)0;
+        const A rho = (A)1 + warp_sum(gv);
+        const A ir = (A)1 / rho;
+        const A u0 = (warp_sum((A)bx * gv) - (A)(0.5 * dv.g[0])) * ir;
+        const A u1 = (warp_sum((A)by * gv) - (A)(0.5 * dv.g[1])) * ir;
+        const A u2 = (warp_sum((A)bz * gv) - (A)(0.5 * dv.g[2])) * ir;
+        const A own = act ? ain[(long long)b * C + c] : (A)0;
+        const A own_opp = __shfl_sync(0xffffffffu, own, ob);
+        A a = own, crb = 0;
+        A acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (act && b > 0) {
+            const int zx = x + bx, zy = y + by, zz = z + bz;
+            const bool wall = (!d.px && (zx < 0 || zx >= d.nx)) || (!d.py && (zy < 0 || zy >= d.ny)) ||
+                              (!d.pz && (zz < 0 || zz >= d.nz));
+            if (wall) {                              // Eq. 4 at step n+1
+                a = own_opp;
+            } else {
+                const long long zc = ((long long)wrap_axis(zz, d.nz) * d.ny + wrap_axis(zy, d.ny)) * d.nx +
+                                     wrap_axis(zx, d.nx);
+                const uint8_t fzc = ap.flags_cur[zc];
+                if (fzc & F_SOLID) {
+                    // link (x, b) of step n: moving bounce-back of step n+1 and
+                    // the momentum exchange of step n share u_w(x + e_b; S^n);
+                    // the offset from the body centre in FP64, the terms in A
+                    const int k = ap.bid_cur[zc];
+                    const BodyState &sk = ap.body[k];
+                    double od[3];
+                    offset_from(d, sk, (double)zx, (double)zy, (double)zz, od);
+                    const A o[3] = {(A)od[0], (A)od[1], (A)od[2]};
+                    const A W[3] = {(A)sk.W[0], (A)sk.W[1], (A)sk.W[2]};
+                    const A uw0 = (A)sk.V[0] + (W[1] * o[2] - W[2] * o[1]);
+                    const A uw1 = (A)sk.V[1] + (W[2] * o[0] - W[0] * o[2]);
+                    const A uw2 = (A)sk.V[2] + (W[0] * o[1] - W[1] * o[0]);
+                    const A ua = -((A)bx * uw0 + (A)by * uw1 + (A)bz * uw2);     // e_-b . u_w
+                    A mh = 0;
+                    if constexpr (!FIRST) {
+                        const double *fa = ap.fadj + 6 * k;
+                        // (mid - X) x e_b, mid = x + e_b / 2 = (x + e_b) - e_b / 2
+                        const A m0 = o[0] - (A)(0.5 * bx), m1 = o[1] - (A)(0.5 * by), m2 = o[2] - (A)(0.5 * bz);
+                        const A t0 = m1 * (A)bz - m2 * (A)by, t1 = m2 * (A)bx - m0 * (A)bz, t2 = m0 * (A)by - m1 * (A)bx;
+                        mh = (A)bx * (A)fa[0] + (A)by * (A)fa[1] + (A)bz * (A)fa[2] + t0 * (A)fa[3] + t1 * (A)fa[4] +
+                             t2 * (A)fa[5];
+                    }
+                    const A wh = own_opp;
+                    a = wh + (A)2 * mh;
+                    crb = (A)6 * wb * ua * (wh + mh);
+                    if (k == kb) {
+                        const A sc = (A)6 * wb * rho * (wh + mh);
+                        const A uh[3] = {-(A)bx * sc, -(A)by * sc, -(A)bz * sc};
+                        adj_surface<A, A>(W, o, uh, acc);
+                    }
+                    // z uncovered at n+1: x (fluid at n and n+1) fed its density
+                    if (!(ap.flags_next[zc] & F_SOLID) && fluid_next) crb += rin[zc];
+                } else {
+                    a = ain[(long long)b * C + zc];
+                }
+            }
+        }
+        a += warp_sum(crb);
+        if constexpr (FIRST) {
+            if (act) aout[(long long)b * C + c] = a;
+        } else {
+            // the transposed collision (collide_adjoint), its sums over the lanes
+            const A om = (A)dv.omega;
+            const A uu = u0 * u0 + u1 * u1 + u2 * u2;
+            const A eu = (A)bx * u0 + (A)by * u1 + (A)bz * u2;
+            const A wa = act ? wb * a : (A)0;
+            const A cc = (A)3 + (A)9 * eu;
+            const A sr = warp_sum(wa * ((A)1 + (A)3 * eu + (A)4.5 * eu * eu - (A)1.5 * uu));
+            const A s0 = warp_sum(wa * (cc * (A)bx - (A)3 * u0));
+            const A s1 = warp_sum(wa * (cc * (A)by - (A)3 * u1));
+            const A s2 = warp_sum(wa * (cc * (A)bz - (A)3 * u2));
+            A f0 = 0, f1 = 0, f2 = 0;
+            if (dv.forced) {
+                const A eg = (A)(bx * dv.g[0] + by * dv.g[1] + bz * dv.g[2]);
+                f0 = warp_sum(wa * ((A)(-3.0 * dv.g[0]) + (A)9 * (A)bx * eg));
+                f1 = warp_sum(wa * ((A)(-3.0 * dv.g[1]) + (A)9 * (A)by * eg));
+                f2 = warp_sum(wa * ((A)(-3.0 * dv.g[2]) + (A)9 * (A)bz * eg));
+            }
+            const A kf = (A)1 - (A)0.5 * om;
+            const A su0 = (om * rho * s0 + kf * f0) * ir, su1 = (om * rho * s1 + kf * f1) * ir,
+                    su2 = (om * rho * s2 + kf * f2) * ir;
+            const A base = om * sr - (su0 * u0 + su1 * u1 + su2 * u2);
+            a = ((A)1 - om) * a + base + (A)bx * su0 + (A)by * su1 + (A)bz * su2;
+            if (act) aout[(long long)b * C + c] = a;
+            A rh_out = 0;
+            if (fcur & F_SOLID_PREV) {
+                // uncovered at n: P = f_eq(rho_avg, u_w(x; S^n)) of the body
+                // that covered x at n-1, rho_avg over the neighbours fluid in
+                // epochs n-1 and n (rho_avg = rho^n(x))
+                bool nf = false;
+                if (act && b > 0) {
+                    const int nx_ = x + bx, ny_ = y + by, nz_ = z + bz;
+                    const bool in = !((!d.px && (nx_ < 0 || nx_ >= d.nx)) || (!d.py && (ny_ < 0 || ny_ >= d.ny)) ||
+                                      (!d.pz && (nz_ < 0 || nz_ >= d.nz)));
+                    const long long nc = ((long long)wrap_axis(nz_, d.nz) * d.ny + wrap_axis(ny_, d.ny)) * d.nx +
+                                         wrap_axis(nx_, d.nx);
+                    nf = in && !(ap.flags_cur[nc] & (F_SOLID | F_SOLID_PREV));
+                }
+                const int cnt = __popc(__ballot_sync(0xffffffffu, nf));
+                const int k = ap.bid_prev[c];
+                if (k != NO_BODY) {
+                    const BodyState &sk = ap.body[k];
+                    double o[3], uw[3];
+                    offset_from(d, sk, (double)x, (double)y, (double)z, o);
+                    uw[0] = sk.V[0] + (sk.W[1] * o[2] - sk.W[2] * o[1]);
+                    uw[1] = sk.V[1] + (sk.W[2] * o[0] - sk.W[0] * o[2]);
+                    uw[2] = sk.V[2] + (sk.W[0] * o[1] - sk.W[1] * o[0]);
+                    const double uuw = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+                    const double rho_d = (double)rho;
+                    const double euw = bx * uw[0] + by * uw[1] + bz * uw[2];
+                    const double pa = act ? (double)a * wgt(b) : 0.0;
+                    const double cw = rho_d * (3.0 + 9.0 * euw);
+                    const double rh = warp_sum(pa * (1.0 + 3.0 * euw + 4.5 * euw * euw - 1.5 * uuw));
+                    const double uh[3] = {warp_sum(pa * (cw * bx - 3.0 * rho_d * uw[0])),
+                                          warp_sum(pa * (cw * by - 3.0 * rho_d * uw[1])),
+                                          warp_sum(pa * (cw * bz - 3.0 * rho_d * uw[2]))};
+                    if (cnt) rh_out = (A)(rh / cnt);
+                    if (k == kb && lane == 0) adj_surface<double, A>(sk.W, o, uh, acc);
+                }
+            }
+            if (lane == 0) static_cast<A *>(ap.rout)[c] = rh_out;
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) wsum[i] += warp_sum(acc[i]);
+    }
+    // 3. the block's body-kb sums, warps in order
+    if (lane == 0)
+        for (int i = 0; i < 9; ++i) wacc[warp][i] = (double)wsum[i];
+    __syncthreads();
+    if (tid < 9) {
+        double v = 0.0;
+        for (int w = 0; w < ADJ_CUBE_WARPS; ++w) v += wacc[w][tid];
+        ap.part[((long long)kb * ap.part_stride + blockIdx.x) * 9 + tid] = v;
+    }
+}
+
 // ---- rigid-body step, reversed ------------------------------------------------
 // Reverse of Algorithm 1 at step t with the state S^n and the hydrodynamic
 // load fh^n of the tape:
@@ -603,7 +834,7 @@ void launch_bulk_cells(const Device &dv, const AdjPtrs &ap, cudaStream_t s) {
 template <typename A, typename T, bool FIRST>
 void launch_boundary_cells(const Device &dv, const AdjPtrs &ap, cudaStream_t s) {
     if (dv.nb > 0)
-        adj_boundary_kernel<A, T, FIRST><<<dim3(ap.part_stride, dv.nb), ADJ_BOUNDARY_THREADS, 0, s>>>(dv, ap, 0);
+        adj_cube_kernel<A, T, FIRST><<<dim3(ap.part_stride, dv.nb), 32 * ADJ_CUBE_WARPS, 0, s>>>(dv, ap);
     if (!(dv.dom.px && dv.dom.py && dv.dom.pz)) {
         const long long nx = dv.dom.nx, ny = dv.dom.ny, nz = dv.dom.nz;
         const long long area = std::max(ny * nz, std::max(nx * nz, nx * ny));

@@ -1514,13 +1514,21 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     // epochs j - 1 and j at `prev` and `cur`, on stream `ms` with the side
     // stream `ss`; `last`: only the remap (the flags of the epoch after the
     // run, which the last reverse step needs)
-    auto recompute_step = [&](const SlotSet &st, int j, const BodyState *prev, const BodyState *cur, bool last,
-                              cudaStream_t ms, cudaStream_t ss, cudaEvent_t fork, cudaEvent_t join) -> int {
-        // the remap rewrites only the cubes around the bodies: the slot
-        // starts from the epoch before it, as the forward's ping-pong
-        // buffers do
+    // The remap rewrites only the cubes around the bodies: a slot starts
+    // from the epoch before it, as the forward's ping-pong buffers do.  The
+    // copy into slot j + 2 is made after step j's bulk kernel (beside the
+    // boundary branch), off the chain; slot 1's before the segment's first
+    // remap.  `copy_next`: step j + 1 follows.
+    auto copy_slot = [&](const SlotSet &st, int j, cudaStream_t ms) -> int {
         CK(cudaMemcpyAsync(st.flags + C * (j + 1), st.flags + C * j, (size_t)C, cudaMemcpyDeviceToDevice, ms));
         CK(cudaMemcpyAsync(st.bid + C * (j + 1), st.bid + C * j, (size_t)C, cudaMemcpyDeviceToDevice, ms));
+        return LBM_OK;
+    };
+    auto recompute_step = [&](const SlotSet &st, int j, const BodyState *prev, const BodyState *cur, bool last,
+                              bool copy_next, cudaStream_t ms, cudaStream_t ss, cudaEvent_t fork,
+                              cudaEvent_t join) -> int {
+        int rc3;
+        if (j == 0 && (rc3 = copy_slot(st, 0, ms))) return rc3;
         lbm::StepPtrs sp{};
         sp.src = slot_pop(st, j);
         sp.dst = slot_pop(st, j + 1);
@@ -1547,6 +1555,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         lbm::launch_links(dr, sp, ss);
         CK(cudaEventRecord(join, ss));
         lbm::launch_stream_collide(dr, sp, ms);
+        if (copy_next && (rc3 = copy_slot(st, j + 1, ms))) return rc3;
         CK(cudaStreamWaitEvent(ms, join, 0));
         lbm::launch_force(dr, sp, ms);
         return LBM_OK;
@@ -1561,8 +1570,8 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         CK(cudaStreamBeginCapture(rcap, cudaStreamCaptureModeThreadLocal));
         int rc2 = LBM_OK;
         for (int j = 0; j < K && rc2 == LBM_OK; ++j)
-            rc2 = recompute_step(st, j, stage[set] + (long long)j * B, stage[set] + (long long)(j + 1) * B, false, rcap,
-                                 rcaps, ev_cfork, ev_cjoin);
+            rc2 = recompute_step(st, j, stage[set] + (long long)j * B, stage[set] + (long long)(j + 1) * B, false,
+                                 j + 1 < K, rcap, rcaps, ev_cfork, ev_cjoin);
         cudaGraph_t g = nullptr;
         const cudaError_t e1 = cudaStreamEndCapture(rcap, &g);
         if (rc2) {
@@ -1595,13 +1604,17 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
                                cudaMemcpyDeviceToDevice, rs));
             CK(cudaGraphLaunch(rgraph[set], rs));
         } else {
+            const bool extra = k == tp.nseg - 1;    // the remap of the epoch after the run
             for (int j = 0; j < L; ++j) {
                 int rc2;
-                if ((rc2 = recompute_step(st, j, S(m + j - 1), S(m + j), false, rs, rss, ev_rfork, ev_rjoin))) return rc2;
+                if ((rc2 = recompute_step(st, j, S(m + j - 1), S(m + j), false, j + 1 < L || extra, rs, rss, ev_rfork,
+                                          ev_rjoin)))
+                    return rc2;
             }
-            if (k == tp.nseg - 1) {
+            if (extra) {
                 int rc2;
-                if ((rc2 = recompute_step(st, L, S(m + L - 1), S(m + L), true, rs, rss, ev_rfork, ev_rjoin))) return rc2;
+                if ((rc2 = recompute_step(st, L, S(m + L - 1), S(m + L), true, false, rs, rss, ev_rfork, ev_rjoin)))
+                    return rc2;
             }
         }
         make_terms(k, rs);
