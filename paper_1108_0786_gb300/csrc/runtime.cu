@@ -1442,8 +1442,12 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     if (fl) {
         CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&rss, cudaStreamNonBlocking));
-        CK(cudaStreamCreateWithFlags(&rcap, cudaStreamNonBlocking));
-        CK(cudaStreamCreateWithFlags(&rcaps, cudaStreamNonBlocking));
+        // the recomputation's graphs run at the greatest priority: its chain
+        // bounds the sweep, and the reverse kernels beside it yield SMs
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&rcap, cudaStreamNonBlocking, greatest));
+        CK(cudaStreamCreateWithPriority(&rcaps, cudaStreamNonBlocking, greatest));
     }
     cudaEvent_t ev_main = nullptr, ev_side = nullptr, ev_rec = nullptr, ev_free_main = nullptr,
                 ev_free_side = nullptr, ev_rfork = nullptr, ev_rjoin = nullptr, ev_cfork = nullptr, ev_cjoin = nullptr;
@@ -1579,7 +1583,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
             return rc2;
         }
         CK(e1);
-        const cudaError_t e2 = cudaGraphInstantiate(&rgraph[set], g, 0);
+        const cudaError_t e2 = cudaGraphInstantiate(&rgraph[set], g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         CK(e2);
         return LBM_OK;
