@@ -60,6 +60,10 @@ struct lbm_s {
     int device = 0;
     cudaStream_t stream = nullptr, cap = nullptr, side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // a third branch of the step graphs: the link lists and loads beside the
+    // boundary kernel (a small lattice's bulk kernel is shorter than both)
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t join2_ev = nullptr;
     // overlapped steps: the far bulk kernels' stream, and by step parity the
     // events "far bulk of step n done" and "near cells of step n done"
     cudaStream_t far = nullptr;
@@ -196,13 +200,20 @@ void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bo
         cudaEventRecord(h->fork_ev, s);
         cudaStreamWaitEvent(h->side, h->fork_ev, 0);
         lbm::launch_boundary_fix(h->dv, sp, h->side);
-        if (bodies) lbm::launch_links(h->dv, sp, h->side);
         cudaEventRecord(h->join_ev, h->side);
+        if (bodies) {
+            cudaStreamWaitEvent(h->side2, h->fork_ev, 0);
+            lbm::launch_links(h->dv, sp, h->side2);
+            cudaEventRecord(h->join2_ev, h->side2);
+        }
     }
     if (fl) run(LBM_KERNEL_STREAM_COLLIDE, s, [&] { lbm::launch_stream_collide(h->dv, sp, s); });
     if (boundary && !forked) run(LBM_KERNEL_BOUNDARY, s, [&] { lbm::launch_boundary_fix(h->dv, sp, s); });
     if (bodies && fl && !forked) run(LBM_KERNEL_LINKS, s, [&] { lbm::launch_links(h->dv, sp, s); });
-    if (forked) cudaStreamWaitEvent(s, h->join_ev, 0);
+    if (forked) {
+        cudaStreamWaitEvent(s, h->join_ev, 0);
+        if (bodies) cudaStreamWaitEvent(s, h->join2_ev, 0);
+    }
     if (bodies && fl) {
         // momentum exchange; the last block of each body runs its rigid-body step
         run(LBM_KERNEL_FORCE, s, [&] { lbm::launch_force(h->dv, sp, s); });
@@ -502,6 +513,8 @@ int build_graphs(lbm_t *h) {
     if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
     if (!h->join_ev) CK(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+    if (!h->side2) CK(cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking));
+    if (!h->join2_ev) CK(cudaEventCreateWithFlags(&h->join2_ev, cudaEventDisableTiming));
     if (ov) {
         if (!h->far) CK(cudaStreamCreateWithPriority(&h->far, cudaStreamNonBlocking, least));
         for (int i = 0; i < 2; ++i) {
@@ -587,6 +600,8 @@ void release_device(lbm_t *h) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->join_ev) cudaEventDestroy(h->join_ev);
+    if (h->side2) cudaStreamDestroy(h->side2);
+    if (h->join2_ev) cudaEventDestroy(h->join2_ev);
     if (h->far) cudaStreamDestroy(h->far);
     for (int i = 0; i < 2; ++i) {
         if (h->far_ev[i]) cudaEventDestroy(h->far_ev[i]);
@@ -1345,15 +1360,15 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     const int K = tp.seg;
     std::vector<void *> bk;         // this call's buffers
     // the recomputation's streams (main, side, graph capture) and graphs
-    cudaStream_t rs = nullptr, rss = nullptr, rcap = nullptr, rcaps = nullptr;
+    cudaStream_t rs = nullptr, rss = nullptr, rss2 = nullptr, rcap = nullptr, rcaps = nullptr, rcaps2 = nullptr;
     cudaGraphExec_t rgraph[2] = {nullptr, nullptr};
     struct Guard {
         lbm_t *h;
         std::vector<void *> &list;
-        cudaStream_t &rs, &rss, &rcap, &rcaps;
+        cudaStream_t &rs, &rss, &rss2, &rcap, &rcaps, &rcaps2;
         cudaGraphExec_t (&rgraph)[2];
         ~Guard() {
-            for (cudaStream_t *st : {&rs, &rss, &rcap, &rcaps})
+            for (cudaStream_t *st : {&rs, &rss, &rss2, &rcap, &rcaps, &rcaps2})
                 if (*st) {
                     cudaStreamSynchronize(*st);
                     cudaStreamDestroy(*st);
@@ -1364,7 +1379,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
             cudaStreamSynchronize(h->stream);
             free_list(h, list);
         }
-    } guard{h, bk, rs, rss, rcap, rcaps, rgraph};
+    } guard{h, bk, rs, rss, rss2, rcap, rcaps, rcaps2, rgraph};
     // a slot set holds one segment's recomputed epochs: populations (slots
     // 0..K), flags and body ids (slots 0..K+1)
     struct SlotSet {
@@ -1442,15 +1457,18 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     if (fl) {
         CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&rss, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&rss2, cudaStreamNonBlocking));
         // the recomputation's graphs run at the greatest priority: its chain
         // bounds the sweep, and the reverse kernels beside it yield SMs
         int least = 0, greatest = 0;
         CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
         CK(cudaStreamCreateWithPriority(&rcap, cudaStreamNonBlocking, greatest));
         CK(cudaStreamCreateWithPriority(&rcaps, cudaStreamNonBlocking, greatest));
+        CK(cudaStreamCreateWithPriority(&rcaps2, cudaStreamNonBlocking, greatest));
     }
     cudaEvent_t ev_main = nullptr, ev_side = nullptr, ev_rec = nullptr, ev_free_main = nullptr,
-                ev_free_side = nullptr, ev_rfork = nullptr, ev_rjoin = nullptr, ev_cfork = nullptr, ev_cjoin = nullptr;
+                ev_free_side = nullptr, ev_rfork = nullptr, ev_rjoin = nullptr, ev_rjoin2 = nullptr, ev_cfork = nullptr,
+                ev_cjoin = nullptr, ev_cjoin2 = nullptr;
     CK(cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_rec, cudaEventDisableTiming));
@@ -1460,13 +1478,16 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
     CK(cudaEventCreateWithFlags(&ev_rjoin, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_cfork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_cjoin, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_rjoin2, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_cjoin2, cudaEventDisableTiming));
     struct Events {
-        cudaEvent_t *e[9];
+        cudaEvent_t *e[11];
         ~Events() {
             for (cudaEvent_t *p : e)
                 if (*p) cudaEventDestroy(*p);
         }
-    } events{{&ev_main, &ev_side, &ev_rec, &ev_free_main, &ev_free_side, &ev_rfork, &ev_rjoin, &ev_cfork, &ev_cjoin}};
+    } events{{&ev_main, &ev_side, &ev_rec, &ev_free_main, &ev_free_side, &ev_rfork, &ev_rjoin, &ev_cfork, &ev_cjoin,
+               &ev_rjoin2, &ev_cjoin2}};
     CK(cudaEventRecord(ev_main, s));
     CK(cudaEventRecord(ev_side, s));
     CK(cudaEventRecord(ev_free_main, s));
@@ -1529,8 +1550,8 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         return LBM_OK;
     };
     auto recompute_step = [&](const SlotSet &st, int j, const BodyState *prev, const BodyState *cur, bool last,
-                              bool copy_next, cudaStream_t ms, cudaStream_t ss, cudaEvent_t fork,
-                              cudaEvent_t join) -> int {
+                              bool copy_next, cudaStream_t ms, cudaStream_t ss, cudaStream_t ss2,
+                              cudaEvent_t fork, cudaEvent_t join, cudaEvent_t join2) -> int {
         int rc3;
         if (j == 0 && (rc3 = copy_slot(st, 0, ms))) return rc3;
         lbm::StepPtrs sp{};
@@ -1551,16 +1572,19 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         const bool prep = j == 0;
         lbm::launch_remap(dr, sp, 0, ms, prep);
         if (last) return LBM_OK;
-        // boundary cells, link lists and loads beside the bulk kernel, as in
-        // the forward step
+        // boundary cells, and link lists with loads, beside the bulk kernel,
+        // as in the forward step
         CK(cudaEventRecord(fork, ms));
         CK(cudaStreamWaitEvent(ss, fork, 0));
         if (lbm::needs_boundary_fix(dr)) lbm::launch_boundary_fix(dr, sp, ss);
-        lbm::launch_links(dr, sp, ss);
         CK(cudaEventRecord(join, ss));
+        CK(cudaStreamWaitEvent(ss2, fork, 0));
+        lbm::launch_links(dr, sp, ss2);
+        CK(cudaEventRecord(join2, ss2));
         lbm::launch_stream_collide(dr, sp, ms);
         if (copy_next && (rc3 = copy_slot(st, j + 1, ms))) return rc3;
         CK(cudaStreamWaitEvent(ms, join, 0));
+        CK(cudaStreamWaitEvent(ms, join2, 0));
         lbm::launch_force(dr, sp, ms);
         return LBM_OK;
     };
@@ -1575,7 +1599,7 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
         int rc2 = LBM_OK;
         for (int j = 0; j < K && rc2 == LBM_OK; ++j)
             rc2 = recompute_step(st, j, stage[set] + (long long)j * B, stage[set] + (long long)(j + 1) * B, false,
-                                 j + 1 < K, rcap, rcaps, ev_cfork, ev_cjoin);
+                                 j + 1 < K, rcap, rcaps, rcaps2, ev_cfork, ev_cjoin, ev_cjoin2);
         cudaGraph_t g = nullptr;
         const cudaError_t e1 = cudaStreamEndCapture(rcap, &g);
         if (rc2) {
@@ -1611,13 +1635,14 @@ int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, doubl
             const bool extra = k == tp.nseg - 1;    // the remap of the epoch after the run
             for (int j = 0; j < L; ++j) {
                 int rc2;
-                if ((rc2 = recompute_step(st, j, S(m + j - 1), S(m + j), false, j + 1 < L || extra, rs, rss, ev_rfork,
-                                          ev_rjoin)))
+                if ((rc2 = recompute_step(st, j, S(m + j - 1), S(m + j), false, j + 1 < L || extra, rs, rss, rss2,
+                                          ev_rfork, ev_rjoin, ev_rjoin2)))
                     return rc2;
             }
             if (extra) {
                 int rc2;
-                if ((rc2 = recompute_step(st, L, S(m + L - 1), S(m + L), true, false, rs, rss, ev_rfork, ev_rjoin)))
+                if ((rc2 = recompute_step(st, L, S(m + L - 1), S(m + L), true, false, rs, rss, rss2, ev_rfork, ev_rjoin,
+                                          ev_rjoin2)))
                     return rc2;
             }
         }
