@@ -129,30 +129,19 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_bulk_kernel(const Device dv, 
     for (int b = 0; b < Q; ++b) aout[(long long)b * C + c] = a[b];
 }
 
-// ---- boundary cells: the full rule ------------------------------------------
-// mode 0: block row blockIdx.y = body k, the cube of side 2 (E_k + REMAP_MARGIN)
-// + 1 around floor(X_k^n); only this body's adjoint terms are summed, into
-// part[k][blockIdx.x].  mode 1: wall faces, no body sums.
+// ---- wall-face cells: the full rule, a thread per cell -----------------------
+// Block row blockIdx.y = wall face (axis * 2 + side) of a non-periodic axis.
+// The body terms of the links of these cells are summed by adj_cube_kernel
+// (a face cell next to a body lies in its cube); this kernel writes the
+// adjoint of every face cell.  A cell in both is written twice with the
+// same rule, this kernel's last.
 template <typename A, typename T, bool FIRST>
-__global__ void __launch_bounds__(ADJ_BOUNDARY_THREADS) adj_boundary_kernel(const Device dv, const AdjPtrs ap, int mode) {
+__global__ void __launch_bounds__(ADJ_BOUNDARY_THREADS) adj_wall_kernel(const Device dv, const AdjPtrs ap) {
     const Domain d = dv.dom;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    const int kb = mode == 0 ? (int)blockIdx.y : -1;
-    A acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int x = 0, y = 0, z = 0;
     bool live = true;
-    if (mode == 0) {
-        const BodyState sb = ap.body[kb];
-        const int half = dv.props[kb].E + REMAP_MARGIN;
-        const int side = 2 * half + 1;
-        if (l >= side * side * side) live = false;
-        x = (int)floor(sb.X[0]) - half + l % side;
-        y = (int)floor(sb.X[1]) - half + (l / side) % side;
-        z = (int)floor(sb.X[2]) - half + l / (side * side);
-        if (d.px) x = ((x % d.nx) + d.nx) % d.nx; else live = live && x >= 0 && x < d.nx;
-        if (d.py) y = ((y % d.ny) + d.ny) % d.ny; else live = live && y >= 0 && y < d.ny;
-        if (d.pz) z = ((z % d.nz) + d.nz) % d.nz; else live = live && z >= 0 && z < d.nz;
-    } else {
+    {
         const int axis = blockIdx.y >> 1, hi = blockIdx.y & 1;
         const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
         if (per[axis]) return;
@@ -182,7 +171,6 @@ __global__ void __launch_bounds__(ADJ_BOUNDARY_THREADS) adj_boundary_kernel(cons
             const T *__restrict__ G = static_cast<const T *>(ap.G);
             A rho, u[3];
             moments_post<A, T>(G, C, c, dv, rho, u);
-            const double rho_d = (double)rho;
             const bool fluid_next = !(fnext & F_SOLID);
             A own[Q], a[Q];
 #pragma unroll
@@ -230,11 +218,6 @@ __global__ void __launch_bounds__(ADJ_BOUNDARY_THREADS) adj_boundary_kernel(cons
                     const A wh = own[opp(b)];
                     a[b] = wh + (A)2 * mh;
                     cr += (A)(6.0 * wgt(b)) * ua * (wh + mh);
-                    if (k == kb) {
-                        const A sc = (A)(6.0 * wgt(b)) * rho * (wh + mh);
-                        const A uh[3] = {-(A)ex(b) * sc, -(A)ey(b) * sc, -(A)ez(b) * sc};
-                        adj_surface<A, A>(W, o, uh, acc);
-                    }
                     // z uncovered at n+1: x (fluid at n and n+1) fed its density
                     if (!(ap.flags_next[zc] & F_SOLID) && fluid_next) cr += rin[zc];
                 } else {
@@ -275,44 +258,17 @@ __global__ void __launch_bounds__(ADJ_BOUNDARY_THREADS) adj_boundary_kernel(cons
                         uw[1] = sk.V[1] + (sk.W[2] * o[0] - sk.W[0] * o[2]);
                         uw[2] = sk.V[2] + (sk.W[0] * o[1] - sk.W[1] * o[0]);
                         const double uu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
-                        double rh = 0.0, uh[3] = {0.0, 0.0, 0.0};
+                        double rh = 0.0;
 #pragma unroll
                         for (int b = 0; b < Q; ++b) {
                             const double eu = ex(b) * uw[0] + ey(b) * uw[1] + ez(b) * uw[2];
-                            const double pa = (double)a[b] * wgt(b);
-                            rh += pa * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-                            const double cc = rho_d * (3.0 + 9.0 * eu);
-                            uh[0] += pa * (cc * ex(b) - 3.0 * rho_d * uw[0]);
-                            uh[1] += pa * (cc * ey(b) - 3.0 * rho_d * uw[1]);
-                            uh[2] += pa * (cc * ez(b) - 3.0 * rho_d * uw[2]);
+                            rh += (double)a[b] * wgt(b) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
                         }
                         if (cnt) rh_out = (A)(rh / cnt);
-                        if (k == kb) adj_surface<double, A>(sk.W, o, uh, acc);
                     }
                 }
                 static_cast<A *>(ap.rout)[c] = rh_out;
             }
-        }
-    }
-    if (mode != 0) return;
-    // fixed-order block sum of this body's adjoint terms
-    __shared__ double part[ADJ_BOUNDARY_THREADS / 32][9];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        A v = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) part[warp][i] = (double)v;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            double v = lane < ADJ_BOUNDARY_THREADS / 32 ? part[lane][i] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) ap.part[((long long)kb * ap.part_stride + blockIdx.x) * 9 + i] = v;
         }
     }
 }
@@ -838,9 +794,9 @@ void launch_boundary_cells(const Device &dv, const AdjPtrs &ap, cudaStream_t s) 
     if (!(dv.dom.px && dv.dom.py && dv.dom.pz)) {
         const long long nx = dv.dom.nx, ny = dv.dom.ny, nz = dv.dom.nz;
         const long long area = std::max(ny * nz, std::max(nx * nz, nx * ny));
-        adj_boundary_kernel<A, T, FIRST>
+        adj_wall_kernel<A, T, FIRST>
             <<<dim3((unsigned)((area + ADJ_BOUNDARY_THREADS - 1) / ADJ_BOUNDARY_THREADS), 6), ADJ_BOUNDARY_THREADS, 0,
-               s>>>(dv, ap, 1);
+               s>>>(dv, ap);
     }
 }
 
