@@ -275,8 +275,9 @@ __global__ void __launch_bounds__(ADJ_BOUNDARY_THREADS) adj_wall_kernel(const De
 
 // ---- boundary cells of the body cubes: a warp per cell -------------------------
 // Block (blk, kb) classifies the ADJ_BOUNDARY_THREADS cells blk * 64 ... of
-// body kb's cube as adj_boundary_kernel does (bulk cells: nothing; solid at
-// n: zero adjoint; the others the full rule) and lists the full-rule cells
+// body kb's cube (cells whose flags are zero in epochs n and n+1 and that
+// were not uncovered at n: adj_bulk's; solid at n: zero adjoint; the
+// others the full rule, as adj_wall_kernel applies it) and lists the full-rule cells
 // in cube order.  Each warp then takes the listed cells w, w + 8, ... with
 // lane b the direction b: the pull, wall and link terms of the 18
 // directions in parallel, the cell's sums (the density terms, the
