@@ -291,22 +291,29 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_batch(const Batch bt) {
 // into [0, n) on a periodic axis (one compare unless the cube exceeds the axis)
 __device__ inline int wrap_up(int v, int n) { return v < n ? v : (v - n < n ? v - n : v % n); }
 
-// Remap: block row blockIdx.y = body b; the threads cover the cube of side
-// 2 (E_b + REMAP_MARGIN) + 1 around floor(X_b) at state n, 32 x 8 threads a
-// block over x and (y, z) rows, REMAP_R rows a thread (ly and ly + 8: their
-// flag loads are issued together, so a block's latency chain covers twice
-// the cells).  Every covered cell gets its epoch-n flags from the geometry
-// of all bodies and the epoch-(n-1) buffer; overlapping cubes write
-// identical values.  A cell tests only body b's candidates, in body order
-// (integer boxes, the FP32 screen, and the FP64 inside test only within the
-// screen's margin).  Fluid cells flagged F_NEAR or F_SOLID_PREV are appended
-// to the boundary kernel's list.
-constexpr int REMAP_TX = 32, REMAP_TY = 8, REMAP_THREADS = REMAP_TX * REMAP_TY;
+// Remap: block row blockIdx.y = body b; the cube of side 2 (E_b +
+// REMAP_MARGIN) + 1 around floor(X_b) at state n is taken as one run of
+// side^3 cells in (z, y, x) order, REMAP_CELLS consecutive cells a block and
+// REMAP_R a thread (i and i + REMAP_THREADS: their flag loads are issued
+// together, so a block's latency chain covers both).  No thread idles on a
+// cube narrower than a warp, and the grid of the 24-capsule swarm (side 23)
+// fits in one wave of resident blocks.  Every covered cell gets its epoch-n
+// flags from the geometry of all bodies and the epoch-(n-1) buffer;
+// overlapping cubes write identical values.  A cell tests only body b's
+// candidates, in body order (integer boxes, the FP32 screen, and the FP64
+// inside test only within the screen's margin).  Fluid cells flagged F_NEAR
+// or F_SOLID_PREV are appended to the boundary kernel's list.
+constexpr int REMAP_THREADS = 256;
 constexpr int REMAP_R = 2;
-constexpr int REMAP_ROWS = REMAP_TY * REMAP_R;  // cube rows a block covers in a layer
+constexpr int REMAP_CELLS = REMAP_THREADS * REMAP_R;    // cube cells a block covers
 constexpr int REMAP_STAGED = 8;
-constexpr int REMAP_LAYERS = 1;         // cube layers a block (more layers serialise each block's latency chain)
-constexpr int REMAP_LIST_BUF = 2048;    // list entries a block gathers before the global append
+constexpr int REMAP_LIST_BUF = REMAP_CELLS;             // a block lists at most all of its cells
+
+// blocks a body of remap-cube side `side` takes
+inline int remap_blocks(int side) {
+    const long long cells = (long long)side * side * side;
+    return (int)((cells + REMAP_CELLS - 1) / REMAP_CELLS);
+}
 static_assert(sizeof(BodyGeom) % sizeof(int) == 0, "geometry records are copied as ints");
 
 template <bool SELF_CAND>
@@ -321,15 +328,15 @@ __device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp,
     __shared__ int s_ncand;
     const int n3[3] = {d.nx, d.ny, d.nz}, per[3] = {d.px, d.py, d.pz};
     const int side = geo[b].side;
-    const int nyb = (side + REMAP_ROWS - 1) / REMAP_ROWS;
-    const int lzb = (bk.x / nyb) * REMAP_LAYERS, ly0 = (bk.x % nyb) * REMAP_ROWS;
-    if (lzb >= side) return;                  // the grid covers the largest body's cube
+    const int side2 = side * side, cells = side2 * side;
+    const int i0 = bk.x * REMAP_CELLS;
+    if (i0 >= cells) return;                  // the grid covers the largest body's cube
     // this block's share of the boundary kernel's list, gathered in shared
     // memory and appended with one atomic at the end
     __shared__ uint32_t lbuf[REMAP_LIST_BUF];
     __shared__ int lcount, lbase;
     const int org[3] = {geo[b].origin[0], geo[b].origin[1], geo[b].origin[2]};
-    const int tid = threadIdx.y * REMAP_TX + threadIdx.x;
+    const int tid = threadIdx.x;
     const int lane = tid & 31;
     if (tid == 0) lcount = 0;
     // the candidates: the bodies, in body order, whose grown box (the cells
@@ -366,20 +373,17 @@ __device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp,
     }
     __syncthreads();
 
-    // REMAP_LAYERS layers of the cube a block, x in chunks of 32 (cubes wider
-    // than a warp take several); every lane runs every chunk and row, so the
-    // ballots below see whole warps
-    const int lz_end = min(side, lzb + REMAP_LAYERS);
-    for (int lz = lzb; lz < lz_end; ++lz)
-        for (int lx0 = 0; lx0 < side; lx0 += REMAP_TX) {
-            const int lx = lx0 + threadIdx.x;
+    // every lane runs each of its cells, so the ballots below see whole warps
+        {
             int xr[REMAP_R], yr[REMAP_R], zr[REMAP_R], idr[REMAP_R];
             long long cr[REMAP_R];
             bool liver[REMAP_R];
 #pragma unroll
             for (int r = 0; r < REMAP_R; ++r) {
-                const int ly = ly0 + threadIdx.y + r * REMAP_TY;
-                bool live = lx < side && ly < side;
+                const int ci = i0 + r * REMAP_THREADS + tid;
+                bool live = ci < cells;
+                const int lz = ci / side2, rem = ci - lz * side2;
+                const int ly = rem / side, lx = rem - ly * side;
                 int x = org[0] + lx, y = org[1] + ly, z = org[2] + lz;
                 if (d.px) x = wrap_up(x, d.nx); else live = live && x >= 0 && x < d.nx;
                 if (d.py) y = wrap_up(y, d.ny); else live = live && y >= 0 && y < d.ny;
@@ -505,6 +509,7 @@ __device__ __forceinline__ void remap_body(const Device &dv, const StepPtrs &sp,
 }
 
 __global__ void __launch_bounds__(REMAP_THREADS, 4) remap_kernel(const Device dv, const StepPtrs sp, int init_mode) {
+    pdl_enter();
     remap_body<true>(dv, sp, launch_blk(), init_mode);
 }
 
@@ -1081,6 +1086,7 @@ __device__ __forceinline__ void force_body(const Device &dv, const StepPtrs &sp,
 
 template <typename T>
 __global__ void __launch_bounds__(FORCE_THREADS) force_kernel(const Device dv, const StepPtrs sp) {
+    pdl_enter();
     force_body<T>(dv, sp, launch_blk());
 }
 
@@ -1271,8 +1277,8 @@ void launch_prep(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
 void launch_remap(const Device &dv, const StepPtrs &sp, int init_mode, cudaStream_t s, bool prep) {
     if (prep) launch_prep(dv, sp, s);
     const int side = dv.remap_side;
-    const unsigned bx = (unsigned)(((side + REMAP_ROWS - 1) / REMAP_ROWS) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS));
-    remap_kernel<<<dim3(bx, dv.nb), dim3(REMAP_TX, REMAP_TY), 0, s>>>(dv, sp, init_mode);
+    launch_kernel(dv.pdl != 0, remap_kernel, dim3((unsigned)remap_blocks(side), dv.nb), dim3(REMAP_THREADS), 0, s,
+                  dv, sp, init_mode);
 }
 
 void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
@@ -1281,12 +1287,13 @@ void launch_links(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
 }
 
 void launch_force(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
-    const dim3 grid(FORCE_BLOCKS, dv.nb);
+    const dim3 grid(FORCE_BLOCKS, dv.nb), block(FORCE_THREADS);
+    const bool pdl = dv.pdl != 0;
     switch (dv.precision) {
-    case 0: force_kernel<double><<<grid, FORCE_THREADS, 0, s>>>(dv, sp); break;
-    case 1: force_kernel<float><<<grid, FORCE_THREADS, 0, s>>>(dv, sp); break;
-    case 2: force_kernel<__half><<<grid, FORCE_THREADS, 0, s>>>(dv, sp); break;
-    default: force_kernel<__nv_bfloat16><<<grid, FORCE_THREADS, 0, s>>>(dv, sp); break;
+    case 0: launch_kernel(pdl, force_kernel<double>, grid, block, 0, s, dv, sp); break;
+    case 1: launch_kernel(pdl, force_kernel<float>, grid, block, 0, s, dv, sp); break;
+    case 2: launch_kernel(pdl, force_kernel<__half>, grid, block, 0, s, dv, sp); break;
+    default: launch_kernel(pdl, force_kernel<__nv_bfloat16>, grid, block, 0, s, dv, sp); break;
     }
 }
 
@@ -1318,7 +1325,7 @@ void batch_grid_small(const Device &dv, int k, int g[3]) {
     switch (k) {
     case BK_PREP: case BK_LOADS: g[0] = g[1] = g[2] = 1; break;
     case BK_REMAP:
-        g[0] = ((side + REMAP_ROWS - 1) / REMAP_ROWS) * ((side + REMAP_LAYERS - 1) / REMAP_LAYERS);
+        g[0] = remap_blocks(side);
         g[1] = dv.nb; g[2] = 1;
         break;
     case BK_LINKS: g[0] = dv.link_side; g[1] = dv.nb; g[2] = 1; break;
@@ -1331,7 +1338,7 @@ void launch_batch_small(int k, const Batch &bt, unsigned blocks, int precision, 
     if (blocks == 0) return;
     switch (k) {
     case BK_PREP: prep_batch<<<blocks, PREP_THREADS, 0, s>>>(bt); break;
-    case BK_REMAP: remap_batch<<<blocks, dim3(REMAP_TX, REMAP_TY), 0, s>>>(bt); break;
+    case BK_REMAP: remap_batch<<<blocks, REMAP_THREADS, 0, s>>>(bt); break;
     case BK_LINKS: links_batch<<<blocks, 256, 0, s>>>(bt); break;
     case BK_LOADS: loads_batch<<<blocks, 64, 0, s>>>(bt); break;
     case BK_FORCE:

@@ -262,7 +262,46 @@ struct Device {
     int *near_count;
     int near_cap;
     long long *tstep;       // [2]
+    // launch the remap, bulk and force kernels with programmatic dependent
+    // launch (pdl_enter, launch_kernel); the step graphs set it for the
+    // remap and force kernels
+    int pdl;
 };
+
+// Programmatic dependent launch, device side: wait until the grids this one
+// depends on have completed with their writes visible (at once in a launch
+// without such a dependency), then let the next grid of the stream start
+// launching if it was launched with the attribute, so that its blocks are
+// resident when this grid ends (the bulk kernel, launched without it, lets
+// the force kernel in early).  A kernel launched with the attribute calls it
+// before touching global memory.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host side: launch `k`, with programmatic stream serialization when `pdl`
+// (then `k` must begin with pdl_enter).  In a captured graph the edge from
+// the kernel before it becomes a programmatic one.
+template <typename... P, typename... A>
+inline void launch_kernel(bool pdl, void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          A &&...args) {
+    if (!pdl) {
+        k<<<grid, block, smem, s>>>(static_cast<A &&>(args)...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1] = {};
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, static_cast<A &&>(args)...);
+}
 
 // ---- batched launches over the members of an ensemble ------------------------
 //

@@ -39,6 +39,7 @@ struct lbm_s {
     bool need_prep = true;
     int expire_waits = 0;               // lbm_debug_set knobs
     int adjoint_sets = 0;
+    int no_pdl = 0;         // LBM_DEBUG_NO_PDL: step graphs without programmatic dependent launch
     long long list_cap_limit = 0;
     // asynchronous reads (lbm_get_bodies_async): a ring of completion events
     // and pinned status words, one per read ticket modulo READS
@@ -207,7 +208,14 @@ void enqueue_step(lbm_t *h, int p, cudaStream_t s, cudaEvent_t *ev = nullptr, bo
             cudaEventRecord(h->join2_ev, h->side2);
         }
     }
-    if (fl) run(LBM_KERNEL_STREAM_COLLIDE, s, [&] { lbm::launch_stream_collide(h->dv, sp, s); });
+    if (fl) run(LBM_KERNEL_STREAM_COLLIDE, s, [&] {
+        // the bulk kernel waits for the remap in full: launched before the
+        // remap ends, its blocks would hold every SM ahead of the boundary
+        // branch, which is launched when the remap ends
+        lbm::Device dvb = h->dv;
+        dvb.pdl = 0;
+        lbm::launch_stream_collide(dvb, sp, s);
+    });
     if (boundary && !forked) run(LBM_KERNEL_BOUNDARY, s, [&] { lbm::launch_boundary_fix(h->dv, sp, s); });
     if (bodies && fl && !forked) run(LBM_KERNEL_LINKS, s, [&] { lbm::launch_links(h->dv, sp, s); });
     if (forked) {
@@ -531,20 +539,31 @@ int build_graphs(lbm_t *h) {
         }
         if (ov) cudaStreamWaitEvent(h->cap, h->far_ev[(p0 + n - 1) & 1], 0);
     };
-    for (int p = 0; p < 2; ++p) {
-        cudaGraph_t g;
-        CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-        steps(p, 1);
-        CK(cudaStreamEndCapture(h->cap, &g));
-        CK(cudaGraphInstantiate(&h->single[p], g, ov ? cudaGraphInstantiateFlagUseNodePriority : 0));
-        cudaGraphDestroy(g);
+    // one graph of n steps from parity p0
+    auto capture = [&](int p0, int n, cudaGraphExec_t *x) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        steps(p0, n);
+        e = cudaStreamEndCapture(h->cap, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(x, g, ov ? cudaGraphInstantiateFlagUseNodePriority : 0);
+        if (g) cudaGraphDestroy(g);
+        return e;
+    };
+    // serial steps launch the force kernel and the next step's remap
+    // programmatically dependent on the kernel before them in the chain, so
+    // that their blocks are resident, waiting, when the bulk kernel and the
+    // force kernel end (overlapped steps order their streams by events and
+    // node priorities instead)
+    h->dv.pdl = !ov && !h->no_pdl;
+    cudaError_t e = capture(0, 1, &h->single[0]);
+    if (e == cudaSuccess) e = capture(1, 1, &h->single[1]);
+    if (e == cudaSuccess) e = capture(0, CHUNK_STEPS, &h->chunk);
+    h->dv.pdl = 0;
+    if (e != cudaSuccess) {
+        drop_graphs(h);
+        return cuda_fail(h, e, "capture of the step graphs");
     }
-    cudaGraph_t g;
-    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    steps(0, CHUNK_STEPS);
-    CK(cudaStreamEndCapture(h->cap, &g));
-    CK(cudaGraphInstantiate(&h->chunk, g, ov ? cudaGraphInstantiateFlagUseNodePriority : 0));
-    cudaGraphDestroy(g);
     h->graphs_ready = true;
     return LBM_OK;
 }
@@ -1230,7 +1249,7 @@ int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm) {
 
 int lbm_debug_set(lbm_t *h, int knob, long long value) {
     if (!h) return LBM_E_ARG;
-    if (h->ready && knob != LBM_DEBUG_ADJOINT_SERIAL)
+    if (h->ready && knob != LBM_DEBUG_ADJOINT_SERIAL && knob != LBM_DEBUG_NO_PDL)
         return fail(h, LBM_E_STATE, "lbm_debug_set must come before the first step");
     if (knob == LBM_DEBUG_EXPIRE_WAITS) {
         if (value != 0 && value != 1) return fail(h, LBM_E_ARG, "LBM_DEBUG_EXPIRE_WAITS takes 0 or 1");
@@ -1241,6 +1260,14 @@ int lbm_debug_set(lbm_t *h, int knob, long long value) {
     } else if (knob == LBM_DEBUG_ADJOINT_SERIAL) {
         if (value != 0 && value != 1) return fail(h, LBM_E_ARG, "LBM_DEBUG_ADJOINT_SERIAL takes 0 or 1");
         h->adjoint_sets = value ? 1 : 0;
+    } else if (knob == LBM_DEBUG_NO_PDL) {
+        if (value != 0 && value != 1) return fail(h, LBM_E_ARG, "LBM_DEBUG_NO_PDL takes 0 or 1");
+        if (h->no_pdl != (int)value && h->ready) {
+            // the step graphs bake the launch attributes in
+            if (int rc = sync_and_check(h)) return rc;
+            drop_graphs(h);
+        }
+        h->no_pdl = (int)value;
     } else {
         return fail(h, LBM_E_ARG, "unknown debug knob %d", knob);
     }

@@ -489,6 +489,7 @@ __device__ __forceinline__ void bulk_body(const Device &dv, const StepPtrs &sp, 
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB)
 bulk_kernel(const Device dv, const StepPtrs sp) {
+    pdl_enter();
     bulk_body<T, V, BX, BY>(dv, sp, launch_blk());
 }
 
@@ -660,6 +661,7 @@ __device__ __forceinline__ void bulk16_body(const Device &dv, const StepPtrs &sp
 template <typename T, int V, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB == 1 ? 0 : MINB)
 bulk16_kernel(const Device dv, const StepPtrs sp) {
+    pdl_enter();
     bulk16_body<T, V, BX, BY>(dv, sp, launch_blk());
 }
 
@@ -972,6 +974,7 @@ __host__ __device__ constexpr size_t tma_stage_bytes(int nx, int elem) { return 
 
 template <typename T, int NSTAGE, int MINB, int ROWS>
 __global__ void __launch_bounds__(TMA_THREADS, MINB) bulk_tma_kernel(const Device dv, const StepPtrs sp) {
+    pdl_enter();
     using Cd = typename Codec<T>::C;
     static_assert((NSTAGE + 1) * sizeof(uint64_t) <= TMA_HEADER, "the mbarriers fit the header");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1110,7 +1113,8 @@ void launch_tma(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     const size_t bytes = tma_smem_bytes<T, NSTAGE, PER_SM, ROWS>(dv.dom.nx);
     const long long rows = (long long)dv.dom.ny * dv.dom.nz;
     const long long grid = std::min<long long>(rows, (long long)sm_count() * PER_SM);
-    bulk_tma_kernel<T, NSTAGE, PER_SM, ROWS><<<(unsigned)grid, TMA_THREADS, bytes, s>>>(dv, sp);
+    launch_kernel(dv.pdl != 0, bulk_tma_kernel<T, NSTAGE, PER_SM, ROWS>, dim3((unsigned)grid), dim3(TMA_THREADS), bytes,
+                  s, dv, sp);
 }
 
 template <typename T, int NSTAGE, int PER_SM, int ROWS = 1>
@@ -1128,14 +1132,14 @@ template <typename T, int V, int BX, int BY, int MINB>
 void launch_bulk(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     const int nxq = dv.dom.nx / V;
     dim3 grid((nxq + BX - 1) / BX, (dv.dom.ny + BY - 1) / BY, dv.dom.nz);
-    bulk_kernel<T, V, BX, BY, MINB><<<grid, dim3(BX, BY), 0, s>>>(dv, sp);
+    launch_kernel(dv.pdl != 0, bulk_kernel<T, V, BX, BY, MINB>, grid, dim3(BX, BY), 0, s, dv, sp);
 }
 
 template <typename T, int V, int BX, int BY, int MINB>
 void launch_bulk16(const Device &dv, const StepPtrs &sp, cudaStream_t s) {
     const int nxq = dv.dom.nx / V;
     dim3 grid((nxq + BX - 1) / BX, (dv.dom.ny + BY - 1) / BY, dv.dom.nz);
-    bulk16_kernel<T, V, BX, BY, MINB><<<grid, dim3(BX, BY), 0, s>>>(dv, sp);
+    launch_kernel(dv.pdl != 0, bulk16_kernel<T, V, BX, BY, MINB>, grid, dim3(BX, BY), 0, s, dv, sp);
 }
 
 template <typename T, int V, int MINB>

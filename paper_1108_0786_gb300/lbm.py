@@ -28,7 +28,7 @@ SHAPE_SPHERE, SHAPE_CAPSULE = 0, 1
 PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = 0, 1, 2, 3
 OPT_NO_FLUID = 1
 OPT_OVERLAP = 4
-DEBUG_EXPIRE_WAITS, DEBUG_CELL_LIST_CAP, DEBUG_ADJOINT_SERIAL = 1, 2, 3
+DEBUG_EXPIRE_WAITS, DEBUG_CELL_LIST_CAP, DEBUG_ADJOINT_SERIAL, DEBUG_NO_PDL = 1, 2, 3, 4
 ENSEMBLE_BATCHED, ENSEMBLE_BRANCHES = 0, 1
 OPT_AVERAGE_FORCE = 2
 FIELD_RHO, FIELD_U, FIELD_FLAGS, FIELD_POP = 0, 1, 2, 3
@@ -281,8 +281,8 @@ class Lattice:
 
     def debug_set(self, knob, value):
         """A check of a failure path (DEBUG_EXPIRE_WAITS, DEBUG_CELL_LIST_CAP:
-        before the first step) or of the reverse sweep's schedule
-        (DEBUG_ADJOINT_SERIAL: any time)."""
+        before the first step) or of a schedule (DEBUG_ADJOINT_SERIAL: the
+        reverse sweep's; DEBUG_NO_PDL: the step graphs' launches; any time)."""
         return self._check(self._lib.lbm_debug_set(self._h, int(knob), int(value)))
 
     def autotune(self, trials=5):

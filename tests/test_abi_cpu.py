@@ -125,5 +125,8 @@ def test_debug_knobs_take_only_their_values_before_the_first_step(lib):
     assert lib.lbm_debug_set(h, lbm.DEBUG_ADJOINT_SERIAL, 1) == 0
     assert lib.lbm_debug_set(h, lbm.DEBUG_ADJOINT_SERIAL, 0) == 0
     assert lib.lbm_debug_set(h, lbm.DEBUG_ADJOINT_SERIAL, 2) == lbm.E_ARG
+    assert lib.lbm_debug_set(h, lbm.DEBUG_NO_PDL, 1) == 0
+    assert lib.lbm_debug_set(h, lbm.DEBUG_NO_PDL, 0) == 0
+    assert lib.lbm_debug_set(h, lbm.DEBUG_NO_PDL, -1) == lbm.E_ARG
     assert lib.lbm_debug_set(h, 99, 0) == lbm.E_ARG
     assert lib.lbm_destroy(h) == 0

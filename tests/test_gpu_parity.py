@@ -428,6 +428,46 @@ def test_averaged_load_option_matches_the_oracle():
     lat.close()
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16"])
+def test_programmatic_launch_gives_the_serial_bits(precision):
+    """Step graphs whose force kernel and next remap are launched
+    programmatically dependent (each grid resident before its predecessor
+    ends, waiting before any memory access) give the bits of graphs that
+    launch every kernel after its predecessor completed: bodies crossing
+    cell centres and periodic faces, walls, a body state set mid-run, kernel
+    timing outside the graphs, the knob switched mid-run."""
+    sc = wl.Scenario("pdl", 64, 40, 36, 0.8, bc=wl.PERIODIC_X | wl.PERIODIC_Z, g=(2e-6, 0.0, 0.0))
+    c = math.cos(0.3)
+    sc.bodies.append(wl.Body(wl.SPHERE, 4.3, 0.0, 1e9, (12.2, 19.7, 12.9)))
+    sc.bodies.append(wl.Body(wl.CAPSULE, 3.1, 6.0, 1e9, (45.4, 18.3, 20.2), (c, 0.0, math.sin(0.3), 0.0)))
+    sc.bodies.append(wl.Body(wl.SPHERE, 3.0, 0.0, 400.0, (62.0, 20.5, 33.5)))
+    runs = []
+    for schedule in ((1, 1, 1), (0, 0, 0), (0, 1, 0)):
+        lat = lbm.from_scenario(sc, precision=precision)
+        for b, v in ((0, (0.11, 0.04, -0.03)), (1, (-0.07, -0.05, 0.06)), (2, (0.03, 0.0, 0.02))):
+            st = lat.bodies()[b].copy()
+            st[7:10] = v
+            lat.set_body_state(b, st)
+        lat.debug_set(lbm.DEBUG_NO_PDL, schedule[0])
+        lat.step(37)
+        st = lat.bodies()[1].copy()
+        st[0] += 0.3
+        st[10:13] = (0.01, -0.02, 0.015)
+        lat.set_body_state(1, st)
+        lat.debug_set(lbm.DEBUG_NO_PDL, schedule[1])
+        lat.step(16)
+        lat.time_kernels(2)
+        lat.debug_set(lbm.DEBUG_NO_PDL, schedule[2])
+        lat.step(33)
+        for _ in range(3):
+            lat.step(1)
+        runs.append((lat.pop(), lat.bodies(), lat.flags(), lat.forces()))
+        lat.close()
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32", "bf16"])
 def test_overlapped_steps_equal_serial_steps(precision):
     """Overlapped steps (the bulk kernel's far tiles beside the force and
