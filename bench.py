@@ -294,7 +294,10 @@ def variant_runs(sc, steps):
             lat, disp_err, u_err = ref, 0.0, 0.0
         lat.step(10)
         lat.sync()
-        ms_k = lat.time_kernels(10)["stream_collide"]
+        # eager launches: a launch the host thread was late to issue (the
+        # oracle's ensemble runs share the host cores) counts its wait, so
+        # the fastest of four means is taken
+        ms_k = min(lat.time_kernels(5)["stream_collide"] for _ in range(4))
         t = timed_steps(lat, 200, 1, None)
         res[prec] = {"mlups": round(sc.cells * 200 / (t / 1e3) / 1e6, 1),
                      "stream_collide_gbs": round(lat.bytes_per_cell * sc.cells / (ms_k / 1e3) / 1e9, 1),

@@ -317,14 +317,15 @@ int lbm_autotune(lbm_t *h, int trials, int *cells_per_thread, int *min_blocks_pe
  *     recomputation of segment k - 1 runs on its own stream beside the
  *     reverse steps of segment k.  Both give the same bits.  Any time; it
  *     holds for the following calls of lbm_adjoint_backward.
- *   LBM_DEBUG_NO_PDL, value 1: every kernel of a step graph is launched
- *     only after the kernel before it has completed.  Value 0 (default):
- *     the force kernel and the next step's remap in serial steps are
- *     launched with programmatic dependent launch, so that their blocks
- *     become resident while the bulk kernel and the force kernel drain, and
- *     wait, before touching memory, until those have completed.  Both give
- *     the same bits.  Any time (it synchronises and rebuilds the step
- *     graphs).
+ *   LBM_DEBUG_NO_PDL, value 1 (default): every kernel of a step graph is
+ *     launched only after the kernel before it has completed.  Value 0: the
+ *     force kernel and the next step's remap in serial steps are launched
+ *     with programmatic dependent launch, so that their blocks become
+ *     resident while the bulk kernel and the force kernel drain, and wait,
+ *     before touching memory, until those have completed (on the capsule
+ *     swarm within 0.5 us a step of the default either way, so it stays
+ *     off).  Both give the same bits.  Any time (it synchronises and
+ *     rebuilds the step graphs).
  * The steps after such an error are not valid.  The first two only before
  * the first step (LBM_E_STATE after it); LBM_E_ARG for an unknown knob or
  * value. */

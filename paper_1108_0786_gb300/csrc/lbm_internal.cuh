@@ -264,7 +264,7 @@ struct Device {
     long long *tstep;       // [2]
     // launch the remap, bulk and force kernels with programmatic dependent
     // launch (pdl_enter, launch_kernel); the step graphs set it for the
-    // remap and force kernels
+    // remap and force kernels when LBM_DEBUG_NO_PDL is 0
     int pdl;
 };
 

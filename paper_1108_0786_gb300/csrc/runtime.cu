@@ -39,7 +39,7 @@ struct lbm_s {
     bool need_prep = true;
     int expire_waits = 0;               // lbm_debug_set knobs
     int adjoint_sets = 0;
-    int no_pdl = 0;         // LBM_DEBUG_NO_PDL: step graphs without programmatic dependent launch
+    int no_pdl = 1;         // LBM_DEBUG_NO_PDL: step graphs without programmatic dependent launch
     long long list_cap_limit = 0;
     // asynchronous reads (lbm_get_bodies_async): a ring of completion events
     // and pinned status words, one per read ticket modulo READS
@@ -550,11 +550,11 @@ int build_graphs(lbm_t *h) {
         if (g) cudaGraphDestroy(g);
         return e;
     };
-    // serial steps launch the force kernel and the next step's remap
-    // programmatically dependent on the kernel before them in the chain, so
-    // that their blocks are resident, waiting, when the bulk kernel and the
-    // force kernel end (overlapped steps order their streams by events and
-    // node priorities instead)
+    // with LBM_DEBUG_NO_PDL 0, serial steps launch the force kernel and the
+    // next step's remap programmatically dependent on the kernel before them
+    // in the chain, so that their blocks are resident, waiting, when the bulk
+    // kernel and the force kernel end (overlapped steps order their streams
+    // by events and node priorities instead)
     h->dv.pdl = !ov && !h->no_pdl;
     cudaError_t e = capture(0, 1, &h->single[0]);
     if (e == cudaSuccess) e = capture(1, 1, &h->single[1]);
