@@ -757,7 +757,7 @@ int lbm_body_properties(int shape, double radius, double length, double mass, do
 
 int lbm_add_body(lbm_t *h, int shape, double radius, double length, double mass, const double pos[3],
                  const double orient[4]) {
-    if (!h || !pos) return LBM_E_ARG;
+    if (!h || !pos) return fail(h, LBM_E_ARG, "lbm_add_body: null position");
     if (h->ready) return fail(h, LBM_E_STATE, "bodies must be added before the first step");
     if ((int)h->props.size() >= LBM_MAX_BODIES) return fail(h, LBM_E_ARG, "at most %d bodies", LBM_MAX_BODIES);
     if (shape != LBM_SHAPE_SPHERE && shape != LBM_SHAPE_CAPSULE) return fail(h, LBM_E_ARG, "unknown shape");
@@ -828,7 +828,8 @@ int lbm_set_drive(lbm_t *h, int body, double amp, double freq, double phase) {
 }
 
 int lbm_set_drive_axis(lbm_t *h, int term, const double axis[3]) {
-    if (!h || !axis || term < 0 || term >= (int)h->drives.size()) return LBM_E_ARG;
+    if (!h || !axis || term < 0 || term >= (int)h->drives.size())
+        return fail(h, LBM_E_ARG, "lbm_set_drive_axis: no drive term %d, or a null axis", term);
     if (h->ready) return fail(h, LBM_E_STATE, "drive axes must be set before the first step");
     for (int i = 0; i < 3; ++i) {
         if (!std::isfinite(axis[i])) return fail(h, LBM_E_ARG, "non-finite drive axis");
@@ -838,14 +839,16 @@ int lbm_set_drive_axis(lbm_t *h, int term, const double axis[3]) {
 }
 
 int lbm_set_drive_window(lbm_t *h, int term, double t_off) {
-    if (!h || term < 0 || term >= (int)h->drives.size()) return LBM_E_ARG;
+    if (!h || term < 0 || term >= (int)h->drives.size())
+        return fail(h, LBM_E_ARG, "lbm_set_drive_window: no drive term %d", term);
     if (h->ready) return fail(h, LBM_E_STATE, "drive windows must be set before the first step");
     h->drives[term].t_off = t_off;
     return LBM_OK;
 }
 
 int lbm_set_body_state(lbm_t *h, int b, const double state[13]) {
-    if (!h || !state || b < 0 || b >= nb(h)) return LBM_E_ARG;
+    if (!h || !state || b < 0 || b >= nb(h))
+        return fail(h, LBM_E_ARG, "lbm_set_body_state: no body %d, or a null state", b);
     BodyState s;
     std::memcpy(&s, state, sizeof s);
     const double n = std::sqrt(s.q[0] * s.q[0] + s.q[1] * s.q[1] + s.q[2] * s.q[2] + s.q[3] * s.q[3]);
@@ -876,7 +879,7 @@ int lbm_set_body_state(lbm_t *h, int b, const double state[13]) {
 }
 
 int lbm_set_fields(lbm_t *h, int what, const void *in, int dtype) {
-    if (!h || !in) return LBM_E_ARG;
+    if (!h || !in) return fail(h, LBM_E_ARG, "lbm_set_fields: null input");
     if (what != LBM_FIELD_POP || dtype != LBM_DTYPE_F64)
         return fail(h, LBM_E_ARG, "only LBM_FIELD_POP as LBM_DTYPE_F64 can be set");
     int rc = ensure_device(h);
@@ -906,7 +909,7 @@ static int wait_read(lbm_t *h, int p) {
 }
 
 int lbm_step(lbm_t *h, int n) {
-    if (!h || n < 0) return LBM_E_ARG;
+    if (!h || n < 0) return fail(h, LBM_E_ARG, "lbm_step: negative step count %d", n);
     int rc = ensure_device(h);
     if (rc) return rc;
     if ((rc = build_graphs(h))) return rc;
@@ -972,7 +975,7 @@ int lbm_average_stop(lbm_t *h) {
 }
 
 int lbm_average_get(lbm_t *h, double *out, long long *steps) {
-    if (!h || !out) return LBM_E_ARG;
+    if (!h || !out) return fail(h, LBM_E_ARG, "lbm_average_get: null output");
     if (!h->avg_sum) return fail(h, LBM_E_STATE, "no average was begun");
     int rc = sync_and_check(h);
     if (rc) return rc;
@@ -989,7 +992,7 @@ int lbm_average_get(lbm_t *h, double *out, long long *steps) {
 long long lbm_steps_done(lbm_t *h) { return h ? h->steps : -1; }
 
 int lbm_get_bodies(lbm_t *h, double *out) {
-    if (!h || !out) return LBM_E_ARG;
+    if (!h || !out) return fail(h, LBM_E_ARG, "lbm_get_bodies: null output");
     if (!h->ready) {
         std::memcpy(out, h->init_state.data(), sizeof(BodyState) * nb(h));
         return LBM_OK;
@@ -1001,7 +1004,7 @@ int lbm_get_bodies(lbm_t *h, double *out) {
 }
 
 int lbm_get_bodies_async(lbm_t *h, double *out, long long *ticket) {
-    if (!h || !out || !ticket) return LBM_E_ARG;
+    if (!h || !out || !ticket) return fail(h, LBM_E_ARG, "lbm_get_bodies_async: null output or ticket");
     *ticket = -1;
     if (!h->ready) {
         std::memcpy(out, h->init_state.data(), sizeof(BodyState) * nb(h));
@@ -1040,7 +1043,7 @@ int lbm_wait_ticket(lbm_t *h, long long ticket) {
 }
 
 int lbm_get_forces(lbm_t *h, double *out) {
-    if (!h || !out) return LBM_E_ARG;
+    if (!h || !out) return fail(h, LBM_E_ARG, "lbm_get_forces: null output");
     if (!h->ready) {
         std::memset(out, 0, sizeof(double) * 6 * nb(h));
         return LBM_OK;
@@ -1063,7 +1066,7 @@ static int check_field_args(lbm_t *h, int what, int dtype) {
 }
 
 int lbm_get_fields_device(lbm_t *h, int what, void *dev_out, int dtype) {
-    if (!h || !dev_out) return LBM_E_ARG;
+    if (!h || !dev_out) return fail(h, LBM_E_ARG, "lbm_get_fields_device: null output");
     int rc = check_field_args(h, what, dtype);
     if (rc) return rc;
     if ((rc = ensure_device(h))) return rc;
@@ -1079,7 +1082,7 @@ int lbm_get_fields_device(lbm_t *h, int what, void *dev_out, int dtype) {
 }
 
 int lbm_get_fields(lbm_t *h, int what, void *out, int dtype) {
-    if (!h || !out) return LBM_E_ARG;
+    if (!h || !out) return fail(h, LBM_E_ARG, "lbm_get_fields: null output");
     int rc = check_field_args(h, what, dtype);
     if (rc) return rc;
     if ((rc = ensure_device(h))) return rc;
@@ -1101,14 +1104,15 @@ int lbm_get_fields(lbm_t *h, int what, void *out, int dtype) {
 }
 
 int lbm_enable_history(lbm_t *h, int capacity) {
-    if (!h || capacity < 0) return LBM_E_ARG;
+    if (!h || capacity < 0) return fail(h, LBM_E_ARG, "lbm_enable_history: negative capacity");
     if (h->ready) return fail(h, LBM_E_STATE, "history must be enabled before the first step");
     h->hist_cap = capacity;
     return LBM_OK;
 }
 
 int lbm_get_history(lbm_t *h, double *out, int max_steps, int *n_out) {
-    if (!h || !out || !n_out || max_steps < 0) return LBM_E_ARG;
+    if (!h || !out || !n_out || max_steps < 0)
+        return fail(h, LBM_E_ARG, "lbm_get_history: null output or negative max_steps");
     *n_out = 0;
     if (!h->ready || h->hist_cap == 0 || nb(h) == 0) return LBM_OK;
     int rc = sync_and_check(h);
@@ -1134,7 +1138,7 @@ struct SaveHeader {
 }  // namespace
 
 int lbm_save(lbm_t *h, const char *path) {
-    if (!h || !path) return LBM_E_ARG;
+    if (!h || !path) return fail(h, LBM_E_ARG, "lbm_save: null path");
     int rc = ensure_device(h);
     if (rc) return rc;
     if ((rc = sync_and_check(h))) return rc;
@@ -1164,7 +1168,7 @@ int lbm_save(lbm_t *h, const char *path) {
 }
 
 int lbm_load(lbm_t *h, const char *path) {
-    if (!h || !path) return LBM_E_ARG;
+    if (!h || !path) return fail(h, LBM_E_ARG, "lbm_load: null path");
     int rc = ensure_device(h);
     if (rc) return rc;
     if ((rc = sync_and_check(h))) return rc;
@@ -1205,7 +1209,8 @@ int lbm_load(lbm_t *h, const char *path) {
 }
 
 int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots) {
-    if (!h || n < 0 || !ms_out || slots < 0) return LBM_E_ARG;
+    if (!h || n < 0 || !ms_out || slots < 0)
+        return fail(h, LBM_E_ARG, "lbm_time_kernels: negative count, null output or negative slots");
     int rc = ensure_device(h);
     if (rc) return rc;
     if ((rc = sync_and_check(h))) return rc;
@@ -1231,7 +1236,7 @@ int lbm_time_kernels(lbm_t *h, int n, double *ms_out, int slots) {
 }
 
 int lbm_tune(lbm_t *h, int cells_per_thread, int min_blocks_per_sm) {
-    if (!h || min_blocks_per_sm < 0) return LBM_E_ARG;
+    if (!h || min_blocks_per_sm < 0) return fail(h, LBM_E_ARG, "lbm_tune: negative min_blocks_per_sm");
     if (h->ready) return fail(h, LBM_E_STATE, "lbm_tune must come before the first step");
     if (cells_per_thread != 0 || min_blocks_per_sm != 0) {
         lbm::Device probe{};
@@ -1275,7 +1280,7 @@ int lbm_debug_set(lbm_t *h, int knob, long long value) {
 }
 
 int lbm_autotune(lbm_t *h, int trials, int *best_cells, int *best_blocks) {
-    if (!h || trials < 1) return LBM_E_ARG;
+    if (!h || trials < 1) return fail(h, LBM_E_ARG, "lbm_autotune: trials must be >= 1");
     int rc = ensure_device(h);
     if (rc) return rc;
     if ((rc = sync_and_check(h))) return rc;
@@ -1315,7 +1320,8 @@ int lbm_autotune(lbm_t *h, int trials, int *best_cells, int *best_blocks) {
 }
 
 int lbm_adjoint_record(lbm_t *h, int n, int segment) {
-    if (!h || n < 1 || segment < 1) return LBM_E_ARG;
+    if (!h || n < 1 || segment < 1)
+        return fail(h, LBM_E_ARG, "lbm_adjoint_record: steps and segment must be >= 1");
     if (h->precision != LBM_PREC_F64 && h->precision != LBM_PREC_F32)
         return fail(h, LBM_E_ARG, "the reverse sweep needs FP64 or FP32 storage");
     if (nb(h) == 0) return fail(h, LBM_E_ARG, "the reverse sweep needs at least one body");
@@ -1371,7 +1377,7 @@ int lbm_adjoint_record(lbm_t *h, int n, int segment) {
 
 int lbm_adjoint_backward(lbm_t *h, const double *seed, double *grad_state, double *grad_prev,
                          double *grad_drive, double *grad_spring, double *grad_body, double *grad_pop) {
-    if (!h || !seed) return LBM_E_ARG;
+    if (!h || !seed) return fail(h, LBM_E_ARG, "lbm_adjoint_backward: null seed");
     auto &tp = h->tape;
     if (!tp.recorded) return fail(h, LBM_E_STATE, "lbm_adjoint_backward needs a recording (lbm_adjoint_record)");
     int rc = sync_and_check(h);
@@ -2211,7 +2217,7 @@ int lbm_ensemble_destroy(lbm_ensemble_t *e) {
 }
 
 int lbm_ensemble_step(lbm_ensemble_t *e, const int *steps) {
-    if (!e || !steps) return LBM_E_ARG;
+    if (!e || !steps) return ens_fail(e, LBM_E_ARG, "lbm_ensemble_step: null step counts");
     const int n = (int)e->members.size();
     std::vector<long long> left(n);
     for (int i = 0; i < n; ++i) {
@@ -2294,7 +2300,8 @@ int lbm_ensemble_sync(lbm_ensemble_t *e) {
 const char *lbm_ensemble_last_error(lbm_ensemble_t *e) { return e ? e->err.c_str() : "null handle"; }
 
 int lbm_ensemble_set_mode(lbm_ensemble_t *e, int mode) {
-    if (!e || (mode != LBM_ENSEMBLE_BATCHED && mode != LBM_ENSEMBLE_BRANCHES)) return LBM_E_ARG;
+    if (!e || (mode != LBM_ENSEMBLE_BATCHED && mode != LBM_ENSEMBLE_BRANCHES))
+        return ens_fail(e, LBM_E_ARG, "lbm_ensemble_set_mode: unknown mode");
     if (mode != e->mode) {
         ens_drop_graphs(e);
         e->mode = mode;
@@ -2303,7 +2310,7 @@ int lbm_ensemble_set_mode(lbm_ensemble_t *e, int mode) {
 }
 
 int lbm_ensemble_autotune(lbm_ensemble_t *e, int trials, int *cells_per_thread) {
-    if (!e || trials < 1) return LBM_E_ARG;
+    if (!e || trials < 1) return ens_fail(e, LBM_E_ARG, "lbm_ensemble_autotune: trials must be >= 1");
     const int n = (int)e->members.size();
     std::vector<int> all(n);
     for (int i = 0; i < n; ++i) {

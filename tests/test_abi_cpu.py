@@ -130,3 +130,77 @@ def test_debug_knobs_take_only_their_values_before_the_first_step(lib):
     assert lib.lbm_debug_set(h, lbm.DEBUG_NO_PDL, -1) == lbm.E_ARG
     assert lib.lbm_debug_set(h, 99, 0) == lbm.E_ARG
     assert lib.lbm_destroy(h) == 0
+
+
+def test_every_entry_point_rejects_a_null_handle(lib):
+    """Each call that takes a handle (or an ensemble) returns LBM_E_ARG for a
+    null one before touching anything; destroying null is a no-op, and the
+    error strings say what happened."""
+    raw = ctypes.CDLL(_build.LIB)           # no argtypes: every argument marshalled as below
+    hdr = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    decls = re.findall(r"^\s*(int|long long|const char \*)\s*(lbm_\w+)\s*\(([^;]*?)\);", hdr, re.M | re.S)
+    seen = 0
+    for ret, name, params in decls:
+        ps = [p.strip() for p in params.replace("\n", " ").split(",")]
+        if not ps[0].startswith(("lbm_t *", "lbm_ensemble_t *")):
+            continue
+        args = []
+        for p in ps:
+            if "*" in p or "[" in p or p.split()[0].endswith("_fn"):
+                args.append(ctypes.c_void_p(None))
+            elif p.startswith("double"):
+                args.append(ctypes.c_double(0.0))
+            elif p.startswith("long long"):
+                args.append(ctypes.c_longlong(0))
+            else:
+                args.append(ctypes.c_int(0))
+        f = getattr(raw, name)
+        f.restype = {"int": ctypes.c_int, "long long": ctypes.c_longlong, "const char *": ctypes.c_char_p}[ret]
+        r = f(*args)
+        if name.endswith("_destroy"):
+            assert r == 0, name
+        elif ret == "const char *":
+            assert r == b"null handle", name
+        else:
+            assert r == lbm.E_ARG, (name, r)
+        seen += 1
+    assert seen >= 40
+
+
+def test_argument_errors_name_the_call(lib):
+    """Bad arguments are refused on the host, before any device work, and
+    lbm_last_error says which call refused them."""
+    L = ctypes.CDLL(_build.LIB)
+    L.lbm_last_error.restype = ctypes.c_char_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    D = ctypes.c_double
+    h = ctypes.c_void_p()
+    assert L.lbm_create(16, 16, 16, D(1.0), 7, ctypes.byref(h)) == 0
+    p = np.array([8.0, 8.0, 8.0])
+    assert L.lbm_add_body(h, 0, D(2.0), D(0.0), D(10.0), p.ctypes.data_as(dp), None) == 0
+    assert L.lbm_set_drive(h, 0, D(1e-4), D(0.01), D(0.0)) == 0
+    cases = [
+        (lambda: L.lbm_add_body(h, 0, D(2.0), D(0.0), D(10.0), None, None), b"lbm_add_body"),
+        (lambda: L.lbm_set_drive_axis(h, 3, p.ctypes.data_as(dp)), b"lbm_set_drive_axis"),
+        (lambda: L.lbm_set_drive_window(h, 9, D(10.0)), b"lbm_set_drive_window"),
+        (lambda: L.lbm_set_body_state(h, 7, np.zeros(13).ctypes.data_as(dp)), b"lbm_set_body_state"),
+        (lambda: L.lbm_set_fields(h, lbm.FIELD_POP, None, lbm.DTYPE_F64), b"lbm_set_fields"),
+        (lambda: L.lbm_step(h, -1), b"lbm_step"),
+        (lambda: L.lbm_get_bodies(h, None), b"lbm_get_bodies"),
+        (lambda: L.lbm_get_forces(h, None), b"lbm_get_forces"),
+        (lambda: L.lbm_get_fields(h, lbm.FIELD_RHO, None, lbm.DTYPE_F64), b"lbm_get_fields"),
+        (lambda: L.lbm_get_fields_device(h, lbm.FIELD_RHO, None, lbm.DTYPE_F64), b"lbm_get_fields_device"),
+        (lambda: L.lbm_enable_history(h, -1), b"lbm_enable_history"),
+        (lambda: L.lbm_get_history(h, None, 10, None), b"lbm_get_history"),
+        (lambda: L.lbm_save(h, None), b"lbm_save"),
+        (lambda: L.lbm_load(h, None), b"lbm_load"),
+        (lambda: L.lbm_tune(h, 2, -1), b"lbm_tune"),
+        (lambda: L.lbm_autotune(h, 0, None, None), b"lbm_autotune"),
+        (lambda: L.lbm_adjoint_record(h, 0, 4), b"lbm_adjoint_record"),
+        (lambda: L.lbm_adjoint_backward(h, None, None, None, None, None, None, None), b"lbm_adjoint_backward"),
+        (lambda: L.lbm_average_get(h, None, None), b"lbm_average_get"),
+    ]
+    for call, name in cases:
+        assert call() == lbm.E_ARG, name
+        assert L.lbm_last_error(h).startswith(name), (name, L.lbm_last_error(h))
+    assert L.lbm_destroy(h) == 0
